@@ -1,0 +1,411 @@
+"""Benchmark: Y_lm evaluations per second on the 192^3 real-space DFT grid.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl shm|reference]
+                    [--extras | --no-extras]
+
+One step = one pass of the evaluator over the whole workload: all R_l^m,
+l <= 9, at the 7,077,888 points of a 192^3 grid (spacing 0.3 bohr, centred on
+a seeded off-grid atom), FP64 in and out (5.66 GB of output per step).  Inputs
+are resident in HBM when the timed region starts; input (170 MB) and output
+(5.66 GB) both exceed the 126 MB L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  N > 1 runs one process per GPU (torchrun);
+each rank evaluates its own copy of the grid (weak scaling, no collective on
+the data path; a barrier and a max-reduction of the elapsed time only).
+
+--impl reference times the CPU FP64 oracle (test infrastructure, the paper
+defines the reference values; there is no reference GPU code) on a bounded
+sample of the same workload, on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Y_lm evals/s at lmax=9"
+UNIT = "Y_lm/s"
+WORKLOAD = "dft_grid_192cubed_fp64_lmax9"
+LMAX = 9
+N_SIDE = 192
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 pipe peak: the nominal 1.25 TFLOP/s dense FP64 of a B300 (148 SMs at
+# up to 2032 MHz), i.e. 0.625e12 FP64 pipe instructions per second (one DFMA,
+# DMUL or DADD each).  No measured FP64 figure is provided for this machine.
+FP64_PEAK_TFLOPS = 1.25
+HBM_FALLBACK_GBS = 6400.0
+
+
+def dp_instr_per_point(lmax: int) -> int:
+    """FP64 pipe instructions per point of the FP64 evaluator (sh_core.cuh).
+
+    normalisation: r^2 (3), x/r, y/r, z/r (3), rsqrt (one MUFU seed refined by
+    Newton steps in FP64; counted as 6);
+    m = 0: S*z for l = 1 (1), l = 2 one FMA with a constant and one scale (2),
+    l >= 3 two for the recurrence and one scale (3);
+    m >= 1: (x+iy)^m update (4, m >= 2), l = m: 2 products, l = m+1: 3,
+    l = m+2: one FMA + scale + 2 products (4), l >= m+3: 5."""
+    n = 12
+    for l in range(1, lmax + 1):
+        n += 1 if l == 1 else (2 if l == 2 else 3)
+    for m in range(1, lmax + 1):
+        n += 4 if m >= 2 else 0
+        n += 2
+        if m + 1 <= lmax:
+            n += 3
+        for l in range(m + 2, lmax + 1):
+            n += 4 if l == m + 2 else 5
+    return n
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def cpu_oracle_rate(points: np.ndarray, lmax: int, budget_s: float, nthreads: int = 0):
+    """Y/s of the oracle on a bounded prefix of `points` (about budget_s of CPU work)."""
+    import oracle
+    oracle.build()
+    probe = min(points.shape[0], 20000)
+    t0 = time.perf_counter()
+    oracle.real_sh(points[:probe], lmax, nthreads=nthreads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    m = int(min(points.shape[0], max(probe, probe * budget_s / dt)))
+    t0 = time.perf_counter()
+    oracle.real_sh(points[:m], lmax, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    nh = (lmax + 1) ** 2
+    return m * nh / dt, m, oracle.max_threads(nthreads)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2510_05282_b300 import inputs
+    pts = inputs.dft_grid_points(N_SIDE)
+    nh = (LMAX + 1) ** 2
+    budget = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    sample_pts = 0
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        r, m, cores = cpu_oracle_rate(pts, LMAX, budget)
+        sample_pts = m
+        if i >= args.warmup:
+            rates.append(r)
+    value = statistics.median(rates)
+    ms = pts.shape[0] * nh / value * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points": int(pts.shape[0]), "lmax": LMAX,
+                   "note": "each step times the oracle on a prefix of the grid; ms_per_step is "
+                           "extrapolated to the full grid"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample_pts} of {pts.shape[0]} grid points per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def timed_launches(fn, steps, stream):
+    """Per-launch CUDA-event durations (ms) on `stream` and the region length."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    region = starts[0].elapsed_time(ends[-1])
+    return per, region
+
+
+def gpu_id_for_smi(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def measure_eval(shm, torch, pts_np, dtype, lmax, steps, warmup, stream):
+    p = torch.from_numpy(pts_np).to(device="cuda", dtype=dtype)
+    out = torch.empty((p.shape[0], (lmax + 1) ** 2), dtype=dtype, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            shm.eval_sh(p, lmax, out=out, stream=stream)
+    torch.cuda.synchronize()
+    per, region = timed_launches(lambda: shm.eval_sh(p, lmax, out=out, stream=stream), steps, stream)
+    del out, p
+    return per, region
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    import paper_2510_05282_b300 as shm
+    from paper_2510_05282_b300 import build, inputs
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    shm.lib()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    peaks, peaks_src = load_peaks()
+    nh = (LMAX + 1) ** 2
+
+    tuned_ms = shm.autotune(LMAX, torch.float64, 1 << 20) if args.tune else None
+    pts = inputs.dft_grid_points(args.grid)
+    n = pts.shape[0]
+    p = torch.from_numpy(pts).cuda()
+    out = torch.empty((n, nh), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        shm.eval_sh(p, LMAX, out=out, stream=stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(gpu_id_for_smi(dev)) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    per, region = timed_launches(lambda: shm.eval_sh(p, LMAX, out=out, stream=stream), args.steps, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([region], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        region = float(t.item())
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+
+    ms_per_step = region / args.steps
+    value = world * n * nh / (ms_per_step * 1e-3)
+    launch_ms = statistics.mean(per)
+
+    # roofline of the (single) kernel: FP64 pipe, with HBM alongside
+    dp_per_launch = dp_instr_per_point(LMAX) * n
+    achieved_tflops = 2.0 * dp_per_launch / (launch_ms * 1e-3) / 1e12
+    bytes_per_launch = n * (3 + nh) * 8
+    achieved_gbs = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    traffic = TRAFFIC_PER_POINT_F64_L9 * n if TRAFFIC_PER_POINT_F64_L9 else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.grid == N_SIDE else f"dft_grid_{args.grid}cubed_fp64_lmax9",
+                   "points": n, "lmax": LMAX, "grid": f"{args.grid}^3, h=0.3 bohr",
+                   "out_bytes_per_step": n * nh * 8, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "no flush: 170 MB input and 5.66 GB output per step exceed the 126 MB L2",
+                   "launch_variant": shm.eval_variant(LMAX, torch.float64), "autotune_probe_ms": tuned_ms},
+        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "peak_source": "recipe nominal FP64 (1.25 TFLOP/s = 0.625e12 FP64 pipe instr/s)",
+                     "achieved_def": f"{dp_instr_per_point(LMAX)} FP64 pipe instructions per point x 2 flop "
+                                     "(FMA-equivalent) / mean launch time",
+                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": achieved_gbs / hbm_peak, "peak_source": peaks_src}},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "kernel_ms": launch_ms,
+    }
+    del out, p
+    torch.cuda.synchronize()
+
+    if rank == 0:
+        # end to end through the host-buffer entry point (pinned host memory)
+        e2e_steps = max(2, min(args.steps, args.e2e_steps))
+        hin = torch.from_numpy(pts).pin_memory()
+        hout = torch.empty((n, nh), dtype=torch.float64).pin_memory()
+        ws = torch.empty(shm.eval_host_workspace_size(LMAX, torch.float64, 1 << 20), dtype=torch.uint8,
+                         device="cuda")
+        shm.eval_host(hin, LMAX, hout, ws, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            shm.eval_host(hin, LMAX, hout, ws, stream=stream)
+            stream.synchronize()
+        dt = (time.perf_counter() - t0) / e2e_steps
+        line["e2e"] = {"value": n * nh / dt, "unit": UNIT, "h2d_bytes_per_step": n * 3 * 8,
+                       "d2h_bytes_per_step": n * nh * 8, "steps": e2e_steps,
+                       "api": "shm_eval_host (pinned host in/out, 1M-point chunks double-buffered)"}
+        del hin, hout, ws
+        rate, m, cores = cpu_oracle_rate(pts, LMAX, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"first {m} of {n} grid points, lmax=9, FP64"}
+        if args.extras:
+            line["extra"] = run_extras(args, shm, torch, inputs, stream, peaks, peaks_src)
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+TRAFFIC_PER_POINT_F64_L9 = None   # DRAM bytes per point from ncu (filled from profiles/)
+
+
+def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
+    """Other workloads, reported beside the headline (not part of `value`)."""
+    res = {}
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    nh = (LMAX + 1) ** 2
+    steps = max(5, min(args.steps, 50))
+    # FP32 on the same grid: HBM-write bound
+    if args.tune:
+        shm.autotune(LMAX, torch.float32, 1 << 20)
+    g32 = inputs.dft_grid_points(N_SIDE).astype(np.float32)
+    per, region = measure_eval(shm, torch, g32, torch.float32, LMAX, steps, 3, stream)
+    ms = statistics.mean(per)
+    gbs = g32.shape[0] * (3 + nh) * 4 / (ms * 1e-3) / 1e9
+    res["dft_grid_192cubed_fp32_lmax9"] = {
+        "value": g32.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+        "launch_variant": shm.eval_variant(LMAX, torch.float32),
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": gbs / hbm_peak, "peak_source": peaks_src}}
+    # the plain random-sphere set (65,600 points): latency-sized
+    sph = inputs.random_sphere_points(65_536)
+    per, region = measure_eval(shm, torch, sph, torch.float64, LMAX, steps, 3, stream)
+    ms = statistics.mean(per)
+    res["random_sphere_65600_fp64_lmax9"] = {"value": sph.shape[0] * nh / (ms * 1e-3), "unit": UNIT,
+                                             "kernel_ms": ms}
+    for fn in EXTRA_WORKLOADS:
+        try:
+            res.update(fn(args, shm, torch, inputs, stream, peaks, peaks_src))
+        except Exception as e:  # reported, never silently dropped
+            res[getattr(fn, "__name__", "extra")] = {"error": repr(e)}
+    return res
+
+
+EXTRA_WORKLOADS: list = []
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["shm", "reference"], default="shm")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--grid", type=int, default=N_SIDE, help="grid side (192 = the benchmark workload; "
+                    "smaller sides only for profiling captures)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-tune", dest="tune", action="store_false", default=True,
+                    help="skip shm_autotune (use the library's default launch variant)")
+    ap.add_argument("--extras", dest="extras", action="store_true", default=True)
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "reference":
+            if rank != 0:
+                return 0
+        else:
+            dist.init_process_group("nccl")
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    try:
+        return run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * shm.h -- C ABI of libshm: real spherical harmonics R_l^m (l <= 9) on a B300.
+ *
+ * The operation is the one defined in "SHarmonic: A fast and accurate
+ * implementation of spherical harmonics for electronic-structure
+ * calculations" (arXiv 2510.05282):
+ *   - R_l^m, Sec. II Eq. 6 (from the complex Y_l^m of Eq. 5, Condon-Shortley
+ *     sign included there), which comes out as
+ *       R_l^0  = N_l^0 P_l^0(cos t),
+ *       R_l^m  = sqrt2 N_l^m P_l^m(cos t) cos(m p),   m > 0,
+ *       R_l^-m = sqrt2 N_l^m P_l^m(cos t) sin(m p),   m > 0,
+ *     with P_l^m free of any further sign (this matches the App. C formulas
+ *     and the App. D reference values);
+ *   - evaluated in normalised Cartesian coordinates x/r, y/r, z/r
+ *     (Sec. II Eq. 8: the harmonics are polynomials there);
+ *   - at r = 0 every harmonic is 0 except R_0^0 = 1/sqrt(4 pi) (Sec. II);
+ *   - l is limited to 9, as in the paper (Sec. III).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named "device" must point to device memory of the current CUDA
+ *     device; pointers named "host" to host memory.  Nothing is copied between
+ *     host and device unless stated.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued asynchronously on it; argument errors are
+ *     detected synchronously, before anything is launched, and nothing is
+ *     launched when an error is returned.
+ *   - Output layout: row-major [n][(lmax+1)^2]; column k = l*l + l + m, m from
+ *     -l to l (the App. C order).
+ *   - Non-finite inputs are not special-cased: NaN propagates.
+ *   - shm_last_error() returns a thread-local text for the last failure.
+ */
+#ifndef SHM_H
+#define SHM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SHM_F32 = 0, /* float  in, float  out, FP32 arithmetic (FP64 for 1/r when r < 1e-2) */
+  SHM_F64 = 1  /* double in, double out, FP64 arithmetic */
+} shm_dtype;
+
+typedef enum {
+  SHM_OK = 0,
+  SHM_EINVAL = 1,       /* bad argument (null/misaligned pointer, lmax, dtype, size) */
+  SHM_ENOMEM = 2,       /* device or pinned memory exhausted */
+  SHM_ECUDA = 3,        /* a CUDA call failed; shm_last_error() has its text */
+  SHM_EBUSY = 4,        /* serving: request not admitted (queue or pool full) */
+  SHM_ETIMEOUT = 5,     /* serving: wait expired / device wait gave up */
+  SHM_EUNSUPPORTED = 6, /* valid request this build cannot do */
+  SHM_ENOTFOUND = 7     /* serving: unknown ticket */
+} shm_status;
+
+#define SHM_LMAX_CAP 9
+
+/* shm_eval_ex flags */
+#define SHM_NORMALIZED_INPUT 0x1u /* points are already x/r, y/r, z/r: skip the r work */
+
+/* Number of harmonics for lmax: (lmax+1)^2. */
+int shm_num_harmonics(int lmax);
+
+/*
+ * shm_eval -- all R_l^m, 0 <= l <= lmax, at n points.
+ *   points : device, [n][3] x, y, z (AoS) relative to the centre, element type
+ *            per dtype, aligned to its element size.
+ *   n      : number of points, >= 0 (0: returns SHM_OK, launches nothing).
+ *   lmax   : 0..9.
+ *   out    : device, [n][(lmax+1)^2] of dtype, aligned to its element size
+ *            (16-byte alignment enables the vector store path).  Must not
+ *            overlap points.
+ * Caller owns both buffers; nothing is allocated.
+ * Errors: SHM_EINVAL (null or misaligned pointer, lmax outside 0..9, n < 0,
+ * bad dtype), SHM_ECUDA (launch failed).
+ */
+shm_status shm_eval(const void* points, int64_t n, int lmax, shm_dtype dtype, void* out, void* stream);
+
+/* shm_eval with flags (SHM_NORMALIZED_INPUT). Unknown flag bits: SHM_EINVAL. */
+shm_status shm_eval_ex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
+                       void* out, void* stream);
+
+/*
+ * shm_eval_host -- shm_eval on HOST buffers, end to end: the points are copied
+ * to the device, evaluated and the rows copied back, in chunks that flow
+ * through a caller-provided device workspace, double-buffered on two internal
+ * streams so that host->device copies, kernels and device->host copies of
+ * consecutive chunks overlap.
+ *   points_host : host, [n][3] of dtype (pinned memory gives full copy speed).
+ *   out_host    : host, [n][(lmax+1)^2] of dtype.
+ *   workspace   : device, >= shm_eval_host_workspace_size(lmax, dtype, 1)
+ *                 bytes; larger workspaces give larger chunks.
+ *   stream      : the work is ordered after prior work on `stream`, and
+ *                 later work on `stream` waits for it; the call returns
+ *                 once everything is enqueued (synchronise `stream` before
+ *                 reading out_host).  The internal streams are created once
+ *                 per device and kept until exit.
+ * Nothing is allocated per call.  Errors: as shm_eval, plus SHM_EINVAL for a
+ * workspace smaller than one point's worth.
+ */
+shm_status shm_eval_host(const void* points_host, int64_t n, int lmax, shm_dtype dtype, void* out_host,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* Device workspace bytes shm_eval_host needs for chunks of `chunk_points` points. */
+size_t shm_eval_host_workspace_size(int lmax, shm_dtype dtype, int64_t chunk_points);
+
+/*
+ * shm_autotune -- time every launch variant of the evaluator (store path x
+ * CTA size) for (lmax, dtype) on n_probe synthetic points and keep the
+ * fastest for later shm_eval / shm_eval_host calls in this process.  When
+ * the environment variable SHM_TUNE_CACHE names a file, the choice is also
+ * appended there, and every process reads that file before its first
+ * evaluation.  Unlike shm_eval this call allocates (and frees) its probe
+ * buffers with cudaMalloc and synchronises the device, so it must not be
+ * called during stream capture.  best_ms (may be NULL) receives the fastest
+ * time.  Errors: SHM_EINVAL (lmax, dtype, n_probe <= 0), SHM_ENOMEM, SHM_ECUDA.
+ */
+shm_status shm_autotune(int lmax, shm_dtype dtype, int64_t n_probe, double* best_ms);
+
+/* Text naming the launch variant shm_eval uses for (lmax, dtype) (always succeeds
+ * for valid arguments; "" otherwise). */
+const char* shm_eval_variant(int lmax, shm_dtype dtype);
+
+/* Number of launch variants, and pinning one of them (0 .. count-1) for
+ * (lmax, dtype) in this process; variant -1 restores the default choice.
+ * Errors: SHM_EINVAL. */
+int shm_eval_variant_count(void);
+shm_status shm_eval_set_variant(int lmax, shm_dtype dtype, int variant);
+
+/* ------------------------------------------------------------------------
+ * Fused non-local projectors.  Sec. I of the paper motivates the method by
+ * the projectors of pseudopotential and PAW methods, which need Y_lm at every
+ * grid point of each atom's sphere; this entry point builds them directly:
+ *
+ *   out[out_offsets[a] + (p - point_offsets[a]) * (L_a+1)^2 + l*l + l + m]
+ *       = f_{s,l}(|d|) * R_l^m(d / |d|)
+ *
+ * for every atom a (species s = atom_species[a], L_a = species_lmax[s]) and
+ * every sphere point p of a, where grid point g = point_index[p] =
+ * (i*ng + j)*ng + k sits at (i, j, k)*h, d = minimum image of (grid point -
+ * atom_pos[a]) in the cubic periodic box of side `box` (each component
+ * d_c -= box * rint(d_c / box)), and f_{s,l} is read from its table on the
+ * log grid r_i = r_min * exp(i * dlog), i < n_rad, by 4-point Lagrange
+ * interpolation at t = ln(|d| / r_min) / dlog clamped to [0, n_rad-1] (t = 0
+ * for |d| = 0, where R follows the r = 0 convention), through the nodes
+ * i0..i0+3, i0 = clamp(floor(t) - 1, 0, n_rad - 4).
+ * ------------------------------------------------------------------------ */
+#define SHM_PROJ_MAX_SPECIES 64
+
+typedef struct {
+  int64_t n_atoms;               /* >= 0 */
+  const double* atom_pos;        /* device [n_atoms][3], bohr */
+  const int32_t* atom_species;   /* device [n_atoms], 0 <= s < n_species */
+  int32_t n_species;             /* 1..SHM_PROJ_MAX_SPECIES */
+  const int32_t* species_lmax;   /* HOST [n_species], each 0..9 */
+  const double* radial;          /* device [n_species][radial_lstride][n_rad] */
+  int32_t radial_lstride;        /* >= 1 + max species lmax */
+  int32_t n_rad;                 /* >= 4 */
+  double r_min;                  /* > 0 */
+  double dlog;                   /* > 0 */
+  double box;                    /* > 0, = ng * h */
+  int32_t ng;                    /* 1..1290 (ng^3 < 2^31) */
+  double h;                      /* > 0 */
+  const int64_t* point_offsets;  /* device [n_atoms+1], non-decreasing, [0] = 0 */
+  const int32_t* point_index;    /* device [n_points], each in [0, ng^3) */
+  const int64_t* out_offsets;    /* device [n_atoms+1], out_offsets[a+1] - out_offsets[a] = n_a (L_a+1)^2 */
+  int64_t n_points;              /* host copy of point_offsets[n_atoms] */
+  int64_t n_values;              /* host copy of out_offsets[n_atoms] */
+} shm_proj_problem;
+
+/* Device workspace bytes shm_projectors needs for this problem and dtype. */
+size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dtype);
+
+/*
+ * shm_projectors -- the fused projector values, one persistent launch (plus a
+ * one-CTA set-up launch) on `stream`.
+ *   dtype     : SHM_F64 (FP64 arithmetic, double out) or SHM_F32 (FP32
+ *               arithmetic on FP32 copies of the tables, float out; grid
+ *               displacements are formed exactly before rounding to float,
+ *               1/r in FP64 for |d| < 1e-2).
+ *   out       : device [n_values] of dtype, caller-owned.
+ *   workspace : device scratch of >= shm_projectors_workspace_size() bytes,
+ *               caller-owned; it holds the work-queue counter, the per-atom
+ *               tile table, an error word and (SHM_F32) the FP32 tables.  One
+ *               workspace must not be shared by calls that overlap on the GPU.
+ * The kernel checks every index it reads through (species, grid index, table
+ * stencil, output range) against the problem's sizes; an inconsistent problem
+ * sets bits of the workspace error word (see shm_projectors_check) and the
+ * offending rows are skipped -- no access goes out of bounds.
+ * Errors (synchronous): SHM_EINVAL for bad scalars, null pointers, host
+ * species_lmax out of range, or a workspace that is too small; SHM_ECUDA.
+ */
+shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Error bits a projector launch found (0 = none); waits for `stream`.
+ * 1: point_offsets not non-decreasing or beyond n_points; 2: species index out
+ * of range; 4: grid index out of range; 8: output block beyond n_values or
+ * inconsistent with out_offsets. */
+shm_status shm_projectors_check(const void* workspace, void* stream, uint32_t* error_bits);
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char* shm_last_error(void);
+
+/* Text name of a status code. */
+const char* shm_status_string(shm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHM_H */

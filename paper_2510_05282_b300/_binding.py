@@ -1,0 +1,166 @@
+"""Thin ctypes binding over libshm.so (argument marshalling only).
+
+Every step of the computation runs in the library's CUDA kernels; PyTorch is
+used here only to hold device memory and to name the current CUDA stream.
+The library is loaded on first use; if it is missing or fails to load, the
+call raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libshm.so")
+
+SHM_F32, SHM_F64 = 0, 1
+SHM_NORMALIZED_INPUT = 0x1
+LMAX_CAP = 9
+
+STATUS = {0: "SHM_OK", 1: "SHM_EINVAL", 2: "SHM_ENOMEM", 3: "SHM_ECUDA", 4: "SHM_EBUSY",
+          5: "SHM_ETIMEOUT", 6: "SHM_EUNSUPPORTED", 7: "SHM_ENOTFOUND"}
+
+
+class ShmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libshm (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise RuntimeError(f"libshm.so is not built ({LIB_PATH}); run "
+                                       "`python -m paper_2510_05282_b300.build`")
+                L = ctypes.CDLL(LIB_PATH)
+                _declare(L)
+                _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, i64, i32, u32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t
+    L.shm_eval.argtypes = [vp, i64, i32, i32, vp, vp]
+    L.shm_eval.restype = i32
+    L.shm_eval_ex.argtypes = [vp, i64, i32, i32, u32, vp, vp]
+    L.shm_eval_ex.restype = i32
+    L.shm_eval_host.argtypes = [vp, i64, i32, i32, vp, vp, sz, vp]
+    L.shm_eval_host.restype = i32
+    L.shm_eval_host_workspace_size.argtypes = [i32, i32, i64]
+    L.shm_eval_host_workspace_size.restype = sz
+    L.shm_autotune.argtypes = [i32, i32, i64, ctypes.POINTER(ctypes.c_double)]
+    L.shm_autotune.restype = i32
+    L.shm_eval_variant.argtypes = [i32, i32]
+    L.shm_eval_variant.restype = ctypes.c_char_p
+    L.shm_eval_variant_count.argtypes = []
+    L.shm_eval_variant_count.restype = i32
+    L.shm_eval_set_variant.argtypes = [i32, i32, i32]
+    L.shm_eval_set_variant.restype = i32
+    L.shm_num_harmonics.argtypes = [i32]
+    L.shm_num_harmonics.restype = i32
+    L.shm_last_error.argtypes = []
+    L.shm_last_error.restype = ctypes.c_char_p
+    L.shm_status_string.argtypes = [i32]
+    L.shm_status_string.restype = ctypes.c_char_p
+    for name, decl in _EXTRA_DECLS:
+        fn = getattr(L, name, None)
+        if fn is not None:
+            fn.argtypes, fn.restype = decl
+
+
+# further entry points register (name, (argtypes, restype)) here
+_EXTRA_DECLS: list = []
+
+
+def check(status: int) -> None:
+    if status != 0:
+        raise ShmError(status, lib().shm_last_error().decode(errors="replace"))
+
+
+def num_harmonics(lmax: int) -> int:
+    return (lmax + 1) * (lmax + 1)
+
+
+def _dtype_code(dtype) -> int:
+    import torch
+    if dtype in (torch.float64, "f64", np.float64):
+        return SHM_F64
+    if dtype in (torch.float32, "f32", np.float32):
+        return SHM_F32
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def eval_sh(points, lmax: int, out=None, normalized: bool = False, stream=None):
+    """All R_l^m, l <= lmax, at device points [n, 3] (float32 or float64 CUDA
+    tensor) -> [n, (lmax+1)^2] of the same dtype, column k = l*l + l + m."""
+    import torch
+    if not (isinstance(points, torch.Tensor) and points.is_cuda):
+        raise TypeError("points must be a CUDA tensor")
+    if points.dim() != 2 or points.shape[1] != 3 or not points.is_contiguous():
+        raise ValueError("points must be a contiguous [n, 3] tensor")
+    code = _dtype_code(points.dtype)
+    n = points.shape[0]
+    if out is None:
+        out = torch.empty((n, num_harmonics(lmax)), dtype=points.dtype, device=points.device)
+    elif out.dtype != points.dtype or not out.is_contiguous() or out.numel() != n * num_harmonics(lmax):
+        raise ValueError("out must be contiguous, of the points dtype and [n, (lmax+1)^2]")
+    flags = SHM_NORMALIZED_INPUT if normalized else 0
+    check(lib().shm_eval_ex(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def autotune(lmax: int, dtype, n_probe: int = 1 << 20) -> float:
+    """Time every launch variant for (lmax, dtype); keep the fastest. Returns its ms."""
+    best = ctypes.c_double(0.0)
+    check(lib().shm_autotune(int(lmax), _dtype_code(dtype), int(n_probe), ctypes.byref(best)))
+    return best.value
+
+
+def eval_variant(lmax: int, dtype) -> str:
+    return lib().shm_eval_variant(int(lmax), _dtype_code(dtype)).decode()
+
+
+def set_eval_variant(lmax: int, dtype, variant: int) -> None:
+    check(lib().shm_eval_set_variant(int(lmax), _dtype_code(dtype), int(variant)))
+
+
+def eval_variant_count() -> int:
+    return int(lib().shm_eval_variant_count())
+
+
+def eval_host_workspace_size(lmax: int, dtype, chunk_points: int) -> int:
+    return int(lib().shm_eval_host_workspace_size(int(lmax), _dtype_code(dtype), int(chunk_points)))
+
+
+def eval_host(points_host, lmax: int, out_host, workspace, stream=None) -> None:
+    """shm_eval_host: host (ideally pinned) points -> host rows, through a device
+    workspace.  Enqueued on `stream`; synchronise it before reading out_host.
+    points_host / out_host are CPU torch tensors or numpy arrays."""
+    import torch
+
+    def ptr(a):
+        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+    dt = points_host.dtype
+    code = _dtype_code(dt)
+    n = points_host.shape[0]
+    check(lib().shm_eval_host(ptr(points_host), n, int(lmax), code, ptr(out_host), workspace.data_ptr(),
+                              workspace.numel() * workspace.element_size(), _stream_ptr(stream)))

@@ -1,0 +1,123 @@
+// Error reporting, pointer checks and device queries shared by libshm.
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "shm_internal.h"
+
+namespace shm {
+
+namespace {
+thread_local std::string g_last_error;
+
+// cuMemGetAddressRange through the runtime's driver entry-point query, so the
+// library does not link libcuda directly and loads on machines without a GPU
+// driver (the CPU-side tests check its exports there).
+typedef CUresult (*AddrRangeFn)(CUdeviceptr*, size_t*, CUdeviceptr);
+AddrRangeFn addr_range_fn() {
+  static AddrRangeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (AddrRangeFn)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+}  // namespace
+
+shm_status fail(shm_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+shm_status fail_cuda(cudaError_t e, const char* what) {
+  return fail(SHM_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+void clear_error() { g_last_error.clear(); }
+
+shm_status check_device_range(const void* p, size_t bytes, const char* what) {
+  if (p == nullptr) return fail(SHM_EINVAL, std::string(what) + " is null");
+  if (bytes == 0) return SHM_OK;
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SHM_EINVAL, std::string(what) + " is not a pointer CUDA knows");
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(SHM_EINVAL, std::string(what) + " is not device memory");
+  if (attr.type == cudaMemoryTypeDevice && attr.device != current_device())
+    return fail(SHM_EINVAL, std::string(what) + " belongs to another device");
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  AddrRangeFn range = addr_range_fn();
+  if (range == nullptr) return fail(SHM_ECUDA, "cuMemGetAddressRange is unavailable");
+  CUresult r = range(&base, &size, (CUdeviceptr)(uintptr_t)p);
+  if (r != CUDA_SUCCESS) {
+    if (attr.type == cudaMemoryTypeManaged) return SHM_OK;  // no range query for managed memory
+    return fail(SHM_EINVAL, std::string(what) + ": allocation range unknown");
+  }
+  const uintptr_t lo = (uintptr_t)p, hi = lo + bytes;
+  if (hi < lo || lo < (uintptr_t)base || hi > (uintptr_t)base + size)
+    return fail(SHM_EINVAL, std::string(what) + ": " + std::to_string(bytes) +
+                                " bytes from this pointer run past the end of its allocation");
+  return SHM_OK;
+}
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+  return na > 0 && nb > 0 && a0 < b0 + nb && b0 < a0 + na;
+}
+
+int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return d;
+}
+
+int sm_count(int dev) {
+  static int cache[64] = {0};
+  if (dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 148;
+    }
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+}  // namespace shm
+
+extern "C" {
+
+const char* shm_last_error(void) { return shm::g_last_error.c_str(); }
+
+const char* shm_status_string(shm_status s) {
+  switch (s) {
+    case SHM_OK: return "SHM_OK";
+    case SHM_EINVAL: return "SHM_EINVAL";
+    case SHM_ENOMEM: return "SHM_ENOMEM";
+    case SHM_ECUDA: return "SHM_ECUDA";
+    case SHM_EBUSY: return "SHM_EBUSY";
+    case SHM_ETIMEOUT: return "SHM_ETIMEOUT";
+    case SHM_EUNSUPPORTED: return "SHM_EUNSUPPORTED";
+    case SHM_ENOTFOUND: return "SHM_ENOTFOUND";
+  }
+  return "SHM_UNKNOWN";
+}
+
+int shm_num_harmonics(int lmax) { return (lmax >= 0 && lmax <= SHM_LMAX_CAP) ? (lmax + 1) * (lmax + 1) : 0; }
+
+}  // extern "C"

@@ -1,0 +1,468 @@
+// shm_eval: all R_l^m, l <= lmax, at n points (the plain evaluator).
+//
+// One thread evaluates one point (sh_core.cuh) and writes its row of
+// (lmax+1)^2 harmonics into a shared-memory tile whose row stride is odd (in
+// elements), so the 32 rows a warp writes at once fall in distinct banks.
+// The tile of TPB consecutive points is one contiguous block of the output;
+// the CTA then copies it out with coalesced 16-byte streaming stores
+// (st.global.cs: the output is written once and never re-read by the kernel).
+// CTAs loop over tiles (grid = SMs x resident CTAs), so the launch size does
+// not grow with n.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <mutex>
+
+#include "sh_core.cuh"
+#include "shm_internal.h"
+
+namespace shm {
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+
+__device__ __forceinline__ void st_stream(double2* p, const double (&v)[2]) { __stcs(p, make_double2(v[0], v[1])); }
+__device__ __forceinline__ void st_stream(float4* p, const float (&v)[4]) {
+  __stcs(p, make_float4(v[0], v[1], v[2], v[3]));
+}
+
+template <int LMAX>
+struct TileShape {
+  static constexpr int L2 = NH<LMAX>::value;
+  static constexpr int RS = (L2 % 2 == 1) ? L2 : L2 + 1;  // odd row stride in elements
+};
+
+// Copies rows [0, rows) of a staged tile (row stride RS) to the contiguous
+// destination dst[rows * L2].  vec: dst is 16-byte aligned.
+template <typename T, int L2, int RS, int TPB>
+__device__ __forceinline__ void copy_out_tile(const T* __restrict__ tile, int rows, T* __restrict__ dst, bool vec) {
+  const int nv = rows * L2;
+  int done = 0;
+  if (vec) {
+    constexpr int E = Vec16<T>::n;
+    using V = typename Vec16<T>::type;
+    const int nvec = nv / E;
+    for (int v = threadIdx.x; v < nvec; v += TPB) {
+      int j = v * E;
+      int r = j / L2;
+      int c = j - r * L2;
+      T vals[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        vals[e] = tile[r * RS + c];
+        if (++c == L2) {
+          c = 0;
+          ++r;
+        }
+      }
+      st_stream(reinterpret_cast<V*>(dst) + v, vals);
+    }
+    done = nvec * E;
+  }
+  for (int j = done + threadIdx.x; j < nv; j += TPB) {
+    const int r = j / L2;
+    dst[j] = tile[r * RS + (j - r * L2)];
+  }
+}
+
+// Store paths.
+//  kStaged: the CTA's rows go through a shared-memory tile (odd row stride)
+//           and leave as coalesced 16-byte streaming stores.
+//  kDirect: each thread stores its own row straight to global memory (the
+//           warp's 32 rows are 32 separate segments; L2 merges the partial
+//           sectors).  Needs no shared memory, so occupancy is bounded by
+//           registers only -- useful when the FP64 pipe, not the store
+//           pattern, is the limit.
+enum StorePath { kStaged = 0, kDirect = 1 };
+
+template <typename T, int LMAX, int TPB, int PATH>
+__global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t n, T* __restrict__ out,
+                                              int64_t ntiles, int normalized, int vec) {
+  constexpr int L2 = TileShape<LMAX>::L2;
+  constexpr int RS = TileShape<LMAX>::RS;
+  if constexpr (PATH == kDirect) {
+    for (int64_t p = (int64_t)blockIdx.x * TPB + threadIdx.x; p < n; p += (int64_t)gridDim.x * TPB) {
+      const T x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
+      T* row = out + p * L2;
+      sh_point<LMAX>(x, y, z, normalized != 0, [&](int k, T v) { __stcs(row + k, v); });
+    }
+  } else {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int64_t p0 = t * TPB;
+      const int rows = (int)min((int64_t)TPB, n - p0);
+      if ((int)threadIdx.x < rows) {
+        const int64_t p = p0 + threadIdx.x;
+        const T x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
+        T* row = tile + threadIdx.x * RS;
+        sh_point<LMAX>(x, y, z, normalized != 0, [&](int k, T v) { row[k] = v; });
+      }
+      __syncthreads();
+      copy_out_tile<T, L2, RS, TPB>(tile, rows, out + p0 * L2, vec != 0);
+      __syncthreads();
+    }
+  }
+}
+
+// Launch variants the tuner chooses among (index = variant id).
+struct Variant {
+  int path, tpb;
+};
+constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64}, {kStaged, 256}, {kDirect, 128}, {kDirect, 256}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+// Default choice before (or without) tuning: staged 128 (the FP32 path is
+// HBM-bound and wants coalesced stores; FP64 is retuned by shm_autotune).
+constexpr int kDefaultVariant = 0;
+
+// chosen[dtype][lmax] (-1 = default)
+int g_choice[2][SHM_LMAX_CAP + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
+
+template <typename T, int LMAX, int TPB, int PATH>
+size_t eval_smem_bytes() {
+  return PATH == kStaged ? (size_t)TPB * TileShape<LMAX>::RS * sizeof(T) : 0;
+}
+
+// Per-device launch set-up of one instantiation (shared-memory opt-in and
+// resident-CTA count), done once.
+template <typename T, int LMAX, int TPB, int PATH>
+shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t stream) {
+  constexpr int MAXDEV = 64;
+  static int blocks_per_sm[MAXDEV] = {0};
+  const int dev = current_device();
+  auto kern = k_eval<T, LMAX, TPB, PATH>;
+  const size_t smem = eval_smem_bytes<T, LMAX, TPB, PATH>();
+  if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
+  if (blocks_per_sm[dev] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_eval)");
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TPB, smem);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_eval)");
+    blocks_per_sm[dev] = std::max(b, 1);
+  }
+  const int64_t ntiles = (n + TPB - 1) / TPB;
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * blocks_per_sm[dev]);
+  kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0, vec ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "k_eval launch");
+  return SHM_OK;
+}
+
+template <typename T, int LMAX>
+shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t s, int variant) {
+  if (variant < 0) {
+    variant = g_choice[sizeof(T) == 8 ? 1 : 0][LMAX];
+    if (variant < 0) variant = kDefaultVariant;
+  }
+  switch (variant) {
+    case 0: return eval_launch_v<T, LMAX, 128, kStaged>(pts, n, out, normalized, vec, s);
+    case 1: return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, s);
+    case 2: return eval_launch_v<T, LMAX, 256, kStaged>(pts, n, out, normalized, vec, s);
+    case 3: return eval_launch_v<T, LMAX, 128, kDirect>(pts, n, out, normalized, vec, s);
+    case 4: return eval_launch_v<T, LMAX, 256, kDirect>(pts, n, out, normalized, vec, s);
+  }
+  return fail(SHM_EINVAL, "unknown launch variant");
+}
+
+template <typename T>
+shm_status eval_dispatch(const T* pts, int64_t n, int lmax, T* out, bool normalized, bool vec, cudaStream_t s,
+                         int variant = -1) {
+  switch (lmax) {
+    case 0: return eval_launch<T, 0>(pts, n, out, normalized, vec, s, variant);
+    case 1: return eval_launch<T, 1>(pts, n, out, normalized, vec, s, variant);
+    case 2: return eval_launch<T, 2>(pts, n, out, normalized, vec, s, variant);
+    case 3: return eval_launch<T, 3>(pts, n, out, normalized, vec, s, variant);
+    case 4: return eval_launch<T, 4>(pts, n, out, normalized, vec, s, variant);
+    case 5: return eval_launch<T, 5>(pts, n, out, normalized, vec, s, variant);
+    case 6: return eval_launch<T, 6>(pts, n, out, normalized, vec, s, variant);
+    case 7: return eval_launch<T, 7>(pts, n, out, normalized, vec, s, variant);
+    case 8: return eval_launch<T, 8>(pts, n, out, normalized, vec, s, variant);
+    case 9: return eval_launch<T, 9>(pts, n, out, normalized, vec, s, variant);
+  }
+  return fail(SHM_EINVAL, "lmax must be in 0..9");
+}
+
+void ensure_tune_cache();
+
+}  // namespace shm
+
+extern "C" shm_status shm_eval_ex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
+                                  void* out, void* stream) {
+  using namespace shm;
+  clear_error();
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9 (the paper's formulas stop at l = 9)");
+  if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
+  if (flags & ~SHM_NORMALIZED_INPUT) return fail(SHM_EINVAL, "unknown flag bits");
+  if (n == 0) return SHM_OK;
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  const int64_t L2 = (int64_t)(lmax + 1) * (lmax + 1);
+  if (n > (INT64_MAX / 8) / (L2 * 8)) return fail(SHM_EINVAL, "n too large");
+  if (!points || !out) return fail(SHM_EINVAL, "points and out must be non-null");
+  if (!aligned(points, es) || !aligned(out, es))
+    return fail(SHM_EINVAL, "points and out must be aligned to the element size");
+  const size_t in_bytes = (size_t)n * 3 * es, out_bytes = (size_t)n * L2 * es;
+  if (ranges_overlap(points, in_bytes, out, out_bytes)) return fail(SHM_EINVAL, "points and out overlap");
+  shm_status st = check_device_range(points, in_bytes, "points");
+  if (st != SHM_OK) return st;
+  st = check_device_range(out, out_bytes, "out");
+  if (st != SHM_OK) return st;
+  const bool vec = aligned(out, 16);
+  const bool norm = (flags & SHM_NORMALIZED_INPUT) != 0;
+  ensure_tune_cache();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == SHM_F64)
+    return eval_dispatch<double>((const double*)points, n, lmax, (double*)out, norm, vec, s);
+  return eval_dispatch<float>((const float*)points, n, lmax, (float*)out, norm, vec, s);
+}
+
+extern "C" shm_status shm_eval(const void* points, int64_t n, int lmax, shm_dtype dtype, void* out, void* stream) {
+  return shm_eval_ex(points, n, lmax, dtype, 0u, out, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Host-buffer entry point: chunked H2D -> kernel -> D2H through a caller
+// workspace, alternating between two internal streams.
+
+namespace shm {
+namespace {
+
+struct HostPipe {
+  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in = nullptr, ev_done[2] = {nullptr, nullptr};
+  bool ready = false;
+};
+
+HostPipe g_pipes[64];
+std::mutex g_pipe_mu;
+
+shm_status get_pipe(int dev, HostPipe** out) {
+  if (dev < 0 || dev >= 64) return fail(SHM_EUNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  HostPipe& p = g_pipes[dev];
+  if (!p.ready) {
+    for (int i = 0; i < 2; ++i) {
+      cudaError_t e = cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaStreamCreateWithFlags");
+      e = cudaEventCreateWithFlags(&p.ev_done[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaEventCreateWithFlags");
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&p.ev_in, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaEventCreateWithFlags");
+    p.ready = true;
+  }
+  *out = &p;
+  return SHM_OK;
+}
+
+}  // namespace
+}  // namespace shm
+
+extern "C" size_t shm_eval_host_workspace_size(int lmax, shm_dtype dtype, int64_t chunk_points) {
+  if (lmax < 0 || lmax > SHM_LMAX_CAP || chunk_points <= 0 || (dtype != SHM_F32 && dtype != SHM_F64)) return 0;
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  const size_t per = es * (3 + (size_t)(lmax + 1) * (lmax + 1));
+  // two buffers, each point block and row block rounded up to 256 bytes
+  return 2 * (((size_t)chunk_points * 3 * es + 255) / 256 * 256 + ((size_t)chunk_points * per + 255) / 256 * 256);
+}
+
+extern "C" shm_status shm_eval_host(const void* points_host, int64_t n, int lmax, shm_dtype dtype, void* out_host,
+                                    void* workspace, size_t workspace_bytes, void* stream) {
+  using namespace shm;
+  clear_error();
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
+  if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
+  if (n == 0) return SHM_OK;
+  if (!points_host || !out_host) return fail(SHM_EINVAL, "points_host and out_host must be non-null");
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  const int64_t L2 = (int64_t)(lmax + 1) * (lmax + 1);
+  // largest chunk whose double buffer fits the workspace
+  int64_t chunk = (int64_t)(workspace_bytes / (2 * es * (3 + L2)));
+  while (chunk > 0 && shm_eval_host_workspace_size(lmax, dtype, chunk) > workspace_bytes) --chunk;
+  if (chunk <= 0) return fail(SHM_EINVAL, "workspace too small for one point");
+  chunk = std::min(chunk, n);
+  shm_status st = check_device_range(workspace, shm_eval_host_workspace_size(lmax, dtype, chunk), "workspace");
+  if (st != SHM_OK) return st;
+  ensure_tune_cache();
+  const int dev = current_device();
+  HostPipe* pipe = nullptr;
+  if ((st = get_pipe(dev, &pipe)) != SHM_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  const size_t in_blk = ((size_t)chunk * 3 * es + 255) / 256 * 256;
+  const size_t out_blk = ((size_t)chunk * L2 * es + 255) / 256 * 256;
+  char* base = (char*)workspace;
+  char* bin[2] = {base, base + in_blk + out_blk};
+  char* bout[2] = {base + in_blk, base + 2 * in_blk + out_blk};
+  cudaError_t e = cudaEventRecord(pipe->ev_in, cs);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaEventRecord");
+  for (int i = 0; i < 2; ++i)
+    if ((e = cudaStreamWaitEvent(pipe->s[i], pipe->ev_in, 0)) != cudaSuccess) return fail_cuda(e, "cudaStreamWaitEvent");
+  int64_t c = 0;
+  for (int64_t p0 = 0; p0 < n; p0 += chunk, ++c) {
+    const int b = (int)(c & 1);
+    const int64_t m = std::min(chunk, n - p0);
+    cudaStream_t s = pipe->s[b];
+    e = cudaMemcpyAsync(bin[b], (const char*)points_host + (size_t)p0 * 3 * es, (size_t)m * 3 * es,
+                        cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync H2D");
+    st = dtype == SHM_F64 ? eval_dispatch<double>((const double*)bin[b], m, lmax, (double*)bout[b], false, true, s)
+                          : eval_dispatch<float>((const float*)bin[b], m, lmax, (float*)bout[b], false, true, s);
+    if (st != SHM_OK) return st;
+    e = cudaMemcpyAsync((char*)out_host + (size_t)p0 * L2 * es, bout[b], (size_t)m * L2 * es, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync D2H");
+  }
+  for (int i = 0; i < 2; ++i) {
+    if ((e = cudaEventRecord(pipe->ev_done[i], pipe->s[i])) != cudaSuccess) return fail_cuda(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(cs, pipe->ev_done[i], 0)) != cudaSuccess) return fail_cuda(e, "cudaStreamWaitEvent");
+  }
+  return SHM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner.
+
+namespace shm {
+namespace {
+
+const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64", "staged-256", "direct-128", "direct-256"};
+
+std::mutex g_tune_mu;
+bool g_cache_loaded = false;
+
+void load_tune_cache_locked() {
+  if (g_cache_loaded) return;
+  g_cache_loaded = true;
+  const char* path = getenv("SHM_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  int dt, l, v;
+  while (fscanf(f, "%d %d %d", &dt, &l, &v) == 3)
+    if (dt >= 0 && dt <= 1 && l >= 0 && l <= SHM_LMAX_CAP && v >= 0 && v < kNumVariants) g_choice[dt][l] = v;
+  fclose(f);
+}
+
+// Fills pts[n][3] with scattered points in [-1, 1]^3 (a hash of the index).
+template <typename T>
+__global__ void k_probe_points(T* pts, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    pts[i] = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+
+template <typename T>
+shm_status autotune_t(int lmax, int64_t n, double* best_ms) {
+  T *pts = nullptr, *out = nullptr;
+  const size_t nh = (size_t)(lmax + 1) * (lmax + 1);
+  cudaError_t e = cudaMalloc(&pts, (size_t)n * 3 * sizeof(T));
+  if (e != cudaSuccess) return fail(SHM_ENOMEM, "autotune: cudaMalloc of probe points failed");
+  e = cudaMalloc(&out, (size_t)n * nh * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaFree(pts);
+    return fail(SHM_ENOMEM, "autotune: cudaMalloc of probe output failed");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_probe_points<T><<<1024, 256>>>(pts, n);
+  int best = -1;
+  float best_t = 0.f;
+  shm_status st = SHM_OK;
+  for (int v = 0; v < kNumVariants && st == SHM_OK; ++v) {
+    float tv = 1e30f;
+    for (int rep = 0; rep < 4 && st == SHM_OK; ++rep) {  // first repetition is a warm-up
+      cudaEventRecord(e0, 0);
+      st = eval_dispatch<T>(pts, n, lmax, out, false, true, 0, v);
+      cudaEventRecord(e1, 0);
+      if (st != SHM_OK) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+        st = fail_cuda(e, "autotune: kernel failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tv = std::min(tv, ms);
+    }
+    if (st == SHM_OK && (best < 0 || tv < best_t)) {
+      best = v;
+      best_t = tv;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(pts);
+  cudaFree(out);
+  if (st != SHM_OK) return st;
+  g_choice[sizeof(T) == 8 ? 1 : 0][lmax] = best;
+  if (best_ms) *best_ms = best_t;
+  const char* path = getenv("SHM_TUNE_CACHE");
+  if (path && *path) {
+    FILE* f = fopen(path, "a");
+    if (f) {
+      fprintf(f, "%d %d %d\n", sizeof(T) == 8 ? 1 : 0, lmax, best);
+      fclose(f);
+    }
+  }
+  return SHM_OK;
+}
+
+}  // namespace
+
+void ensure_tune_cache() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  load_tune_cache_locked();
+}
+
+}  // namespace shm
+
+extern "C" shm_status shm_autotune(int lmax, shm_dtype dtype, int64_t n_probe, double* best_ms) {
+  using namespace shm;
+  clear_error();
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
+  if (n_probe <= 0 || n_probe > (int64_t)1 << 26) return fail(SHM_EINVAL, "n_probe must be in 1..2^26");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  load_tune_cache_locked();
+  return dtype == SHM_F64 ? autotune_t<double>(lmax, n_probe, best_ms) : autotune_t<float>(lmax, n_probe, best_ms);
+}
+
+extern "C" const char* shm_eval_variant(int lmax, shm_dtype dtype) {
+  using namespace shm;
+  if (lmax < 0 || lmax > SHM_LMAX_CAP || (dtype != SHM_F32 && dtype != SHM_F64)) return "";
+  ensure_tune_cache();
+  const int v = g_choice[dtype == SHM_F64 ? 1 : 0][lmax];
+  return kVariantNames[v < 0 ? kDefaultVariant : v];
+}
+
+extern "C" int shm_eval_variant_count(void) { return shm::kNumVariants; }
+
+extern "C" shm_status shm_eval_set_variant(int lmax, shm_dtype dtype, int variant) {
+  using namespace shm;
+  clear_error();
+  if (lmax < 0 || lmax > SHM_LMAX_CAP || (dtype != SHM_F32 && dtype != SHM_F64))
+    return fail(SHM_EINVAL, "bad lmax or dtype");
+  if (variant < -1 || variant >= kNumVariants) return fail(SHM_EINVAL, "variant out of range");
+  ensure_tune_cache();
+  g_choice[dtype == SHM_F64 ? 1 : 0][lmax] = variant;
+  return SHM_OK;
+}

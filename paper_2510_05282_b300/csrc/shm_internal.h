@@ -1,0 +1,33 @@
+// Internal helpers shared by the libshm translation units (host side).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/shm.h"
+
+namespace shm {
+
+// Records msg as this thread's last error and returns st.
+shm_status fail(shm_status st, const std::string& msg);
+shm_status fail_cuda(cudaError_t e, const char* what);
+void clear_error();
+
+// Checks that [p, p + bytes) is device-accessible memory inside one
+// allocation of the current device (cuMemGetAddressRange), so that a wrong
+// pointer or size is rejected on the host instead of faulting the GPU.
+// `what` names the argument in the error message.
+shm_status check_device_range(const void* p, size_t bytes, const char* what);
+
+// True when the byte ranges [a, a + na) and [b, b + nb) intersect.
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb);
+
+int current_device();
+int sm_count(int dev);
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace shm

@@ -1,0 +1,564 @@
+// shm_projectors: fused non-local projectors f_{s,l}(|d|) R_l^m(d/|d|) on
+// atom spheres of a periodic real-space grid (the use the paper's Sec. I
+// motivates: projectors of pseudopotential / PAW methods on a 3-D grid).
+//
+// Launch structure (both on the caller's stream):
+//  1. k_proj_setup (one CTA): validates every atom's offsets and species,
+//     builds the tile table (tiles = TPB consecutive sphere points of one
+//     atom; tile_offsets[a] = number of tiles of atoms before a, 0 tiles for
+//     an atom that failed validation), zeroes the work counter and the error
+//     word, and for FP32 converts the radial tables and builds the exponent
+//     table of the log-grid index.
+//  2. k_proj (persistent: SMs x resident CTAs): each CTA takes the next tile
+//     from an atomic work counter, evaluates its rows -- minimum-image
+//     displacement, 1/r, log-grid index, 4-point Lagrange interpolation of the
+//     l radial functions, the real harmonics (sh_core.cuh), and their product
+//     -- into a shared-memory tile with an odd row stride, then copies the
+//     tile (one contiguous block of the output) out with coalesced stores.
+// Uneven sphere sizes (4k..65k points) and per-species lmax balance through
+// the dynamic queue; a tile never spans two atoms, so every row of a tile has
+// the same width.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "sh_core.cuh"
+#include "shm_internal.h"
+
+namespace shm {
+
+constexpr int kProjTPB = 128;
+constexpr int kExpLo = -160;  // FP32 log-grid exponent table covers frexpf exponents kExpLo..kExpHi
+constexpr int kExpHi = 140;
+constexpr int kExpN = kExpHi - kExpLo + 1;
+
+// Workspace layout (byte offsets; every block 256-byte aligned).
+struct ProjWs {
+  size_t counter = 0;      // unsigned long long work counter, uint32 error word at +8
+  size_t tiles = 256;      // int64 tile_offsets[n_atoms + 1]
+  size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
+  size_t rad32 = 0;        // FP32: float radial[n_species][lstride][n_rad]
+  size_t total = 0;
+};
+
+inline size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+ProjWs proj_layout(const shm_proj_problem& p, shm_dtype dt) {
+  ProjWs w;
+  w.tiles = 256;
+  size_t end = w.tiles + round256((size_t)(p.n_atoms + 1) * 8);
+  if (dt == SHM_F32) {
+    w.etab = end;
+    end += round256((size_t)kExpN * 8);
+    w.rad32 = end;
+    end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 4);
+  }
+  w.total = end;
+  return w;
+}
+
+struct ProjParams {
+  int64_t n_atoms, n_points, n_values;
+  const double* atom_pos;
+  const int32_t* atom_species;
+  const double* radial;
+  const int64_t* point_offsets;
+  const int32_t* point_index;
+  const int64_t* out_offsets;
+  int32_t n_species, lstride, n_rad, ng;
+  double r_min, dlog, box, h;
+  signed char lmax[SHM_PROJ_MAX_SPECIES];
+  // workspace views
+  unsigned long long* counter;
+  unsigned* err;
+  int64_t* tile_offsets;
+  int2* etab;
+  float* rad32;
+};
+
+enum : unsigned { kErrOffsets = 1u, kErrSpecies = 2u, kErrGrid = 4u, kErrOut = 8u };
+
+// ---------------------------------------------------------------------------
+// Set-up: validation, tile table (block-wide scan), counters, FP32 tables.
+
+__global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int fp32) {
+  __shared__ int64_t warp_sums[32];
+  __shared__ int64_t carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    *P.counter = 0ull;
+    *P.err = 0u;
+    carry = 0;
+    P.tile_offsets[0] = 0;
+  }
+  __syncthreads();
+  unsigned err = 0;
+  for (int64_t base = 0; base < P.n_atoms; base += blockDim.x) {
+    const int64_t a = base + tid;
+    int64_t ntiles = 0;
+    if (a < P.n_atoms) {
+      const int64_t p0 = P.point_offsets[a], p1 = P.point_offsets[a + 1];
+      const int s = P.atom_species[a];
+      bool ok = true;
+      if (!(p0 >= 0 && p1 >= p0 && p1 <= P.n_points)) {
+        err |= kErrOffsets;
+        ok = false;
+      }
+      if (s < 0 || s >= P.n_species) {
+        err |= kErrSpecies;
+        ok = false;
+      }
+      if (ok) {
+        const int64_t L2 = (int64_t)(P.lmax[s] + 1) * (P.lmax[s] + 1);
+        const int64_t o0 = P.out_offsets[a], o1 = P.out_offsets[a + 1];
+        if (!(o0 >= 0 && o1 <= P.n_values && o1 - o0 == (p1 - p0) * L2)) {
+          err |= kErrOut;
+          ok = false;
+        }
+      }
+      if (ok) ntiles = (p1 - p0 + tpb - 1) / tpb;
+    }
+    // inclusive block scan of ntiles
+    int64_t v = ntiles;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      const int nw = blockDim.x >> 5;
+      int64_t w = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += u;
+      }
+      if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const int64_t incl = v + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+    if (a < P.n_atoms) P.tile_offsets[a + 1] = incl;
+    __syncthreads();
+    if (tid == blockDim.x - 1) carry = incl;
+    __syncthreads();
+  }
+  if (err) atomicOr(P.err, err);
+  if (fp32) {
+    // exponent table: r = m 2^e (m in [0.5, 1)), t = (e ln2 - ln r_min)/dlog + ln(m)/dlog
+    //                 = I_e + c_e + ln(m)/dlog with I_e integer, c_e in [0, 1)
+    for (int i = tid; i < kExpN; i += blockDim.x) {
+      const int e = kExpLo + i;
+      const double C = ((double)e * 0.69314718055994530942 - log(P.r_min)) / P.dlog;
+      const double I = floor(C);
+      const double I_cl = fmin(fmax(I, -2147483000.0), 2147483000.0);
+      P.etab[i] = make_int2((int)I_cl, __float_as_int((float)(C - I)));
+    }
+    const int64_t nt = (int64_t)P.n_species * P.lstride * P.n_rad;
+    for (int64_t i = tid; i < nt; i += blockDim.x) P.rad32[i] = (float)P.radial[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-row pieces.
+
+template <typename T>
+struct Lagrange4 {
+  int i0;
+  T w[4];
+};
+
+// Stencil and weights of 4-point Lagrange interpolation at continuous index t
+// (already clamped to [0, n_rad - 1]).
+template <typename T>
+__device__ __forceinline__ Lagrange4<T> lagrange_at(int it, T u, int n_rad) {
+  // t = it + u, 0 <= u < 1
+  Lagrange4<T> L;
+  int i0 = it - 1;
+  i0 = i0 < 0 ? 0 : (i0 > n_rad - 4 ? n_rad - 4 : i0);
+  const T x = (T)(it - i0) + u;  // t - i0, in [0, 3]
+  const T x1 = x - (T)1, x2 = x - (T)2, x3 = x - (T)3;
+  L.i0 = i0;
+  L.w[0] = -(x1 * x2 * x3) * (T)(1.0 / 6.0);
+  L.w[1] = (x * x2 * x3) * (T)0.5;
+  L.w[2] = -(x * x1 * x3) * (T)0.5;
+  L.w[3] = (x * x1 * x2) * (T)(1.0 / 6.0);
+  return L;
+}
+
+constexpr int l_of_k(int k) {
+  int l = 0;
+  while ((l + 1) * (l + 1) <= k) ++l;
+  return l;
+}
+
+// Evaluate one row (lmax = LMAX) into row[0..(LMAX+1)^2).
+template <int LMAX, typename T>
+__device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, const T (&f)[SHM_LMAX_CAP + 1],
+                                         T* __restrict__ row) {
+  auto store = [&](int k, T v) { row[k] = v * f[l_of_k(k)]; };
+  if (origin) {
+    row[0] = (T)kInvSqrt4Pi * f[0];
+#pragma unroll
+    for (int k = 1; k < NH<LMAX>::value; ++k) row[k] = (T)0;
+    return;
+  }
+  T xb, yb, zb;
+  unit_dir(dx, dy, dz, xb, yb, zb);
+  sh_row<LMAX>(xb, yb, zb, store);
+}
+
+template <typename T>
+__device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin,
+                                                  const T (&f)[SHM_LMAX_CAP + 1], T* row) {
+  switch (lmax) {
+    case 0: proj_row<0>(dx, dy, dz, origin, f, row); break;
+    case 1: proj_row<1>(dx, dy, dz, origin, f, row); break;
+    case 2: proj_row<2>(dx, dy, dz, origin, f, row); break;
+    case 3: proj_row<3>(dx, dy, dz, origin, f, row); break;
+    case 4: proj_row<4>(dx, dy, dz, origin, f, row); break;
+    case 5: proj_row<5>(dx, dy, dz, origin, f, row); break;
+    case 6: proj_row<6>(dx, dy, dz, origin, f, row); break;
+    case 7: proj_row<7>(dx, dy, dz, origin, f, row); break;
+    case 8: proj_row<8>(dx, dy, dz, origin, f, row); break;
+    default: proj_row<9>(dx, dy, dz, origin, f, row); break;
+  }
+}
+
+// FP64 row: the displacement is formed exactly as the definition states
+// (grid point i*h minus the atom, then the minimum image), without FMA
+// contraction, so it is the correctly rounded binary64 value of each step.
+__device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, double ax, double ay, double az,
+                                               int s, int lmax, double inv_box, double inv_rmin,
+                                               double inv_dlog, double* row) {
+  const int ng = P.ng;
+  const int gi = g / (ng * ng), gj = (g / ng) % ng, gk = g % ng;
+  double d[3] = {__dsub_rn(__dmul_rn((double)gi, P.h), ax), __dsub_rn(__dmul_rn((double)gj, P.h), ay),
+                 __dsub_rn(__dmul_rn((double)gk, P.h), az)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d[c] = __dsub_rn(d[c], __dmul_rn(P.box, rint(d[c] * inv_box)));
+  const bool origin = is_origin(d[0], d[1], d[2]);
+  double t = 0.0;
+  if (!origin) {
+    const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2])));
+    t = log(r * inv_rmin) * inv_dlog;
+    t = fmin(fmax(t, 0.0), (double)(P.n_rad - 1));
+  }
+  const double tf = floor(t);
+  const Lagrange4<double> L = lagrange_at<double>((int)tf, t - tf, P.n_rad);
+  double f[SHM_LMAX_CAP + 1];
+  const double* tab = P.radial + (int64_t)s * P.lstride * P.n_rad + L.i0;
+#pragma unroll
+  for (int l = 0; l <= SHM_LMAX_CAP; ++l) {
+    f[l] = 0.0;
+    if (l <= lmax) {
+      const double* F = tab + (int64_t)l * P.n_rad;
+      f[l] = fma(L.w[3], __ldg(F + 3), fma(L.w[2], __ldg(F + 2), fma(L.w[1], __ldg(F + 1), L.w[0] * __ldg(F))));
+    }
+  }
+  proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, f, row);
+}
+
+// FP32 row.  The displacement in grid units, (i - U) - frac with U = floor of
+// the atom coordinate in grid units, is formed exactly as a float-float (the
+// integer part is exact; frac is split into hi + lo on the host side of the
+// tile), then rounded once; the log-grid index uses the exponent table so
+// that only ln(mantissa) is taken in FP32 and t keeps ~1e-5 absolute accuracy
+// at t ~ 2000.
+struct AtomF32 {
+  int U[3];
+  float fhi[3], flo[3];
+};
+
+__device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const AtomF32& A, int s, int lmax,
+                                               float h, float inv_dlog, float* row) {
+  const int ng = P.ng;
+  const int gi = g / (ng * ng), gj = (g / ng) % ng, gk = g % ng;
+  const int gg[3] = {gi, gj, gk};
+  float d[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    int n = gg[c] - A.U[c];  // minimum image in whole grid units: n - frac in [-ng/2, ng/2)
+    n -= ng * (int)floorf(((float)n - A.fhi[c]) / (float)ng + 0.5f);
+    const ff sdiff = two_sum((float)n, -A.fhi[c]);
+    const float lo = __fsub_rn(sdiff.lo, A.flo[c]);
+    const float v = __fadd_rn(sdiff.hi, lo);  // grid units, rounded once
+    d[c] = v * h;
+  }
+  const bool origin = is_origin(d[0], d[1], d[2]);
+  int it = 0;
+  float u = 0.0f;
+  if (!origin) {
+    const float r2 = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    float r;
+    if (r2 < 1e-4f) {  // r < 1e-2: r in FP64
+      r = (float)sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
+    } else {
+      r = sqrtf(r2);
+    }
+    int e;
+    const float m = frexpf(r, &e);  // r = m 2^e, m in [0.5, 1)
+    const int ei = min(max(e - kExpLo, 0), kExpN - 1);
+    const int2 E = P.etab[ei];
+    const float v = __int_as_float(E.y) + logf(m) * inv_dlog;
+    const float fl = floorf(v);
+    long long itl = (long long)E.x + (long long)fl;
+    u = v - fl;
+    if (itl < 0) {
+      itl = 0;
+      u = 0.0f;
+    } else if (itl >= P.n_rad - 1) {
+      itl = P.n_rad - 1;
+      u = 0.0f;
+    }
+    it = (int)itl;
+  }
+  const Lagrange4<float> L = lagrange_at<float>(it, u, P.n_rad);
+  float f[SHM_LMAX_CAP + 1];
+  const float* tab = P.rad32 + (int64_t)s * P.lstride * P.n_rad + L.i0;
+#pragma unroll
+  for (int l = 0; l <= SHM_LMAX_CAP; ++l) {
+    f[l] = 0.0f;
+    if (l <= lmax) {
+      const float* F = tab + (int64_t)l * P.n_rad;
+      f[l] = fmaf(L.w[3], F[3], fmaf(L.w[2], F[2], fmaf(L.w[1], F[1], L.w[0] * F[0])));
+    }
+  }
+  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, f, row);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent main kernel.
+
+template <typename T>
+__device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int rows, int L2, int RS,
+                                              T* __restrict__ dst) {
+  const int nv = rows * L2;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    const int r = j / L2;
+    __stcs(dst + j, tile[r * RS + (j - r * L2)]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__ out, int64_t total_tiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  __shared__ int64_t s_tile, s_atom;
+  __shared__ AtomF32 s_af;
+  const double inv_box = 1.0 / P.box, inv_rmin = 1.0 / P.r_min, inv_dlog = 1.0 / P.dlog;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t t = (int64_t)atomicAdd(P.counter, 1ull);
+      s_tile = t;
+      int64_t a = -1;
+      if (t < total_tiles) {  // last atom with tile_offsets[a] <= t
+        int64_t lo = 0, hi = P.n_atoms - 1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi + 1) >> 1;
+          if (P.tile_offsets[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        a = lo;
+        if constexpr (sizeof(T) == 4) {
+          const double pos[3] = {P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2]};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double q = pos[c] / P.h;  // atom coordinate in grid units
+            const double U = floor(q);
+            const double fr = q - U;
+            s_af.U[c] = (int)U;
+            s_af.fhi[c] = (float)fr;
+            s_af.flo[c] = (float)(fr - (double)s_af.fhi[c]);
+          }
+        }
+      }
+      s_atom = a;
+    }
+    __syncthreads();
+    const int64_t t = s_tile, a = s_atom;
+    if (t >= total_tiles) break;
+    const int64_t pa0 = P.point_offsets[a], pa1 = P.point_offsets[a + 1];
+    const int64_t c = t - P.tile_offsets[a];
+    const int64_t p0 = pa0 + c * kProjTPB;
+    const int rows = (int)min((int64_t)kProjTPB, pa1 - p0);
+    const int s = P.atom_species[a];
+    const int lmax = P.lmax[s];
+    const int L2 = (lmax + 1) * (lmax + 1);
+    const int RS = L2 | 1;
+    const int64_t o0 = P.out_offsets[a] + c * kProjTPB * (int64_t)L2;
+    if ((int)threadIdx.x < rows) {
+      const int64_t p = p0 + threadIdx.x;
+      const int g = P.point_index[p];
+      T* row = tile + threadIdx.x * RS;
+      if (g < 0 || g >= P.ng * P.ng * P.ng) {
+        atomicOr(P.err, kErrGrid);
+        for (int k = 0; k < L2; ++k) row[k] = (T)0;
+      } else if constexpr (sizeof(T) == 8) {
+        proj_point_f64(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
+                       inv_rmin, inv_dlog, reinterpret_cast<double*>(row));
+      } else {
+        proj_point_f32(P, g, s_af, s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
+      }
+    }
+    __syncthreads();
+    copy_rows_out<T>(tile, rows, L2, RS, out + o0);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+shm_status launch_proj(const ProjParams& P, int max_lmax, T* out, int64_t total_tiles, cudaStream_t s) {
+  constexpr int MAXDEV = 64;
+  static int bps[MAXDEV][SHM_LMAX_CAP + 1] = {};
+  const int dev = current_device();
+  if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
+  const int RS = ((max_lmax + 1) * (max_lmax + 1)) | 1;
+  const size_t smem = (size_t)kProjTPB * RS * sizeof(T);
+  auto kern = k_proj<T>;
+  if (bps[dev][max_lmax] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)kProjTPB * 101 * sizeof(T)));
+    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_proj)");
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kProjTPB, smem);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_proj)");
+    bps[dev][max_lmax] = std::max(b, 1);
+  }
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(total_tiles, (int64_t)sm_count(dev) * bps[dev][max_lmax]));
+  kern<<<(unsigned)grid, kProjTPB, smem, s>>>(P, out, total_tiles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "k_proj launch");
+  return SHM_OK;
+}
+
+// Validates the host-visible part of the problem and fills the kernel
+// parameters; the device-side arrays are validated by k_proj_setup.
+shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* workspace, size_t ws_bytes,
+                        ProjParams* P, int* max_lmax, int64_t* tile_upper) {
+  if (!prob) return fail(SHM_EINVAL, "prob is null");
+  const shm_proj_problem& p = *prob;
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (p.n_atoms < 0 || p.n_points < 0 || p.n_values < 0) return fail(SHM_EINVAL, "negative size");
+  if (p.n_species < 1 || p.n_species > SHM_PROJ_MAX_SPECIES) return fail(SHM_EINVAL, "n_species must be 1..64");
+  if (!p.species_lmax) return fail(SHM_EINVAL, "species_lmax (host) is null");
+  if (p.n_rad < 4) return fail(SHM_EINVAL, "n_rad must be >= 4");
+  if (p.ng < 1 || p.ng > 1290) return fail(SHM_EINVAL, "ng must be in 1..1290");
+  if (!(p.r_min > 0) || !(p.dlog > 0) || !(p.box > 0) || !(p.h > 0) || !std::isfinite(p.r_min) ||
+      !std::isfinite(p.dlog) || !std::isfinite(p.box) || !std::isfinite(p.h))
+    return fail(SHM_EINVAL, "r_min, dlog, box and h must be finite and > 0");
+  if (std::fabs(p.ng * p.h - p.box) > 1e-9 * p.box) return fail(SHM_EINVAL, "box must equal ng * h");
+  int ml = 0;
+  for (int s = 0; s < p.n_species; ++s) {
+    const int l = p.species_lmax[s];
+    if (l < 0 || l > SHM_LMAX_CAP) return fail(SHM_EINVAL, "species_lmax must be in 0..9");
+    ml = std::max(ml, l);
+  }
+  if (p.radial_lstride < ml + 1) return fail(SHM_EINVAL, "radial_lstride < 1 + max species lmax");
+  const ProjWs w = proj_layout(p, dtype);
+  if (!workspace) return fail(SHM_EINVAL, "workspace is null");
+  if (ws_bytes < w.total) return fail(SHM_EINVAL, "workspace too small (see shm_projectors_workspace_size)");
+  if (!aligned(workspace, 256)) return fail(SHM_EINVAL, "workspace must be 256-byte aligned");
+  shm_status st;
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  if ((st = check_device_range(workspace, w.total, "workspace")) != SHM_OK) return st;
+  if (p.n_atoms > 0) {
+    if ((st = check_device_range(p.atom_pos, (size_t)p.n_atoms * 24, "atom_pos")) != SHM_OK) return st;
+    if ((st = check_device_range(p.atom_species, (size_t)p.n_atoms * 4, "atom_species")) != SHM_OK) return st;
+    if ((st = check_device_range(p.point_offsets, (size_t)(p.n_atoms + 1) * 8, "point_offsets")) != SHM_OK) return st;
+    if ((st = check_device_range(p.out_offsets, (size_t)(p.n_atoms + 1) * 8, "out_offsets")) != SHM_OK) return st;
+  }
+  if (p.n_points > 0 && (st = check_device_range(p.point_index, (size_t)p.n_points * 4, "point_index")) != SHM_OK)
+    return st;
+  if ((st = check_device_range(p.radial, (size_t)p.n_species * p.radial_lstride * p.n_rad * 8, "radial")) != SHM_OK)
+    return st;
+  memset(P, 0, sizeof(*P));
+  P->n_atoms = p.n_atoms;
+  P->n_points = p.n_points;
+  P->n_values = p.n_values;
+  P->atom_pos = p.atom_pos;
+  P->atom_species = p.atom_species;
+  P->radial = p.radial;
+  P->point_offsets = p.point_offsets;
+  P->point_index = p.point_index;
+  P->out_offsets = p.out_offsets;
+  P->n_species = p.n_species;
+  P->lstride = p.radial_lstride;
+  P->n_rad = p.n_rad;
+  P->ng = p.ng;
+  P->r_min = p.r_min;
+  P->dlog = p.dlog;
+  P->box = p.box;
+  P->h = p.h;
+  for (int s = 0; s < p.n_species; ++s) P->lmax[s] = (signed char)p.species_lmax[s];
+  char* ws = (char*)workspace;
+  P->counter = (unsigned long long*)(ws + w.counter);
+  P->err = (unsigned*)(ws + w.counter + 8);
+  P->tile_offsets = (int64_t*)(ws + w.tiles);
+  P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
+  P->rad32 = dtype == SHM_F32 ? (float*)(ws + w.rad32) : nullptr;
+  *max_lmax = ml;
+  // an upper bound of the tile count: every point of every atom in its own partial tile
+  *tile_upper = p.n_points / kProjTPB + p.n_atoms;
+  (void)es;
+  return SHM_OK;
+}
+
+// Device side of the launch pair (set-up, then the persistent kernel) that
+// reads the exact tile count from the table the set-up kernel builds.
+template <typename T>
+__global__ void k_proj_total(const int64_t* tile_offsets, int64_t n_atoms, int64_t* total) {
+  *total = tile_offsets[n_atoms];
+}
+
+}  // namespace shm
+
+extern "C" size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dtype) {
+  if (!prob || prob->n_atoms < 0 || prob->n_species < 1 || prob->n_rad < 1 || prob->radial_lstride < 1) return 0;
+  if (dtype != SHM_F32 && dtype != SHM_F64) return 0;
+  return shm::proj_layout(*prob, dtype).total;
+}
+
+extern "C" shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+  using namespace shm;
+  clear_error();
+  ProjParams P;
+  int max_lmax = 0;
+  int64_t tile_upper = 0;
+  shm_status st = proj_prepare(prob, dtype, workspace, workspace_bytes, &P, &max_lmax, &tile_upper);
+  if (st != SHM_OK) return st;
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  if (prob->n_values > 0) {
+    if (!out) return fail(SHM_EINVAL, "out is null");
+    if (!aligned(out, es)) return fail(SHM_EINVAL, "out must be aligned to the element size");
+    if ((st = check_device_range(out, (size_t)prob->n_values * es, "out")) != SHM_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  k_proj_setup<<<1, 1024, 0, s>>>(P, kProjTPB, dtype == SHM_F32 ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
+  if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
+  // The persistent kernel stops when the work counter passes the real tile
+  // count, which it reads from the table (tile_offsets[n_atoms]); the host
+  // bound only sizes the grid.
+  return dtype == SHM_F64 ? launch_proj<double>(P, max_lmax, (double*)out, tile_upper, s)
+                          : launch_proj<float>(P, max_lmax, (float*)out, tile_upper, s);
+}
+
+extern "C" shm_status shm_projectors_check(const void* workspace, void* stream, uint32_t* error_bits) {
+  using namespace shm;
+  clear_error();
+  if (!workspace || !error_bits) return fail(SHM_EINVAL, "null argument");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+  unsigned v = 0;
+  e = cudaMemcpy(&v, (const char*)workspace + 8, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpy(error word)");
+  *error_bits = v;
+  return SHM_OK;
+}

@@ -1,0 +1,212 @@
+"""GPU parity of shm_eval against the CPU FP64 oracle (through the C ABI).
+
+Tolerances (see helpers.py): normwise per l, 1e-13 for FP64 and 2e-6 for FP32
+against the oracle at the FP32 inputs upcast exactly.
+"""
+import numpy as np
+import pytest
+
+from helpers import TOL_F32, TOL_F64, assert_normwise, normwise_err, per_l_max
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2510_05282_b300 as shm  # noqa: E402
+from paper_2510_05282_b300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_05282_b300 import build
+    build.build()
+    shm.lib()
+
+
+def gpu_eval(pts_np, lmax, dtype=torch.float64, normalized=False):
+    p = torch.from_numpy(np.ascontiguousarray(pts_np)).to(device="cuda", dtype=dtype)
+    out = shm.eval_sh(p, lmax, normalized=normalized)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_random_sphere_fp64_all_points(oracle_mod):
+    pts = inputs.random_sphere_points(65_536)          # 65,600 points incl. 64 on the axes
+    got = gpu_eval(pts, 9)
+    assert_normwise(got, oracle_mod.real_sh(pts, 9), TOL_F64, "random sphere FP64")
+
+
+@pytest.mark.parametrize("lmax", list(range(10)))
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 4099])
+def test_every_lmax_and_ragged_sizes_fp64(oracle_mod, lmax, n):
+    pts = inputs.random_sphere_points(n, stream="tests", with_axes=False)
+    got = gpu_eval(pts, lmax)
+    assert got.shape == (n, (lmax + 1) ** 2)
+    assert_normwise(got, oracle_mod.real_sh(pts, lmax), TOL_F64, f"lmax={lmax} n={n}")
+
+
+@pytest.mark.parametrize("lmax", [0, 3, 9])
+@pytest.mark.parametrize("n", [1, 129, 4099])
+def test_every_lmax_and_ragged_sizes_fp32(oracle_mod, lmax, n):
+    pts32 = inputs.random_sphere_points(n, stream="tests", with_axes=False).astype(np.float32)
+    got = gpu_eval(pts32, lmax, dtype=torch.float32)
+    ref = oracle_mod.real_sh(pts32.astype(np.float64), lmax)
+    assert_normwise(got, ref, TOL_F32, f"FP32 lmax={lmax} n={n}")
+
+
+def test_edge_points_fp64(oracle_mod):
+    pts = inputs.edge_points()
+    got = gpu_eval(pts, 9)
+    ref = oracle_mod.real_sh(pts, 9)
+    assert_normwise(got, ref, TOL_F64, "edge points")
+    # r = 0 rows are exactly [1/sqrt(4 pi), 0, ...] (Sec. II)
+    for i in (0, 1):
+        assert got[i, 0] == np.float64(0.28209479177387814347)
+        assert np.all(got[i, 1:] == 0.0)
+    # on the z axis every m != 0 harmonic is exactly zero
+    l = np.array([int(np.sqrt(k)) for k in range(100)])
+    m = np.arange(100) - l * l - l
+    for i in (2, 3):
+        assert np.all(got[i, m != 0] == 0.0)
+
+
+def test_edge_points_fp32(oracle_mod):
+    pts32 = inputs.edge_points()
+    pts32 = pts32[np.all(np.abs(pts32) < 1e30, axis=1)].astype(np.float32)
+    got = gpu_eval(pts32, 9, dtype=torch.float32)
+    ref = oracle_mod.real_sh(pts32.astype(np.float64), 9)
+    assert_normwise(got, ref, TOL_F32, "FP32 edge points")
+
+
+def test_nan_propagates():
+    got = gpu_eval(np.array([[np.nan, 0.0, 1.0], [0.0, 0.0, 1.0]]), 4)
+    assert np.all(np.isnan(got[0, 1:]))
+    assert not np.isnan(got[1]).any()
+
+
+def test_normalized_input_flag(oracle_mod):
+    pts = inputs.random_sphere_points(5000, stream="tests", with_axes=False)
+    unit = pts / np.linalg.norm(pts, axis=1, keepdims=True)
+    got = gpu_eval(unit, 9, normalized=True)
+    assert_normwise(got, oracle_mod.real_sh(pts, 9), TOL_F64, "normalized input")
+
+
+def test_unaligned_output_uses_scalar_path(oracle_mod):
+    pts = inputs.random_sphere_points(1001, stream="tests", with_axes=False)
+    p = torch.from_numpy(pts).cuda()
+    buf = torch.empty(1001 * 100 + 1, dtype=torch.float64, device="cuda")
+    out = buf[1:]                                  # 8-byte but not 16-byte aligned
+    assert out.data_ptr() % 16 == 8
+    shm.eval_sh(p, 9, out=out)
+    torch.cuda.synchronize()
+    assert_normwise(out.view(1001, 100).cpu().numpy(), oracle_mod.real_sh(pts, 9), TOL_F64, "unaligned")
+
+
+def test_bad_arguments_launch_nothing():
+    from cuda.bindings import runtime as rt
+    L = shm.lib()
+    p = torch.zeros((20, 3), dtype=torch.float64, device="cuda")
+    # an exact 10-row output allocation (not a slice of a larger pool block)
+    err, raw = rt.cudaMalloc(10 * 100 * 8)
+    assert err == rt.cudaError_t.cudaSuccess
+    try:
+        out = torch.full((10, 100), 7.0, dtype=torch.float64, device="cuda")
+        rt.cudaMemcpy(raw, out.data_ptr(), 8000, rt.cudaMemcpyKind.cudaMemcpyDeviceToDevice)
+        # n = 20 rows do not fit the 10-row allocation: rejected on the host
+        assert L.shm_eval(p.data_ptr(), 20, 9, 1, int(raw), None) == 1
+        assert b"past the end" in L.shm_last_error()
+        # host memory passed as device memory
+        host = np.zeros((10, 3))
+        assert L.shm_eval(host.ctypes.data, 10, 9, 1, int(raw), None) == 1
+        # overlapping input and output
+        assert L.shm_eval(int(raw), 10, 9, 1, int(raw) + 64, None) == 1
+        torch.cuda.synchronize()
+        back = torch.empty((10, 100), dtype=torch.float64, device="cuda")
+        rt.cudaMemcpy(back.data_ptr(), raw, 8000, rt.cudaMemcpyKind.cudaMemcpyDeviceToDevice)
+        assert torch.all(back == 7.0)
+    finally:
+        rt.cudaFree(raw)
+
+
+def test_host_buffer_entry_point(oracle_mod):
+    pts = inputs.random_sphere_points(30_000, stream="tests")
+    n = pts.shape[0]
+    for pinned in (True, False):
+        hin = torch.from_numpy(pts)
+        hout = torch.empty((n, 100), dtype=torch.float64)
+        if pinned:
+            hin, hout = hin.pin_memory(), hout.pin_memory()
+        ws = torch.empty(shm.eval_host_workspace_size(9, torch.float64, 7000), dtype=torch.uint8, device="cuda")
+        shm.eval_host(hin, 9, hout, ws)
+        torch.cuda.synchronize()
+        assert_normwise(hout.numpy(), oracle_mod.real_sh(pts, 9), TOL_F64, f"host entry pinned={pinned}")
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lmax", [0, 4, 9])
+def test_every_launch_variant(oracle_mod, dtype, lmax):
+    pts = inputs.random_sphere_points(3001, stream="tests")
+    if dtype == torch.float32:
+        pts = pts.astype(np.float32).astype(np.float64)
+    ref = oracle_mod.real_sh(pts, lmax)
+    tol = TOL_F64 if dtype == torch.float64 else TOL_F32
+    try:
+        for v in range(shm.eval_variant_count()):
+            shm.set_eval_variant(lmax, dtype, v)
+            got = gpu_eval(pts, lmax, dtype=dtype)
+            assert_normwise(got, ref, tol, f"variant {shm.eval_variant(lmax, dtype)}")
+    finally:
+        shm.set_eval_variant(lmax, dtype, -1)
+
+
+def test_autotune_keeps_results_correct(oracle_mod):
+    ms = shm.autotune(9, torch.float64, 1 << 16)
+    assert ms > 0 and shm.eval_variant(9, torch.float64)
+    pts = inputs.random_sphere_points(2000, stream="tests")
+    assert_normwise(gpu_eval(pts, 9), oracle_mod.real_sh(pts, 9), TOL_F64, "after autotune")
+    shm.set_eval_variant(9, torch.float64, -1)
+
+
+def test_dft_grid_fp64_full_size_sampled(oracle_mod):
+    """192^3 grid (7.08M points, 5.7 GB out) in every launch configuration the
+    tuner may pick for bench.py: sampled rows against the oracle; the addition
+    theorem on every row."""
+    pts = inputs.dft_grid_points(192)
+    p = torch.from_numpy(pts).cuda()
+    g = inputs.rng("tests", 77)
+    n = pts.shape[0]
+    rows = np.unique(np.concatenate([np.arange(256), np.arange(n - 300, n), g.integers(0, n, 20000)]))
+    ref = oracle_mod.real_sh(pts[rows], 9)
+    rows_t = torch.from_numpy(rows).cuda()
+    try:
+        for v in range(shm.eval_variant_count()):
+            shm.set_eval_variant(9, torch.float64, v)
+            out = shm.eval_sh(p, 9)
+            torch.cuda.synchronize()
+            assert_normwise(out[rows_t].cpu().numpy(), ref, TOL_F64, f"192^3 grid sample, variant {v}")
+            for l in range(10):
+                s = (out[:, l * l:(l + 1) ** 2] ** 2).sum(dim=1)
+                dev = (s - (2 * l + 1) / (4 * np.pi)).abs().max().item()
+                assert dev <= 4 * TOL_F64 * (2 * l + 1) / (4 * np.pi), (v, l, dev)
+            del out
+    finally:
+        shm.set_eval_variant(9, torch.float64, -1)
+
+
+def test_fp32_grid_and_sphere_per_l_report(oracle_mod, capsys):
+    """The FP32 workload: the 192^3 grid (sampled) and 1M random-sphere points
+    (all rows) against the oracle at the upcast FP32 inputs, error per l."""
+    sph = inputs.random_sphere_points(1 << 20, stream="sphere32", with_axes=False).astype(np.float32)
+    got = gpu_eval(sph, 9, dtype=torch.float32)
+    err = normwise_err(got, oracle_mod.real_sh(sph.astype(np.float64), 9))
+    with capsys.disabled():
+        print("\nFP32 1M sphere, max normwise error per l:", " ".join(f"{e:.2e}" for e in per_l_max(err)))
+    assert float(err.max()) <= TOL_F32
+    grid = inputs.dft_grid_points(192).astype(np.float32)
+    p = torch.from_numpy(grid).cuda()
+    out = shm.eval_sh(p, 9)
+    torch.cuda.synchronize()
+    rows = np.unique(inputs.rng("tests", 78).integers(0, grid.shape[0], 20000))
+    got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert_normwise(got, oracle_mod.real_sh(grid[rows].astype(np.float64), 9), TOL_F32, "FP32 grid sample")
