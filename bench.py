@@ -366,7 +366,38 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
     return res
 
 
-EXTRA_WORKLOADS: list = []
+def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
+    """Fused projectors: 512 atoms, 40 bohr box, h = 0.2, spheres 2-5 bohr,
+    lmax in {2, 3, 4}; values/s of one shm_projectors call (set-up + persistent
+    launch), FP64 and FP32."""
+    res = {}
+    prob = inputs.projector_problem()
+    d = shm.DeviceProjectors(prob)
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    for dt, name, es in ((torch.float64, "fp64", 8), (torch.float32, "fp32", 4)):
+        ws = d.workspace(dt)
+        out = torch.empty(d.n_values, dtype=dt, device="cuda")
+        fn = lambda: shm.projectors(d, dt, out=out, workspace=ws, stream=stream)  # noqa: E731
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        per, _ = timed_launches(fn, max(5, min(args.steps, 30)), stream)
+        ms = statistics.mean(per)
+        err_bits = shm.projectors_check(ws, stream=stream)
+        algo_bytes = d.n_values * es + d.n_points * 4
+        gbs = algo_bytes / (ms * 1e-3) / 1e9
+        res[f"projectors_512atoms_{name}"] = {
+            "value": d.n_values / (ms * 1e-3), "unit": "projector values/s", "ms_per_call": ms,
+            "atoms": prob.n_atoms, "points": d.n_points, "values": d.n_values, "error_bits": err_bits,
+            "launches_per_call": 2,
+            "roofline": {"bound": "hbm" if es == 4 else "alu", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
+                         "hbm_frac": gbs / hbm_peak, "unit": "GB/s", "peak_source": peaks_src,
+                         "algorithmic_bytes": algo_bytes}}
+        del out, ws
+    return res
+
+
+EXTRA_WORKLOADS: list = [extra_projectors]
 
 
 def main():

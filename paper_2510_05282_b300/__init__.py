@@ -6,5 +6,5 @@ input generators used by tests and benchmarks.
 """
 from ._binding import (LMAX_CAP, SHM_F32, SHM_F64, ShmError, autotune, check, eval_host,  # noqa: F401
                        eval_host_workspace_size, eval_sh, eval_variant, eval_variant_count, lib,
-                       num_harmonics, set_eval_variant)
+                       num_harmonics, set_eval_variant, DeviceProjectors, projectors, projectors_check)
 from . import inputs  # noqa: F401

@@ -164,3 +164,75 @@ def eval_host(points_host, lmax: int, out_host, workspace, stream=None) -> None:
     n = points_host.shape[0]
     check(lib().shm_eval_host(ptr(points_host), n, int(lmax), code, ptr(out_host), workspace.data_ptr(),
                               workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
+
+
+# --------------------------------------------------------------------------- projectors
+
+class _ProjProblem(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("atom_pos", ctypes.c_void_p), ("atom_species", ctypes.c_void_p),
+                ("n_species", ctypes.c_int32), ("species_lmax", ctypes.c_void_p), ("radial", ctypes.c_void_p),
+                ("radial_lstride", ctypes.c_int32), ("n_rad", ctypes.c_int32), ("r_min", ctypes.c_double),
+                ("dlog", ctypes.c_double), ("box", ctypes.c_double), ("ng", ctypes.c_int32), ("h", ctypes.c_double),
+                ("point_offsets", ctypes.c_void_p), ("point_index", ctypes.c_void_p),
+                ("out_offsets", ctypes.c_void_p), ("n_points", ctypes.c_int64), ("n_values", ctypes.c_int64)]
+
+
+_EXTRA_DECLS.extend([
+    ("shm_projectors_workspace_size", ([ctypes.POINTER(_ProjProblem), ctypes.c_int], ctypes.c_size_t)),
+    ("shm_projectors", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int)),
+    ("shm_projectors_check", ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int)),
+])
+
+
+class DeviceProjectors:
+    """A projector problem uploaded to the GPU (device tensors kept alive here),
+    with the C struct the library reads.  `prob` is an
+    ``inputs.ProjectorProblem``-like object with numpy fields."""
+
+    def __init__(self, prob, device="cuda"):
+        import torch
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)  # noqa: E731
+        self.atom_pos = t(prob.atom_pos, np.float64)
+        self.atom_species = t(prob.atom_species, np.int32)
+        self.radial = t(prob.radial, np.float64)
+        self.point_offsets = t(prob.point_offsets, np.int64)
+        self.point_index = t(prob.point_index, np.int32)
+        self.out_offsets = t(prob.out_offsets, np.int64)
+        self.species_lmax = np.ascontiguousarray(prob.species_lmax, dtype=np.int32)   # host
+        self.n_values = int(prob.out_offsets[-1])
+        self.n_points = int(prob.point_offsets[-1])
+        self.c = _ProjProblem(
+            n_atoms=int(prob.atom_pos.shape[0]), atom_pos=self.atom_pos.data_ptr(),
+            atom_species=self.atom_species.data_ptr(), n_species=int(self.species_lmax.shape[0]),
+            species_lmax=self.species_lmax.ctypes.data, radial=self.radial.data_ptr(),
+            radial_lstride=int(prob.radial.shape[1]), n_rad=int(prob.radial.shape[2]),
+            r_min=float(prob.r_min), dlog=float(prob.dlog), box=float(prob.box), ng=int(prob.ng), h=float(prob.h),
+            point_offsets=self.point_offsets.data_ptr(), point_index=self.point_index.data_ptr(),
+            out_offsets=self.out_offsets.data_ptr(), n_points=self.n_points, n_values=self.n_values)
+
+    def workspace_size(self, dtype) -> int:
+        return int(lib().shm_projectors_workspace_size(ctypes.byref(self.c), _dtype_code(dtype)))
+
+    def workspace(self, dtype):
+        import torch
+        return torch.empty(max(self.workspace_size(dtype), 256), dtype=torch.uint8, device=self.atom_pos.device)
+
+
+def projectors(dprob: DeviceProjectors, dtype, out=None, workspace=None, stream=None):
+    """Fused projector values (flat CSR, [n_values]) of a DeviceProjectors problem."""
+    import torch
+    tdt = torch.float64 if _dtype_code(dtype) == SHM_F64 else torch.float32
+    if out is None:
+        out = torch.empty(dprob.n_values, dtype=tdt, device=dprob.atom_pos.device)
+    if workspace is None:
+        workspace = dprob.workspace(dtype)
+    check(lib().shm_projectors(ctypes.byref(dprob.c), _dtype_code(dtype), out.data_ptr(), workspace.data_ptr(),
+                               workspace.numel(), _stream_ptr(stream)))
+    return out
+
+
+def projectors_check(workspace, stream=None) -> int:
+    bits = ctypes.c_uint32(0)
+    check(lib().shm_projectors_check(workspace.data_ptr(), _stream_ptr(stream), ctypes.byref(bits)))
+    return int(bits.value)

@@ -45,7 +45,7 @@ __device__ __forceinline__ bool is_origin(float x, float y, float z) {
 
 // Scale (x, y, z) by a power of two so that the largest |component| lies in
 // [1, 2): exact, and keeps x^2 + y^2 + z^2 away from overflow and underflow.
-__device__ __noinline__ void rescale_pow2(double& x, double& y, double& z) {
+static __device__ __noinline__ void rescale_pow2(double& x, double& y, double& z) {
   const double ax = fabs(x), ay = fabs(y), az = fabs(z);
   const double mx = fmax(ax, fmax(ay, az));
   int e;

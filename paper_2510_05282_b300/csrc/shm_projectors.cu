@@ -196,11 +196,21 @@ constexpr int l_of_k(int k) {
   return l;
 }
 
-// Evaluate one row (lmax = LMAX) into row[0..(LMAX+1)^2).
+__device__ __forceinline__ double interp4(const Lagrange4<double>& L, const double* F) {
+  return fma(L.w[3], __ldg(F + 3), fma(L.w[2], __ldg(F + 2), fma(L.w[1], __ldg(F + 1), L.w[0] * __ldg(F))));
+}
+__device__ __forceinline__ float interp4(const Lagrange4<float>& L, const float* F) {
+  return fmaf(L.w[3], F[3], fmaf(L.w[2], F[2], fmaf(L.w[1], F[1], L.w[0] * F[0])));
+}
+
+// One row (lmax = LMAX): interpolate f_0..f_LMAX at the stencil, then write
+// f_l(r) R_l^m into row[0..(LMAX+1)^2).  tab points at f_{s,0}[i0].
 template <int LMAX, typename T>
-__device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, const T (&f)[SHM_LMAX_CAP + 1],
-                                         T* __restrict__ row) {
-  auto store = [&](int k, T v) { row[k] = v * f[l_of_k(k)]; };
+__device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, const Lagrange4<T>& L,
+                                         const T* __restrict__ tab, int n_rad, T* __restrict__ row) {
+  T f[LMAX + 1];
+#pragma unroll
+  for (int l = 0; l <= LMAX; ++l) f[l] = interp4(L, tab + (int64_t)l * n_rad);
   if (origin) {
     row[0] = (T)kInvSqrt4Pi * f[0];
 #pragma unroll
@@ -209,23 +219,23 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, const T 
   }
   T xb, yb, zb;
   unit_dir(dx, dy, dz, xb, yb, zb);
-  sh_row<LMAX>(xb, yb, zb, store);
+  sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
 }
 
 template <typename T>
-__device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin,
-                                                  const T (&f)[SHM_LMAX_CAP + 1], T* row) {
+__device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin, const Lagrange4<T>& L,
+                                                  const T* tab, int n_rad, T* row) {
   switch (lmax) {
-    case 0: proj_row<0>(dx, dy, dz, origin, f, row); break;
-    case 1: proj_row<1>(dx, dy, dz, origin, f, row); break;
-    case 2: proj_row<2>(dx, dy, dz, origin, f, row); break;
-    case 3: proj_row<3>(dx, dy, dz, origin, f, row); break;
-    case 4: proj_row<4>(dx, dy, dz, origin, f, row); break;
-    case 5: proj_row<5>(dx, dy, dz, origin, f, row); break;
-    case 6: proj_row<6>(dx, dy, dz, origin, f, row); break;
-    case 7: proj_row<7>(dx, dy, dz, origin, f, row); break;
-    case 8: proj_row<8>(dx, dy, dz, origin, f, row); break;
-    default: proj_row<9>(dx, dy, dz, origin, f, row); break;
+    case 0: proj_row<0>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 1: proj_row<1>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 2: proj_row<2>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 3: proj_row<3>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 4: proj_row<4>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 5: proj_row<5>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 6: proj_row<6>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 7: proj_row<7>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 8: proj_row<8>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    default: proj_row<9>(dx, dy, dz, origin, L, tab, n_rad, row); break;
   }
 }
 
@@ -250,17 +260,8 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
   }
   const double tf = floor(t);
   const Lagrange4<double> L = lagrange_at<double>((int)tf, t - tf, P.n_rad);
-  double f[SHM_LMAX_CAP + 1];
   const double* tab = P.radial + (int64_t)s * P.lstride * P.n_rad + L.i0;
-#pragma unroll
-  for (int l = 0; l <= SHM_LMAX_CAP; ++l) {
-    f[l] = 0.0;
-    if (l <= lmax) {
-      const double* F = tab + (int64_t)l * P.n_rad;
-      f[l] = fma(L.w[3], __ldg(F + 3), fma(L.w[2], __ldg(F + 2), fma(L.w[1], __ldg(F + 1), L.w[0] * __ldg(F))));
-    }
-  }
-  proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, f, row);
+  proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, L, tab, P.n_rad, row);
 }
 
 // FP32 row.  The displacement in grid units, (i - U) - frac with U = floor of
@@ -318,17 +319,8 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
     it = (int)itl;
   }
   const Lagrange4<float> L = lagrange_at<float>(it, u, P.n_rad);
-  float f[SHM_LMAX_CAP + 1];
   const float* tab = P.rad32 + (int64_t)s * P.lstride * P.n_rad + L.i0;
-#pragma unroll
-  for (int l = 0; l <= SHM_LMAX_CAP; ++l) {
-    f[l] = 0.0f;
-    if (l <= lmax) {
-      const float* F = tab + (int64_t)l * P.n_rad;
-      f[l] = fmaf(L.w[3], F[3], fmaf(L.w[2], F[2], fmaf(L.w[1], F[1], L.w[0] * F[0])));
-    }
-  }
-  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, f, row);
+  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, L, tab, P.n_rad, row);
 }
 
 // ---------------------------------------------------------------------------
@@ -345,12 +337,14 @@ __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int ro
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__ out, int64_t total_tiles) {
+__global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   __shared__ int64_t s_tile, s_atom;
   __shared__ AtomF32 s_af;
   const double inv_box = 1.0 / P.box, inv_rmin = 1.0 / P.r_min, inv_dlog = 1.0 / P.dlog;
+  // exact tile count, from the table the set-up kernel built earlier on this stream
+  const int64_t total_tiles = P.tile_offsets[P.n_atoms];
   for (;;) {
     if (threadIdx.x == 0) {
       const int64_t t = (int64_t)atomicAdd(P.counter, 1ull);
@@ -412,7 +406,7 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
 }
 
 template <typename T>
-shm_status launch_proj(const ProjParams& P, int max_lmax, T* out, int64_t total_tiles, cudaStream_t s) {
+shm_status launch_proj(const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, cudaStream_t s) {
   constexpr int MAXDEV = 64;
   static int bps[MAXDEV][SHM_LMAX_CAP + 1] = {};
   const int dev = current_device();
@@ -429,8 +423,8 @@ shm_status launch_proj(const ProjParams& P, int max_lmax, T* out, int64_t total_
     if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_proj)");
     bps[dev][max_lmax] = std::max(b, 1);
   }
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(total_tiles, (int64_t)sm_count(dev) * bps[dev][max_lmax]));
-  kern<<<(unsigned)grid, kProjTPB, smem, s>>>(P, out, total_tiles);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tile_upper, (int64_t)sm_count(dev) * bps[dev][max_lmax]));
+  kern<<<(unsigned)grid, kProjTPB, smem, s>>>(P, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_proj launch");
   return SHM_OK;
@@ -508,13 +502,6 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   return SHM_OK;
 }
 
-// Device side of the launch pair (set-up, then the persistent kernel) that
-// reads the exact tile count from the table the set-up kernel builds.
-template <typename T>
-__global__ void k_proj_total(const int64_t* tile_offsets, int64_t n_atoms, int64_t* total) {
-  *total = tile_offsets[n_atoms];
-}
-
 }  // namespace shm
 
 extern "C" size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dtype) {
@@ -544,8 +531,8 @@ extern "C" shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dty
   if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
   if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
   // The persistent kernel stops when the work counter passes the real tile
-  // count, which it reads from the table (tile_offsets[n_atoms]); the host
-  // bound only sizes the grid.
+  // count, which it reads from the table (tile_offsets[n_atoms]); the host's
+  // upper bound only sizes the grid.
   return dtype == SHM_F64 ? launch_proj<double>(P, max_lmax, (double*)out, tile_upper, s)
                           : launch_proj<float>(P, max_lmax, (float*)out, tile_upper, s);
 }

@@ -1,0 +1,183 @@
+"""GPU parity of shm_projectors against the oracle's fused projectors.
+
+Tolerance per value: |P_gpu - P_oracle| <= tol * F_sl * sqrt((2l+1)/4pi) with
+F_sl = max |f_{s,l}| over the table, i.e. normwise against the size of the
+product's l-shell.  FP64: tol = 1e-13.  FP32: tol = 4e-6 (see
+PROJ_TOL_F32 below).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2510_05282_b300 as shm  # noqa: E402
+from paper_2510_05282_b300 import inputs  # noqa: E402
+
+PROJ_TOL_F64 = 1e-13
+# FP32: table values rounded to float (0.5 ulp), Lagrange weights and the
+# 4-term sum in FP32 (a few ulps of the local table magnitude), the log-grid
+# index to ~1e-5 (which moves f by ~1e-5 * dlog * |d ln f / d ln r| ~ 1e-7
+# relative), and the FP32 harmonics (<= 1e-6 of the l-shell norm at l = 9).
+PROJ_TOL_F32 = 4e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_05282_b300 import build
+    build.build()
+    shm.lib()
+
+
+def small_problem(extra=0, **kw):
+    args = dict(n_atoms=6, box=6.0, h=0.25, rc_range=(1.0, 2.0), n_species=3,
+                lmax_choices=(2, 3, 4), n_rad=200, r_min=1e-3, r_max=3.0, extra=extra)
+    args.update(kw)
+    return inputs.projector_problem(**args)
+
+
+def value_scale(prob):
+    """Per-value scale F_sl * sqrt((2l+1)/4pi)."""
+    F = np.abs(prob.radial).max(axis=2)            # [S, lstride]
+    out = np.empty(prob.n_values)
+    for a in range(prob.n_atoms):
+        s = prob.atom_species[a]
+        L = int(prob.species_lmax[s])
+        n = int(prob.point_offsets[a + 1] - prob.point_offsets[a])
+        ls = np.array([int(math.isqrt(k)) for k in range((L + 1) ** 2)])
+        row = F[s, ls] * np.sqrt((2 * ls + 1) / (4 * np.pi))
+        out[prob.out_offsets[a]:prob.out_offsets[a + 1]] = np.tile(row, n)
+    return out
+
+
+def check(prob, got, ref, tol, what):
+    scale = value_scale(prob)
+    err = np.abs(got.astype(np.float64) - ref) / scale
+    worst = float(err.max()) if err.size else 0.0
+    assert not np.isnan(err).any(), what
+    assert worst <= tol, f"{what}: max scaled error {worst:.3e} > {tol:.1e}"
+    return worst
+
+
+def run(prob, dtype):
+    d = shm.DeviceProjectors(prob)
+    ws = d.workspace(dtype)
+    out = shm.projectors(d, dtype, workspace=ws)
+    torch.cuda.synchronize()
+    assert shm.projectors_check(ws) == 0
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("extra", [0, 1, 2])
+def test_small_fp64(oracle_mod, extra):
+    prob = small_problem(extra)
+    check(prob, run(prob, torch.float64), oracle_mod.projectors(prob), PROJ_TOL_F64, "FP64 small")
+
+
+@pytest.mark.parametrize("extra", [0, 1])
+def test_small_fp32(oracle_mod, extra):
+    prob = small_problem(extra)
+    check(prob, run(prob, torch.float32), oracle_mod.projectors(prob), PROJ_TOL_F32, "FP32 small")
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, PROJ_TOL_F64), (torch.float32, PROJ_TOL_F32)])
+def test_every_lmax_up_to_9(oracle_mod, dtype, tol):
+    prob = small_problem(5, n_atoms=10, n_species=10, lmax_choices=tuple(range(10)))
+    check(prob, run(prob, dtype), oracle_mod.projectors(prob), tol, f"lmax 0..9 {dtype}")
+
+
+def test_atom_on_a_grid_point_uses_origin_rule(oracle_mod):
+    prob = small_problem(3)
+    # move atom 0 exactly onto grid point (8, 9, 10): its own row is at r = 0
+    prob.atom_pos[0] = np.array([8, 9, 10], dtype=np.float64) * prob.h
+    off, idx = inputs.sphere_lists(prob.atom_pos, prob.atom_rc, prob.ng, prob.h, prob.box)
+    prob.point_offsets, prob.point_index = off, idx
+    nh = (prob.atom_lmax().astype(np.int64) + 1) ** 2
+    prob.out_offsets = np.concatenate([[0], np.cumsum(np.diff(off) * nh)]).astype(np.int64)
+    for dtype, tol in ((torch.float64, PROJ_TOL_F64), (torch.float32, PROJ_TOL_F32)):
+        got = run(prob, dtype)
+        ref = oracle_mod.projectors(prob)
+        check(prob, got, ref, tol, f"origin {dtype}")
+        g0 = (8 * prob.ng + 9) * prob.ng + 10
+        p = int(np.nonzero(prob.point_index[:off[1]] == g0)[0][0])
+        L2 = int(nh[0])
+        row = got[p * L2:(p + 1) * L2]
+        assert np.all(row[1:] == 0.0)
+
+
+def test_empty_atoms_and_no_points():
+    prob = small_problem(4)
+    # atom 2 keeps no points
+    a = 2
+    cut = prob.point_offsets[a + 1] - prob.point_offsets[a]
+    idx = np.concatenate([prob.point_index[:prob.point_offsets[a]], prob.point_index[prob.point_offsets[a + 1]:]])
+    off = prob.point_offsets.copy()
+    off[a + 1:] -= cut
+    prob.point_index, prob.point_offsets = idx, off
+    nh = (prob.atom_lmax().astype(np.int64) + 1) ** 2
+    prob.out_offsets = np.concatenate([[0], np.cumsum(np.diff(off) * nh)]).astype(np.int64)
+    import oracle
+    check(prob, run(prob, torch.float64), oracle.projectors(prob), PROJ_TOL_F64, "empty atom")
+
+
+def test_inconsistent_problem_sets_error_bits_without_faulting():
+    prob = small_problem(6)
+    d = shm.DeviceProjectors(prob)
+    ws = d.workspace(torch.float64)
+    # (a) a grid index out of range: flagged, the row is zeroed
+    d.point_index[5] = prob.ng ** 3 + 7
+    out = shm.projectors(d, torch.float64, workspace=ws)
+    assert shm.projectors_check(ws) & 4
+    # (b) output offsets inconsistent with the row widths: that atom is skipped
+    d.point_index[5] = int(prob.point_index[5])
+    d.out_offsets[2] += 1
+    out = shm.projectors(d, torch.float64, workspace=ws)
+    assert shm.projectors_check(ws) & 8
+    # (c) a species index out of range
+    d.out_offsets[2] -= 1
+    d.atom_species[1] = 99
+    out = shm.projectors(d, torch.float64, workspace=ws)
+    assert shm.projectors_check(ws) & 2
+    # (d) point offsets running past n_points
+    d.atom_species[1] = int(prob.atom_species[1])
+    d.point_offsets[3] = prob.n_points + 1000
+    out = shm.projectors(d, torch.float64, workspace=ws)
+    assert shm.projectors_check(ws) & 1
+    # and a clean problem again reports nothing
+    d.point_offsets[3] = int(prob.point_offsets[3])
+    out = shm.projectors(d, torch.float64, workspace=ws)
+    assert shm.projectors_check(ws) == 0
+    del out
+
+
+def test_host_side_validation():
+    prob = small_problem(7)
+    d = shm.DeviceProjectors(prob)
+    ws = d.workspace(torch.float64)
+    L = shm.lib()
+    import ctypes
+    bad = shm._binding._ProjProblem.from_buffer_copy(d.c)
+    bad.radial_lstride = 1                      # smaller than 1 + max lmax
+    out = torch.empty(d.n_values, dtype=torch.float64, device="cuda")
+    assert L.shm_projectors(ctypes.byref(bad), 1, out.data_ptr(), ws.data_ptr(), ws.numel(), None) == 1
+    bad = shm._binding._ProjProblem.from_buffer_copy(d.c)
+    bad.box = 7.0                               # != ng * h
+    assert L.shm_projectors(ctypes.byref(bad), 1, out.data_ptr(), ws.data_ptr(), ws.numel(), None) == 1
+    assert L.shm_projectors(ctypes.byref(d.c), 1, out.data_ptr(), ws.data_ptr(), 16, None) == 1   # workspace
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, PROJ_TOL_F64), (torch.float32, PROJ_TOL_F32)])
+def test_full_projector_workload(oracle_mod, dtype, tol, capsys):
+    """512 atoms in a 40 bohr box, h = 0.2 bohr, spheres of 2-5 bohr, lmax in
+    {2, 3, 4}: every value against the oracle, in bench.py's launch set-up."""
+    prob = inputs.projector_problem()
+    got = run(prob, dtype)
+    ref = oracle_mod.projectors(prob)
+    worst = check(prob, got, ref, tol, f"full workload {dtype}")
+    with capsys.disabled():
+        print(f"\nprojectors {dtype}: {prob.n_atoms} atoms, {prob.n_points} points, {prob.n_values} values, "
+              f"max scaled error {worst:.2e}")
