@@ -201,6 +201,36 @@ shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* o
  * inconsistent with out_offsets. */
 shm_status shm_projectors_check(const void* workspace, void* stream, uint32_t* error_bits);
 
+/*
+ * shm_projectors_noalloc -- shm_projectors for callers that cannot allocate
+ * device memory.  (The paper has no counterpart: it is a calling convention
+ * of this library.)  Some callers own no allocation rights on the device:
+ * a host code whose framework has already reserved the device memory in its
+ * own pool (a further cudaMalloc fails or fragments that pool), or a time-step
+ * loop with a fixed memory budget that may not grow or synchronise the device
+ * through cudaMalloc/cudaFree.  They pass only the problem and the output;
+ * the scratch (work counter, error word, per-atom tile table and, for
+ * SHM_F32, the FP32 copies of the radial tables) lives in a static device
+ * array of SHM_PROJ_NOALLOC_SCRATCH_BYTES bytes inside this library, which
+ * every GPU that loads the library holds until the process exits.
+ *   prob, dtype, out, stream : as shm_projectors.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current) and caches it; make that
+ * first call before any stream capture.  No call allocates or frees memory.
+ * The counter and the error word are cleared at the start of every call, on
+ * `stream`.  All calls share the one array: calls that overlap on the GPU
+ * (on different streams or threads) race and must not be issued; calls on
+ * one stream are ordered and safe.  The error word of this variant cannot be
+ * read back (use shm_projectors with a workspace for that report); rows the
+ * kernel finds inconsistent are skipped as in shm_projectors.
+ * Errors: those of shm_projectors; SHM_EINVAL, with the byte counts in
+ * shm_last_error(), when the problem needs more scratch than
+ * SHM_PROJ_NOALLOC_SCRATCH_BYTES (shm_projectors_workspace_size tells how
+ * much); SHM_ECUDA if the symbol lookup fails.
+ */
+#define SHM_PROJ_NOALLOC_SCRATCH_BYTES (1u << 20)
+shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* stream);
+
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* shm_last_error(void);
 

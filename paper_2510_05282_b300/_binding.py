@@ -182,7 +182,11 @@ _EXTRA_DECLS.extend([
     ("shm_projectors", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int)),
     ("shm_projectors_check", ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int)),
+    ("shm_projectors_noalloc", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+                                ctypes.c_int)),
 ])
+
+PROJ_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 
 class DeviceProjectors:
@@ -236,3 +240,12 @@ def projectors_check(workspace, stream=None) -> int:
     bits = ctypes.c_uint32(0)
     check(lib().shm_projectors_check(workspace.data_ptr(), _stream_ptr(stream), ctypes.byref(bits)))
     return int(bits.value)
+
+
+def projectors_noalloc(dprob: DeviceProjectors, dtype, out, stream=None):
+    """shm_projectors_noalloc: the projector values into the caller's `out`
+    ([n_values] CUDA tensor of dtype) with no device allocation by the library
+    (its scratch is a static device array of PROJ_NOALLOC_SCRATCH_BYTES)."""
+    check(lib().shm_projectors_noalloc(ctypes.byref(dprob.c), _dtype_code(dtype), out.data_ptr(),
+                                       _stream_ptr(stream)))
+    return out

@@ -24,6 +24,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "sh_core.cuh"
 #include "shm_internal.h"
@@ -548,4 +550,71 @@ extern "C" shm_status shm_projectors_check(const void* workspace, void* stream, 
   if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpy(error word)");
   *error_bits = v;
   return SHM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point: the same two launches with the scratch in a
+// static device array of this library instead of a caller workspace.
+
+static __device__ __align__(256) unsigned char g_proj_noalloc_scratch[SHM_PROJ_NOALLOC_SCRATCH_BYTES];
+
+namespace shm {
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of g_proj_noalloc_scratch on the current device, looked up
+// once per device (host code only holds a stand-in for the array's name).
+shm_status noalloc_scratch(void** ptr) {
+  const int dev = current_device();
+  if (dev < 0 || dev >= 64) return fail(SHM_EUNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_proj_noalloc_scratch);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetSymbolAddress(projector scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  return SHM_OK;
+}
+}  // namespace
+}  // namespace shm
+
+extern "C" shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_dtype dtype, void* out,
+                                              void* stream) {
+  using namespace shm;
+  clear_error();
+  if (!prob) return fail(SHM_EINVAL, "prob is null");
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (prob->n_atoms < 0 || prob->n_species < 1 || prob->n_species > SHM_PROJ_MAX_SPECIES || prob->n_rad < 4 ||
+      prob->radial_lstride < 1)
+    return fail(SHM_EINVAL, "bad problem sizes");
+  const size_t need = proj_layout(*prob, dtype).total;
+  if (need > SHM_PROJ_NOALLOC_SCRATCH_BYTES)
+    return fail(SHM_EINVAL, "problem needs " + std::to_string(need) + " bytes of scratch; the allocation-free "
+                            "entry point has " + std::to_string((size_t)SHM_PROJ_NOALLOC_SCRATCH_BYTES) +
+                            " (use shm_projectors with a workspace)");
+  void* scratch = nullptr;
+  shm_status st = noalloc_scratch(&scratch);
+  if (st != SHM_OK) return st;
+  ProjParams P;
+  int max_lmax = 0;
+  int64_t tile_upper = 0;
+  st = proj_prepare(prob, dtype, scratch, SHM_PROJ_NOALLOC_SCRATCH_BYTES, &P, &max_lmax, &tile_upper);
+  if (st != SHM_OK) return st;
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  if (prob->n_values > 0) {
+    if (!out) return fail(SHM_EINVAL, "out is null");
+    if (!aligned(out, es)) return fail(SHM_EINVAL, "out must be aligned to the element size");
+    if ((st = check_device_range(out, (size_t)prob->n_values * es, "out")) != SHM_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // k_proj_setup clears the work counter and the error word before anything reads them
+  k_proj_setup<<<1, 1024, 0, s>>>(P, kProjTPB, dtype == SHM_F32 ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
+  if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
+  return dtype == SHM_F64 ? launch_proj<double>(P, max_lmax, (double*)out, tile_upper, s)
+                          : launch_proj<float>(P, max_lmax, (float*)out, tile_upper, s);
 }
