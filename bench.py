@@ -397,7 +397,46 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
     return res
 
 
-EXTRA_WORKLOADS: list = [extra_projectors]
+def extra_serving(args, shm, torch, inputs, stream, peaks, peaks_src):
+    """Serving: Poisson request streams (sizes log-uniform in [1e3, 4e6] points,
+    lmax uniform in 0..9, dtype 50/50 FP32/FP64, points generated on the device
+    from each request's seed), continuous batching, per-rate throughput and
+    submit-to-done latency percentiles.  Requests are submitted with
+    SHM_REQ_DISCARD (the client does not read rows back)."""
+    res = {}
+    for rate in args.serve_rates:
+        reqs = inputs.serving_requests(rate, args.serve_seconds)
+        with shm.Server(pool_bytes=48 << 30, max_slots=256, queue_capacity=2048, batch_points=8 << 20,
+                        chunk_points=1 << 20, inflight_batches=3) as srv:
+            t0 = time.perf_counter()
+            for r in reqs:
+                while True:
+                    dt = r.arrival_s - (time.perf_counter() - t0)
+                    if dt <= 0:
+                        break
+                    if dt > 2e-3:
+                        time.sleep(dt - 1e-3)
+                srv.submit(r.n, r.lmax, r.dtype, seed=r.seed, discard=True)
+            t_sub = time.perf_counter() - t0
+            deadline = time.perf_counter() + 300
+            while time.perf_counter() < deadline:
+                st = srv.stats()
+                if st["completed"] + st["rejected"] >= st["submitted"]:
+                    break
+                time.sleep(0.001)
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        res[f"serve_poisson_{rate}_per_s"] = {
+            "offered_req_per_s": rate, "submitted": st["submitted"], "submit_rate_achieved": len(reqs) / t_sub,
+            "completed": st["completed"], "rejected_busy": st["rejected"],
+            "completed_req_per_s": st["completed"] / wall, "value": st["harmonics_done"] / wall, "unit": UNIT,
+            "lat_p50_ms": st["lat_p50_ms"], "lat_p99_ms": st["lat_p99_ms"], "lat_max_ms": st["lat_max_ms"],
+            "batches": st["batches"], "gpu_busy_frac": st["busy_ms"] / (wall * 1e3), "wall_s": wall,
+            "duration_s": args.serve_seconds, "pool_peak_bytes": st["pool_peak"]}
+    return res
+
+
+EXTRA_WORKLOADS: list = [extra_projectors, extra_serving]
 
 
 def main():
@@ -410,6 +449,10 @@ def main():
     ap.add_argument("--grid", type=int, default=N_SIDE, help="grid side (192 = the benchmark workload; "
                     "smaller sides only for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="length of each Poisson request stream of the serving extra (30 for the full run)")
+    ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")],
+                    default=[1000.0, 5000.0, 20000.0, 50000.0])
     ap.add_argument("--no-tune", dest="tune", action="store_false", default=True,
                     help="skip shm_autotune (use the library's default launch variant)")
     ap.add_argument("--extras", dest="extras", action="store_true", default=True)

@@ -201,6 +201,97 @@ shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* o
  * inconsistent with out_offsets. */
 shm_status shm_projectors_check(const void* workspace, void* stream, uint32_t* error_bits);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of evaluation requests on one GPU (not in the
+ * paper; the paper's evaluator is the unit of work).  Requests of any size,
+ * lmax and dtype are admitted as device memory (a pool allocated at create)
+ * and request slots free up; a scheduler thread forms each GPU batch from
+ * chunks of every admitted, unfinished request (round robin, at most
+ * chunk_points per request and batch_points per batch), so requests that
+ * arrive while others run join the next batch and their work shares the
+ * same kernel launches.  Each request's rows are computed by the same device
+ * code as shm_eval, so a result does not depend on what it was batched with.
+ * There is no device-side polling: every batch is an ordinary launch and
+ * completion is observed through CUDA events.
+ * ------------------------------------------------------------------------ */
+typedef struct shm_server shm_server;
+
+typedef struct {
+  size_t pool_bytes;        /* device memory for request outputs (one cudaMalloc at create) */
+  int32_t max_slots;        /* requests admitted (on the device) at once, >= 1 */
+  int32_t queue_capacity;   /* requests waiting for admission; beyond it submit returns SHM_EBUSY */
+  int64_t batch_points;     /* points per GPU batch (all requests together), >= 1 */
+  int64_t chunk_points;     /* points per request per batch, >= 1 */
+  int32_t inflight_batches; /* batches enqueued ahead of completion, 1..8 */
+  int32_t device;           /* CUDA device ordinal */
+} shm_serve_config;
+
+#define SHM_REQ_DISCARD 0x1u /* free the output as soon as the request completes (no result rows) */
+
+typedef struct {
+  const void* points;       /* device [n][3] of dtype, kept alive by the caller until the request
+                               completes; NULL: the server generates point i from `seed` (see
+                               shm_serve_generated_point) */
+  int64_t n;                /* >= 1 */
+  int32_t lmax;             /* 0..9 */
+  shm_dtype dtype;
+  uint64_t seed;
+  uint32_t flags;           /* SHM_REQ_DISCARD */
+} shm_request;
+
+typedef struct {
+  shm_status status;        /* SHM_OK once complete */
+  void* out;                /* device [n][(lmax+1)^2] of dtype, valid until shm_serve_release
+                               (NULL for SHM_REQ_DISCARD) */
+  int64_t n;
+  int32_t lmax;
+  shm_dtype dtype;
+  double t_submit_ms;       /* server clock: ms since shm_serve_create */
+  double t_admit_ms;
+  double t_done_ms;         /* when the server saw the last batch holding the request finish */
+} shm_result;
+
+typedef struct {
+  uint64_t submitted, rejected, admitted, completed, batches;
+  uint64_t queued_now, active_now;
+  double harmonics_done;    /* sum over completed requests of n (lmax+1)^2 */
+  double busy_ms;           /* sum of batch GPU times (CUDA events) */
+  double lat_p50_ms, lat_p99_ms, lat_max_ms;   /* submit -> done, over completed requests */
+  size_t pool_bytes, pool_in_use, pool_peak;
+} shm_serve_stats;
+
+/* Creates a server: allocates the pool and starts the scheduler thread.
+ * Errors: SHM_EINVAL (config), SHM_ENOMEM (pool), SHM_ECUDA. */
+shm_status shm_serve_create(const shm_serve_config* cfg, shm_server** server);
+
+/* Queues a request and returns its ticket.  SHM_EBUSY when the queue is full
+ * (the request is counted as rejected); SHM_EINVAL for a bad request or one
+ * whose output can never fit the pool. */
+shm_status shm_serve_submit(shm_server* server, const shm_request* req, uint64_t* ticket);
+
+/* Waits up to timeout_ms (< 0: no limit) for the request; fills *result.
+ * SHM_ETIMEOUT when it is still running; SHM_ENOTFOUND for an unknown or
+ * released ticket. */
+shm_status shm_serve_wait(shm_server* server, uint64_t ticket, int timeout_ms, shm_result* result);
+
+/* Returns a completed request's output memory to the pool and forgets the
+ * ticket.  SHM_EBUSY if it has not completed. */
+shm_status shm_serve_release(shm_server* server, uint64_t ticket);
+
+/* Counters and latency percentiles since create (or the last reset). */
+shm_status shm_serve_stats_get(shm_server* server, shm_serve_stats* stats);
+shm_status shm_serve_stats_reset(shm_server* server);
+
+/* Stops the scheduler after the admitted work drains, frees the pool. */
+shm_status shm_serve_destroy(shm_server* server);
+
+/* Point i of a generated request (points == NULL) with this seed, as double
+ * x, y, z: SplitMix64 counter words 4i..4i+3 mapped with correctly rounded
+ * IEEE operations only, so any binary64 implementation reproduces it
+ * exactly (host function; the device uses the same arithmetic).  FP32
+ * requests round these to float. */
+void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3]);
+
 /*
  * shm_projectors_noalloc -- shm_projectors for callers that cannot allocate
  * device memory.  (The paper has no counterpart: it is a calling convention

@@ -249,3 +249,134 @@ def projectors_noalloc(dprob: DeviceProjectors, dtype, out, stream=None):
     check(lib().shm_projectors_noalloc(ctypes.byref(dprob.c), _dtype_code(dtype), out.data_ptr(),
                                        _stream_ptr(stream)))
     return out
+
+
+# --------------------------------------------------------------------------- serving
+
+SHM_REQ_DISCARD = 0x1
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("pool_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("batch_points", ctypes.c_int64), ("chunk_points", ctypes.c_int64),
+                ("inflight_batches", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("lmax", ctypes.c_int32),
+                ("dtype", ctypes.c_int), ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("out", ctypes.c_void_p), ("n", ctypes.c_int64), ("lmax", ctypes.c_int32),
+                ("dtype", ctypes.c_int), ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("queued_now", ctypes.c_uint64),
+                ("active_now", ctypes.c_uint64), ("harmonics_done", ctypes.c_double), ("busy_ms", ctypes.c_double),
+                ("lat_p50_ms", ctypes.c_double), ("lat_p99_ms", ctypes.c_double), ("lat_max_ms", ctypes.c_double),
+                ("pool_bytes", ctypes.c_size_t), ("pool_in_use", ctypes.c_size_t), ("pool_peak", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_EXTRA_DECLS.extend([
+    ("shm_serve_create", ([ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)], ctypes.c_int)),
+    ("shm_serve_submit", ([_vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int)),
+    ("shm_serve_wait", ([_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ServeResult)], ctypes.c_int)),
+    ("shm_serve_release", ([_vp, ctypes.c_uint64], ctypes.c_int)),
+    ("shm_serve_stats_get", ([_vp, ctypes.POINTER(ServeStats)], ctypes.c_int)),
+    ("shm_serve_stats_reset", ([_vp], ctypes.c_int)),
+    ("shm_serve_destroy", ([_vp], ctypes.c_int)),
+    ("shm_serve_generated_point", ([ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)], None)),
+])
+
+
+def serve_generated_point(seed: int, i: int):
+    xyz = (ctypes.c_double * 3)()
+    lib().shm_serve_generated_point(int(seed), int(i), xyz)
+    return [xyz[0], xyz[1], xyz[2]]
+
+
+class Server:
+    """Continuous-batching evaluation server (shm_serve_*)."""
+
+    def __init__(self, pool_bytes=8 << 30, max_slots=64, queue_capacity=1024, batch_points=4 << 20,
+                 chunk_points=1 << 19, inflight_batches=3, device=None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.cfg = ServeConfig(pool_bytes=int(pool_bytes), max_slots=int(max_slots),
+                               queue_capacity=int(queue_capacity), batch_points=int(batch_points),
+                               chunk_points=int(chunk_points), inflight_batches=int(inflight_batches),
+                               device=int(device))
+        h = ctypes.c_void_p()
+        check(lib().shm_serve_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, n: int, lmax: int, dtype, seed: int = 0, points=None, discard: bool = False):
+        """Returns a ticket, or None when the server answered SHM_EBUSY."""
+        req = _Request(points=points.data_ptr() if points is not None else None, n=int(n), lmax=int(lmax),
+                       dtype=_dtype_code(dtype), seed=int(seed) & 0xFFFFFFFFFFFFFFFF,
+                       flags=SHM_REQ_DISCARD if discard else 0)
+        t = ctypes.c_uint64(0)
+        st = lib().shm_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st == 4:
+            return None
+        check(st)
+        if points is not None:
+            self._keep[t.value] = points
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> ServeResult:
+        r = ServeResult()
+        check(lib().shm_serve_wait(self.h, int(ticket), int(timeout_ms), ctypes.byref(r)))
+        return r
+
+    def wait_status(self, ticket: int, timeout_ms: int = 0):
+        r = ServeResult()
+        st = lib().shm_serve_wait(self.h, int(ticket), int(timeout_ms), ctypes.byref(r))
+        return st, r
+
+    def result_tensor(self, r: ServeResult):
+        """A copy of a completed request's rows as a CUDA tensor [n, (lmax+1)^2]."""
+        import torch
+        dt = torch.float64 if r.dtype == SHM_F64 else torch.float32
+        nh = num_harmonics(r.lmax)
+        out = torch.empty((r.n, nh), dtype=dt, device="cuda")
+        from cuda.bindings import runtime as rt
+        err, = rt.cudaMemcpy(out.data_ptr(), r.out, r.n * nh * out.element_size(),
+                             rt.cudaMemcpyKind.cudaMemcpyDeviceToDevice)
+        if err != rt.cudaError_t.cudaSuccess:
+            raise RuntimeError(f"cudaMemcpy failed: {err}")
+        return out
+
+    def release(self, ticket: int) -> None:
+        check(lib().shm_serve_release(self.h, int(ticket)))
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = ServeStats()
+        check(lib().shm_serve_stats_get(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self) -> None:
+        check(lib().shm_serve_stats_reset(self.h))
+
+    def close(self) -> None:
+        if self.h:
+            check(lib().shm_serve_destroy(self.h))
+            self.h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,673 @@
+// Serving: continuous batching of evaluation requests on one GPU.
+//
+// A scheduler thread owns the device side.  Each iteration it
+//  1. retires finished batches (CUDA events, in stream order): requests whose
+//     last chunk finished become complete, their latency is recorded and
+//     waiters are woken; discarded outputs go back to the pool;
+//  2. admits queued requests in arrival order while a request slot is free
+//     and the device pool can hold the request's output (first fit);
+//  3. if fewer than `inflight_batches` batches are on the GPU, forms the next
+//     batch: a round robin over the admitted, unfinished requests taking at
+//     most chunk_points points from each and batch_points in total, so large
+//     requests progress in slices while newly admitted requests join at once;
+//     the chunk descriptors go to the device with one copy from pinned memory
+//     and one k_serve launch evaluates every tile of every chunk.
+// k_serve evaluates each tile with the same per-point code and the same
+// staged store as shm_eval (sh_core.cuh, sh_tile.cuh), so a request's rows do
+// not depend on which other requests shared its batches.  The kernel never
+// waits on anything: there is no device-side polling to bound.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "sh_core.cuh"
+#include "sh_tile.cuh"
+#include "shm_internal.h"
+
+namespace shm {
+
+constexpr int kServeTPB = 64;
+constexpr int kMaxChunksPerBatch = 4096;
+
+struct ServeChunk {
+  const void* pts;          // device points, or null: generate from seed
+  void* out;                // request output base
+  unsigned long long seed;
+  long long p0;             // first point of the chunk within its request
+  long long tile0;          // first tile of the chunk within the batch
+  int n;                    // points in the chunk
+  int lmax;
+  int dtype;                // SHM_F32 / SHM_F64
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// Counter-based point generator (SplitMix64 of Steele, Lea and Flood 2014 as
+// a counter-based source: word(seed, c) = mix(seed + (c + 1) * golden gamma)).
+// Only correctly rounded IEEE operations, written with _rn intrinsics so no
+// FMA contraction can change a bit: any binary64 implementation reproduces
+// the points exactly.
+
+__host__ __device__ inline unsigned long long splitmix_word(unsigned long long seed, unsigned long long c) {
+  unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ inline void gen_point_dev(unsigned long long seed, long long i, double& x, double& y, double& z) {
+  const unsigned long long c = 4ull * (unsigned long long)i;
+  const unsigned long long w0 = splitmix_word(seed, c), w1 = splitmix_word(seed, c + 1),
+                           w2 = splitmix_word(seed, c + 2), w3 = splitmix_word(seed, c + 3);
+  const double two53 = 1.0 / 9007199254740992.0;
+  const double zb = __dsub_rn(2.0 * ((double)(w0 >> 11) * two53), 1.0);
+  const double t = __dsub_rn(2.0 * ((double)(w1 >> 11) * two53), 1.0);
+  const double t2 = __dmul_rn(t, t);
+  const double den = __dadd_rn(1.0, t2);
+  double cc = __ddiv_rn(__dsub_rn(1.0, t2), den);
+  const double ss = __ddiv_rn(2.0 * t, den);
+  if (w3 & 1ull) cc = -cc;
+  const double rho = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(zb, zb)));
+  const int e = (int)((w3 >> 32) % 14ull) - 10;
+  const double radius = ldexp(1.0 + (double)(w2 >> 12) * (1.0 / 4503599627370496.0), e);
+  x = __dmul_rn(__dmul_rn(rho, cc), radius);
+  y = __dmul_rn(__dmul_rn(rho, ss), radius);
+  z = __dmul_rn(zb, radius);
+}
+
+// Host twin of gen_point_dev (host code is compiled without FMA contraction
+// on x86-64, whose baseline ISA has no FMA).
+void gen_point_host(unsigned long long seed, long long i, double* xyz) {
+  const unsigned long long c = 4ull * (unsigned long long)i;
+  const unsigned long long w0 = splitmix_word(seed, c), w1 = splitmix_word(seed, c + 1),
+                           w2 = splitmix_word(seed, c + 2), w3 = splitmix_word(seed, c + 3);
+  const double two53 = 1.0 / 9007199254740992.0;
+  volatile double zb = 2.0 * ((double)(w0 >> 11) * two53) - 1.0;
+  volatile double t = 2.0 * ((double)(w1 >> 11) * two53) - 1.0;
+  volatile double t2 = t * t;
+  volatile double den = 1.0 + t2;
+  double cc = (1.0 - t2) / den;
+  const double ss = (2.0 * t) / den;
+  if (w3 & 1ull) cc = -cc;
+  volatile double zz = zb * zb;
+  const double rho = std::sqrt(1.0 - zz);
+  const int e = (int)((w3 >> 32) % 14ull) - 10;
+  const double radius = std::ldexp(1.0 + (double)(w2 >> 12) * (1.0 / 4503599627370496.0), e);
+  volatile double rc = rho * cc, rs = rho * ss;
+  xyz[0] = rc * radius;
+  xyz[1] = rs * radius;
+  xyz[2] = zb * radius;
+}
+
+// ---------------------------------------------------------------------------
+// Batch kernel.
+
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+template <typename T, int LMAX>
+__device__ __forceinline__ void serve_tile(const ServeChunk& c, long long p, int rows, unsigned char* smem) {
+  constexpr int L2 = TileShape<LMAX>::L2;
+  constexpr int RS = TileShape<LMAX>::RS;
+  T* tile = reinterpret_cast<T*>(smem);
+  if ((int)threadIdx.x < rows) {
+    const long long pi = p + threadIdx.x;
+    T x, y, z;
+    if (c.pts) {
+      const T* P = reinterpret_cast<const T*>(c.pts);
+      x = P[3 * pi];
+      y = P[3 * pi + 1];
+      z = P[3 * pi + 2];
+    } else {
+      double dx, dy, dz;
+      gen_point_dev(c.seed, pi, dx, dy, dz);
+      x = (T)dx;
+      y = (T)dy;
+      z = (T)dz;
+    }
+    T* row = tile + threadIdx.x * RS;
+    sh_point<LMAX>(x, y, z, false, [&](int k, T v) { row[k] = v; });
+  }
+  __syncthreads();
+  T* dst = reinterpret_cast<T*>(c.out) + p * L2;
+  copy_out_tile<T, L2, RS, kServeTPB>(tile, rows, dst, aligned16(dst));
+}
+
+template <typename T>
+__device__ __forceinline__ void serve_tile_l(const ServeChunk& c, long long p, int rows, unsigned char* smem) {
+  switch (c.lmax) {
+    case 0: serve_tile<T, 0>(c, p, rows, smem); break;
+    case 1: serve_tile<T, 1>(c, p, rows, smem); break;
+    case 2: serve_tile<T, 2>(c, p, rows, smem); break;
+    case 3: serve_tile<T, 3>(c, p, rows, smem); break;
+    case 4: serve_tile<T, 4>(c, p, rows, smem); break;
+    case 5: serve_tile<T, 5>(c, p, rows, smem); break;
+    case 6: serve_tile<T, 6>(c, p, rows, smem); break;
+    case 7: serve_tile<T, 7>(c, p, rows, smem); break;
+    case 8: serve_tile<T, 8>(c, p, rows, smem); break;
+    default: serve_tile<T, 9>(c, p, rows, smem); break;
+  }
+}
+
+__global__ void __launch_bounds__(kServeTPB) k_serve(const ServeChunk* __restrict__ chunks, int nchunks,
+                                                     long long ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ServeChunk c;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (threadIdx.x == 0) {  // last chunk with tile0 <= t
+      int lo = 0, hi = nchunks - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunks[mid].tile0 <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      c = chunks[lo];
+    }
+    __syncthreads();
+    const long long p = c.p0 + (t - c.tile0) * kServeTPB;
+    const int rows = (int)min((long long)kServeTPB, c.p0 + c.n - p);
+    if (c.dtype == SHM_F64) serve_tile_l<double>(c, p, rows, smem_raw);
+    else serve_tile_l<float>(c, p, rows, smem_raw);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+using Clock = std::chrono::steady_clock;
+
+struct PoolAllocator {
+  size_t size = 0, in_use = 0, peak = 0;
+  std::map<size_t, size_t> free_;  // offset -> length
+  void init(size_t s) {
+    size = s;
+    free_.clear();
+    free_[0] = s;
+  }
+  bool alloc(size_t len, size_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= len) {
+        *off = it->first;
+        const size_t rest = it->second - len;
+        const size_t noff = it->first + len;
+        free_.erase(it);
+        if (rest) free_[noff] = rest;
+        in_use += len;
+        peak = std::max(peak, in_use);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t len) {
+    in_use -= len;
+    auto it = free_.emplace(off, len).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+enum ReqState { kQueued, kActive, kDone };
+
+struct Request {
+  shm_request r;
+  ReqState state = kQueued;
+  size_t L2 = 0, es = 0, out_bytes = 0, pool_off = 0;
+  void* out = nullptr;
+  int64_t next_point = 0, done_points = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  bool failed = false;  // a batch holding part of it failed to launch or run
+};
+
+struct Batch {
+  cudaEvent_t start = nullptr, end = nullptr;
+  ServeChunk* host = nullptr;  // pinned
+  ServeChunk* dev = nullptr;
+  std::vector<std::pair<uint64_t, int64_t>> parts;  // (ticket, points)
+  bool inflight = false;
+  bool failed = false;
+  uint64_t seq = 0;
+};
+
+}  // namespace shm
+
+struct shm_server {
+  shm_serve_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char* pool = nullptr;
+  shm::PoolAllocator alloc;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::vector<uint64_t> active;  // admitted and not yet fully scheduled, round-robin order
+  size_t rr = 0;
+  std::unordered_map<uint64_t, shm::Request> reqs;
+  std::vector<shm::Batch> batches;
+  uint64_t batch_seq = 0, next_retire = 0;
+  uint64_t next_ticket = 1;
+  int slots_used = 0;
+  std::thread sched;
+  bool stop = false;
+  shm::Clock::time_point t0;
+  // stats
+  uint64_t submitted = 0, rejected = 0, admitted = 0, completed = 0, nbatches = 0;
+  double harmonics = 0, busy_ms = 0;
+  std::vector<double> lat;
+  std::string thread_error;
+  int smem_ok = 0, grid = 0;
+
+  double now_ms() const { return std::chrono::duration<double, std::milli>(shm::Clock::now() - t0).count(); }
+  void run();
+  bool retire_locked();
+  bool admit_locked();
+  bool launch_locked();
+};
+
+namespace shm {
+namespace {
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+}  // namespace shm
+
+bool shm_server::retire_locked() {
+  bool any = false;
+  for (;;) {
+    // batches retire in launch order (one stream)
+    shm::Batch* b = nullptr;
+    for (auto& x : batches)
+      if (x.inflight && x.seq == next_retire) b = &x;
+    if (!b) break;
+    const cudaError_t q = b->failed ? cudaSuccess : cudaEventQuery(b->end);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) {
+      thread_error = std::string("batch failed: ") + cudaGetErrorString(q);
+      cudaGetLastError();
+      b->failed = true;
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->start, b->end) == cudaSuccess) busy_ms += ms;
+    else cudaGetLastError();
+    const double t = now_ms();
+    for (auto& pr : b->parts) {
+      auto it = reqs.find(pr.first);
+      if (it == reqs.end()) continue;
+      shm::Request& R = it->second;
+      R.done_points += pr.second;
+      if (b->failed) R.failed = true;
+      if (R.done_points == R.r.n) {
+        R.state = shm::kDone;
+        R.t_done = t;
+        lat.push_back(R.t_done - R.t_submit);
+        ++completed;
+        harmonics += (double)R.r.n * (double)R.L2;
+        --slots_used;
+        if (R.r.flags & SHM_REQ_DISCARD) {
+          alloc.release(R.pool_off, R.out_bytes);
+          reqs.erase(it);
+        }
+      }
+    }
+    b->parts.clear();
+    b->inflight = false;
+    b->failed = false;
+    ++next_retire;
+    any = true;
+  }
+  if (any) cv_done.notify_all();
+  return any;
+}
+
+bool shm_server::admit_locked() {
+  bool any = false;
+  while (!queue.empty() && slots_used < cfg.max_slots) {
+    auto it = reqs.find(queue.front());
+    if (it == reqs.end()) {
+      queue.pop_front();
+      continue;
+    }
+    shm::Request& R = it->second;
+    size_t off = 0;
+    if (!alloc.alloc(R.out_bytes, &off)) break;  // head of line waits for memory
+    R.pool_off = off;
+    R.out = pool + off;
+    R.state = shm::kActive;
+    R.t_admit = now_ms();
+    ++admitted;
+    ++slots_used;
+    active.push_back(queue.front());
+    queue.pop_front();
+    any = true;
+  }
+  return any;
+}
+
+bool shm_server::launch_locked() {
+  if (active.empty()) return false;
+  shm::Batch* b = nullptr;
+  int inflight = 0;
+  for (auto& x : batches) {
+    if (x.inflight) ++inflight;
+    else if (!b) b = &x;
+  }
+  if (!b) return false;
+  int64_t budget = cfg.batch_points;
+  int nch = 0;
+  long long tiles = 0;
+  const size_t na = active.size();
+  size_t visited = 0;
+  if (rr >= na) rr = 0;
+  size_t i = rr;
+  while (budget > 0 && nch < shm::kMaxChunksPerBatch && visited < na) {
+    shm::Request& R = reqs[active[i]];
+    const int64_t left = R.r.n - R.next_point;
+    if (left > 0) {
+      const int64_t take = std::min<int64_t>({left, cfg.chunk_points, budget});
+      shm::ServeChunk& c = b->host[nch++];
+      c.pts = R.r.points;
+      c.out = R.out;
+      c.seed = R.r.seed;
+      c.p0 = R.next_point;
+      c.tile0 = tiles;
+      c.n = (int)take;
+      c.lmax = R.r.lmax;
+      c.dtype = (int)R.r.dtype;
+      c.pad = 0;
+      tiles += (take + shm::kServeTPB - 1) / shm::kServeTPB;
+      R.next_point += take;
+      budget -= take;
+      b->parts.emplace_back(active[i], take);
+    }
+    ++visited;
+    i = (i + 1) % na;
+  }
+  rr = i;
+  // drop fully scheduled requests from the round robin (they stay admitted until done)
+  active.erase(std::remove_if(active.begin(), active.end(),
+                              [&](uint64_t t) { return reqs[t].next_point >= reqs[t].r.n; }),
+               active.end());
+  if (nch == 0) return false;
+  cudaError_t e = cudaMemcpyAsync(b->dev, b->host, sizeof(shm::ServeChunk) * nch, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->start, stream);
+  if (e == cudaSuccess) {
+    const long long grid_l = std::max(1LL, std::min<long long>(tiles, grid));
+    shm::k_serve<<<(unsigned)grid_l, shm::kServeTPB, (size_t)shm::kServeTPB * 101 * 8, stream>>>(b->dev, nch, tiles);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->end, stream);
+  if (e != cudaSuccess) {
+    thread_error = std::string("batch launch failed: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    b->failed = true;
+  }
+  b->inflight = true;
+  b->seq = batch_seq++;
+  ++nbatches;
+  return true;
+}
+
+void shm_server::run() {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lk(mu);
+  for (;;) {
+    bool progress = retire_locked();
+    if (!stop) progress |= admit_locked();  // after destroy starts, only admitted work drains
+    progress |= launch_locked();
+    bool inflight = false;
+    for (auto& b : batches) inflight |= b.inflight;
+    if (stop && !inflight && active.empty()) break;  // queued, unadmitted requests are dropped
+    if (!progress) {
+      if (inflight)
+        cv_work.wait_for(lk, std::chrono::microseconds(20));
+      else
+        cv_work.wait_for(lk, std::chrono::milliseconds(2));
+    }
+  }
+}
+
+extern "C" void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3]) {
+  shm::gen_point_host(seed, i, xyz);
+}
+
+extern "C" shm_status shm_serve_create(const shm_serve_config* cfg, shm_server** server) {
+  using namespace shm;
+  clear_error();
+  if (!cfg || !server) return fail(SHM_EINVAL, "null argument");
+  if (cfg->pool_bytes < 256 || cfg->max_slots < 1 || cfg->queue_capacity < 1 || cfg->batch_points < 1 ||
+      cfg->chunk_points < 1 || cfg->chunk_points > (1 << 30) || cfg->inflight_batches < 1 || cfg->inflight_batches > 8)
+    return fail(SHM_EINVAL, "bad serve config");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDeviceCount");
+  if (cfg->device < 0 || cfg->device >= ndev) return fail(SHM_EINVAL, "device ordinal out of range");
+  auto* S = new shm_server();
+  S->cfg = *cfg;
+  S->device = cfg->device;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(S->device);
+  auto cleanup = [&](shm_status st) {
+    for (auto& b : S->batches) {
+      if (b.start) cudaEventDestroy(b.start);
+      if (b.end) cudaEventDestroy(b.end);
+      if (b.host) cudaFreeHost(b.host);
+      if (b.dev) cudaFree(b.dev);
+    }
+    if (S->pool) cudaFree(S->pool);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+    cudaSetDevice(prev);
+    return st;
+  };
+  if ((e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cleanup(fail_cuda(e, "cudaStreamCreateWithFlags"));
+  if ((e = cudaMalloc(&S->pool, cfg->pool_bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(SHM_ENOMEM, "cannot allocate the serve pool of " + std::to_string(cfg->pool_bytes) + " bytes"));
+  }
+  S->alloc.init(cfg->pool_bytes);
+  S->batches.resize(cfg->inflight_batches);
+  for (auto& b : S->batches) {
+    if ((e = cudaEventCreate(&b.start)) != cudaSuccess || (e = cudaEventCreate(&b.end)) != cudaSuccess)
+      return cleanup(fail_cuda(e, "cudaEventCreate"));
+    if ((e = cudaHostAlloc(&b.host, sizeof(ServeChunk) * kMaxChunksPerBatch, cudaHostAllocDefault)) != cudaSuccess)
+      return cleanup(fail(SHM_ENOMEM, "cudaHostAlloc for batch descriptors failed"));
+    if ((e = cudaMalloc(&b.dev, sizeof(ServeChunk) * kMaxChunksPerBatch)) != cudaSuccess)
+      return cleanup(fail(SHM_ENOMEM, "cudaMalloc for batch descriptors failed"));
+  }
+  const size_t smem = (size_t)kServeTPB * 101 * 8;
+  if ((e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return cleanup(fail_cuda(e, "cudaFuncSetAttribute(k_serve)"));
+  int bps = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_serve, kServeTPB, smem)) != cudaSuccess)
+    return cleanup(fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_serve)"));
+  S->grid = sm_count(S->device) * std::max(bps, 1);
+  S->t0 = Clock::now();
+  cudaSetDevice(prev);
+  S->sched = std::thread([S] { S->run(); });
+  *server = S;
+  return SHM_OK;
+}
+
+extern "C" shm_status shm_serve_submit(shm_server* S, const shm_request* req, uint64_t* ticket) {
+  using namespace shm;
+  clear_error();
+  if (!S || !req || !ticket) return fail(SHM_EINVAL, "null argument");
+  if (req->n < 1) return fail(SHM_EINVAL, "n must be >= 1");
+  if (req->lmax < 0 || req->lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
+  if (req->dtype != SHM_F32 && req->dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (req->flags & ~SHM_REQ_DISCARD) return fail(SHM_EINVAL, "unknown request flags");
+  Request R;
+  R.r = *req;
+  R.es = req->dtype == SHM_F64 ? 8 : 4;
+  R.L2 = (size_t)(req->lmax + 1) * (req->lmax + 1);
+  if (req->n > (int64_t)1 << 40) return fail(SHM_EINVAL, "n too large");
+  R.out_bytes = round256((size_t)req->n * R.L2 * R.es);
+  if (R.out_bytes > S->cfg.pool_bytes) return fail(SHM_EINVAL, "request output can never fit the serve pool");
+  if (req->points) {
+    if (!aligned(req->points, R.es)) return fail(SHM_EINVAL, "points must be aligned to the element size");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != S->device) cudaSetDevice(S->device);
+    const shm_status st = check_device_range(req->points, (size_t)req->n * 3 * R.es, "points");
+    if (prev != S->device) cudaSetDevice(prev);
+    if (st != SHM_OK) return st;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    ++S->submitted;
+    if ((int)S->queue.size() >= S->cfg.queue_capacity) {
+      ++S->rejected;
+      return fail(SHM_EBUSY, "serve queue full");
+    }
+    R.t_submit = S->now_ms();
+    const uint64_t t = S->next_ticket++;
+    S->reqs.emplace(t, R);
+    S->queue.push_back(t);
+    *ticket = t;
+  }
+  S->cv_work.notify_one();
+  return SHM_OK;
+}
+
+static void fill_result(const shm::Request& R, shm_result* res) {
+  res->status = R.state != shm::kDone ? SHM_ETIMEOUT : (R.failed ? SHM_ECUDA : SHM_OK);
+  res->out = (R.r.flags & SHM_REQ_DISCARD) ? nullptr : R.out;
+  res->n = R.r.n;
+  res->lmax = R.r.lmax;
+  res->dtype = R.r.dtype;
+  res->t_submit_ms = R.t_submit;
+  res->t_admit_ms = R.t_admit;
+  res->t_done_ms = R.t_done;
+}
+
+extern "C" shm_status shm_serve_wait(shm_server* S, uint64_t ticket, int timeout_ms, shm_result* res) {
+  using namespace shm;
+  clear_error();
+  if (!S || !res) return fail(SHM_EINVAL, "null argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto done = [&] {
+    auto it = S->reqs.find(ticket);
+    return it == S->reqs.end() || it->second.state == kDone;
+  };
+  if (timeout_ms < 0)
+    S->cv_done.wait(lk, done);
+  else
+    S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return fail(SHM_ENOTFOUND, "unknown or released ticket");
+  fill_result(it->second, res);
+  if (it->second.state != kDone) return fail(SHM_ETIMEOUT, "request not complete");
+  if (it->second.failed) return fail(SHM_ECUDA, "a batch holding this request failed: " + S->thread_error);
+  return SHM_OK;
+}
+
+extern "C" shm_status shm_serve_release(shm_server* S, uint64_t ticket) {
+  using namespace shm;
+  clear_error();
+  if (!S) return fail(SHM_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return fail(SHM_ENOTFOUND, "unknown or released ticket");
+  if (it->second.state != kDone) return fail(SHM_EBUSY, "request not complete");
+  S->alloc.release(it->second.pool_off, it->second.out_bytes);
+  S->reqs.erase(it);
+  S->cv_work.notify_one();
+  return SHM_OK;
+}
+
+extern "C" shm_status shm_serve_stats_get(shm_server* S, shm_serve_stats* st) {
+  using namespace shm;
+  clear_error();
+  if (!S || !st) return fail(SHM_EINVAL, "null argument");
+  std::vector<double> lat;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    st->submitted = S->submitted;
+    st->rejected = S->rejected;
+    st->admitted = S->admitted;
+    st->completed = S->completed;
+    st->batches = S->nbatches;
+    st->queued_now = S->queue.size();
+    st->active_now = (uint64_t)S->slots_used;
+    st->harmonics_done = S->harmonics;
+    st->busy_ms = S->busy_ms;
+    st->pool_bytes = S->alloc.size;
+    st->pool_in_use = S->alloc.in_use;
+    st->pool_peak = S->alloc.peak;
+    lat = S->lat;
+    if (!S->thread_error.empty()) return fail(SHM_ECUDA, S->thread_error);
+  }
+  auto pct = [&](double q) {
+    if (lat.empty()) return 0.0;
+    const size_t k = std::min(lat.size() - 1, (size_t)(q * (double)(lat.size() - 1) + 0.5));
+    std::nth_element(lat.begin(), lat.begin() + k, lat.end());
+    return lat[k];
+  };
+  st->lat_p50_ms = pct(0.50);
+  st->lat_p99_ms = pct(0.99);
+  st->lat_max_ms = lat.empty() ? 0.0 : *std::max_element(lat.begin(), lat.end());
+  return SHM_OK;
+}
+
+extern "C" shm_status shm_serve_stats_reset(shm_server* S) {
+  using namespace shm;
+  clear_error();
+  if (!S) return fail(SHM_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->submitted = S->rejected = S->admitted = S->completed = S->nbatches = 0;
+  S->harmonics = S->busy_ms = 0;
+  S->lat.clear();
+  S->alloc.peak = S->alloc.in_use;
+  return SHM_OK;
+}
+
+extern "C" shm_status shm_serve_destroy(shm_server* S) {
+  using namespace shm;
+  clear_error();
+  if (!S) return fail(SHM_EINVAL, "null server");
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->sched.joinable()) S->sched.join();
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(S->device);
+  cudaStreamSynchronize(S->stream);
+  for (auto& b : S->batches) {
+    cudaEventDestroy(b.start);
+    cudaEventDestroy(b.end);
+    cudaFreeHost(b.host);
+    cudaFree(b.dev);
+  }
+  cudaFree(S->pool);
+  cudaStreamDestroy(S->stream);
+  cudaGetLastError();
+  cudaSetDevice(prev);
+  delete S;
+  return SHM_OK;
+}
