@@ -144,6 +144,99 @@ __device__ __forceinline__ void sh_row(double xb, double yb, double zb, Store&& 
   }
 }
 
+// FP64 row in l-major order: same arithmetic as sh_row<LMAX>(double...) (the
+// same operations on the same operands, so bit-identical results), but the
+// values come out l by l: all (x+iy)^m first, then for each l the next step of
+// every m-recurrence.  The l-shells are grouped into phases of at most
+// PHMAX values; phase(k0, width) is called after each group so the caller can
+// stage and flush it.  store(k - k0, v) writes within the current phase.
+template <int LMAX>
+struct LPhases {
+  // phase p covers l in [first[p], first[p+1])
+  static constexpr int PHMAX = 37;
+  static constexpr int count() {
+    int n = 0, w = 0;
+    for (int l = 0; l <= LMAX; ++l) {
+      const int wl = 2 * l + 1;
+      if (w > 0 && w + wl > PHMAX) {
+        ++n;
+        w = 0;
+      }
+      w += wl;
+    }
+    return n + 1;
+  }
+  static constexpr bool ends_phase(int l) {  // true if l is the last shell of its phase
+    if (l == LMAX) return true;
+    int w = 0;
+    for (int ll = 0; ll <= l; ++ll) {
+      const int wl = 2 * ll + 1;
+      if (w > 0 && w + wl > PHMAX) w = 0;
+      w += wl;
+    }
+    return w + 2 * (l + 1) + 1 > PHMAX;
+  }
+  static constexpr int max_width() {
+    int w = 0, mx = 0;
+    for (int l = 0; l <= LMAX; ++l) {
+      const int wl = 2 * l + 1;
+      if (w > 0 && w + wl > PHMAX) w = 0;
+      w += wl;
+      mx = w > mx ? w : mx;
+    }
+    return mx;
+  }
+};
+
+template <int LMAX, typename Store, typename Phase>
+__device__ __forceinline__ void sh_row_lmajor(double xb, double yb, double zb, Store&& store, Phase&& phase) {
+  double A[LMAX + 1], B[LMAX + 1], q1[LMAX + 1], q2[LMAX + 1];
+  A[0] = 1.0;
+  B[0] = 0.0;
+  if constexpr (LMAX >= 1) {
+    A[1] = xb;
+    B[1] = yb;
+  }
+#pragma unroll
+  for (int m = 2; m <= LMAX; ++m) {
+    A[m] = fma(A[m - 1], xb, -B[m - 1] * yb);
+    B[m] = fma(A[m - 1], yb, B[m - 1] * xb);
+  }
+  int k0 = 0;
+#pragma unroll
+  for (int l = 0; l <= LMAX; ++l) {
+#pragma unroll
+    for (int m = 0; m <= l; ++m) {
+      double s;
+      if (l == m) {
+        s = SHM_S[l][m];
+        q2[m] = 1.0;
+        q1[m] = 1.0;  // Qh_m^m
+      } else if (l == m + 1) {
+        s = SHM_S[l][m] * zb;
+        q2[m] = 1.0;
+        q1[m] = zb;
+      } else {
+        const double q = fma(zb, q1[m], -SHM_G[l][m] * q2[m]);
+        s = SHM_S[l][m] * q;
+        q2[m] = q1[m];
+        q1[m] = q;
+      }
+      const int k = l * l + l;
+      if (m == 0) {
+        store(k - k0, s);
+      } else {
+        store(k + m - k0, (l == m) ? SHM_S[l][m] * A[m] : s * A[m]);
+        store(k - m - k0, (l == m) ? SHM_S[l][m] * B[m] : s * B[m]);
+      }
+    }
+    if (LPhases<LMAX>::ends_phase(l)) {
+      phase(k0, (l + 1) * (l + 1) - k0);
+      k0 = (l + 1) * (l + 1);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Float-float (unevaluated sum hi + lo) helpers for the FP32 path.  The
 // error-free transformations use the _rn intrinsics so that the compiler

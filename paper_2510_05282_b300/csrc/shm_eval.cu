@@ -62,11 +62,69 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
   }
 }
 
+// kPhased (FP64): l-major evaluation (sh_row_lmajor) staged one phase of
+// l-shells at a time (<= 37 values per row), so a tile needs ~1/3 of the
+// shared memory of a full-row tile and ~2.5x more warps fit on an SM; every
+// l-step advances up to 10 independent m-recurrences, which feeds the FP64
+// pipe with independent work.  Rows are written phase by phase (one
+// contiguous segment of each row per phase).  Results are bit-identical to
+// the other variants.  For FP32 this variant is the staged path.
+enum { kPhased = 2 };
+
+template <int LMAX, int TPB>
+__global__ void __launch_bounds__(TPB) k_eval_phased(const double* __restrict__ pts, int64_t n,
+                                                     double* __restrict__ out, int64_t ntiles, int normalized) {
+  constexpr int L2 = NH<LMAX>::value;
+  constexpr int RS = LPhases<LMAX>::max_width() | 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* tile = reinterpret_cast<double*>(smem_raw);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * TPB;
+    const int rows = (int)min((int64_t)TPB, n - p0);
+    const bool valid = (int)threadIdx.x < rows;
+    double x = 0.0, y = 0.0, z = 1.0;
+    if (valid) {
+      const int64_t p = p0 + threadIdx.x;
+      x = pts[3 * p];
+      y = pts[3 * p + 1];
+      z = pts[3 * p + 2];
+    }
+    const bool origin = valid && is_origin(x, y, z);
+    double xb = 0.0, yb = 0.0, zb = 1.0;
+    if (valid && !origin) {
+      if (normalized) {
+        xb = x;
+        yb = y;
+        zb = z;
+      } else {
+        unit_dir(x, y, z, xb, yb, zb);
+      }
+    }
+    double* row = tile + threadIdx.x * RS;
+    sh_row_lmajor<LMAX>(
+        xb, yb, zb, [&](int kk, double v) { row[kk] = v; },
+        [&](int k0, int w) {
+          if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
+            for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
+          }
+          __syncthreads();
+          const int nv = rows * w;
+          for (int j = threadIdx.x; j < nv; j += TPB) {
+            const int r = j / w;
+            const int c = j - r * w;
+            __stcs(out + (p0 + r) * L2 + k0 + c, tile[r * RS + c]);
+          }
+          __syncthreads();
+        });
+  }
+}
+
 // Launch variants the tuner chooses among (index = variant id).
 struct Variant {
   int path, tpb;
 };
-constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64}, {kStaged, 256}, {kDirect, 128}, {kDirect, 256}};
+constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},
+                                 {kDirect, 128}, {kDirect, 256}, {kPhased, 64}, {kPhased, 128}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // Default choice before (or without) tuning: staged 128 (the FP32 path is
@@ -78,7 +136,17 @@ int g_choice[2][SHM_LMAX_CAP + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1}, {
 
 template <typename T, int LMAX, int TPB, int PATH>
 size_t eval_smem_bytes() {
+  if (PATH == kPhased) return (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * sizeof(double);
   return PATH == kStaged ? (size_t)TPB * TileShape<LMAX>::RS * sizeof(T) : 0;
+}
+
+template <typename T, int LMAX, int TPB, int PATH>
+auto pick_kernel() {
+  if constexpr (PATH == kPhased && sizeof(T) == 8) {
+    return k_eval_phased<LMAX, TPB>;
+  } else {
+    return k_eval<T, LMAX, TPB, PATH == kPhased ? kStaged : PATH>;
+  }
 }
 
 // Per-device launch set-up of one instantiation (shared-memory opt-in and
@@ -87,8 +155,13 @@ template <typename T, int LMAX, int TPB, int PATH>
 shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t stream) {
   constexpr int MAXDEV = 64;
   static int blocks_per_sm[MAXDEV] = {0};
+  if constexpr (PATH == kPhased) {
+    if constexpr (sizeof(T) == 4) {
+      return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, stream);
+    }
+  }
   const int dev = current_device();
-  auto kern = k_eval<T, LMAX, TPB, PATH>;
+  auto kern = pick_kernel<T, LMAX, TPB, PATH>();
   const size_t smem = eval_smem_bytes<T, LMAX, TPB, PATH>();
   if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
   if (blocks_per_sm[dev] == 0) {
@@ -101,7 +174,10 @@ shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool 
   }
   const int64_t ntiles = (n + TPB - 1) / TPB;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * blocks_per_sm[dev]);
-  kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0, vec ? 1 : 0);
+  if constexpr (PATH == kPhased && sizeof(T) == 8)
+    kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0);
+  else
+    kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0, vec ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_eval launch");
   return SHM_OK;
@@ -119,6 +195,8 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
     case 2: return eval_launch_v<T, LMAX, 256, kStaged>(pts, n, out, normalized, vec, s);
     case 3: return eval_launch_v<T, LMAX, 128, kDirect>(pts, n, out, normalized, vec, s);
     case 4: return eval_launch_v<T, LMAX, 256, kDirect>(pts, n, out, normalized, vec, s);
+    case 5: return eval_launch_v<T, LMAX, 64, kPhased>(pts, n, out, normalized, vec, s);
+    case 6: return eval_launch_v<T, LMAX, 128, kPhased>(pts, n, out, normalized, vec, s);
   }
   return fail(SHM_EINVAL, "unknown launch variant");
 }
@@ -284,7 +362,8 @@ extern "C" shm_status shm_eval_host(const void* points_host, int64_t n, int lmax
 namespace shm {
 namespace {
 
-const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64", "staged-256", "direct-128", "direct-256"};
+const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64",  "staged-256", "direct-128",
+                                           "direct-256", "phased-64", "phased-128"};
 
 std::mutex g_tune_mu;
 bool g_cache_loaded = false;

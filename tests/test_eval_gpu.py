@@ -160,6 +160,23 @@ def test_every_launch_variant(oracle_mod, dtype, lmax):
         shm.set_eval_variant(lmax, dtype, -1)
 
 
+@pytest.mark.parametrize("lmax", [1, 6, 9])
+def test_fp64_variants_are_bitwise_identical(lmax):
+    """Every FP64 launch variant runs the same operations on the same operands."""
+    pts = np.concatenate([inputs.random_sphere_points(5001, stream="tests"), inputs.edge_points()])
+    p = torch.from_numpy(pts).cuda()
+    outs = []
+    try:
+        for v in range(shm.eval_variant_count()):
+            shm.set_eval_variant(lmax, torch.float64, v)
+            outs.append(shm.eval_sh(p, lmax).clone())
+    finally:
+        shm.set_eval_variant(lmax, torch.float64, -1)
+    torch.cuda.synchronize()
+    for v, o in enumerate(outs[1:], start=1):
+        assert torch.equal(torch.nan_to_num(o, nan=7.0), torch.nan_to_num(outs[0], nan=7.0)), v
+
+
 def test_autotune_keeps_results_correct(oracle_mod):
     ms = shm.autotune(9, torch.float64, 1 << 16)
     assert ms > 0 and shm.eval_variant(9, torch.float64)
