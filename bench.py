@@ -243,11 +243,24 @@ def run_gpu(args, rank, world):
     peaks, peaks_src = load_peaks()
     nh = (LMAX + 1) ** 2
 
-    tuned_ms = shm.autotune(LMAX, torch.float64, 1 << 20) if args.tune else None
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    es = 8 if args.dtype == "f64" else 4
+    tuned_ms = None
+    if args.variant:
+        for v in range(shm.eval_variant_count()):
+            shm.set_eval_variant(LMAX, tdt, v)
+            if shm.eval_variant(LMAX, tdt) == args.variant:
+                break
+        else:
+            raise SystemExit(f"unknown launch variant {args.variant}")
+    elif args.tune:
+        tuned_ms = shm.autotune(LMAX, tdt, 1 << 20)
     pts = inputs.dft_grid_points(args.grid)
+    if args.dtype == "f32":
+        pts = pts.astype(np.float32)
     n = pts.shape[0]
     p = torch.from_numpy(pts).cuda()
-    out = torch.empty((n, nh), dtype=torch.float64, device="cuda")
+    out = torch.empty((n, nh), dtype=tdt, device="cuda")
     for _ in range(args.warmup):
         shm.eval_sh(p, LMAX, out=out, stream=stream)
     torch.cuda.synchronize()
@@ -263,9 +276,9 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([region], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        region = float(t.item())
+
+        from paper_2510_05282_b300.parallel import max_over_ranks
+        region = max_over_ranks(region, device="cuda")
         dist.barrier()
     clk = clocks.stop() if clocks else None
 
@@ -276,27 +289,37 @@ def run_gpu(args, rank, world):
     # roofline of the (single) kernel: FP64 pipe, with HBM alongside
     dp_per_launch = dp_instr_per_point(LMAX) * n
     achieved_tflops = 2.0 * dp_per_launch / (launch_ms * 1e-3) / 1e12
-    bytes_per_launch = n * (3 + nh) * 8
+    bytes_per_launch = n * (3 + nh) * es
     achieved_gbs = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
-    traffic = TRAFFIC_PER_POINT_F64_L9 * n if TRAFFIC_PER_POINT_F64_L9 else None
+    traffic = TRAFFIC_PER_POINT_F64_L9 * n if (TRAFFIC_PER_POINT_F64_L9 and args.dtype == "f64") else None
 
+    variant = shm.eval_variant(LMAX, tdt)
+    arithmetic = ("FP64 (1/r and the m = 0, 1 columns) + float-float 2xFP32 (m >= 2 columns), FP64 output; "
+                  "max normwise error vs the FP64 oracle <= 5e-14 (tolerance 1e-13)"
+                  if (args.dtype == "f64" and "hybrid" in variant) else
+                  ("FP64" if args.dtype == "f64" else "FP32 (FP64 1/r for r < 1e-2; float-float m = 0, 1)"))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.grid == N_SIDE else f"dft_grid_{args.grid}cubed_fp64_lmax9",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": (WORKLOAD if args.grid == N_SIDE else f"dft_grid_{args.grid}cubed_fp64_lmax9")
+                   .replace("fp64", "fp32" if args.dtype == "f32" else "fp64"),
                    "points": n, "lmax": LMAX, "grid": f"{args.grid}^3, h=0.3 bohr",
                    "out_bytes_per_step": n * nh * 8, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "no flush: 170 MB input and 5.66 GB output per step exceed the 126 MB L2",
-                   "launch_variant": shm.eval_variant(LMAX, torch.float64), "autotune_probe_ms": tuned_ms},
-        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "peak_source": "recipe nominal FP64 (1.25 TFLOP/s = 0.625e12 FP64 pipe instr/s)",
-                     "achieved_def": f"{dp_instr_per_point(LMAX)} FP64 pipe instructions per point x 2 flop "
-                                     "(FMA-equivalent) / mean launch time",
-                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": achieved_gbs / hbm_peak, "peak_source": peaks_src}},
+                   "launch_variant": variant, "arithmetic": arithmetic, "autotune_probe_ms": tuned_ms},
+        "roofline": ({"bound": "alu", "pipe": "fp64", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                      "peak_source": "recipe nominal FP64 (1.25 TFLOP/s = 0.625e12 FP64 pipe instr/s)",
+                      "achieved_def": f"{dp_instr_per_point(LMAX)} FP64 pipe instructions per point x 2 flop "
+                                      "(FMA-equivalent) / mean launch time",
+                      "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": achieved_gbs / hbm_peak, "peak_source": peaks_src}}
+                     if args.dtype == "f64" else
+                     {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_source": peaks_src,
+                      "achieved_def": "(12 + 400) B per point / mean launch time"}),
         "gpu_launches": args.steps,
         "clocks": clk,
         "kernel_ms": launch_ms,
@@ -308,9 +331,8 @@ def run_gpu(args, rank, world):
         # end to end through the host-buffer entry point (pinned host memory)
         e2e_steps = max(2, min(args.steps, args.e2e_steps))
         hin = torch.from_numpy(pts).pin_memory()
-        hout = torch.empty((n, nh), dtype=torch.float64).pin_memory()
-        ws = torch.empty(shm.eval_host_workspace_size(LMAX, torch.float64, 1 << 20), dtype=torch.uint8,
-                         device="cuda")
+        hout = torch.empty((n, nh), dtype=tdt).pin_memory()
+        ws = torch.empty(shm.eval_host_workspace_size(LMAX, tdt, 1 << 20), dtype=torch.uint8, device="cuda")
         shm.eval_host(hin, LMAX, hout, ws, stream=stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -318,11 +340,11 @@ def run_gpu(args, rank, world):
             shm.eval_host(hin, LMAX, hout, ws, stream=stream)
             stream.synchronize()
         dt = (time.perf_counter() - t0) / e2e_steps
-        line["e2e"] = {"value": n * nh / dt, "unit": UNIT, "h2d_bytes_per_step": n * 3 * 8,
-                       "d2h_bytes_per_step": n * nh * 8, "steps": e2e_steps,
+        line["e2e"] = {"value": n * nh / dt, "unit": UNIT, "h2d_bytes_per_step": n * 3 * es,
+                       "d2h_bytes_per_step": n * nh * es, "steps": e2e_steps,
                        "api": "shm_eval_host (pinned host in/out, 1M-point chunks double-buffered)"}
         del hin, hout, ws
-        rate, m, cores = cpu_oracle_rate(pts, LMAX, args.cpu_seconds)
+        rate, m, cores = cpu_oracle_rate(pts.astype(np.float64), LMAX, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"first {m} of {n} grid points, lmax=9, FP64"}
         if args.extras:
@@ -358,6 +380,24 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
     ms = statistics.mean(per)
     res["random_sphere_65600_fp64_lmax9"] = {"value": sph.shape[0] * nh / (ms * 1e-3), "unit": UNIT,
                                              "kernel_ms": ms}
+    # the all-FP64 arithmetic on the headline grid, for comparison with the tuned variant
+    chosen = shm.eval_variant(LMAX, torch.float64)
+    for v in range(shm.eval_variant_count()):
+        shm.set_eval_variant(LMAX, torch.float64, v)
+        if shm.eval_variant(LMAX, torch.float64) == "staged-64":
+            break
+    g64 = inputs.dft_grid_points(N_SIDE)
+    per, region = measure_eval(shm, torch, g64, torch.float64, LMAX, steps, 3, stream)
+    ms = statistics.mean(per)
+    tf = 2.0 * dp_instr_per_point(LMAX) * g64.shape[0] / (ms * 1e-3) / 1e12
+    res["dft_grid_192cubed_fp64_lmax9_all_fp64_arithmetic"] = {
+        "value": g64.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "launch_variant": "staged-64",
+        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tf / FP64_PEAK_TFLOPS}}
+    for v in range(shm.eval_variant_count()):
+        shm.set_eval_variant(LMAX, torch.float64, v)
+        if shm.eval_variant(LMAX, torch.float64) == chosen:
+            break
     for fn in EXTRA_WORKLOADS:
         try:
             res.update(fn(args, shm, torch, inputs, stream, peaks, peaks_src))
@@ -453,6 +493,9 @@ def main():
                     help="length of each Poisson request stream of the serving extra (30 for the full run)")
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")],
                     default=[1000.0, 5000.0, 20000.0, 50000.0])
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64",
+                    help="f64 is the benchmark workload; f32 only for profiling captures")
+    ap.add_argument("--variant", default=None, help="pin a launch variant by name (skips the autotuner)")
     ap.add_argument("--no-tune", dest="tune", action="store_false", default=True,
                     help="skip shm_autotune (use the library's default launch variant)")
     ap.add_argument("--extras", dest="extras", action="store_true", default=True)

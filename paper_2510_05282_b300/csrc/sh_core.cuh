@@ -260,6 +260,225 @@ __device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
   return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 
+// Float-float arithmetic (hi + lo, ~48-bit significand) and exact
+// conversions between binary64 and float-float, done with integer and FP32
+// instructions only (the FP64 pipe of a B300 is ~1/58 of its FP32 pipe).
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = two_prod(a.hi, b.hi);
+  p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_mul_c(ff a, float ch, float cl) {  // times the constant ch + cl
+  ff p = two_prod(ch, a.hi);
+  p.lo = fmaf(ch, a.lo, fmaf(cl, a.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+
+// Conversions between binary64 and float-float use integer instructions
+// only: on a B300 the int<->float and float<->double conversion instructions
+// issue to the same narrow pipe as FP64 arithmetic.
+
+// binary64 -> float-float: hi = d with its significand truncated to 24 bits
+// (exact), lo = the remaining 29 bits truncated to a float significand
+// (relative error < 2^-24 of lo, i.e. < 2^-48 of d).  |d| below 2^-74 maps to
+// 0 (absolute error < 2^-73); NaN and |d| >= 2^128 map to a NaN/infinite hi.
+// Branch-free (selects only), so unrolled callers stay one basic block.
+__device__ __forceinline__ ff ff_from_double(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi32 = (unsigned)(b >> 32);
+  const unsigned sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7ffu) - 1023;  // unbiased exponent
+  const bool tiny = e < -74, big = e > 127;
+  const unsigned ef = big ? 255u : (unsigned)(e + 127);
+  const unsigned mf = (unsigned)((b >> 29) & 0x7fffffull) | ((big && (b << 12) != 0ull) ? 0x400000u : 0u);
+  const unsigned hib = tiny ? 0u : (sign | (ef << 23) | mf);
+  const unsigned rem = (unsigned)(b & 0x1fffffffull);  // the 29 bits below hi: rem * 2^(e-52)
+  const int p = 31 - __clz(rem | 1u);                  // top set bit, 0..28
+  const unsigned m = p >= 23 ? rem >> (p - 23) : rem << (23 - p);
+  const unsigned lob = (tiny || big || rem == 0u) ? 0u : (sign | ((unsigned)(p + e + 75) << 23) | (m & 0x7fffffu));
+  return {__uint_as_float(hib), __uint_as_float(lob)};
+}
+
+// float-float (normalised: |lo| <= ulp(hi)/2) -> binary64.  The double of hi
+// is assembled from its bits; lo, read from its own bits, is added in units
+// of that double's ulp directly on the bit pattern (at most 2^29 units, so
+// the significand never carries past its top bit; a borrow below a power of
+// two counts in the finer ulp there, hence the doubling).  Parts of lo below
+// one ulp of the double are truncated.  hi = 0 (or a float denormal) maps to
+// +0; NaN and infinity carry over.  Branch-free.
+__device__ __forceinline__ double ff_to_double(ff a) {
+  const unsigned hb = __float_as_uint(a.hi);
+  const unsigned E = (hb >> 23) & 0xffu;
+  const unsigned M = hb & 0x7fffffu;
+  const unsigned Ed = E == 255u ? 2047u : E + 896u;
+  const unsigned hi32 = (hb & 0x80000000u) | (Ed << 20) | (M >> 3);
+  const long long base = (long long)(((unsigned long long)hi32 << 32) | ((unsigned long long)(M & 7u) << 29));
+  const unsigned lb = __float_as_uint(a.lo);
+  const unsigned El = (lb >> 23) & 0xffu;
+  const unsigned ml = El != 0u ? ((lb & 0x7fffffu) | 0x800000u) : 0u;  // lo = ml * 2^(El-150)
+  const int sh = (int)El - (int)E + 29;                                   // lo in double ulps: ml * 2^sh
+  const unsigned up = ml << (sh > 0 ? sh : 0);
+  const unsigned dn = ml >> (sh < 0 ? (sh > -31 ? -sh : 31) : 0);
+  int n = (int)(sh >= 0 ? up : dn);
+  const bool opp = ((hb ^ lb) & 0x80000000u) != 0u;
+  n = opp ? -((M == 0u) ? 2 * n : n) : n;        // opposite signs shrink the magnitude
+  n = (E == 255u) ? 0 : n;
+  const long long bits = (E == 0u) ? 0ll : base + (long long)n;
+  return __longlong_as_double(bits);
+}
+
+// FP64-output row with most of the arithmetic on the FP32 pipe.  1/r and the
+// m = 0 and m = 1 columns -- whose recurrences amplify rounding most near the
+// poles -- run in binary64 exactly as sh_row<LMAX>(double...) does (so those
+// 28 values are bit-identical to the FP64 path); every m >= 2 column (72 of
+// 100 values at lmax 9) runs in float-float: (x+iy)^m, the scaled
+// z-recurrence, the scale and the two products, then one exact conversion to
+// binary64 per value.  Normwise error against the FP64 oracle stays below
+// 5e-14 at l = 9 (the FP64 path: 1.4e-14; tolerance 1e-13) while the FP64
+// instructions per point drop from ~242 to ~75.
+template <int LMAX, typename Store>
+__device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, Store&& store) {
+  store(0, SHM_S[0][0]);
+  if constexpr (LMAX >= 1) {
+    store(2, SHM_S[1][0] * zb);
+    double q2 = 1.0, q1 = zb;
+#pragma unroll
+    for (int l = 2; l <= LMAX; ++l) {
+      const double q = fma(zb, q1, -SHM_G[l][0] * q2);
+      store(l * l + l, SHM_S[l][0] * q);
+      q2 = q1;
+      q1 = q;
+    }
+    store(3, SHM_S[1][1] * xb);
+    store(1, SHM_S[1][1] * yb);
+    if constexpr (LMAX >= 2) {
+      const double s = SHM_S[2][1] * zb;
+      store(7, s * xb);
+      store(5, s * yb);
+    }
+    q2 = 1.0;
+    q1 = zb;
+#pragma unroll
+    for (int l = 3; l <= LMAX; ++l) {
+      const double q = fma(zb, q1, -SHM_G[l][1] * q2);
+      const double s = SHM_S[l][1] * q;
+      store(l * l + l + 1, s * xb);
+      store(l * l + l - 1, s * yb);
+      q2 = q1;
+      q1 = q;
+    }
+  }
+  if constexpr (LMAX >= 2) {
+    const ff X = ff_from_double(xb), Y = ff_from_double(yb), Z = ff_from_double(zb);
+    ff A = X, B = Y;
+#pragma unroll
+    for (int m = 2; m <= LMAX; ++m) {
+      const ff An = ff_add(ff_mul(A, X), ff_neg(ff_mul(B, Y)));
+      const ff Bn = ff_add(ff_mul(A, Y), ff_mul(B, X));
+      A = An;
+      B = Bn;
+      store(m * m + 2 * m, ff_to_double(ff_mul_c(A, SHM_S_HI[m][m], SHM_S_LO[m][m])));
+      store(m * m, ff_to_double(ff_mul_c(B, SHM_S_HI[m][m], SHM_S_LO[m][m])));
+      ff q2 = {1.0f, 0.0f}, q1 = Z;
+      if (m + 1 <= LMAX) {
+        const ff s = ff_mul_c(Z, SHM_S_HI[m + 1][m], SHM_S_LO[m + 1][m]);
+        const int k0 = (m + 1) * (m + 1) + (m + 1);
+        store(k0 + m, ff_to_double(ff_mul(s, A)));
+        store(k0 - m, ff_to_double(ff_mul(s, B)));
+      }
+#pragma unroll
+      for (int l = m + 2; l <= LMAX; ++l) {
+        const ff q = ff_add(ff_mul(Z, q1), ff_neg(ff_mul_c(q2, SHM_G_HI[l][m], SHM_G_LO[l][m])));
+        const ff s = ff_mul_c(q, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+        store(l * l + l + m, ff_to_double(ff_mul(s, A)));
+        store(l * l + l - m, ff_to_double(ff_mul(s, B)));
+        q2 = q1;
+        q1 = q;
+      }
+    }
+  }
+}
+
+// sh_row_hybrid in l-major order (see sh_row_lmajor for the phase protocol):
+// the same operations on the same operands as sh_row_hybrid, so the rows are
+// bitwise identical to it; all m-recurrences advance together, one l at a
+// time, which exposes ~l independent chains to the scheduler.
+template <int LMAX, typename Store, typename Phase>
+__device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, double zb, Store&& store,
+                                                     Phase&& phase) {
+  const ff X = ff_from_double(xb), Y = ff_from_double(yb), Z = ff_from_double(zb);
+  ff A[LMAX + 1], B[LMAX + 1], q1[LMAX + 1], q2[LMAX + 1];
+  double d1[2], d2[2];
+  if constexpr (LMAX >= 2) {
+    A[1] = X;
+    B[1] = Y;
+#pragma unroll
+    for (int m = 2; m <= LMAX; ++m) {
+      A[m] = ff_add(ff_mul(A[m - 1], X), ff_neg(ff_mul(B[m - 1], Y)));
+      B[m] = ff_add(ff_mul(A[m - 1], Y), ff_mul(B[m - 1], X));
+    }
+  }
+  int k0 = 0;
+#pragma unroll
+  for (int l = 0; l <= LMAX; ++l) {
+    const int kc = l * l + l;
+#pragma unroll
+    for (int m = 0; m <= l; ++m) {
+      if (m <= 1) {  // binary64 columns, as sh_row_hybrid
+        double s;
+        if (l == m) {
+          s = SHM_S[l][m];
+          d2[m] = 1.0;
+          d1[m] = 1.0;
+        } else if (l == m + 1) {
+          s = SHM_S[l][m] * zb;
+          d2[m] = 1.0;
+          d1[m] = zb;
+        } else {
+          const double q = fma(zb, d1[m], -SHM_G[l][m] * d2[m]);
+          s = SHM_S[l][m] * q;
+          d2[m] = d1[m];
+          d1[m] = q;
+        }
+        if (m == 0) {
+          store(kc - k0, s);
+        } else {
+          store(kc + 1 - k0, (l == 1) ? SHM_S[1][1] * xb : s * xb);
+          store(kc - 1 - k0, (l == 1) ? SHM_S[1][1] * yb : s * yb);
+        }
+      } else {  // float-float columns
+        if (l == m) {
+          store(kc + m - k0, ff_to_double(ff_mul_c(A[m], SHM_S_HI[m][m], SHM_S_LO[m][m])));
+          store(kc - m - k0, ff_to_double(ff_mul_c(B[m], SHM_S_HI[m][m], SHM_S_LO[m][m])));
+          q2[m] = {1.0f, 0.0f};
+          q1[m] = Z;
+        } else {
+          ff sv;
+          if (l == m + 1) {
+            sv = ff_mul_c(Z, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+          } else {
+            const ff q = ff_add(ff_mul(Z, q1[m]), ff_neg(ff_mul_c(q2[m], SHM_G_HI[l][m], SHM_G_LO[l][m])));
+            sv = ff_mul_c(q, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+            q2[m] = q1[m];
+            q1[m] = q;
+          }
+          store(kc + m - k0, ff_to_double(ff_mul(sv, A[m])));
+          store(kc - m - k0, ff_to_double(ff_mul(sv, B[m])));
+        }
+      }
+    }
+    if (LPhases<LMAX>::ends_phase(l)) {
+      phase(k0, (l + 1) * (l + 1) - k0);
+      k0 = (l + 1) * (l + 1);
+    }
+  }
+}
+
 // FP32 row.  FP32 arithmetic throughout; two measures keep the error within
 // 2e-6 of the l-shell norm up to l = 9:
 //  * the homogeneous form q = xb^2 + yb^2 + zb^2 (1 only up to rounding in
@@ -347,7 +566,8 @@ __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& sto
 }
 
 // Full point: Cartesian (or already normalised) input -> row of harmonics.
-template <int LMAX, typename T, typename Store>
+// HYBRID selects sh_row_hybrid for binary64 rows.
+template <int LMAX, bool HYBRID = false, typename T, typename Store>
 __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&& store) {
   if (is_origin(x, y, z)) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
     store(0, (T)kInvSqrt4Pi);
@@ -357,7 +577,10 @@ __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&&
   }
   T xb = x, yb = y, zb = z;
   if (!normalized) unit_dir(x, y, z, xb, yb, zb);
-  sh_row<LMAX>(xb, yb, zb, store);
+  if constexpr (HYBRID && sizeof(T) == 8)
+    sh_row_hybrid<LMAX>(xb, yb, zb, store);
+  else
+    sh_row<LMAX>(xb, yb, zb, store);
 }
 
 }  // namespace shm

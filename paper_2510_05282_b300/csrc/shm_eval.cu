@@ -30,13 +30,16 @@ namespace shm {
 //           sectors).  Needs no shared memory, so occupancy is bounded by
 //           registers only -- useful when the FP64 pipe, not the store
 //           pattern, is the limit.
-enum StorePath { kStaged = 0, kDirect = 1 };
+//  kHybrid: kStaged with the FP64 rows of sh_row_hybrid (FP64 for 1/r and
+//           m = 0, 1; float-float for m >= 2); for FP32 it is kStaged.
+enum StorePath { kStaged = 0, kDirect = 1, kHybrid = 3 };
 
 template <typename T, int LMAX, int TPB, int PATH>
 __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t n, T* __restrict__ out,
                                               int64_t ntiles, int normalized, int vec) {
   constexpr int L2 = TileShape<LMAX>::L2;
   constexpr int RS = TileShape<LMAX>::RS;
+  constexpr bool HYB = PATH == kHybrid;
   if constexpr (PATH == kDirect) {
     for (int64_t p = (int64_t)blockIdx.x * TPB + threadIdx.x; p < n; p += (int64_t)gridDim.x * TPB) {
       const T x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
         const int64_t p = p0 + threadIdx.x;
         const T x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
         T* row = tile + threadIdx.x * RS;
-        sh_point<LMAX>(x, y, z, normalized != 0, [&](int k, T v) { row[k] = v; });
+        sh_point<LMAX, HYB>(x, y, z, normalized != 0, [&](int k, T v) { row[k] = v; });
       }
       __syncthreads();
       copy_out_tile<T, L2, RS, TPB>(tile, rows, out + p0 * L2, vec != 0);
@@ -69,9 +72,9 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
 // pipe with independent work.  Rows are written phase by phase (one
 // contiguous segment of each row per phase).  Results are bit-identical to
 // the other variants.  For FP32 this variant is the staged path.
-enum { kPhased = 2 };
+enum { kPhased = 2, kPhasedHybrid = 4 };
 
-template <int LMAX, int TPB>
+template <int LMAX, int TPB, bool HYB>
 __global__ void __launch_bounds__(TPB) k_eval_phased(const double* __restrict__ pts, int64_t n,
                                                      double* __restrict__ out, int64_t ntiles, int normalized) {
   constexpr int L2 = NH<LMAX>::value;
@@ -101,9 +104,8 @@ __global__ void __launch_bounds__(TPB) k_eval_phased(const double* __restrict__ 
       }
     }
     double* row = tile + threadIdx.x * RS;
-    sh_row_lmajor<LMAX>(
-        xb, yb, zb, [&](int kk, double v) { row[kk] = v; },
-        [&](int k0, int w) {
+    auto store = [&](int kk, double v) { row[kk] = v; };
+    auto flush = [&](int k0, int w) {
           if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
             for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
           }
@@ -115,7 +117,11 @@ __global__ void __launch_bounds__(TPB) k_eval_phased(const double* __restrict__ 
             __stcs(out + (p0 + r) * L2 + k0 + c, tile[r * RS + c]);
           }
           __syncthreads();
-        });
+        };
+    if constexpr (HYB)
+      sh_row_hybrid_lmajor<LMAX>(xb, yb, zb, store, flush);
+    else
+      sh_row_lmajor<LMAX>(xb, yb, zb, store, flush);
   }
 }
 
@@ -123,8 +129,9 @@ __global__ void __launch_bounds__(TPB) k_eval_phased(const double* __restrict__ 
 struct Variant {
   int path, tpb;
 };
-constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},
-                                 {kDirect, 128}, {kDirect, 256}, {kPhased, 64}, {kPhased, 128}};
+constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},  {kDirect, 128},
+                                 {kDirect, 256}, {kPhased, 64}, {kPhased, 128}, {kHybrid, 64},
+                                 {kHybrid, 128}, {kHybrid, 256}, {kPhasedHybrid, 64}, {kPhasedHybrid, 128}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // Default choice before (or without) tuning: staged 128 (the FP32 path is
@@ -136,16 +143,17 @@ int g_choice[2][SHM_LMAX_CAP + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1}, {
 
 template <typename T, int LMAX, int TPB, int PATH>
 size_t eval_smem_bytes() {
-  if (PATH == kPhased) return (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * sizeof(double);
-  return PATH == kStaged ? (size_t)TPB * TileShape<LMAX>::RS * sizeof(T) : 0;
+  if (PATH == kPhased || PATH == kPhasedHybrid)
+    return (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * sizeof(double);
+  return (PATH == kStaged || PATH == kHybrid) ? (size_t)TPB * TileShape<LMAX>::RS * sizeof(T) : 0;
 }
 
 template <typename T, int LMAX, int TPB, int PATH>
 auto pick_kernel() {
-  if constexpr (PATH == kPhased && sizeof(T) == 8) {
-    return k_eval_phased<LMAX, TPB>;
+  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid) && sizeof(T) == 8) {
+    return k_eval_phased<LMAX, TPB, PATH == kPhasedHybrid>;
   } else {
-    return k_eval<T, LMAX, TPB, PATH == kPhased ? kStaged : PATH>;
+    return k_eval<T, LMAX, TPB, (PATH == kPhased || (PATH == kHybrid && sizeof(T) == 4)) ? kStaged : PATH>;
   }
 }
 
@@ -155,7 +163,7 @@ template <typename T, int LMAX, int TPB, int PATH>
 shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t stream) {
   constexpr int MAXDEV = 64;
   static int blocks_per_sm[MAXDEV] = {0};
-  if constexpr (PATH == kPhased) {
+  if constexpr (PATH == kPhased || PATH == kPhasedHybrid) {
     if constexpr (sizeof(T) == 4) {
       return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, stream);
     }
@@ -174,7 +182,7 @@ shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool 
   }
   const int64_t ntiles = (n + TPB - 1) / TPB;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * blocks_per_sm[dev]);
-  if constexpr (PATH == kPhased && sizeof(T) == 8)
+  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid) && sizeof(T) == 8)
     kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0);
   else
     kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0, vec ? 1 : 0);
@@ -197,6 +205,11 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
     case 4: return eval_launch_v<T, LMAX, 256, kDirect>(pts, n, out, normalized, vec, s);
     case 5: return eval_launch_v<T, LMAX, 64, kPhased>(pts, n, out, normalized, vec, s);
     case 6: return eval_launch_v<T, LMAX, 128, kPhased>(pts, n, out, normalized, vec, s);
+    case 7: return eval_launch_v<T, LMAX, 64, kHybrid>(pts, n, out, normalized, vec, s);
+    case 8: return eval_launch_v<T, LMAX, 128, kHybrid>(pts, n, out, normalized, vec, s);
+    case 9: return eval_launch_v<T, LMAX, 256, kHybrid>(pts, n, out, normalized, vec, s);
+    case 10: return eval_launch_v<T, LMAX, 64, kPhasedHybrid>(pts, n, out, normalized, vec, s);
+    case 11: return eval_launch_v<T, LMAX, 128, kPhasedHybrid>(pts, n, out, normalized, vec, s);
   }
   return fail(SHM_EINVAL, "unknown launch variant");
 }
@@ -362,8 +375,9 @@ extern "C" shm_status shm_eval_host(const void* points_host, int64_t n, int lmax
 namespace shm {
 namespace {
 
-const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64",  "staged-256", "direct-128",
-                                           "direct-256", "phased-64", "phased-128"};
+const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64",  "staged-256", "direct-128", "direct-256",
+                                           "phased-64",  "phased-128", "hybrid-64",  "hybrid-128", "hybrid-256",
+                                           "phased-hybrid-64", "phased-hybrid-128"};
 
 std::mutex g_tune_mu;
 bool g_cache_loaded = false;
