@@ -273,6 +273,18 @@ __device__ __forceinline__ ff ff_mul_c(ff a, float ch, float cl) {  // times the
   p.lo = fmaf(ch, a.lo, fmaf(cl, a.hi, p.lo));
   return fast_two_sum(p.hi, p.lo);
 }
+// Products left unnormalised (|lo| may reach ~ulp(hi)): for operands of a
+// following ff_add or ff_mul, which renormalise.
+__device__ __forceinline__ ff ff_mul_u(ff a, ff b) {
+  ff p = two_prod(a.hi, b.hi);
+  p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+  return p;
+}
+__device__ __forceinline__ ff ff_mul_c_u(ff a, float ch, float cl) {
+  ff p = two_prod(ch, a.hi);
+  p.lo = fmaf(ch, a.lo, fmaf(cl, a.hi, p.lo));
+  return p;
+}
 __device__ __forceinline__ ff ff_add(ff a, ff b) {
   const ff s = two_sum(a.hi, b.hi);
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
@@ -378,23 +390,23 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
     ff A = X, B = Y;
 #pragma unroll
     for (int m = 2; m <= LMAX; ++m) {
-      const ff An = ff_add(ff_mul(A, X), ff_neg(ff_mul(B, Y)));
-      const ff Bn = ff_add(ff_mul(A, Y), ff_mul(B, X));
+      const ff An = ff_add(ff_mul_u(A, X), ff_neg(ff_mul_u(B, Y)));
+      const ff Bn = ff_add(ff_mul_u(A, Y), ff_mul_u(B, X));
       A = An;
       B = Bn;
       store(m * m + 2 * m, ff_to_double(ff_mul_c(A, SHM_S_HI[m][m], SHM_S_LO[m][m])));
       store(m * m, ff_to_double(ff_mul_c(B, SHM_S_HI[m][m], SHM_S_LO[m][m])));
       ff q2 = {1.0f, 0.0f}, q1 = Z;
       if (m + 1 <= LMAX) {
-        const ff s = ff_mul_c(Z, SHM_S_HI[m + 1][m], SHM_S_LO[m + 1][m]);
+        const ff s = ff_mul_c_u(Z, SHM_S_HI[m + 1][m], SHM_S_LO[m + 1][m]);
         const int k0 = (m + 1) * (m + 1) + (m + 1);
         store(k0 + m, ff_to_double(ff_mul(s, A)));
         store(k0 - m, ff_to_double(ff_mul(s, B)));
       }
 #pragma unroll
       for (int l = m + 2; l <= LMAX; ++l) {
-        const ff q = ff_add(ff_mul(Z, q1), ff_neg(ff_mul_c(q2, SHM_G_HI[l][m], SHM_G_LO[l][m])));
-        const ff s = ff_mul_c(q, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+        const ff q = ff_add(ff_mul_u(Z, q1), ff_neg(ff_mul_c_u(q2, SHM_G_HI[l][m], SHM_G_LO[l][m])));
+        const ff s = ff_mul_c_u(q, SHM_S_HI[l][m], SHM_S_LO[l][m]);
         store(l * l + l + m, ff_to_double(ff_mul(s, A)));
         store(l * l + l - m, ff_to_double(ff_mul(s, B)));
         q2 = q1;
@@ -419,8 +431,8 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
     B[1] = Y;
 #pragma unroll
     for (int m = 2; m <= LMAX; ++m) {
-      A[m] = ff_add(ff_mul(A[m - 1], X), ff_neg(ff_mul(B[m - 1], Y)));
-      B[m] = ff_add(ff_mul(A[m - 1], Y), ff_mul(B[m - 1], X));
+      A[m] = ff_add(ff_mul_u(A[m - 1], X), ff_neg(ff_mul_u(B[m - 1], Y)));
+      B[m] = ff_add(ff_mul_u(A[m - 1], Y), ff_mul_u(B[m - 1], X));
     }
   }
   int k0 = 0;
@@ -460,10 +472,10 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
         } else {
           ff sv;
           if (l == m + 1) {
-            sv = ff_mul_c(Z, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+            sv = ff_mul_c_u(Z, SHM_S_HI[l][m], SHM_S_LO[l][m]);
           } else {
-            const ff q = ff_add(ff_mul(Z, q1[m]), ff_neg(ff_mul_c(q2[m], SHM_G_HI[l][m], SHM_G_LO[l][m])));
-            sv = ff_mul_c(q, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+            const ff q = ff_add(ff_mul_u(Z, q1[m]), ff_neg(ff_mul_c_u(q2[m], SHM_G_HI[l][m], SHM_G_LO[l][m])));
+            sv = ff_mul_c_u(q, SHM_S_HI[l][m], SHM_S_LO[l][m]);
             q2[m] = q1[m];
             q1[m] = q;
           }
