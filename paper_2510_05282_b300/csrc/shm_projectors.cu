@@ -37,11 +37,19 @@ constexpr int kExpLo = -160;  // FP32 log-grid exponent table covers frexpf expo
 constexpr int kExpHi = 140;
 constexpr int kExpN = kExpHi - kExpLo + 1;
 
+// An atom coordinate in grid units, q = pos / h = U + frac, frac in [0, 1)
+// held as the float-float fhi + flo (FP32 path).
+struct AtomF32 {
+  int U[3];
+  float fhi[3], flo[3];
+};
+
 // Workspace layout (byte offsets; every block 256-byte aligned).
 struct ProjWs {
   size_t counter = 0;      // unsigned long long work counter, uint32 error word at +8
   size_t tiles = 256;      // int64 tile_offsets[n_atoms + 1]
   size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
+  size_t atomf = 0;        // FP32: AtomF32[n_atoms] (atom coordinates in grid units)
   size_t rad32 = 0;        // FP32: float radial[n_species][lstride][n_rad]
   size_t total = 0;
 };
@@ -55,6 +63,8 @@ ProjWs proj_layout(const shm_proj_problem& p, shm_dtype dt) {
   if (dt == SHM_F32) {
     w.etab = end;
     end += round256((size_t)kExpN * 8);
+    w.atomf = end;
+    end += round256((size_t)p.n_atoms * sizeof(AtomF32));
     w.rad32 = end;
     end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 4);
   }
@@ -73,12 +83,15 @@ struct ProjParams {
   int32_t n_species, lstride, n_rad, ng;
   double r_min, dlog, box, h;
   signed char lmax[SHM_PROJ_MAX_SPECIES];
+  unsigned ng_magic;  // division by ng without division instructions (see div_ng)
+  int ng_shift;
   // workspace views
   unsigned long long* counter;
   unsigned* err;
   int64_t* tile_offsets;
   int2* etab;
   float* rad32;
+  AtomF32* atomf;
 };
 
 enum : unsigned { kErrOffsets = 1u, kErrSpecies = 2u, kErrGrid = 4u, kErrOut = 8u };
@@ -162,7 +175,64 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
     }
     const int64_t nt = (int64_t)P.n_species * P.lstride * P.n_rad;
     for (int64_t i = tid; i < nt; i += blockDim.x) P.rad32[i] = (float)P.radial[i];
+    for (int64_t a = tid; a < P.n_atoms; a += blockDim.x) {
+      AtomF32 A;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double q = P.atom_pos[3 * a + c] / P.h;  // atom coordinate in grid units
+        const double U = floor(q);
+        const double fr = q - U;
+        A.U[c] = (int)U;
+        A.fhi[c] = (float)fr;
+        A.flo[c] = (float)(fr - (double)A.fhi[c]);
+      }
+      P.atomf[a] = A;
+    }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Integer / float helpers without conversion instructions.  On a B300,
+// integer division, int<->float conversion and float rounding-to-int issue to
+// the same narrow pipe as FP64 arithmetic; these replacements use integer and
+// FP32 instructions only.
+
+// floor(n / ng) for 0 <= n < 2^31 (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, unsigned case: m and
+// l = ceil(log2 ng) precomputed on the host).
+__device__ __forceinline__ unsigned div_ng(unsigned n, unsigned magic, int shift) {
+  if (shift == 0) return n;  // ng = 1
+  const unsigned t1 = __umulhi(magic, n);
+  return (t1 + ((n - t1) >> 1)) >> (shift - 1);
+}
+
+// float <-> int for |v| < 2^22 through the 1.5 * 2^23 rounding constant.
+__device__ __forceinline__ float small_int_to_float(int n) {
+  return __int_as_float(0x4B400000 + n) - 12582912.0f;
+}
+__device__ __forceinline__ int floor_small(float v) {  // floor(v), |v| < 2^22
+  const float r = v + 12582912.0f;                     // round to nearest integer, biased
+  int n = __float_as_int(r) - 0x4B400000;
+  return (r - 12582912.0f > v) ? n - 1 : n;
+}
+
+// ln(m) for m in [0.5, 1) to ~7e-8 absolute: range-reduce to m' in
+// [1/sqrt2, sqrt2) (m' = 2m, e -= 1 below 1/sqrt2) and sum the atanh series
+// ln(m') = 2 atanh(z), z = (m' - 1)/(m' + 1), |z| <= 0.172, to z^11.
+__device__ __forceinline__ float log_unit(float m, int& e) {
+  if (m < 0.70710678f) {
+    m *= 2.0f;
+    e -= 1;
+  }
+  const float z = __fdividef(m - 1.0f, m + 1.0f);
+  const float z2 = z * z;
+  float p = 1.0f / 11.0f;
+  p = fmaf(p, z2, 1.0f / 9.0f);
+  p = fmaf(p, z2, 1.0f / 7.0f);
+  p = fmaf(p, z2, 1.0f / 5.0f);
+  p = fmaf(p, z2, 1.0f / 3.0f);
+  p = fmaf(p, z2, 1.0f);
+  return 2.0f * z * p;
 }
 
 // ---------------------------------------------------------------------------
@@ -182,7 +252,11 @@ __device__ __forceinline__ Lagrange4<T> lagrange_at(int it, T u, int n_rad) {
   Lagrange4<T> L;
   int i0 = it - 1;
   i0 = i0 < 0 ? 0 : (i0 > n_rad - 4 ? n_rad - 4 : i0);
-  const T x = (T)(it - i0) + u;  // t - i0, in [0, 3]
+  T x;  // t - i0, in [0, 3]
+  if constexpr (sizeof(T) == 4)
+    x = small_int_to_float(it - i0) + u;
+  else
+    x = (T)(it - i0) + u;
   const T x1 = x - (T)1, x2 = x - (T)2, x3 = x - (T)3;
   L.i0 = i0;
   L.w[0] = -(x1 * x2 * x3) * (T)(1.0 / 6.0);
@@ -248,7 +322,9 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
                                                int s, int lmax, double inv_box, double inv_rmin,
                                                double inv_dlog, double* row) {
   const int ng = P.ng;
-  const int gi = g / (ng * ng), gj = (g / ng) % ng, gk = g % ng;
+  const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
+  const int gi = (int)div_ng((unsigned)q1, P.ng_magic, P.ng_shift);
+  const int gj = q1 - gi * ng, gk = g - q1 * ng;
   double d[3] = {__dsub_rn(__dmul_rn((double)gi, P.h), ax), __dsub_rn(__dmul_rn((double)gj, P.h), ay),
                  __dsub_rn(__dmul_rn((double)gk, P.h), az)};
 #pragma unroll
@@ -272,22 +348,20 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
 // tile), then rounded once; the log-grid index uses the exponent table so
 // that only ln(mantissa) is taken in FP32 and t keeps ~1e-5 absolute accuracy
 // at t ~ 2000.
-struct AtomF32 {
-  int U[3];
-  float fhi[3], flo[3];
-};
-
 __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const AtomF32& A, int s, int lmax,
                                                float h, float inv_dlog, float* row) {
   const int ng = P.ng;
-  const int gi = g / (ng * ng), gj = (g / ng) % ng, gk = g % ng;
-  const int gg[3] = {gi, gj, gk};
+  const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
+  const int gi = (int)div_ng((unsigned)q1, P.ng_magic, P.ng_shift);
+  const int gg[3] = {gi, q1 - gi * ng, g - q1 * ng};
+  const float half_box = 0.5f * small_int_to_float(ng);
   float d[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    int n = gg[c] - A.U[c];  // minimum image in whole grid units: n - frac in [-ng/2, ng/2)
-    n -= ng * (int)floorf(((float)n - A.fhi[c]) / (float)ng + 0.5f);
-    const ff sdiff = two_sum((float)n, -A.fhi[c]);
+    int n = gg[c] - A.U[c];  // whole grid units; displacement n - frac, minimum image in [-ng/2, ng/2)
+    const float dn = small_int_to_float(n) - A.fhi[c];
+    n = dn >= half_box ? n - ng : (dn < -half_box ? n + ng : n);
+    const ff sdiff = two_sum(small_int_to_float(n), -A.fhi[c]);
     const float lo = __fsub_rn(sdiff.lo, A.flo[c]);
     const float v = __fadd_rn(sdiff.hi, lo);  // grid units, rounded once
     d[c] = v * h;
@@ -303,14 +377,17 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
     } else {
       r = sqrtf(r2);
     }
-    int e;
-    const float m = frexpf(r, &e);  // r = m 2^e, m in [0.5, 1)
+    // r = m 2^e with m in [0.5, 1), read from the bits (r is a normal float here)
+    const unsigned rb = __float_as_uint(r);
+    int e = (int)((rb >> 23) & 0xffu) - 126;
+    const float m = __uint_as_float((rb & 0x807fffffu) | (126u << 23));
+    const float lm = log_unit(m, e);
     const int ei = min(max(e - kExpLo, 0), kExpN - 1);
     const int2 E = P.etab[ei];
-    const float v = __int_as_float(E.y) + logf(m) * inv_dlog;
-    const float fl = floorf(v);
-    long long itl = (long long)E.x + (long long)fl;
-    u = v - fl;
+    const float v = __int_as_float(E.y) + lm * inv_dlog;  // |v| < 64
+    const int fl = floor_small(v);
+    u = v - small_int_to_float(fl);
+    long long itl = (long long)E.x + fl;
     if (itl < 0) {
       itl = 0;
       u = 0.0f;
@@ -328,58 +405,62 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
 // ---------------------------------------------------------------------------
 // Persistent main kernel.
 
+// Copies rows [0, rows) of a staged tile (row stride RS) to dst[rows * L2].
+// The row of element j is floor(j / L2) = umulhi(j, ceil(2^32 / L2)), exact
+// for j < 2^32 / L2^2 (here j < 128 * 100): no division instructions, which
+// on a B300 would issue conversions to the narrow FP64-class pipe.
 template <typename T>
 __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int rows, int L2, int RS,
                                               T* __restrict__ dst) {
   const int nv = rows * L2;
+  const unsigned inv = L2 > 1 ? (unsigned)((0x100000000ull + (unsigned)L2 - 1) / (unsigned)L2) : 0u;
   for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-    const int r = j / L2;
+    const int r = L2 > 1 ? (int)__umulhi((unsigned)j, inv) : j;
     __stcs(dst + j, tile[r * RS + (j - r * L2)]);
   }
 }
 
+// Atoms whose tile table a CTA keeps in shared memory (int32 entries); larger
+// problems search the table in global memory.
+constexpr int kSmemAtoms = 4096;
+
 template <typename T>
-__global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__ out) {
+__global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__ out, int tile_bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
-  __shared__ int64_t s_tile, s_atom;
-  __shared__ AtomF32 s_af;
+  int* tt = reinterpret_cast<int*>(smem_raw + tile_bytes);
+  __shared__ long long s_next;
   const double inv_box = 1.0 / P.box, inv_rmin = 1.0 / P.r_min, inv_dlog = 1.0 / P.dlog;
   // exact tile count, from the table the set-up kernel built earlier on this stream
   const int64_t total_tiles = P.tile_offsets[P.n_atoms];
+  const bool cached = P.n_atoms + 1 <= kSmemAtoms;
+  if (cached)
+    for (int i = threadIdx.x; i <= P.n_atoms; i += kProjTPB) tt[i] = (int)P.tile_offsets[i];
+  if (threadIdx.x == 0) s_next = (long long)atomicAdd(P.counter, 1ull);
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) {
-      const int64_t t = (int64_t)atomicAdd(P.counter, 1ull);
-      s_tile = t;
-      int64_t a = -1;
-      if (t < total_tiles) {  // last atom with tile_offsets[a] <= t
-        int64_t lo = 0, hi = P.n_atoms - 1;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi + 1) >> 1;
-          if (P.tile_offsets[mid] <= t) lo = mid;
-          else hi = mid - 1;
-        }
-        a = lo;
-        if constexpr (sizeof(T) == 4) {
-          const double pos[3] = {P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2]};
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const double q = pos[c] / P.h;  // atom coordinate in grid units
-            const double U = floor(q);
-            const double fr = q - U;
-            s_af.U[c] = (int)U;
-            s_af.fhi[c] = (float)fr;
-            s_af.flo[c] = (float)(fr - (double)s_af.fhi[c]);
-          }
-        }
-      }
-      s_atom = a;
-    }
-    __syncthreads();
-    const int64_t t = s_tile, a = s_atom;
+    const int64_t t = s_next;
     if (t >= total_tiles) break;
+    __syncthreads();  // every thread has read s_next
+    if (threadIdx.x == 0) s_next = (long long)atomicAdd(P.counter, 1ull);  // next tile, fetched early
+    // owning atom: the last a with tile_offsets[a] <= t
+    int64_t lo = 0, hi = P.n_atoms - 1;
+    if (cached) {
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)tt[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+    } else {
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (P.tile_offsets[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+    }
+    const int64_t a = lo;
     const int64_t pa0 = P.point_offsets[a], pa1 = P.point_offsets[a + 1];
-    const int64_t c = t - P.tile_offsets[a];
+    const int64_t c = t - (cached ? (int64_t)tt[a] : P.tile_offsets[a]);
     const int64_t p0 = pa0 + c * kProjTPB;
     const int rows = (int)min((int64_t)kProjTPB, pa1 - p0);
     const int s = P.atom_species[a];
@@ -398,12 +479,12 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
         proj_point_f64(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
                        inv_rmin, inv_dlog, reinterpret_cast<double*>(row));
       } else {
-        proj_point_f32(P, g, s_af, s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
+        proj_point_f32(P, g, P.atomf[a], s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
       }
     }
     __syncthreads();
     copy_rows_out<T>(tile, rows, L2, RS, out + o0);
-    __syncthreads();
+    __syncthreads();  // the tile buffer is free and s_next holds the next tile
   }
 }
 
@@ -414,19 +495,28 @@ shm_status launch_proj(const ProjParams& P, int max_lmax, T* out, int64_t tile_u
   const int dev = current_device();
   if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
   const int RS = ((max_lmax + 1) * (max_lmax + 1)) | 1;
-  const size_t smem = (size_t)kProjTPB * RS * sizeof(T);
+  const size_t tile_bytes = ((size_t)kProjTPB * RS * sizeof(T) + 15) / 16 * 16;
+  const size_t smem = tile_bytes + (P.n_atoms + 1 <= kSmemAtoms ? (size_t)(P.n_atoms + 1) * 4 : 0);
   auto kern = k_proj<T>;
   if (bps[dev][max_lmax] == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)kProjTPB * 101 * sizeof(T)));
+                                         (int)((size_t)kProjTPB * 101 * sizeof(T) + kSmemAtoms * 4));
     if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_proj)");
     int b = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kProjTPB, smem);
     if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_proj)");
     bps[dev][max_lmax] = std::max(b, 1);
   }
+  // the occupancy was taken for the first problem's table size; recompute when it grows
+  {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kProjTPB, smem) == cudaSuccess && b > 0)
+      bps[dev][max_lmax] = b;
+    else
+      cudaGetLastError();
+  }
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tile_upper, (int64_t)sm_count(dev) * bps[dev][max_lmax]));
-  kern<<<(unsigned)grid, kProjTPB, smem, s>>>(P, out);
+  kern<<<(unsigned)grid, kProjTPB, smem, s>>>(P, out, (int)tile_bytes);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_proj launch");
   return SHM_OK;
@@ -491,12 +581,20 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   P->box = p.box;
   P->h = p.h;
   for (int s = 0; s < p.n_species; ++s) P->lmax[s] = (signed char)p.species_lmax[s];
+  {  // Granlund-Montgomery constants for division by ng (unsigned, dividends < 2^31)
+    int l = 0;
+    while ((1u << l) < (unsigned)p.ng) ++l;
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - (unsigned long long)p.ng)) / (unsigned long long)p.ng + 1ull;
+    P->ng_magic = (unsigned)m;
+    P->ng_shift = l;
+  }
   char* ws = (char*)workspace;
   P->counter = (unsigned long long*)(ws + w.counter);
   P->err = (unsigned*)(ws + w.counter + 8);
   P->tile_offsets = (int64_t*)(ws + w.tiles);
   P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
   P->rad32 = dtype == SHM_F32 ? (float*)(ws + w.rad32) : nullptr;
+  P->atomf = dtype == SHM_F32 ? (AtomF32*)(ws + w.atomf) : nullptr;
   *max_lmax = ml;
   // an upper bound of the tile count: every point of every atom in its own partial tile
   *tile_upper = p.n_points / kProjTPB + p.n_atoms;
