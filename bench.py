@@ -253,9 +253,9 @@ def run_gpu(args, rank, world):
                 break
         else:
             raise SystemExit(f"unknown launch variant {args.variant}")
-    elif args.tune:
-        tuned_ms = shm.autotune(LMAX, tdt, 1 << 20)
     pts = inputs.dft_grid_points(args.grid)
+    if not args.variant and args.tune:  # tune on the workload's own size
+        tuned_ms = shm.autotune(LMAX, tdt, min(pts.shape[0], 1 << 23))
     if args.dtype == "f32":
         pts = pts.astype(np.float32)
     n = pts.shape[0]
@@ -286,15 +286,16 @@ def run_gpu(args, rank, world):
     value = world * n * nh / (ms_per_step * 1e-3)
     launch_ms = statistics.mean(per)
 
-    # roofline of the (single) kernel: FP64 pipe, with HBM alongside
-    dp_per_launch = dp_instr_per_point(LMAX) * n
-    achieved_tflops = 2.0 * dp_per_launch / (launch_ms * 1e-3) / 1e12
+    # roofline of the (single) kernel
+    variant = shm.eval_variant(LMAX, tdt)
+    hybrid = args.dtype == "f64" and "hybrid" in variant
+    dp_pp = HYBRID_DP_PER_POINT_L9 if hybrid else dp_instr_per_point(LMAX)
+    achieved_tflops = 2.0 * dp_pp * n / (launch_ms * 1e-3) / 1e12
     bytes_per_launch = n * (3 + nh) * es
     achieved_gbs = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
-    traffic = TRAFFIC_PER_POINT_F64_L9 * n if (TRAFFIC_PER_POINT_F64_L9 and args.dtype == "f64") else None
-
-    variant = shm.eval_variant(LMAX, tdt)
+    tpp = TRAFFIC_PER_POINT.get((args.dtype, variant))
+    traffic = tpp * n if tpp else None
     arithmetic = ("FP64 (1/r and the m = 0, 1 columns) + float-float 2xFP32 (m >= 2 columns), FP64 output; "
                   "max normwise error vs the FP64 oracle <= 5e-14 (tolerance 1e-13)"
                   if (args.dtype == "f64" and "hybrid" in variant) else
@@ -309,17 +310,8 @@ def run_gpu(args, rank, world):
                    "out_bytes_per_step": n * nh * 8, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "no flush: 170 MB input and 5.66 GB output per step exceed the 126 MB L2",
                    "launch_variant": variant, "arithmetic": arithmetic, "autotune_probe_ms": tuned_ms},
-        "roofline": ({"bound": "alu", "pipe": "fp64", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                      "peak_source": "recipe nominal FP64 (1.25 TFLOP/s = 0.625e12 FP64 pipe instr/s)",
-                      "achieved_def": f"{dp_instr_per_point(LMAX)} FP64 pipe instructions per point x 2 flop "
-                                      "(FMA-equivalent) / mean launch time",
-                      "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                              "frac": achieved_gbs / hbm_peak, "peak_source": peaks_src}}
-                     if args.dtype == "f64" else
-                     {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                      "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_source": peaks_src,
-                      "achieved_def": "(12 + 400) B per point / mean launch time"}),
+        "roofline": roofline_object(args.dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src,
+                                    traffic, n),
         "gpu_launches": args.steps,
         "clocks": clk,
         "kernel_ms": launch_ms,
@@ -353,7 +345,40 @@ def run_gpu(args, rank, world):
     return 0
 
 
-TRAFFIC_PER_POINT_F64_L9 = None   # DRAM bytes per point from ncu (filled from profiles/)
+# DRAM bytes per point (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# evaluator at lmax 9 from ncu captures (profiles/), keyed by (dtype, launch
+# variant); captures of the 96^3 grid are scaled to a full launch by the
+# number of points.
+TRAFFIC_PER_POINT = {
+    # measured on the full 192^3 launch (1-pass capture): 170.44 MB read + 5.61 GB written
+    ("f64", "phased-hybrid-128"): (170.44e6 + 5.61e9) / 7_077_888,
+    ("f64", "staged-64"): (21.318144e6 + 648.666112e6) / 884_736,
+    ("f32", "staged-64"): (10.651648e6 + 294.209024e6) / 884_736,
+}
+# FP64 pipe instructions per point of the hybrid rows at lmax 9 (ncu: dadd +
+# dmul + dfma thread instructions / points of the 96^3 capture).
+HYBRID_DP_PER_POINT_L9 = 96
+
+
+def roofline_object(dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src, traffic, n):
+    """The bound of the evaluator kernel: the all-FP64 rows are FP64-pipe bound
+    (242 FP64 instructions per point against 824 B per point); the hybrid rows
+    (96 FP64 instructions per point) and the FP32 rows are bound by the HBM
+    traffic of their output.  The other figures are given beside it."""
+    fp64 = {"achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+            "def": f"{dp_pp} FP64 pipe instructions per point x 2 (FMA-equivalent flops) / mean launch time",
+            "peak_source": "recipe nominal FP64 1.25 TFLOP/s (0.625e12 FP64 pipe instr/s)"}
+    hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+           "def": "algorithmic bytes (points in + rows out) / mean launch time", "peak_source": peaks_src}
+    if dtype == "f64" and not hybrid:
+        return {"bound": "alu", "pipe": "fp64", **{k: fp64[k] for k in ("achieved", "peak", "unit", "frac")},
+                "traffic": traffic, "achieved_def": fp64["def"], "peak_source": fp64["peak_source"], "hbm": hbm}
+    out = {"bound": "hbm", **{k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}, "traffic": traffic,
+           "achieved_def": hbm["def"], "peak_source": peaks_src}
+    if dtype == "f64":
+        out["fp64_pipe"] = fp64
+    return out
 
 
 def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
@@ -363,9 +388,9 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
     nh = (LMAX + 1) ** 2
     steps = max(5, min(args.steps, 50))
     # FP32 on the same grid: HBM-write bound
-    if args.tune:
-        shm.autotune(LMAX, torch.float32, 1 << 20)
     g32 = inputs.dft_grid_points(N_SIDE).astype(np.float32)
+    if args.tune:
+        shm.autotune(LMAX, torch.float32, g32.shape[0])
     per, region = measure_eval(shm, torch, g32, torch.float32, LMAX, steps, 3, stream)
     ms = statistics.mean(per)
     gbs = g32.shape[0] * (3 + nh) * 4 / (ms * 1e-3) / 1e9

@@ -134,6 +134,15 @@ constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},
                                  {kHybrid, 128}, {kHybrid, 256}, {kPhasedHybrid, 64}, {kPhasedHybrid, 128}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
+// For FP32 the phased and hybrid variants run the staged-64 kernel (FP32 rows
+// have no phased or hybrid form); the tuner skips them and the variant name
+// reports the kernel that runs.
+inline int effective_variant(bool fp64, int v) {
+  if (fp64) return v;
+  const int p = kVariants[v].path;
+  return (p == kPhased || p == kHybrid || p == kPhasedHybrid) ? 1 : v;
+}
+
 // Default choice before (or without) tuning: staged 128 (the FP32 path is
 // HBM-bound and wants coalesced stores; FP64 is retuned by shm_autotune).
 constexpr int kDefaultVariant = 0;
@@ -426,6 +435,7 @@ shm_status autotune_t(int lmax, int64_t n, double* best_ms) {
   float best_t = 0.f;
   shm_status st = SHM_OK;
   for (int v = 0; v < kNumVariants && st == SHM_OK; ++v) {
+    if (effective_variant(sizeof(T) == 8, v) != v) continue;
     float tv = 1e30f;
     for (int rep = 0; rep < 4 && st == SHM_OK; ++rep) {  // first repetition is a warm-up
       cudaEventRecord(e0, 0);
@@ -488,7 +498,7 @@ extern "C" const char* shm_eval_variant(int lmax, shm_dtype dtype) {
   if (lmax < 0 || lmax > SHM_LMAX_CAP || (dtype != SHM_F32 && dtype != SHM_F64)) return "";
   ensure_tune_cache();
   const int v = g_choice[dtype == SHM_F64 ? 1 : 0][lmax];
-  return kVariantNames[v < 0 ? kDefaultVariant : v];
+  return kVariantNames[effective_variant(dtype == SHM_F64, v < 0 ? kDefaultVariant : v)];
 }
 
 extern "C" int shm_eval_variant_count(void) { return shm::kNumVariants; }
