@@ -431,6 +431,30 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
     return res
 
 
+def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
+    """Complex Y_l^m on the 192^3 grid (FP64 and FP32 out, interleaved re/im)."""
+    res = {}
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    nh = (LMAX + 1) ** 2
+    g = inputs.dft_grid_points(N_SIDE)
+    for dt, name, es in ((torch.float64, "fp64", 8), (torch.float32, "fp32", 4)):
+        p = torch.from_numpy(g).to(device="cuda", dtype=dt)
+        out = torch.empty((p.shape[0], nh, 2), dtype=dt, device="cuda")
+        fn = lambda: shm.eval_complex(p, LMAX, out=out, stream=stream)  # noqa: E731
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        per, _ = timed_launches(fn, max(5, min(args.steps, 30)), stream)
+        ms = statistics.mean(per)
+        gbs = p.shape[0] * (3 + 2 * nh) * es / (ms * 1e-3) / 1e9
+        res[f"complex_dft_grid_192cubed_{name}_lmax9"] = {
+            "value": p.shape[0] * nh / (ms * 1e-3), "unit": "complex Y_lm/s", "kernel_ms": ms,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                         "peak_source": peaks_src}}
+        del out, p
+    return res
+
+
 def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
     """Fused projectors: 512 atoms, 40 bohr box, h = 0.2, spheres 2-5 bohr,
     lmax in {2, 3, 4}; values/s of one shm_projectors call (set-up + persistent
@@ -501,7 +525,7 @@ def extra_serving(args, shm, torch, inputs, stream, peaks, peaks_src):
     return res
 
 
-EXTRA_WORKLOADS: list = [extra_projectors, extra_serving]
+EXTRA_WORKLOADS: list = [extra_complex, extra_projectors, extra_serving]
 
 
 def main():

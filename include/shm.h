@@ -322,6 +322,21 @@ void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3]);
 #define SHM_PROJ_NOALLOC_SCRATCH_BYTES (1u << 20)
 shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* stream);
 
+/*
+ * shm_eval_complex -- the complex harmonics Y_l^m, l <= lmax (Sec. II Eq. 5,
+ * Condon-Shortley sign included, and Sec. III Eq. 10 for negative m), at n
+ * points.  Equivalently, from the real harmonics of shm_eval: Y_l^0 = R_l^0,
+ * Y_l^{+m} = (-1)^m (R_l^m + i R_l^{-m}) / sqrt2, Y_l^{-m} = (R_l^m - i R_l^{-m}) / sqrt2
+ * for m > 0 (the Sec. III relation printed without the 1/sqrt2).
+ *   points, n, lmax, dtype, flags, stream : as shm_eval_ex.
+ *   out : device, [n][(lmax+1)^2][2] of dtype: (Re, Im) at k = l*l + l + m.
+ * FP64 rows use binary64 for 1/r and the m = 0, 1 columns and float-float
+ * arithmetic for m >= 2 (within 1e-13 of the l-shell norm); FP32 rows as
+ * shm_eval.  Nothing is allocated.  Errors: as shm_eval.
+ */
+shm_status shm_eval_complex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags, void* out,
+                            void* stream);
+
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* shm_last_error(void);
 

@@ -53,6 +53,8 @@ def _load():
         lib.oracle_real_sh.restype = i32
         lib.oracle_real_sh_angles.argtypes = [dp, dp, i64, i32, dp]
         lib.oracle_real_sh_angles.restype = i32
+        lib.oracle_complex_sh.argtypes = [dp, i64, i32, dp, i32]
+        lib.oracle_complex_sh.restype = i32
         lib.oracle_max_threads.argtypes = [i32]
         lib.oracle_max_threads.restype = i32
         lib.oracle_projectors.argtypes = [i64, dp, dp, dp, i32, dp, i32, i32, ctypes.c_double,
@@ -84,6 +86,16 @@ def real_sh(points, lmax: int, nthreads: int = 0) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"oracle_real_sh rejected its arguments (lmax={lmax})")
     return out
+
+
+def complex_sh(points, lmax: int, nthreads: int = 0) -> np.ndarray:
+    """Complex Y_l^m (Eq. 5, Eq. 10) at Cartesian points -> [n, (lmax+1)^2] complex128."""
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    out = np.empty((pts.shape[0], n_harmonics(lmax), 2), dtype=np.float64)
+    rc = _load().oracle_complex_sh(_ptr(pts), pts.shape[0], int(lmax), _ptr(out), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_complex_sh rejected its arguments (lmax={lmax})")
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def real_sh_angles(theta, phi, lmax: int) -> np.ndarray:

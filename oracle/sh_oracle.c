@@ -140,6 +140,42 @@ int oracle_real_sh(const double* xyz, int64_t n, int lmax, double* out, int nthr
   return 0;
 }
 
+/* Complex harmonics Y_l^m (Eq. 5 for m >= 0, Eq. 10 for m < 0) at Cartesian
+ * points: out[i][k][0..1] = (Re, Im) of Y_l^m, k = l*l + l + m; at r = 0 only
+ * Y_0^0 = 1/sqrt(4 pi) is nonzero (Sec. II). */
+int oracle_complex_sh(const double* xyz, int64_t n, int lmax, double* out, int nthreads) {
+  if (!check_lmax(lmax) || n < 0 || (n > 0 && (!xyz || !out))) return 1;
+  const int L2 = (lmax + 1) * (lmax + 1);
+  set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    double* row = out + i * (int64_t)L2 * 2;
+    if (x == 0.0 && y == 0.0 && z == 0.0) {
+      for (int k = 0; k < 2 * L2; ++k) row[k] = 0.0;
+      row[0] = 1.0 / sqrt(4.0 * ORACLE_PI);
+      continue;
+    }
+    const double theta = atan2(sqrt(x * x + y * y), z), phi = atan2(y, x);
+    double P[ORACLE_LMAX_CAP + 1][ORACLE_LMAX_CAP + 1];
+    legendre_table(lmax, cos(theta), sin(theta), P);
+    for (int l = 0; l <= lmax; ++l) {
+      for (int m = 0; m <= l; ++m) {
+        const double sgn = (m & 1) ? -1.0 : 1.0;
+        const double complex Y = sgn * norm_lm(l, m) * P[l][m] * (cos(m * phi) + I * sin(m * phi));
+        row[2 * (l * l + l + m)] = creal(Y);
+        row[2 * (l * l + l + m) + 1] = cimag(Y);
+        if (m > 0) { /* Eq. 10: Y_l^{-m} = (-1)^m conj(Y_l^m) */
+          const double complex Yn = sgn * conj(Y);
+          row[2 * (l * l + l - m)] = creal(Yn);
+          row[2 * (l * l + l - m) + 1] = cimag(Yn);
+        }
+      }
+    }
+  }
+  return 0;
+}
+
 /* Real harmonics at angular inputs (theta[i], phi[i]) (the angular interface). */
 int oracle_real_sh_angles(const double* theta, const double* phi, int64_t n, int lmax, double* out) {
   if (!check_lmax(lmax) || n < 0 || (n > 0 && (!theta || !phi || !out))) return 1;

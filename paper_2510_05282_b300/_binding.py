@@ -67,6 +67,8 @@ def _declare(L):
     L.shm_eval_variant_count.restype = i32
     L.shm_eval_set_variant.argtypes = [i32, i32, i32]
     L.shm_eval_set_variant.restype = i32
+    L.shm_eval_complex.argtypes = [vp, i64, i32, i32, u32, vp, vp]
+    L.shm_eval_complex.restype = i32
     L.shm_num_harmonics.argtypes = [i32]
     L.shm_num_harmonics.restype = i32
     L.shm_last_error.argtypes = []
@@ -125,6 +127,25 @@ def eval_sh(points, lmax: int, out=None, normalized: bool = False, stream=None):
     flags = SHM_NORMALIZED_INPUT if normalized else 0
     check(lib().shm_eval_ex(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+def eval_complex(points, lmax: int, out=None, normalized: bool = False, stream=None):
+    """Complex Y_l^m, l <= lmax, at device points [n, 3] -> complex CUDA tensor
+    [n, (lmax+1)^2] (complex128 for float64 points, complex64 for float32)."""
+    import torch
+    if not (isinstance(points, torch.Tensor) and points.is_cuda):
+        raise TypeError("points must be a CUDA tensor")
+    if points.dim() != 2 or points.shape[1] != 3 or not points.is_contiguous():
+        raise ValueError("points must be a contiguous [n, 3] tensor")
+    code = _dtype_code(points.dtype)
+    n = points.shape[0]
+    if out is None:
+        out = torch.empty((n, num_harmonics(lmax), 2), dtype=points.dtype, device=points.device)
+    elif out.dtype != points.dtype or not out.is_contiguous() or out.numel() != 2 * n * num_harmonics(lmax):
+        raise ValueError("out must be a contiguous [n, (lmax+1)^2, 2] tensor of the points dtype")
+    flags = SHM_NORMALIZED_INPUT if normalized else 0
+    check(lib().shm_eval_complex(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
+    return torch.view_as_complex(out.view(n, num_harmonics(lmax), 2))
 
 
 def autotune(lmax: int, dtype, n_probe: int = 1 << 20) -> float:

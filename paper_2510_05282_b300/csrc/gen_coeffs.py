@@ -48,6 +48,11 @@ def S(l, m):
     return K(l, m) * mp.mpf(s.numerator) / s.denominator
 
 
+def SC(l, m):
+    """S_lm / sqrt2 for m > 0 (the complex harmonics, Y = (R + i R')/sqrt2), S_l0 for m = 0."""
+    return S(l, m) / mp.sqrt(2) if m > 0 else S(l, m)
+
+
 def fmt64(v):
     return mp.nstr(mp.mpf(v), 21, min_fixed=-1, max_fixed=-1)
 
@@ -84,9 +89,15 @@ def main():
     for l in range(LMAX + 1):
         lines.append("  {" + ", ".join(fmt64(S(l, m)) if m <= l else "0.0" for m in range(LMAX + 1)) + "},")
     lines.append("};")
+    lines.append("// SC[l][m] = S[l][m] / sqrt2 for m > 0 (complex harmonics), S[l][0] for m = 0")
+    lines.append(f"__device__ constexpr double SHM_SC[{LMAX + 1}][{LMAX + 1}] = {{")
+    for l in range(LMAX + 1):
+        lines.append("  {" + ", ".join(fmt64(SC(l, m)) if m <= l else "0.0" for m in range(LMAX + 1)) + "},")
+    lines.append("};")
     # float hi/lo splits for the compensated FP32 path
     for name, fn in (("G", lambda l, m: mp.mpf(G(l, m).numerator) / G(l, m).denominator if l >= m + 2 else 0),
-                     ("S", lambda l, m: S(l, m) if m <= l else 0)):
+                     ("S", lambda l, m: S(l, m) if m <= l else 0),
+                     ("SC", lambda l, m: SC(l, m) if m <= l else 0)):
         his, los = [], []
         for l in range(LMAX + 1):
             hr, lr = [], []

@@ -28,6 +28,24 @@ struct NH {
   static constexpr int value = (LMAX + 1) * (LMAX + 1);
 };
 
+// Scale constants: S for the real harmonics, S / sqrt2 (m > 0) for the
+// complex ones (Y_l^{+-m} = (+-1)^m (R_l^m +- i R_l^{-m}) / sqrt2, m > 0).
+template <bool CX>
+__device__ __forceinline__ constexpr double Sd(int l, int m) { return CX ? SHM_SC[l][m] : SHM_S[l][m]; }
+template <bool CX>
+__device__ __forceinline__ constexpr float Shi(int l, int m) { return CX ? SHM_SC_HI[l][m] : SHM_S_HI[l][m]; }
+template <bool CX>
+__device__ __forceinline__ constexpr float Slo(int l, int m) { return CX ? SHM_SC_LO[l][m] : SHM_S_LO[l][m]; }
+
+// l of the flat index k = l*l + l + m, as a table so that a constant k folds
+// to a constant at compile time.
+__device__ constexpr int SHM_L_OF_K[(SHM_COEFF_LMAX + 1) * (SHM_COEFF_LMAX + 1)] = {
+    0, 1, 1, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4,
+    5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6, 6, 6, 6, 6, 6, 6, 7,
+    7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8,
+    8, 8, 8, 8, 8, 8, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9};
+__device__ __forceinline__ constexpr int l_of_k(int k) { return SHM_L_OF_K[k]; }
+
 // ---------------------------------------------------------------------------
 // Cartesian -> normalised coordinates.
 
@@ -99,17 +117,17 @@ __device__ __forceinline__ void unit_dir(float x, float y, float z, float& xb, f
 // q = 1 (the non-homogeneous form): in binary64 the extra rounding of the
 // coordinates costs < 1e-14 normwise at l = 9.
 
-template <int LMAX, typename Store>
+template <int LMAX, bool CX = false, typename Store>
 __device__ __forceinline__ void sh_row(double xb, double yb, double zb, Store&& store) {
   // m = 0
-  store(0, SHM_S[0][0]);
+  store(0, Sd<CX>(0, 0));
   if constexpr (LMAX >= 1) {
-    store(2, SHM_S[1][0] * zb);
+    store(2, Sd<CX>(1, 0) * zb);
     double q2 = 1.0, q1 = zb;
 #pragma unroll
     for (int l = 2; l <= LMAX; ++l) {
       const double q = fma(zb, q1, -SHM_G[l][0] * q2);
-      store(l * l + l, SHM_S[l][0] * q);
+      store(l * l + l, Sd<CX>(l, 0) * q);
       q2 = q1;
       q1 = q;
     }
@@ -123,10 +141,10 @@ __device__ __forceinline__ void sh_row(double xb, double yb, double zb, Store&& 
       A = An;
       B = Bn;
     }
-    store(m * m + 2 * m, SHM_S[m][m] * A);
-    store(m * m, SHM_S[m][m] * B);
+    store(m * m + 2 * m, Sd<CX>(m, m) * A);
+    store(m * m, Sd<CX>(m, m) * B);
     if (m + 1 <= LMAX) {
-      const double s = SHM_S[m + 1][m] * zb;
+      const double s = Sd<CX>(m + 1, m) * zb;
       const int k0 = (m + 1) * (m + 1) + (m + 1);
       store(k0 + m, s * A);
       store(k0 - m, s * B);
@@ -135,7 +153,7 @@ __device__ __forceinline__ void sh_row(double xb, double yb, double zb, Store&& 
 #pragma unroll
     for (int l = m + 2; l <= LMAX; ++l) {
       const double q = fma(zb, q1, -SHM_G[l][m] * q2);
-      const double s = SHM_S[l][m] * q;
+      const double s = Sd<CX>(l, m) * q;
       store(l * l + l + m, s * A);
       store(l * l + l - m, s * B);
       q2 = q1;
@@ -149,11 +167,11 @@ __device__ __forceinline__ void sh_row(double xb, double yb, double zb, Store&& 
 // values come out l by l: all (x+iy)^m first, then for each l the next step of
 // every m-recurrence.  The l-shells are grouped into phases of at most
 // PHMAX values; phase(k0, width) is called after each group so the caller can
-// stage and flush it.  store(k - k0, v) writes within the current phase.
-template <int LMAX>
+// stage and flush it.  store(k, k0, v) writes value k of the current phase,
+// which starts at k0.
+template <int LMAX, int PHMAX_ = 37>
 struct LPhases {
-  // phase p covers l in [first[p], first[p+1])
-  static constexpr int PHMAX = 37;
+  static constexpr int PHMAX = PHMAX_;  // values per phase at most (a single shell may exceed it)
   static constexpr int count() {
     int n = 0, w = 0;
     for (int l = 0; l <= LMAX; ++l) {
@@ -188,7 +206,7 @@ struct LPhases {
   }
 };
 
-template <int LMAX, typename Store, typename Phase>
+template <int LMAX, bool CX = false, int PHMAX = 37, typename Store, typename Phase>
 __device__ __forceinline__ void sh_row_lmajor(double xb, double yb, double zb, Store&& store, Phase&& phase) {
   double A[LMAX + 1], B[LMAX + 1], q1[LMAX + 1], q2[LMAX + 1];
   A[0] = 1.0;
@@ -209,28 +227,28 @@ __device__ __forceinline__ void sh_row_lmajor(double xb, double yb, double zb, S
     for (int m = 0; m <= l; ++m) {
       double s;
       if (l == m) {
-        s = SHM_S[l][m];
+        s = Sd<CX>(l, m);
         q2[m] = 1.0;
         q1[m] = 1.0;  // Qh_m^m
       } else if (l == m + 1) {
-        s = SHM_S[l][m] * zb;
+        s = Sd<CX>(l, m) * zb;
         q2[m] = 1.0;
         q1[m] = zb;
       } else {
         const double q = fma(zb, q1[m], -SHM_G[l][m] * q2[m]);
-        s = SHM_S[l][m] * q;
+        s = Sd<CX>(l, m) * q;
         q2[m] = q1[m];
         q1[m] = q;
       }
       const int k = l * l + l;
       if (m == 0) {
-        store(k - k0, s);
+        store(k, k0, s);
       } else {
-        store(k + m - k0, (l == m) ? SHM_S[l][m] * A[m] : s * A[m]);
-        store(k - m - k0, (l == m) ? SHM_S[l][m] * B[m] : s * B[m]);
+        store(k + m, k0, (l == m) ? Sd<CX>(l, m) * A[m] : s * A[m]);
+        store(k - m, k0, (l == m) ? Sd<CX>(l, m) * B[m] : s * B[m]);
       }
     }
-    if (LPhases<LMAX>::ends_phase(l)) {
+    if (LPhases<LMAX, PHMAX>::ends_phase(l)) {
       phase(k0, (l + 1) * (l + 1) - k0);
       k0 = (l + 1) * (l + 1);
     }
@@ -353,23 +371,23 @@ __device__ __forceinline__ double ff_to_double(ff a) {
 // binary64 per value.  Normwise error against the FP64 oracle stays below
 // 5e-14 at l = 9 (the FP64 path: 1.4e-14; tolerance 1e-13) while the FP64
 // instructions per point drop from ~242 to ~75.
-template <int LMAX, typename Store>
+template <int LMAX, bool CX = false, typename Store>
 __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, Store&& store) {
-  store(0, SHM_S[0][0]);
+  store(0, Sd<CX>(0, 0));
   if constexpr (LMAX >= 1) {
-    store(2, SHM_S[1][0] * zb);
+    store(2, Sd<CX>(1, 0) * zb);
     double q2 = 1.0, q1 = zb;
 #pragma unroll
     for (int l = 2; l <= LMAX; ++l) {
       const double q = fma(zb, q1, -SHM_G[l][0] * q2);
-      store(l * l + l, SHM_S[l][0] * q);
+      store(l * l + l, Sd<CX>(l, 0) * q);
       q2 = q1;
       q1 = q;
     }
-    store(3, SHM_S[1][1] * xb);
-    store(1, SHM_S[1][1] * yb);
+    store(3, Sd<CX>(1, 1) * xb);
+    store(1, Sd<CX>(1, 1) * yb);
     if constexpr (LMAX >= 2) {
-      const double s = SHM_S[2][1] * zb;
+      const double s = Sd<CX>(2, 1) * zb;
       store(7, s * xb);
       store(5, s * yb);
     }
@@ -378,7 +396,7 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
 #pragma unroll
     for (int l = 3; l <= LMAX; ++l) {
       const double q = fma(zb, q1, -SHM_G[l][1] * q2);
-      const double s = SHM_S[l][1] * q;
+      const double s = Sd<CX>(l, 1) * q;
       store(l * l + l + 1, s * xb);
       store(l * l + l - 1, s * yb);
       q2 = q1;
@@ -394,11 +412,11 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
       const ff Bn = ff_add(ff_mul_u(A, Y), ff_mul_u(B, X));
       A = An;
       B = Bn;
-      store(m * m + 2 * m, ff_to_double(ff_mul_c(A, SHM_S_HI[m][m], SHM_S_LO[m][m])));
-      store(m * m, ff_to_double(ff_mul_c(B, SHM_S_HI[m][m], SHM_S_LO[m][m])));
+      store(m * m + 2 * m, ff_to_double(ff_mul_c(A, Shi<CX>(m, m), Slo<CX>(m, m))));
+      store(m * m, ff_to_double(ff_mul_c(B, Shi<CX>(m, m), Slo<CX>(m, m))));
       ff q2 = {1.0f, 0.0f}, q1 = Z;
       if (m + 1 <= LMAX) {
-        const ff s = ff_mul_c_u(Z, SHM_S_HI[m + 1][m], SHM_S_LO[m + 1][m]);
+        const ff s = ff_mul_c_u(Z, Shi<CX>(m + 1, m), Slo<CX>(m + 1, m));
         const int k0 = (m + 1) * (m + 1) + (m + 1);
         store(k0 + m, ff_to_double(ff_mul(s, A)));
         store(k0 - m, ff_to_double(ff_mul(s, B)));
@@ -406,7 +424,7 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
 #pragma unroll
       for (int l = m + 2; l <= LMAX; ++l) {
         const ff q = ff_add(ff_mul_u(Z, q1), ff_neg(ff_mul_c_u(q2, SHM_G_HI[l][m], SHM_G_LO[l][m])));
-        const ff s = ff_mul_c_u(q, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+        const ff s = ff_mul_c_u(q, Shi<CX>(l, m), Slo<CX>(l, m));
         store(l * l + l + m, ff_to_double(ff_mul(s, A)));
         store(l * l + l - m, ff_to_double(ff_mul(s, B)));
         q2 = q1;
@@ -420,7 +438,7 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
 // the same operations on the same operands as sh_row_hybrid, so the rows are
 // bitwise identical to it; all m-recurrences advance together, one l at a
 // time, which exposes ~l independent chains to the scheduler.
-template <int LMAX, typename Store, typename Phase>
+template <int LMAX, bool CX = false, int PHMAX = 37, typename Store, typename Phase>
 __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, double zb, Store&& store,
                                                      Phase&& phase) {
   const ff X = ff_from_double(xb), Y = ff_from_double(yb), Z = ff_from_double(zb);
@@ -444,47 +462,47 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
       if (m <= 1) {  // binary64 columns, as sh_row_hybrid
         double s;
         if (l == m) {
-          s = SHM_S[l][m];
+          s = Sd<CX>(l, m);
           d2[m] = 1.0;
           d1[m] = 1.0;
         } else if (l == m + 1) {
-          s = SHM_S[l][m] * zb;
+          s = Sd<CX>(l, m) * zb;
           d2[m] = 1.0;
           d1[m] = zb;
         } else {
           const double q = fma(zb, d1[m], -SHM_G[l][m] * d2[m]);
-          s = SHM_S[l][m] * q;
+          s = Sd<CX>(l, m) * q;
           d2[m] = d1[m];
           d1[m] = q;
         }
         if (m == 0) {
-          store(kc - k0, s);
+          store(kc, k0, s);
         } else {
-          store(kc + 1 - k0, (l == 1) ? SHM_S[1][1] * xb : s * xb);
-          store(kc - 1 - k0, (l == 1) ? SHM_S[1][1] * yb : s * yb);
+          store(kc + 1, k0, (l == 1) ? Sd<CX>(1, 1) * xb : s * xb);
+          store(kc - 1, k0, (l == 1) ? Sd<CX>(1, 1) * yb : s * yb);
         }
       } else {  // float-float columns
         if (l == m) {
-          store(kc + m - k0, ff_to_double(ff_mul_c(A[m], SHM_S_HI[m][m], SHM_S_LO[m][m])));
-          store(kc - m - k0, ff_to_double(ff_mul_c(B[m], SHM_S_HI[m][m], SHM_S_LO[m][m])));
+          store(kc + m, k0, ff_to_double(ff_mul_c(A[m], Shi<CX>(m, m), Slo<CX>(m, m))));
+          store(kc - m, k0, ff_to_double(ff_mul_c(B[m], Shi<CX>(m, m), Slo<CX>(m, m))));
           q2[m] = {1.0f, 0.0f};
           q1[m] = Z;
         } else {
           ff sv;
           if (l == m + 1) {
-            sv = ff_mul_c_u(Z, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+            sv = ff_mul_c_u(Z, Shi<CX>(l, m), Slo<CX>(l, m));
           } else {
             const ff q = ff_add(ff_mul_u(Z, q1[m]), ff_neg(ff_mul_c_u(q2[m], SHM_G_HI[l][m], SHM_G_LO[l][m])));
-            sv = ff_mul_c_u(q, SHM_S_HI[l][m], SHM_S_LO[l][m]);
+            sv = ff_mul_c_u(q, Shi<CX>(l, m), Slo<CX>(l, m));
             q2[m] = q1[m];
             q1[m] = q;
           }
-          store(kc + m - k0, ff_to_double(ff_mul(sv, A[m])));
-          store(kc - m - k0, ff_to_double(ff_mul(sv, B[m])));
+          store(kc + m, k0, ff_to_double(ff_mul(sv, A[m])));
+          store(kc - m, k0, ff_to_double(ff_mul(sv, B[m])));
         }
       }
     }
-    if (LPhases<LMAX>::ends_phase(l)) {
+    if (LPhases<LMAX, PHMAX>::ends_phase(l)) {
       phase(k0, (l + 1) * (l + 1) - k0);
       k0 = (l + 1) * (l + 1);
     }
@@ -501,12 +519,12 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
 //    poles, the zb-recurrence runs in float-float (FMA-based error-free
 //    products and sums, constants split into hi + lo); the result is rounded
 //    to float once per value.
-template <int LMAX, int M, typename Store>
+template <int LMAX, int M, bool CX, typename Store>
 __device__ __forceinline__ void sh_column_ff(float zb, float dq, float A, float B, Store&& store) {
   ff q2 = {1.0f, 0.0f}, q1 = {zb, 0.0f};
   auto emit = [&](int l, ff Q) {
-    const ff p = two_prod(SHM_S_HI[l][M], Q.hi);
-    const float v = __fadd_rn(p.hi, fmaf(SHM_S_HI[l][M], Q.lo, fmaf(SHM_S_LO[l][M], Q.hi, p.lo)));
+    const ff p = two_prod(Shi<CX>(l, M), Q.hi);
+    const float v = __fadd_rn(p.hi, fmaf(Shi<CX>(l, M), Q.lo, fmaf(Slo<CX>(l, M), Q.hi, p.lo)));
     if constexpr (M == 0) {
       store(l * l + l, v);
     } else {
@@ -515,10 +533,10 @@ __device__ __forceinline__ void sh_column_ff(float zb, float dq, float A, float 
     }
   };
   if constexpr (M == 0) {
-    store(0, SHM_S_HI[0][0]);
+    store(0, Shi<CX>(0, 0));
   } else {
-    store(M * M + 2 * M, SHM_S_HI[M][M] * A);
-    store(M * M, SHM_S_HI[M][M] * B);
+    store(M * M + 2 * M, Shi<CX>(M, M) * A);
+    store(M * M, Shi<CX>(M, M) * B);
   }
   if constexpr (M + 1 <= LMAX) emit(M + 1, q1);
 #pragma unroll
@@ -536,7 +554,7 @@ __device__ __forceinline__ void sh_column_ff(float zb, float dq, float A, float 
   }
 }
 
-template <int LMAX, typename Store>
+template <int LMAX, bool CX = false, typename Store>
 __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& store) {
   // q = xb^2 + yb^2 + zb^2 as a float-float, then dq = q - 1
   const ff px = two_prod(xb, xb), py = two_prod(yb, yb), pz = two_prod(zb, zb);
@@ -547,8 +565,8 @@ __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& sto
   const float dq = __fadd_rn(__fsub_rn(qf.hi, 1.0f), qf.lo);
   const float qq = qf.hi;
 
-  sh_column_ff<LMAX, 0>(zb, dq, 0.0f, 0.0f, store);
-  if constexpr (LMAX >= 1) sh_column_ff<LMAX, 1>(zb, dq, xb, yb, store);
+  sh_column_ff<LMAX, 0, CX>(zb, dq, 0.0f, 0.0f, store);
+  if constexpr (LMAX >= 1) sh_column_ff<LMAX, 1, CX>(zb, dq, xb, yb, store);
   float A = xb, B = yb;
 #pragma unroll
   for (int m = 2; m <= LMAX; ++m) {
@@ -556,10 +574,10 @@ __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& sto
     const float Bn = fmaf(A, yb, B * xb);
     A = An;
     B = Bn;
-    store(m * m + 2 * m, (float)SHM_S[m][m] * A);
-    store(m * m, (float)SHM_S[m][m] * B);
+    store(m * m + 2 * m, (float)Sd<CX>(m, m) * A);
+    store(m * m, (float)Sd<CX>(m, m) * B);
     if (m + 1 <= LMAX) {
-      const float s = (float)SHM_S[m + 1][m] * zb;
+      const float s = (float)Sd<CX>(m + 1, m) * zb;
       const int k0 = (m + 1) * (m + 1) + (m + 1);
       store(k0 + m, s * A);
       store(k0 - m, s * B);
@@ -568,7 +586,7 @@ __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& sto
 #pragma unroll
     for (int l = m + 2; l <= LMAX; ++l) {
       const float q = fmaf(zb, q1, -(float)SHM_G[l][m] * (qq * q2));
-      const float s = (float)SHM_S[l][m] * q;
+      const float s = (float)Sd<CX>(l, m) * q;
       store(l * l + l + m, s * A);
       store(l * l + l - m, s * B);
       q2 = q1;
@@ -579,7 +597,7 @@ __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& sto
 
 // Full point: Cartesian (or already normalised) input -> row of harmonics.
 // HYBRID selects sh_row_hybrid for binary64 rows.
-template <int LMAX, bool HYBRID = false, typename T, typename Store>
+template <int LMAX, bool HYBRID = false, bool CX = false, typename T, typename Store>
 __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&& store) {
   if (is_origin(x, y, z)) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
     store(0, (T)kInvSqrt4Pi);
@@ -590,9 +608,9 @@ __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&&
   T xb = x, yb = y, zb = z;
   if (!normalized) unit_dir(x, y, z, xb, yb, zb);
   if constexpr (HYBRID && sizeof(T) == 8)
-    sh_row_hybrid<LMAX>(xb, yb, zb, store);
+    sh_row_hybrid<LMAX, CX>(xb, yb, zb, store);
   else
-    sh_row<LMAX>(xb, yb, zb, store);
+    sh_row<LMAX, CX>(xb, yb, zb, store);
 }
 
 }  // namespace shm

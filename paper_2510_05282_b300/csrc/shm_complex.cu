@@ -1,0 +1,194 @@
+// shm_eval_complex: the complex harmonics Y_l^m (Sec. II Eq. 5, with Eq. 10
+// for negative m) fused into the evaluator.  With the real harmonics of the
+// same rows, Y_l^0 = R_l^0 and, for m > 0,
+//   Y_l^{+m} = (-1)^m (R_l^m + i R_l^{-m}) / sqrt2,
+//   Y_l^{-m} =        (R_l^m - i R_l^{-m}) / sqrt2
+// (the paper's Sec. III relation without its missing 1/sqrt2).  The rows are
+// computed by the real-harmonic row code with the scale constants divided by
+// sqrt2 for m > 0 (coefficient set CX), so each real value v lands, with a
+// sign, in the real or imaginary part of Y_l^{+m} and Y_l^{-m} at no extra
+// arithmetic.  Output: [n][(lmax+1)^2][2] (re, im) of the dtype.
+//
+// FP64 rows use the hybrid arithmetic in l-major order (binary64 for 1/r and
+// m = 0, 1, float-float for m >= 2), staged one group of l-shells at a time;
+// FP32 rows use the FP32 row code, staged a full row at a time.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "sh_core.cuh"
+#include "sh_tile.cuh"
+#include "shm_internal.h"
+
+namespace shm {
+
+// Writes the real value v = R_l^m (already divided by sqrt2 for m != 0) of
+// k = l*l + l + m into the complex row c[2k + part], relative to base k0.
+template <typename T>
+__device__ __forceinline__ void cx_store(T* c, int k, int k0, T v) {
+  const int l = l_of_k(k);
+  const int m = k - l * l - l;
+  const int kc = l * l + l;
+  if (m == 0) {
+    c[2 * (k - k0)] = v;
+    c[2 * (k - k0) + 1] = (T)0;
+  } else if (m > 0) {  // Re Y_l^{+m} = (-1)^m v, Re Y_l^{-m} = v
+    c[2 * (k - k0)] = (m & 1) ? -v : v;
+    c[2 * (kc - m - k0)] = v;
+  } else {  // v = R_l^{-mu}: Im Y_l^{+mu} = (-1)^mu v, Im Y_l^{-mu} = -v
+    const int mu = -m;
+    c[2 * (kc + mu - k0) + 1] = (mu & 1) ? -v : v;
+    c[2 * (k - k0) + 1] = -v;
+  }
+}
+
+constexpr int kCxTPB64 = 128;
+constexpr int kCxPhase = 19;  // l-shell values per phase: 2 x 19 complex components staged per row
+constexpr int kCxTPB32 = 64;
+
+template <int LMAX>
+__global__ void __launch_bounds__(kCxTPB64) k_eval_cx64(const double* __restrict__ pts, int64_t n,
+                                                        double* __restrict__ out, int64_t ntiles, int normalized) {
+  constexpr int L2 = NH<LMAX>::value;
+  constexpr int RS = (2 * LPhases<LMAX, kCxPhase>::max_width()) | 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* tile = reinterpret_cast<double*>(smem_raw);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * kCxTPB64;
+    const int rows = (int)min((int64_t)kCxTPB64, n - p0);
+    const bool valid = (int)threadIdx.x < rows;
+    double x = 0.0, y = 0.0, z = 1.0;
+    if (valid) {
+      const int64_t p = p0 + threadIdx.x;
+      x = pts[3 * p];
+      y = pts[3 * p + 1];
+      z = pts[3 * p + 2];
+    }
+    const bool origin = valid && is_origin(x, y, z);
+    double xb = 0.0, yb = 0.0, zb = 1.0;
+    if (valid && !origin) {
+      if (normalized) {
+        xb = x;
+        yb = y;
+        zb = z;
+      } else {
+        unit_dir(x, y, z, xb, yb, zb);
+      }
+    }
+    double* row = tile + threadIdx.x * RS;
+    auto store = [&](int k, int k0, double v) { cx_store(row, k, k0, v); };
+    auto flush = [&](int k0, int w) {
+      if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
+        for (int c = 0; c < 2 * w; ++c) row[c] = (k0 == 0 && c == 0) ? kInvSqrt4Pi : 0.0;
+      }
+      __syncthreads();
+      const int w2 = 2 * w;
+      const int nv = rows * w2;
+      for (int j = threadIdx.x; j < nv; j += kCxTPB64) {
+        const int r = j / w2;
+        const int c = j - r * w2;
+        __stcs(out + (p0 + r) * (2 * L2) + 2 * k0 + c, tile[r * RS + c]);
+      }
+      __syncthreads();
+    };
+    sh_row_hybrid_lmajor<LMAX, true, kCxPhase>(xb, yb, zb, store, flush);
+  }
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(kCxTPB32) k_eval_cx32(const float* __restrict__ pts, int64_t n,
+                                                        float* __restrict__ out, int64_t ntiles, int normalized,
+                                                        int vec) {
+  constexpr int L2 = NH<LMAX>::value;
+  constexpr int RS = (2 * L2) | 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tile = reinterpret_cast<float*>(smem_raw);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * kCxTPB32;
+    const int rows = (int)min((int64_t)kCxTPB32, n - p0);
+    if ((int)threadIdx.x < rows) {
+      const int64_t p = p0 + threadIdx.x;
+      const float x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
+      float* row = tile + threadIdx.x * RS;
+      if (is_origin(x, y, z)) {
+        for (int c = 0; c < 2 * L2; ++c) row[c] = c == 0 ? (float)kInvSqrt4Pi : 0.0f;
+      } else {
+        float xb = x, yb = y, zb = z;
+        if (!normalized) unit_dir(x, y, z, xb, yb, zb);
+        sh_row<LMAX, true>(xb, yb, zb, [&](int k, float v) { cx_store(row, k, 0, v); });
+      }
+    }
+    __syncthreads();
+    copy_out_tile<float, 2 * L2, RS, kCxTPB32>(tile, rows, out + p0 * 2 * L2, vec != 0);
+    __syncthreads();
+  }
+}
+
+template <int LMAX>
+shm_status cx_launch(const void* pts, int64_t n, bool f64, void* out, bool normalized, bool vec, cudaStream_t s) {
+  constexpr int MAXDEV = 64;
+  static int bps[2][MAXDEV] = {};
+  const int dev = current_device();
+  if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
+  const int tpb = f64 ? kCxTPB64 : kCxTPB32;
+  const size_t smem = f64 ? (size_t)kCxTPB64 * ((2 * LPhases<LMAX, kCxPhase>::max_width()) | 1) * 8
+                          : (size_t)kCxTPB32 * ((2 * NH<LMAX>::value) | 1) * 4;
+  const void* kern = f64 ? (const void*)k_eval_cx64<LMAX> : (const void*)k_eval_cx32<LMAX>;
+  int& b = bps[f64 ? 1 : 0][dev];
+  if (b == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_eval_cx)");
+    int bb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, kern, tpb, smem);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_eval_cx)");
+    b = std::max(bb, 1);
+  }
+  const int64_t ntiles = (n + tpb - 1) / tpb;
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * b);
+  if (f64)
+    k_eval_cx64<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const double*)pts, n, (double*)out, ntiles, normalized);
+  else
+    k_eval_cx32<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const float*)pts, n, (float*)out, ntiles, normalized, vec);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "k_eval_cx launch");
+  return SHM_OK;
+}
+
+}  // namespace shm
+
+extern "C" shm_status shm_eval_complex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
+                                       void* out, void* stream) {
+  using namespace shm;
+  clear_error();
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
+  if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
+  if (flags & ~SHM_NORMALIZED_INPUT) return fail(SHM_EINVAL, "unknown flag bits");
+  if (n == 0) return SHM_OK;
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  const int64_t L2 = (int64_t)(lmax + 1) * (lmax + 1);
+  if (n > (INT64_MAX / 16) / (L2 * 16)) return fail(SHM_EINVAL, "n too large");
+  if (!points || !out) return fail(SHM_EINVAL, "points and out must be non-null");
+  if (!aligned(points, es) || !aligned(out, es))
+    return fail(SHM_EINVAL, "points and out must be aligned to the element size");
+  const size_t in_bytes = (size_t)n * 3 * es, out_bytes = (size_t)n * L2 * 2 * es;
+  if (ranges_overlap(points, in_bytes, out, out_bytes)) return fail(SHM_EINVAL, "points and out overlap");
+  shm_status st = check_device_range(points, in_bytes, "points");
+  if (st != SHM_OK) return st;
+  if ((st = check_device_range(out, out_bytes, "out")) != SHM_OK) return st;
+  const bool f64 = dtype == SHM_F64, norm = (flags & SHM_NORMALIZED_INPUT) != 0, vec = aligned(out, 16);
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (lmax) {
+    case 0: return cx_launch<0>(points, n, f64, out, norm, vec, s);
+    case 1: return cx_launch<1>(points, n, f64, out, norm, vec, s);
+    case 2: return cx_launch<2>(points, n, f64, out, norm, vec, s);
+    case 3: return cx_launch<3>(points, n, f64, out, norm, vec, s);
+    case 4: return cx_launch<4>(points, n, f64, out, norm, vec, s);
+    case 5: return cx_launch<5>(points, n, f64, out, norm, vec, s);
+    case 6: return cx_launch<6>(points, n, f64, out, norm, vec, s);
+    case 7: return cx_launch<7>(points, n, f64, out, norm, vec, s);
+    case 8: return cx_launch<8>(points, n, f64, out, norm, vec, s);
+    default: return cx_launch<9>(points, n, f64, out, norm, vec, s);
+  }
+}

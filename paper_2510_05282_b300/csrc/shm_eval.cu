@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(TPB) k_eval_phased(const double* __restrict__ 
       }
     }
     double* row = tile + threadIdx.x * RS;
-    auto store = [&](int kk, double v) { row[kk] = v; };
+    auto store = [&](int k, int k0, double v) { row[k - k0] = v; };
     auto flush = [&](int k0, int w) {
           if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
             for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;

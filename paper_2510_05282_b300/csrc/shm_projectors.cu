@@ -266,12 +266,6 @@ __device__ __forceinline__ Lagrange4<T> lagrange_at(int it, T u, int n_rad) {
   return L;
 }
 
-constexpr int l_of_k(int k) {
-  int l = 0;
-  while ((l + 1) * (l + 1) <= k) ++l;
-  return l;
-}
-
 __device__ __forceinline__ double interp4(const Lagrange4<double>& L, const double* F) {
   return fma(L.w[3], __ldg(F + 3), fma(L.w[2], __ldg(F + 2), fma(L.w[1], __ldg(F + 1), L.w[0] * __ldg(F))));
 }

@@ -231,3 +231,30 @@ def test_prefix_property(oracle_mod, lmax):
     full = oracle_mod.real_sh(pts, LMAX)
     part = oracle_mod.real_sh(pts, lmax)
     assert np.array_equal(part, full[:, : (lmax + 1) ** 2])
+
+
+def test_complex_harmonics_against_scipy_and_eq10(oracle_mod):
+    special = pytest.importorskip("scipy.special")
+    pts = inputs.random_sphere_points(800, stream="tests")
+    r = np.linalg.norm(pts, axis=1)
+    theta = np.arccos(np.clip(pts[:, 2] / r, -1, 1))
+    phi = np.arctan2(pts[:, 1], pts[:, 0])
+    Y = oracle_mod.complex_sh(pts, LMAX)
+    for l in range(LMAX + 1):
+        for m in range(-l, l + 1):
+            ref = special.sph_harm_y(l, m, theta, phi)       # Condon-Shortley included, as Eq. 5
+            k = l * l + l + m
+            assert np.max(np.abs(Y[:, k] - ref)) <= 1e-13 * NORM_BOUND[k], (l, m)
+            if m > 0:  # Eq. 10
+                assert np.array_equal(Y[:, l * l + l - m], (-1) ** m * np.conj(Y[:, k]))
+    # the addition theorem for |Y|^2 and the link to the real harmonics (Eq. 6)
+    R = oracle_mod.real_sh(pts, LMAX)
+    for l in range(LMAX + 1):
+        np.testing.assert_allclose(np.sum(np.abs(Y[:, l * l:(l + 1) ** 2]) ** 2, axis=1),
+                                   (2 * l + 1) / (4 * np.pi), rtol=2e-14)
+        for m in range(1, l + 1):
+            k = l * l + l + m
+            re = (-1) ** m * np.sqrt(2) * Y[:, k].real
+            im = (-1) ** m * np.sqrt(2) * Y[:, k].imag
+            assert np.max(np.abs(re - R[:, k])) <= 1e-14 * NORM_BOUND[k]
+            assert np.max(np.abs(im - R[:, l * l + l - m])) <= 1e-14 * NORM_BOUND[k]
