@@ -432,7 +432,8 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
 
 
 def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
-    """Complex Y_l^m on the 192^3 grid (FP64 and FP32 out, interleaved re/im)."""
+    """Complex Y_l^m on the 192^3 grid (FP64 and FP32 out, interleaved re/im),
+    and the angular interface on the grid's directions."""
     res = {}
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     nh = (LMAX + 1) ** 2
@@ -452,6 +453,21 @@ def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                          "peak_source": peaks_src}}
         del out, p
+    # the angular interface on the same directions
+    r = np.linalg.norm(g, axis=1)
+    ang = np.stack([np.arccos(np.clip(g[:, 2] / r, -1, 1)), np.arctan2(g[:, 1], g[:, 0])], axis=1)
+    for dt, name in ((torch.float64, "fp64"), (torch.float32, "fp32")):
+        a = torch.from_numpy(ang).to(device="cuda", dtype=dt)
+        out = torch.empty((a.shape[0], nh), dtype=dt, device="cuda")
+        fn = lambda: shm.eval_angles(a, LMAX, out=out, stream=stream)  # noqa: E731
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        per, _ = timed_launches(fn, max(5, min(args.steps, 30)), stream)
+        ms = statistics.mean(per)
+        res[f"angular_input_192cubed_directions_{name}_lmax9"] = {"value": a.shape[0] * nh / (ms * 1e-3),
+                                                                  "unit": UNIT, "kernel_ms": ms}
+        del out, a
     return res
 
 

@@ -337,6 +337,19 @@ shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_dtype dtype,
 shm_status shm_eval_complex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags, void* out,
                             void* stream);
 
+/*
+ * shm_eval_angles -- the angular interface (Sec. II: the paper offers angular,
+ * Cartesian and normalised-Cartesian inputs): all R_l^m, l <= lmax, at n
+ * directions given by their angles.
+ *   angles : device, [n][2] (theta, phi) in radians, theta from +z (Eq. 3),
+ *            phi = atan2(y, x) (Eq. 4), element type per dtype.
+ *   out    : device, [n][(lmax+1)^2] of dtype, as shm_eval.
+ * The unit vector (sin t cos p, sin t sin p, cos t) is formed with CUDA's
+ * sincos, then the rows are those of shm_eval (FP64: the hybrid rows).
+ * Nothing is allocated.  Errors: as shm_eval.
+ */
+shm_status shm_eval_angles(const void* angles, int64_t n, int lmax, shm_dtype dtype, void* out, void* stream);
+
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* shm_last_error(void);
 

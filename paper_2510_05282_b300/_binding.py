@@ -69,6 +69,8 @@ def _declare(L):
     L.shm_eval_set_variant.restype = i32
     L.shm_eval_complex.argtypes = [vp, i64, i32, i32, u32, vp, vp]
     L.shm_eval_complex.restype = i32
+    L.shm_eval_angles.argtypes = [vp, i64, i32, i32, vp, vp]
+    L.shm_eval_angles.restype = i32
     L.shm_num_harmonics.argtypes = [i32]
     L.shm_num_harmonics.restype = i32
     L.shm_last_error.argtypes = []
@@ -146,6 +148,22 @@ def eval_complex(points, lmax: int, out=None, normalized: bool = False, stream=N
     flags = SHM_NORMALIZED_INPUT if normalized else 0
     check(lib().shm_eval_complex(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
     return torch.view_as_complex(out.view(n, num_harmonics(lmax), 2))
+
+
+def eval_angles(angles, lmax: int, out=None, stream=None):
+    """All R_l^m, l <= lmax, at directions given as a device tensor [n, 2] of
+    (theta, phi) -> [n, (lmax+1)^2] of the same dtype."""
+    import torch
+    if not (isinstance(angles, torch.Tensor) and angles.is_cuda):
+        raise TypeError("angles must be a CUDA tensor")
+    if angles.dim() != 2 or angles.shape[1] != 2 or not angles.is_contiguous():
+        raise ValueError("angles must be a contiguous [n, 2] tensor")
+    n = angles.shape[0]
+    if out is None:
+        out = torch.empty((n, num_harmonics(lmax)), dtype=angles.dtype, device=angles.device)
+    check(lib().shm_eval_angles(angles.data_ptr(), n, int(lmax), _dtype_code(angles.dtype), out.data_ptr(),
+                                _stream_ptr(stream)))
+    return out
 
 
 def autotune(lmax: int, dtype, n_probe: int = 1 << 20) -> float:

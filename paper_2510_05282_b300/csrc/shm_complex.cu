@@ -192,3 +192,114 @@ extern "C" shm_status shm_eval_complex(const void* points, int64_t n, int lmax, 
     default: return cx_launch<9>(points, n, f64, out, norm, vec, s);
   }
 }
+
+// ---------------------------------------------------------------------------
+// Angular interface: (theta, phi) per point (Sec. II Eq. 3-4 read backwards:
+// x/r = sin(theta) cos(phi), y/r = sin(theta) sin(phi), z/r = cos(theta)),
+// then the rows of shm_eval.  The sines and cosines are CUDA's sincos
+// (binary64 on the FP64 pipe for FP64 rows, sincosf for FP32).
+
+namespace shm {
+
+constexpr int kAngTPB = 64;
+
+template <typename T, int LMAX>
+__global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ ang, int64_t n, T* __restrict__ out,
+                                                          int64_t ntiles, int vec) {
+  constexpr int L2 = TileShape<LMAX>::L2;
+  constexpr int RS = TileShape<LMAX>::RS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * kAngTPB;
+    const int rows = (int)min((int64_t)kAngTPB, n - p0);
+    if ((int)threadIdx.x < rows) {
+      const int64_t p = p0 + threadIdx.x;
+      const T th = ang[2 * p], ph = ang[2 * p + 1];
+      T st, ct, sp, cp;
+      if constexpr (sizeof(T) == 8) {
+        sincos(th, &st, &ct);
+        sincos(ph, &sp, &cp);
+      } else {
+        sincosf(th, &st, &ct);
+        sincosf(ph, &sp, &cp);
+      }
+      T* row = tile + threadIdx.x * RS;
+      auto store = [&](int k, T v) { row[k] = v; };
+      if constexpr (sizeof(T) == 8)
+        sh_row_hybrid<LMAX>(st * cp, st * sp, ct, store);
+      else
+        sh_row<LMAX>(st * cp, st * sp, ct, store);
+    }
+    __syncthreads();
+    copy_out_tile<T, L2, RS, kAngTPB>(tile, rows, out + p0 * L2, vec != 0);
+    __syncthreads();
+  }
+}
+
+template <typename T, int LMAX>
+shm_status ang_launch(const T* ang, int64_t n, T* out, bool vec, cudaStream_t s) {
+  constexpr int MAXDEV = 64;
+  static int bps[MAXDEV] = {};
+  const int dev = current_device();
+  if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
+  const size_t smem = (size_t)kAngTPB * TileShape<LMAX>::RS * sizeof(T);
+  auto kern = k_eval_angles<T, LMAX>;
+  if (bps[dev] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_eval_angles)");
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kAngTPB, smem);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_eval_angles)");
+    bps[dev] = std::max(b, 1);
+  }
+  const int64_t ntiles = (n + kAngTPB - 1) / kAngTPB;
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * bps[dev]);
+  kern<<<(unsigned)grid, kAngTPB, smem, s>>>(ang, n, out, ntiles, vec ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "k_eval_angles launch");
+  return SHM_OK;
+}
+
+template <typename T>
+shm_status ang_dispatch(const T* ang, int64_t n, int lmax, T* out, bool vec, cudaStream_t s) {
+  switch (lmax) {
+    case 0: return ang_launch<T, 0>(ang, n, out, vec, s);
+    case 1: return ang_launch<T, 1>(ang, n, out, vec, s);
+    case 2: return ang_launch<T, 2>(ang, n, out, vec, s);
+    case 3: return ang_launch<T, 3>(ang, n, out, vec, s);
+    case 4: return ang_launch<T, 4>(ang, n, out, vec, s);
+    case 5: return ang_launch<T, 5>(ang, n, out, vec, s);
+    case 6: return ang_launch<T, 6>(ang, n, out, vec, s);
+    case 7: return ang_launch<T, 7>(ang, n, out, vec, s);
+    case 8: return ang_launch<T, 8>(ang, n, out, vec, s);
+    default: return ang_launch<T, 9>(ang, n, out, vec, s);
+  }
+}
+
+}  // namespace shm
+
+extern "C" shm_status shm_eval_angles(const void* angles, int64_t n, int lmax, shm_dtype dtype, void* out,
+                                      void* stream) {
+  using namespace shm;
+  clear_error();
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
+  if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
+  if (n == 0) return SHM_OK;
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  const int64_t L2 = (int64_t)(lmax + 1) * (lmax + 1);
+  if (n > (INT64_MAX / 8) / (L2 * 8)) return fail(SHM_EINVAL, "n too large");
+  if (!angles || !out) return fail(SHM_EINVAL, "angles and out must be non-null");
+  if (!aligned(angles, es) || !aligned(out, es))
+    return fail(SHM_EINVAL, "angles and out must be aligned to the element size");
+  const size_t in_bytes = (size_t)n * 2 * es, out_bytes = (size_t)n * L2 * es;
+  if (ranges_overlap(angles, in_bytes, out, out_bytes)) return fail(SHM_EINVAL, "angles and out overlap");
+  shm_status st = check_device_range(angles, in_bytes, "angles");
+  if (st != SHM_OK) return st;
+  if ((st = check_device_range(out, out_bytes, "out")) != SHM_OK) return st;
+  const bool vec = aligned(out, 16);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == SHM_F64) return ang_dispatch<double>((const double*)angles, n, lmax, (double*)out, vec, s);
+  return ang_dispatch<float>((const float*)angles, n, lmax, (float*)out, vec, s);
+}
