@@ -55,7 +55,10 @@ typedef enum {
   SHM_ENOTFOUND = 7     /* serving: unknown ticket */
 } shm_status;
 
-#define SHM_LMAX_CAP 9
+#define SHM_LMAX_CAP 9  /* the paper's formulas stop at l = 9 (Sec. III) */
+#define SHM_LMAX_EXT 16 /* shm_eval, shm_eval_ex, shm_eval_host and the tuner accept lmax up to this:
+                           the recurrence behind the rows has no l limit (the paper's conclusion
+                           points to recurrences for l > 9); l > 9 rows are all-FP64 for SHM_F64 */
 
 /* shm_eval_ex flags */
 #define SHM_NORMALIZED_INPUT 0x1u /* points are already x/r, y/r, z/r: skip the r work */
@@ -68,12 +71,12 @@ int shm_num_harmonics(int lmax);
  *   points : device, [n][3] x, y, z (AoS) relative to the centre, element type
  *            per dtype, aligned to its element size.
  *   n      : number of points, >= 0 (0: returns SHM_OK, launches nothing).
- *   lmax   : 0..9.
+ *   lmax   : 0..16 (SHM_LMAX_EXT; 0..9 is the paper's range).
  *   out    : device, [n][(lmax+1)^2] of dtype, aligned to its element size
  *            (16-byte alignment enables the vector store path).  Must not
  *            overlap points.
  * Caller owns both buffers; nothing is allocated.
- * Errors: SHM_EINVAL (null or misaligned pointer, lmax outside 0..9, n < 0,
+ * Errors: SHM_EINVAL (null or misaligned pointer, lmax outside 0..16, n < 0,
  * bad dtype), SHM_ECUDA (launch failed).
  */
 shm_status shm_eval(const void* points, int64_t n, int lmax, shm_dtype dtype, void* out, void* stream);

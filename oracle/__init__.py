@@ -25,7 +25,7 @@ _SRC = os.environ.get("SHM_ORACLE_SRC", os.path.join(_HERE, "sh_oracle.c"))
 _BUILD_DIR = os.environ.get("SHM_ORACLE_BUILD_DIR", os.path.join(_HERE, "_build"))
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 
-LMAX_CAP = 9
+LMAX_CAP = 16
 
 _lib = None
 

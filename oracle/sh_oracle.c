@@ -41,10 +41,10 @@
 #include <omp.h>
 #endif
 
-#define ORACLE_LMAX_CAP 9
+#define ORACLE_LMAX_CAP 16
 #define ORACLE_PI 3.14159265358979323846264338327950288
 
-/* n! for n <= 18 is exact in binary64 (18! < 2^53). */
+/* n! (exact in binary64 up to 18!; one rounding beyond, up to 32! for l = 16). */
 static double factorial(int n) {
   double f = 1.0;
   for (int i = 2; i <= n; ++i) f *= (double)i;

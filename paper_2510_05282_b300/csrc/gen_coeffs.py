@@ -2,6 +2,9 @@
 
 Run from the repository root:  python paper_2510_05282_b300/csrc/gen_coeffs.py
 
+Tables run to l = 16: the paper's formulas stop at l = 9, the recurrence
+does not (the paper's conclusion names recurrences as the way past l = 9).
+
 Scheme (normalised Cartesian coordinates xb, yb, zb, Sec. II Eq. 8):
   R_l^{+m} = S_lm * Qh_l^m(zb) * A_m,   R_l^{-m} = S_lm * Qh_l^m(zb) * B_m,
   R_l^0    = S_l0 * Qh_l^0(zb),
@@ -23,8 +26,8 @@ from fractions import Fraction
 
 import mpmath as mp
 
-LMAX = 9
-mp.mp.dps = 40
+LMAX = 16
+mp.mp.dps = 50
 
 
 def sigma(l, m):
@@ -113,6 +116,13 @@ def main():
         lines.append(f"__device__ constexpr float SHM_{name}_LO[{LMAX + 1}][{LMAX + 1}] = {{")
         lines += los
         lines.append("};")
+    nk = (LMAX + 1) ** 2
+    lines.append("// l of the flat index k = l*l + l + m (a table, so a constant k folds at compile time)")
+    lines.append(f"__device__ constexpr int SHM_L_OF_K[{nk}] = {{")
+    ls = [str(int(math.isqrt(k))) for k in range(nk)]
+    for i in range(0, nk, 25):
+        lines.append("    " + ", ".join(ls[i:i + 25]) + ",")
+    lines.append("};")
     with open(os.path.join(here, "sh_coeffs.h"), "w") as f:
         f.write("\n".join(lines) + "\n")
 

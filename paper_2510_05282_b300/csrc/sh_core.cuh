@@ -37,13 +37,6 @@ __device__ __forceinline__ constexpr float Shi(int l, int m) { return CX ? SHM_S
 template <bool CX>
 __device__ __forceinline__ constexpr float Slo(int l, int m) { return CX ? SHM_SC_LO[l][m] : SHM_S_LO[l][m]; }
 
-// l of the flat index k = l*l + l + m, as a table so that a constant k folds
-// to a constant at compile time.
-__device__ constexpr int SHM_L_OF_K[(SHM_COEFF_LMAX + 1) * (SHM_COEFF_LMAX + 1)] = {
-    0, 1, 1, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4,
-    5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6, 6, 6, 6, 6, 6, 6, 7,
-    7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 7, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8,
-    8, 8, 8, 8, 8, 8, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9, 9};
 __device__ __forceinline__ constexpr int l_of_k(int k) { return SHM_L_OF_K[k]; }
 
 // ---------------------------------------------------------------------------

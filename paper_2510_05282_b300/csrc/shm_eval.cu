@@ -137,10 +137,41 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 // For FP32 the phased and hybrid variants run the staged-64 kernel (FP32 rows
 // have no phased or hybrid form); the tuner skips them and the variant name
 // reports the kernel that runs.
-inline int effective_variant(bool fp64, int v) {
-  if (fp64) return v;
+// Shared memory of a variant's CTA (mirrors eval_smem_bytes) and the limit.
+inline size_t variant_smem(int v, int lmax, size_t es) {
+  const int L2 = (lmax + 1) * (lmax + 1);
+  const int p = kVariants[v].path, tpb = kVariants[v].tpb;
+  if (p == kDirect) return 0;
+  if (p == kPhased || p == kPhasedHybrid) {
+    int w = 0, mx = 0;  // LPhases<LMAX>::max_width()
+    for (int l = 0; l <= lmax; ++l) {
+      if (w > 0 && w + 2 * l + 1 > 37) w = 0;
+      w += 2 * l + 1;
+      mx = std::max(mx, w);
+    }
+    return (size_t)tpb * (mx | 1) * 8;
+  }
+  return (size_t)tpb * (size_t)(L2 % 2 ? L2 : L2 + 1) * es;
+}
+constexpr size_t kMaxSmemPerCta = 232448;  // B300 opt-in limit per CTA
+
+// The variant that actually runs: FP32 rows have no phased or hybrid form
+// (staged-64 runs); for l > 9 the FP64 rows are all-FP64 (a hybrid variant
+// runs its all-FP64 counterpart); a staged variant whose tile does not fit
+// in shared memory at this l runs phased-64 (FP64) or staged-64 (FP32).
+inline int effective_variant(bool fp64, int v, int lmax = 0) {
   const int p = kVariants[v].path;
-  return (p == kPhased || p == kHybrid || p == kPhasedHybrid) ? 1 : v;
+  if (!fp64) {
+    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid) ? 1 : v;
+  } else if (lmax > SHM_LMAX_CAP) {
+    if (v == 7) v = 1;              // hybrid-64 -> staged-64
+    else if (v == 8) v = 0;         // hybrid-128 -> staged-128
+    else if (v == 9) v = 2;         // hybrid-256 -> staged-256
+    else if (v == 10) v = 5;        // phased-hybrid-64 -> phased-64
+    else if (v == 11) v = 6;        // phased-hybrid-128 -> phased-128
+  }
+  if (variant_smem(v, lmax, fp64 ? 8 : 4) > kMaxSmemPerCta) v = fp64 ? 5 : 1;
+  return v;
 }
 
 // Default choice before (or without) tuning: staged 128 (the FP32 path is
@@ -148,7 +179,8 @@ inline int effective_variant(bool fp64, int v) {
 constexpr int kDefaultVariant = 0;
 
 // chosen[dtype][lmax] (-1 = default)
-int g_choice[2][SHM_LMAX_CAP + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
+int g_choice[2][SHM_LMAX_EXT + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
+                                     {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
 
 template <typename T, int LMAX, int TPB, int PATH>
 size_t eval_smem_bytes() {
@@ -206,6 +238,19 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
     variant = g_choice[sizeof(T) == 8 ? 1 : 0][LMAX];
     if (variant < 0) variant = kDefaultVariant;
   }
+  variant = effective_variant(sizeof(T) == 8, variant, LMAX);
+  if constexpr (LMAX > SHM_LMAX_CAP) {
+    switch (variant) {
+      case 0: return eval_launch_v<T, LMAX, 128, kStaged>(pts, n, out, normalized, vec, s);
+      case 1: return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, s);
+      case 2: return eval_launch_v<T, LMAX, 256, kStaged>(pts, n, out, normalized, vec, s);
+      case 3: return eval_launch_v<T, LMAX, 128, kDirect>(pts, n, out, normalized, vec, s);
+      case 4: return eval_launch_v<T, LMAX, 256, kDirect>(pts, n, out, normalized, vec, s);
+      case 5: return eval_launch_v<T, LMAX, 64, kPhased>(pts, n, out, normalized, vec, s);
+      case 6: return eval_launch_v<T, LMAX, 128, kPhased>(pts, n, out, normalized, vec, s);
+    }
+    return fail(SHM_EINVAL, "unknown launch variant");
+  }
   switch (variant) {
     case 0: return eval_launch_v<T, LMAX, 128, kStaged>(pts, n, out, normalized, vec, s);
     case 1: return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, s);
@@ -237,8 +282,15 @@ shm_status eval_dispatch(const T* pts, int64_t n, int lmax, T* out, bool normali
     case 7: return eval_launch<T, 7>(pts, n, out, normalized, vec, s, variant);
     case 8: return eval_launch<T, 8>(pts, n, out, normalized, vec, s, variant);
     case 9: return eval_launch<T, 9>(pts, n, out, normalized, vec, s, variant);
+    case 10: return eval_launch<T, 10>(pts, n, out, normalized, vec, s, variant);
+    case 11: return eval_launch<T, 11>(pts, n, out, normalized, vec, s, variant);
+    case 12: return eval_launch<T, 12>(pts, n, out, normalized, vec, s, variant);
+    case 13: return eval_launch<T, 13>(pts, n, out, normalized, vec, s, variant);
+    case 14: return eval_launch<T, 14>(pts, n, out, normalized, vec, s, variant);
+    case 15: return eval_launch<T, 15>(pts, n, out, normalized, vec, s, variant);
+    case 16: return eval_launch<T, 16>(pts, n, out, normalized, vec, s, variant);
   }
-  return fail(SHM_EINVAL, "lmax must be in 0..9");
+  return fail(SHM_EINVAL, "lmax must be in 0..16");
 }
 
 void ensure_tune_cache();
@@ -250,7 +302,7 @@ extern "C" shm_status shm_eval_ex(const void* points, int64_t n, int lmax, shm_d
   using namespace shm;
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
-  if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9 (the paper's formulas stop at l = 9)");
+  if (lmax < 0 || lmax > SHM_LMAX_EXT) return fail(SHM_EINVAL, "lmax must be in 0..16");
   if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
   if (flags & ~SHM_NORMALIZED_INPUT) return fail(SHM_EINVAL, "unknown flag bits");
   if (n == 0) return SHM_OK;
@@ -318,7 +370,7 @@ shm_status get_pipe(int dev, HostPipe** out) {
 }  // namespace shm
 
 extern "C" size_t shm_eval_host_workspace_size(int lmax, shm_dtype dtype, int64_t chunk_points) {
-  if (lmax < 0 || lmax > SHM_LMAX_CAP || chunk_points <= 0 || (dtype != SHM_F32 && dtype != SHM_F64)) return 0;
+  if (lmax < 0 || lmax > SHM_LMAX_EXT || chunk_points <= 0 || (dtype != SHM_F32 && dtype != SHM_F64)) return 0;
   const size_t es = dtype == SHM_F64 ? 8 : 4;
   const size_t per = es * (3 + (size_t)(lmax + 1) * (lmax + 1));
   // two buffers, each point block and row block rounded up to 256 bytes
@@ -330,7 +382,7 @@ extern "C" shm_status shm_eval_host(const void* points_host, int64_t n, int lmax
   using namespace shm;
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
-  if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
+  if (lmax < 0 || lmax > SHM_LMAX_EXT) return fail(SHM_EINVAL, "lmax must be in 0..16");
   if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
   if (n == 0) return SHM_OK;
   if (!points_host || !out_host) return fail(SHM_EINVAL, "points_host and out_host must be non-null");
@@ -400,7 +452,7 @@ void load_tune_cache_locked() {
   if (!f) return;
   int dt, l, v;
   while (fscanf(f, "%d %d %d", &dt, &l, &v) == 3)
-    if (dt >= 0 && dt <= 1 && l >= 0 && l <= SHM_LMAX_CAP && v >= 0 && v < kNumVariants) g_choice[dt][l] = v;
+    if (dt >= 0 && dt <= 1 && l >= 0 && l <= SHM_LMAX_EXT && v >= 0 && v < kNumVariants) g_choice[dt][l] = v;
   fclose(f);
 }
 
@@ -435,7 +487,7 @@ shm_status autotune_t(int lmax, int64_t n, double* best_ms) {
   float best_t = 0.f;
   shm_status st = SHM_OK;
   for (int v = 0; v < kNumVariants && st == SHM_OK; ++v) {
-    if (effective_variant(sizeof(T) == 8, v) != v) continue;
+    if (effective_variant(sizeof(T) == 8, v, lmax) != v) continue;
     float tv = 1e30f;
     for (int rep = 0; rep < 4 && st == SHM_OK; ++rep) {  // first repetition is a warm-up
       cudaEventRecord(e0, 0);
@@ -486,7 +538,7 @@ extern "C" shm_status shm_autotune(int lmax, shm_dtype dtype, int64_t n_probe, d
   using namespace shm;
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
-  if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
+  if (lmax < 0 || lmax > SHM_LMAX_EXT) return fail(SHM_EINVAL, "lmax must be in 0..16");
   if (n_probe <= 0 || n_probe > (int64_t)1 << 26) return fail(SHM_EINVAL, "n_probe must be in 1..2^26");
   std::lock_guard<std::mutex> lk(g_tune_mu);
   load_tune_cache_locked();
@@ -495,10 +547,10 @@ extern "C" shm_status shm_autotune(int lmax, shm_dtype dtype, int64_t n_probe, d
 
 extern "C" const char* shm_eval_variant(int lmax, shm_dtype dtype) {
   using namespace shm;
-  if (lmax < 0 || lmax > SHM_LMAX_CAP || (dtype != SHM_F32 && dtype != SHM_F64)) return "";
+  if (lmax < 0 || lmax > SHM_LMAX_EXT || (dtype != SHM_F32 && dtype != SHM_F64)) return "";
   ensure_tune_cache();
   const int v = g_choice[dtype == SHM_F64 ? 1 : 0][lmax];
-  return kVariantNames[effective_variant(dtype == SHM_F64, v < 0 ? kDefaultVariant : v)];
+  return kVariantNames[effective_variant(dtype == SHM_F64, v < 0 ? kDefaultVariant : v, lmax)];
 }
 
 extern "C" int shm_eval_variant_count(void) { return shm::kNumVariants; }
@@ -506,7 +558,7 @@ extern "C" int shm_eval_variant_count(void) { return shm::kNumVariants; }
 extern "C" shm_status shm_eval_set_variant(int lmax, shm_dtype dtype, int variant) {
   using namespace shm;
   clear_error();
-  if (lmax < 0 || lmax > SHM_LMAX_CAP || (dtype != SHM_F32 && dtype != SHM_F64))
+  if (lmax < 0 || lmax > SHM_LMAX_EXT || (dtype != SHM_F32 && dtype != SHM_F64))
     return fail(SHM_EINVAL, "bad lmax or dtype");
   if (variant < -1 || variant >= kNumVariants) return fail(SHM_EINVAL, "variant out of range");
   ensure_tune_cache();

@@ -47,7 +47,7 @@ def test_num_harmonics_and_status_strings(L):
 
 
 @pytest.mark.parametrize("args,msg", [
-    ((1, 10, 10, 1, 1, None), "lmax"),
+    ((1, 10, 17, 1, 1, None), "lmax"),
     ((1, 10, -1, 1, 1, None), "lmax"),
     ((1, 10, 3, 7, 1, None), "dtype"),
     ((1, -5, 3, 1, 1, None), "n must"),
@@ -78,5 +78,5 @@ def test_host_entry_validation(L):
 
 def test_binding_errors_carry_text(L):
     with pytest.raises(shm.ShmError) as ei:
-        shm.check(L.shm_eval(None, 3, 11, 1, None, None))
+        shm.check(L.shm_eval(None, 3, 17, 1, None, None))
     assert ei.value.status == 1 and "lmax" in str(ei.value)

@@ -243,3 +243,33 @@ def test_fp32_grid_and_sphere_per_l_report(oracle_mod, capsys):
     rows = np.unique(inputs.rng("tests", 78).integers(0, grid.shape[0], 20000))
     got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
     assert_normwise(got, oracle_mod.real_sh(grid[rows].astype(np.float64), 9), TOL_F32, "FP32 grid sample")
+
+
+# ---------------------------------------------------------------- beyond l = 9
+
+def tol_high_l(lmax, base):
+    """Tolerance above the paper's l <= 9: rounding in the l-steps of the
+    recurrence grows about linearly with l, so the l <= 9 bound is scaled by
+    l / 9."""
+    return base * max(1.0, lmax / 9.0)
+
+
+@pytest.mark.parametrize("lmax", [10, 12, 16])
+def test_high_l_every_variant(oracle_mod, lmax, capsys):
+    pts = np.concatenate([inputs.random_sphere_points(3001, stream="tests"), inputs.edge_points()[:14]])
+    ref = oracle_mod.real_sh(pts, lmax)
+    worst = {}
+    try:
+        for dtype, base in ((torch.float64, TOL_F64), (torch.float32, TOL_F32)):
+            ref_d = ref if dtype == torch.float64 else oracle_mod.real_sh(pts.astype(np.float32).astype(np.float64), lmax)
+            for v in range(shm.eval_variant_count()):
+                shm.set_eval_variant(lmax, dtype, v)
+                got = gpu_eval(pts, lmax, dtype=dtype)
+                err = normwise_err(got, ref_d)
+                worst[(str(dtype), shm.eval_variant(lmax, dtype))] = float(err.max())
+                assert_normwise(got, ref_d, tol_high_l(lmax, base), f"l={lmax} {dtype} {shm.eval_variant(lmax, dtype)}")
+    finally:
+        shm.set_eval_variant(lmax, torch.float64, -1)
+        shm.set_eval_variant(lmax, torch.float32, -1)
+    with capsys.disabled():
+        print(f"\nlmax={lmax} worst normwise errors:", {k: f"{v:.2e}" for k, v in worst.items()})

@@ -219,7 +219,7 @@ def test_origin_convention_and_nan(oracle_mod):
 
 def test_rejects_bad_lmax(oracle_mod):
     with pytest.raises(ValueError):
-        oracle_mod.real_sh(np.ones((1, 3)), 10)
+        oracle_mod.real_sh(np.ones((1, 3)), 17)
     with pytest.raises(ValueError):
         oracle_mod.real_sh(np.ones((1, 3)), -1)
 
@@ -258,3 +258,61 @@ def test_complex_harmonics_against_scipy_and_eq10(oracle_mod):
             im = (-1) ** m * np.sqrt(2) * Y[:, k].imag
             assert np.max(np.abs(re - R[:, k])) <= 1e-14 * NORM_BOUND[k]
             assert np.max(np.abs(im - R[:, l * l + l - m])) <= 1e-14 * NORM_BOUND[k]
+
+
+# ---------------------------------------------------------------- beyond l = 9
+
+def test_high_l_against_scipy_and_identities(oracle_mod):
+    """l up to 16 (the recurrence has no l limit): scipy's complex harmonics
+    through Eq. 6, the addition theorem and orthonormality on an exact
+    24 x 48 Gauss-Legendre x uniform-phi quadrature (degree <= 47)."""
+    special = pytest.importorskip("scipy.special")
+    L = 16
+    nb = np.sqrt((2 * np.array([int(math.isqrt(k)) for k in range((L + 1) ** 2)]) + 1) / (4 * np.pi))
+    pts = inputs.random_sphere_points(300, stream="tests", with_axes=False)
+    R = oracle_mod.real_sh(pts, L)
+    r = np.linalg.norm(pts, axis=1)
+    theta = np.arccos(np.clip(pts[:, 2] / r, -1, 1))
+    phi = np.arctan2(pts[:, 1], pts[:, 0])
+    for l in range(10, L + 1):
+        for m in range(-l, l + 1):
+            a = abs(m)
+            Y = special.sph_harm_y(l, a, theta, phi)
+            ref = Y.real if m == 0 else (-1) ** a * math.sqrt(2) * (Y.real if m > 0 else Y.imag)
+            k = l * l + l + m
+            assert np.max(np.abs(R[:, k] - ref)) <= 1e-13 * nb[k], (l, m)
+        s = np.sum(R[:, l * l:(l + 1) ** 2] ** 2, axis=1)
+        np.testing.assert_allclose(s, (2 * l + 1) / (4 * np.pi), rtol=4e-14)
+    xg, wg = np.polynomial.legendre.leggauss(24)
+    ph = 2 * np.pi * np.arange(48) / 48
+    ct = np.repeat(xg, 48)
+    st = np.sqrt(1 - ct * ct)
+    p = np.tile(ph, 24)
+    q = np.stack([st * np.cos(p), st * np.sin(p), ct], axis=1)
+    w = np.repeat(wg, 48) * (2 * np.pi / 48)
+    Rq = oracle_mod.real_sh(q, L)
+    G = (Rq * w[:, None]).T @ Rq
+    assert np.max(np.abs(G - np.eye(G.shape[0]))) <= 1e-12
+
+
+def test_high_l_against_40_digit_explicit_sum(oracle_mod):
+    mp = pytest.importorskip("mpmath").mp
+    mp.dps = 40
+    g = inputs.rng("tests", 4)
+    pts = g.standard_normal((40, 3))
+    L = 16
+    O = oracle_mod.real_sh(pts, L)
+    worst = 0.0
+    for i, (x, y, z) in enumerate(pts):
+        X, Y, Z = mp.mpf(x), mp.mpf(y), mp.mpf(z)
+        rr = mp.sqrt(X * X + Y * Y + Z * Z)
+        ct, phi = Z / rr, mp.atan2(Y, X)
+        for l in (10, 13, 16):
+            for m in range(0, l + 1):
+                N = mp.sqrt(mp.mpf(2 * l + 1) / (4 * mp.pi) * mp.factorial(l - m) / mp.factorial(l + m))
+                P = _legendre_mp(l, m, ct, mp)
+                vals = {0: N * P} if m == 0 else {m: mp.sqrt(2) * N * P * mp.cos(m * phi),
+                                                  -m: mp.sqrt(2) * N * P * mp.sin(m * phi)}
+                for mm, v in vals.items():
+                    worst = max(worst, abs(float(v) - O[i, l * l + l + mm]) / math.sqrt((2 * l + 1) / (4 * math.pi)))
+    assert worst <= 4e-14, worst
