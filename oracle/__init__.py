@@ -55,6 +55,8 @@ def _load():
         lib.oracle_real_sh_angles.restype = i32
         lib.oracle_complex_sh.argtypes = [dp, i64, i32, dp, i32]
         lib.oracle_complex_sh.restype = i32
+        lib.oracle_spinor_sh.argtypes = [dp, i64, i32, dp, i32]
+        lib.oracle_spinor_sh.restype = i32
         lib.oracle_max_threads.argtypes = [i32]
         lib.oracle_max_threads.restype = i32
         lib.oracle_projectors.argtypes = [i64, dp, dp, dp, i32, dp, i32, i32, ctypes.c_double,
@@ -95,6 +97,28 @@ def complex_sh(points, lmax: int, nthreads: int = 0) -> np.ndarray:
     rc = _load().oracle_complex_sh(_ptr(pts), pts.shape[0], int(lmax), _ptr(out), int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle_complex_sh rejected its arguments (lmax={lmax})")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def n_spinors(lmax: int) -> int:
+    """Spinor harmonics per point: j = l +- 1/2 for l <= lmax, 2 (lmax+1)^2."""
+    return 2 * (lmax + 1) ** 2
+
+
+def spinor_index(l: int, s: int, two_mj: int) -> int:
+    """Position of the spinor (l, j = l + s/2, m_j = two_mj/2) in a row."""
+    two_j = 2 * l + s
+    return 2 * l * l + (0 if s < 0 else 2 * l) + (two_mj + two_j) // 2
+
+
+def spinor_sh(points, lmax: int, nthreads: int = 0) -> np.ndarray:
+    """Spinor harmonics (Eq. 7) at Cartesian points -> [n, 2 (lmax+1)^2, 2]
+    complex128: (upper, lower) component of each spinor, order spinor_index."""
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    out = np.empty((pts.shape[0], n_spinors(lmax), 2, 2), dtype=np.float64)
+    rc = _load().oracle_spinor_sh(_ptr(pts), pts.shape[0], int(lmax), _ptr(out), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_spinor_sh rejected its arguments (lmax={lmax})")
     return out[..., 0] + 1j * out[..., 1]
 
 

@@ -20,6 +20,7 @@
  *                      Condon-Shortley sign (the (-1)^m is written explicitly).
  *   Sec. III, Eq. 10   Y_l^{-m} = (-1)^m (Y_l^m)^*  (used for negative m).
  *   Sec. II, Eq. 6     R_l^m from Y_l^{+-m}.
+ *   Sec. II, Eq. 7     spinor harmonics (spin 1/2) from the complex Y_l^m.
  *   Sec. II            at r = 0 every harmonic is 0 except l = 0, which is the
  *                      constant 1/sqrt(4 pi).
  *
@@ -143,32 +144,79 @@ int oracle_real_sh(const double* xyz, int64_t n, int lmax, double* out, int nthr
 /* Complex harmonics Y_l^m (Eq. 5 for m >= 0, Eq. 10 for m < 0) at Cartesian
  * points: out[i][k][0..1] = (Re, Im) of Y_l^m, k = l*l + l + m; at r = 0 only
  * Y_0^0 = 1/sqrt(4 pi) is nonzero (Sec. II). */
+static void complex_sh_point(const double* p, int lmax, double* row) {
+  const int L2 = (lmax + 1) * (lmax + 1);
+  const double x = p[0], y = p[1], z = p[2];
+  if (x == 0.0 && y == 0.0 && z == 0.0) {
+    for (int k = 0; k < 2 * L2; ++k) row[k] = 0.0;
+    row[0] = 1.0 / sqrt(4.0 * ORACLE_PI);
+    return;
+  }
+  const double theta = atan2(sqrt(x * x + y * y), z), phi = atan2(y, x);
+  double P[ORACLE_LMAX_CAP + 1][ORACLE_LMAX_CAP + 1];
+  legendre_table(lmax, cos(theta), sin(theta), P);
+  for (int l = 0; l <= lmax; ++l) {
+    for (int m = 0; m <= l; ++m) {
+      const double sgn = (m & 1) ? -1.0 : 1.0;
+      const double complex Y = sgn * norm_lm(l, m) * P[l][m] * (cos(m * phi) + I * sin(m * phi));
+      row[2 * (l * l + l + m)] = creal(Y);
+      row[2 * (l * l + l + m) + 1] = cimag(Y);
+      if (m > 0) { /* Eq. 10: Y_l^{-m} = (-1)^m conj(Y_l^m) */
+        const double complex Yn = sgn * conj(Y);
+        row[2 * (l * l + l - m)] = creal(Yn);
+        row[2 * (l * l + l - m) + 1] = cimag(Yn);
+      }
+    }
+  }
+}
+
 int oracle_complex_sh(const double* xyz, int64_t n, int lmax, double* out, int nthreads) {
   if (!check_lmax(lmax) || n < 0 || (n > 0 && (!xyz || !out))) return 1;
   const int L2 = (lmax + 1) * (lmax + 1);
   set_threads(nthreads);
 #pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) complex_sh_point(xyz + 3 * i, lmax, out + i * (int64_t)L2 * 2);
+  return 0;
+}
+
+/* Spinor harmonics for spin 1/2 (Sec. II, Eq. 7) at Cartesian points, from
+ * the complex harmonics of the same point.  For orbital l and total angular
+ * momentum j = l + s/2 (s = +1, or s = -1 when l >= 1), m_j = -j .. j:
+ *   upper = s sqrt(l + s m_j + 1/2) / sqrt(2l+1) * Y_l^{m_j - 1/2}
+ *   lower =   sqrt(l - s m_j + 1/2) / sqrt(2l+1) * Y_l^{m_j + 1/2}
+ * (Eq. 7 with its +- read as s and l = j -+ 1/2), where Y_l^m = 0 for |m| > l.
+ * Output out[i][q][c][re/im]: spinor q = 2 l^2 + (s < 0 ? 0 : 2l) + (m_j + j),
+ * component c = 0 (upper), 1 (lower); 2 (lmax+1)^2 spinors per point.  */
+int oracle_spinor_sh(const double* xyz, int64_t n, int lmax, double* out, int nthreads) {
+  if (!check_lmax(lmax) || n < 0 || (n > 0 && (!xyz || !out))) return 1;
+  const int L2 = (lmax + 1) * (lmax + 1);
+  set_threads(nthreads);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
-    const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-    double* row = out + i * (int64_t)L2 * 2;
-    if (x == 0.0 && y == 0.0 && z == 0.0) {
-      for (int k = 0; k < 2 * L2; ++k) row[k] = 0.0;
-      row[0] = 1.0 / sqrt(4.0 * ORACLE_PI);
-      continue;
-    }
-    const double theta = atan2(sqrt(x * x + y * y), z), phi = atan2(y, x);
-    double P[ORACLE_LMAX_CAP + 1][ORACLE_LMAX_CAP + 1];
-    legendre_table(lmax, cos(theta), sin(theta), P);
+    double Y[2 * (ORACLE_LMAX_CAP + 1) * (ORACLE_LMAX_CAP + 1)];
+    complex_sh_point(xyz + 3 * i, lmax, Y);
+    double* row = out + i * (int64_t)L2 * 8;
     for (int l = 0; l <= lmax; ++l) {
-      for (int m = 0; m <= l; ++m) {
-        const double sgn = (m & 1) ? -1.0 : 1.0;
-        const double complex Y = sgn * norm_lm(l, m) * P[l][m] * (cos(m * phi) + I * sin(m * phi));
-        row[2 * (l * l + l + m)] = creal(Y);
-        row[2 * (l * l + l + m) + 1] = cimag(Y);
-        if (m > 0) { /* Eq. 10: Y_l^{-m} = (-1)^m conj(Y_l^m) */
-          const double complex Yn = sgn * conj(Y);
-          row[2 * (l * l + l - m)] = creal(Yn);
-          row[2 * (l * l + l - m) + 1] = cimag(Yn);
+      const double pre = 1.0 / sqrt(2.0 * l + 1.0);
+      for (int s = -1; s <= 1; s += 2) {
+        if (s < 0 && l == 0) continue;
+        const double j = l + 0.5 * s;
+        const int q0 = 2 * l * l + (s < 0 ? 0 : 2 * l);
+        const int nmj = (int)(2.0 * j + 1.0);
+        for (int t = 0; t < nmj; ++t) {
+          const double mj = -j + t;
+          const int mu = (int)lround(mj - 0.5), md = (int)lround(mj + 0.5); /* m of the two Y */
+          const double cu = s * sqrt(l + s * mj + 0.5) * pre, cd = sqrt(l - s * mj + 0.5) * pre;
+          double* o = row + 4 * (q0 + t);
+          o[0] = o[1] = o[2] = o[3] = 0.0;
+          if (mu >= -l && mu <= l) {
+            o[0] = cu * Y[2 * (l * l + l + mu)];
+            o[1] = cu * Y[2 * (l * l + l + mu) + 1];
+          }
+          if (md >= -l && md <= l) {
+            o[2] = cd * Y[2 * (l * l + l + md)];
+            o[3] = cd * Y[2 * (l * l + l + md) + 1];
+          }
         }
       }
     }

@@ -23,6 +23,12 @@ MUTATIONS = {
     "r = 0 convention lost": ("row[0] = 1.0 / sqrt(4.0 * ORACLE_PI);", "row[0] = 0.0;"),
     "minimum image by floor": ("rint(d[c] / box)", "floor(d[c] / box)"),
     "Lagrange stencil shifted": ("int i0 = (int)floor(t) - 1;", "int i0 = (int)floor(t);"),
+    "spinor upper sign dropped": ("const double cu = s * sqrt(l + s * mj + 0.5) * pre",
+                                  "const double cu = sqrt(l + s * mj + 0.5) * pre"),
+    "spinor components swapped": ("mu = (int)lround(mj - 0.5), md = (int)lround(mj + 0.5)",
+                                  "mu = (int)lround(mj + 0.5), md = (int)lround(mj - 0.5)"),
+    "spinor normalisation": ("const double pre = 1.0 / sqrt(2.0 * l + 1.0);",
+                                      "const double pre = 1.0 / sqrt(2.0 * l + 2.0);"),
     "radial index off by one": ("((int64_t)s * radial_lstride + l) * n_rad", "((int64_t)s * radial_lstride + l + 1) * n_rad"),
 }
 
@@ -37,6 +43,7 @@ def test_planted_mistake_is_caught(tmp_path, name):
     env = dict(os.environ, SHM_ORACLE_SRC=str(mutated), SHM_ORACLE_BUILD_DIR=str(tmp_path / "build"))
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
            os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-           os.path.join(ROOT, "tests", "test_oracle_projector_pins.py")]
+           os.path.join(ROOT, "tests", "test_oracle_projector_pins.py"),
+           os.path.join(ROOT, "tests", "test_oracle_spinor_pins.py")]
     res = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"mutation '{name}' survived every pin:\n{res.stdout[-2000:]}"
