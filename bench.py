@@ -541,7 +541,33 @@ def extra_serving(args, shm, torch, inputs, stream, peaks, peaks_src):
     return res
 
 
-EXTRA_WORKLOADS: list = [extra_complex, extra_projectors, extra_serving]
+def extra_spinor(args, shm, torch, inputs, stream, peaks, peaks_src):
+    """Spin-1/2 spinor harmonics (Eq. 7) on the 192^3 grid: 2 (lmax+1)^2 two-component
+    complex spinors per point (FP64: 6,400 B per point, 45 GB per launch)."""
+    res = {}
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    nh = (LMAX + 1) ** 2
+    g = inputs.dft_grid_points(N_SIDE)
+    for dt, name, es in ((torch.float64, "fp64", 8), (torch.float32, "fp32", 4)):
+        p = torch.from_numpy(g).to(device="cuda", dtype=dt)
+        out = torch.empty((p.shape[0], 2 * nh, 2, 2), dtype=dt, device="cuda")
+        fn = lambda: shm.eval_spinor(p, LMAX, out=out, stream=stream)  # noqa: E731
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        per, _ = timed_launches(fn, max(5, min(args.steps, 20)), stream)
+        ms = statistics.mean(per)
+        gbs = p.shape[0] * (3 + 8 * nh) * es / (ms * 1e-3) / 1e9
+        res[f"spinor_dft_grid_192cubed_{name}_lmax9"] = {
+            "value": p.shape[0] * 2 * nh / (ms * 1e-3), "unit": "spinor harmonics/s", "kernel_ms": ms,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                         "peak_source": peaks_src}}
+        del out, p
+        torch.cuda.empty_cache()
+    return res
+
+
+EXTRA_WORKLOADS: list = [extra_complex, extra_spinor, extra_projectors, extra_serving]
 
 
 def main():

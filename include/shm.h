@@ -1,5 +1,5 @@
 /*
- * shm.h -- C ABI of libshm: real spherical harmonics R_l^m (l <= 9) on a B300.
+ * shm.h -- C ABI of libshm: spherical harmonics (real, complex, spin-1/2 spinor) on a B300.
  *
  * The operation is the one defined in "SHarmonic: A fast and accurate
  * implementation of spherical harmonics for electronic-structure
@@ -14,7 +14,8 @@
  *   - evaluated in normalised Cartesian coordinates x/r, y/r, z/r
  *     (Sec. II Eq. 8: the harmonics are polynomials there);
  *   - at r = 0 every harmonic is 0 except R_0^0 = 1/sqrt(4 pi) (Sec. II);
- *   - l is limited to 9, as in the paper (Sec. III).
+ *   - l is limited to 9, as in the paper (Sec. III), except for the real rows
+ *     of shm_eval, which extend the same recurrence to l = 16 (SHM_LMAX_EXT).
  *
  * Conventions shared by every entry point:
  *   - Pointers named "device" must point to device memory of the current CUDA
@@ -63,7 +64,7 @@ typedef enum {
 /* shm_eval_ex flags */
 #define SHM_NORMALIZED_INPUT 0x1u /* points are already x/r, y/r, z/r: skip the r work */
 
-/* Number of harmonics for lmax: (lmax+1)^2. */
+/* Number of harmonics for lmax: (lmax+1)^2 (0 for lmax outside 0..16). */
 int shm_num_harmonics(int lmax);
 
 /*
@@ -352,6 +353,29 @@ shm_status shm_eval_complex(const void* points, int64_t n, int lmax, shm_dtype d
  * Nothing is allocated.  Errors: as shm_eval.
  */
 shm_status shm_eval_angles(const void* angles, int64_t n, int lmax, shm_dtype dtype, void* out, void* stream);
+
+/*
+ * shm_eval_spinor -- the spin-1/2 spinor harmonics (Sec. II Eq. 7) for every
+ * orbital l <= lmax and both total angular momenta j = l + s/2 (s = +1; and
+ * s = -1 when l >= 1), m_j = -j .. j, at n points:
+ *   upper = s sqrt((l + s m_j + 1/2) / (2l+1)) Y_l^{m_j - 1/2}
+ *   lower =   sqrt((l - s m_j + 1/2) / (2l+1)) Y_l^{m_j + 1/2}
+ * with Y_l^m the complex harmonics of shm_eval_complex (Y_l^m = 0 for |m| > l).
+ *   points, n, lmax (0..9), dtype, flags, stream : as shm_eval_ex.
+ *   out : device, [n][2 (lmax+1)^2][2][2] of dtype: spinor q, component
+ *         (0 = upper, 1 = lower), (Re, Im).  Spinor order: l ascending; in
+ *         each l first j = l - 1/2, then j = l + 1/2; m_j ascending, i.e.
+ *         q = 2 l^2 + (s < 0 ? 0 : 2l) + (m_j + j).  16-byte (FP64) or
+ *         8-byte (FP32) alignment of out enables the vector store path.
+ * FP64 rows: the hybrid real rows times binary64 coefficients (within 1e-13
+ * of the l-shell norm sqrt((2l+1)/4pi)); FP32 rows as shm_eval.  Nothing is
+ * allocated.  Errors: as shm_eval (lmax outside 0..9: SHM_EINVAL).
+ */
+shm_status shm_eval_spinor(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags, void* out,
+                           void* stream);
+
+/* Spinor harmonics per point for lmax: 2 (lmax+1)^2 (-1 for lmax outside 0..9). */
+int shm_num_spinors(int lmax);
 
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* shm_last_error(void);

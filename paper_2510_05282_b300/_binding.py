@@ -71,6 +71,10 @@ def _declare(L):
     L.shm_eval_complex.restype = i32
     L.shm_eval_angles.argtypes = [vp, i64, i32, i32, vp, vp]
     L.shm_eval_angles.restype = i32
+    L.shm_eval_spinor.argtypes = [vp, i64, i32, i32, u32, vp, vp]
+    L.shm_eval_spinor.restype = i32
+    L.shm_num_spinors.argtypes = [i32]
+    L.shm_num_spinors.restype = i32
     L.shm_num_harmonics.argtypes = [i32]
     L.shm_num_harmonics.restype = i32
     L.shm_last_error.argtypes = []
@@ -148,6 +152,35 @@ def eval_complex(points, lmax: int, out=None, normalized: bool = False, stream=N
     flags = SHM_NORMALIZED_INPUT if normalized else 0
     check(lib().shm_eval_complex(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
     return torch.view_as_complex(out.view(n, num_harmonics(lmax), 2))
+
+
+def num_spinors(lmax: int) -> int:
+    """Spinor harmonics per point: 2 (lmax+1)^2."""
+    n = lib().shm_num_spinors(int(lmax))
+    if n < 0:
+        raise ShmError(1, "lmax must be in 0..9")
+    return n
+
+
+def eval_spinor(points, lmax: int, out=None, normalized: bool = False, stream=None):
+    """Spin-1/2 spinor harmonics (Eq. 7) for l <= lmax at device points [n, 3]
+    -> complex CUDA tensor [n, 2 (lmax+1)^2, 2]: spinor q (l ascending, j = l - 1/2
+    before j = l + 1/2, m_j ascending), component (upper, lower)."""
+    import torch
+    if not (isinstance(points, torch.Tensor) and points.is_cuda):
+        raise TypeError("points must be a CUDA tensor")
+    if points.dim() != 2 or points.shape[1] != 3 or not points.is_contiguous():
+        raise ValueError("points must be a contiguous [n, 3] tensor")
+    code = _dtype_code(points.dtype)
+    n = points.shape[0]
+    ns = num_spinors(lmax)
+    if out is None:
+        out = torch.empty((n, ns, 2, 2), dtype=points.dtype, device=points.device)
+    elif out.dtype != points.dtype or not out.is_contiguous() or out.numel() != 4 * n * ns:
+        raise ValueError("out must be a contiguous [n, 2 (lmax+1)^2, 2, 2] tensor of the points dtype")
+    flags = SHM_NORMALIZED_INPUT if normalized else 0
+    check(lib().shm_eval_spinor(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
+    return torch.view_as_complex(out.view(n, ns, 2, 2))
 
 
 def eval_angles(angles, lmax: int, out=None, stream=None):

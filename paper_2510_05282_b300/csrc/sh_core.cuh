@@ -431,9 +431,25 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
 // the same operations on the same operands as sh_row_hybrid, so the rows are
 // bitwise identical to it; all m-recurrences advance together, one l at a
 // time, which exposes ~l independent chains to the scheduler.
-template <int LMAX, bool CX = false, int PHMAX = 37, typename Store, typename Phase>
+// NEG_FF: the m < 0 values are handed to store as normalised float-float
+// (type ff) instead of binary64 -- the m <= -2 ones before their conversion,
+// the m = -1 ones converted exactly to 48 bits -- for callers that keep
+// working on them with FP32 instructions.
+template <int LMAX, bool CX = false, int PHMAX = 37, bool NEG_FF = false, typename Store, typename Phase>
 __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, double zb, Store&& store,
                                                      Phase&& phase) {
+  auto store_neg_d = [&](int k, int kbase, double v) {
+    if constexpr (NEG_FF)
+      store(k, kbase, ff_from_double(v));
+    else
+      store(k, kbase, v);
+  };
+  auto store_neg_ff = [&](int k, int kbase, ff v) {
+    if constexpr (NEG_FF)
+      store(k, kbase, v);
+    else
+      store(k, kbase, ff_to_double(v));
+  };
   const ff X = ff_from_double(xb), Y = ff_from_double(yb), Z = ff_from_double(zb);
   ff A[LMAX + 1], B[LMAX + 1], q1[LMAX + 1], q2[LMAX + 1];
   double d1[2], d2[2];
@@ -472,12 +488,12 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
           store(kc, k0, s);
         } else {
           store(kc + 1, k0, (l == 1) ? Sd<CX>(1, 1) * xb : s * xb);
-          store(kc - 1, k0, (l == 1) ? Sd<CX>(1, 1) * yb : s * yb);
+          store_neg_d(kc - 1, k0, (l == 1) ? Sd<CX>(1, 1) * yb : s * yb);
         }
       } else {  // float-float columns
         if (l == m) {
           store(kc + m, k0, ff_to_double(ff_mul_c(A[m], Shi<CX>(m, m), Slo<CX>(m, m))));
-          store(kc - m, k0, ff_to_double(ff_mul_c(B[m], Shi<CX>(m, m), Slo<CX>(m, m))));
+          store_neg_ff(kc - m, k0, ff_mul_c(B[m], Shi<CX>(m, m), Slo<CX>(m, m)));
           q2[m] = {1.0f, 0.0f};
           q1[m] = Z;
         } else {
@@ -491,7 +507,7 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
             q1[m] = q;
           }
           store(kc + m, k0, ff_to_double(ff_mul(sv, A[m])));
-          store(kc - m, k0, ff_to_double(ff_mul(sv, B[m])));
+          store_neg_ff(kc - m, k0, ff_mul(sv, B[m]));
         }
       }
     }

@@ -118,6 +118,6 @@ const char* shm_status_string(shm_status s) {
   return "SHM_UNKNOWN";
 }
 
-int shm_num_harmonics(int lmax) { return (lmax >= 0 && lmax <= SHM_LMAX_CAP) ? (lmax + 1) * (lmax + 1) : 0; }
+int shm_num_harmonics(int lmax) { return (lmax >= 0 && lmax <= SHM_LMAX_EXT) ? (lmax + 1) * (lmax + 1) : 0; }
 
 }  // extern "C"

@@ -10,8 +10,12 @@
 // arithmetic.  Output: [n][(lmax+1)^2][2] (re, im) of the dtype.
 //
 // FP64 rows use the hybrid arithmetic in l-major order (binary64 for 1/r and
-// m = 0, 1, float-float for m >= 2), staged one group of l-shells at a time;
-// FP32 rows use the FP32 row code, staged a full row at a time.
+// m = 0, 1, float-float for m >= 2), staged as real values one group of
+// l-shells at a time; the copy-out pairs them into (re, im) with a per-CTA map
+// and writes 16-byte complex values.  (Scattering the values into complex
+// slots as they are produced raised the row code's register use from 96 to
+// 162 and cut the resident warps.)  FP32 rows use the FP32 row code, staged a
+// full row at a time in complex layout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,16 +48,37 @@ __device__ __forceinline__ void cx_store(T* c, int k, int k0, T v) {
 }
 
 constexpr int kCxTPB64 = 128;
-constexpr int kCxPhase = 19;  // l-shell values per phase: 2 x 19 complex components staged per row
+constexpr int kCxPhase = 37;  // real values staged per row and phase
 constexpr int kCxTPB32 = 64;
+
+// Copy-out map of complex slot k = l*l + l + m: the real values it is made of
+// (ka = index of R_l^{|m|}, kb = index of R_l^{-|m|}) and their signs.
+__device__ __forceinline__ uint32_t cx_map_entry(int k) {
+  int l = 0;
+  while ((l + 1) * (l + 1) <= k) ++l;
+  const int kc = l * l + l, m = k - kc, mu = m < 0 ? -m : m;
+  uint32_t e = (uint32_t)(kc + mu) | ((uint32_t)(kc - mu) << 10);
+  if (m == 0) e |= 1u << 29;                            // Y_l^0 = R_l^0
+  else if (m > 0 && (m & 1)) e |= (1u << 30) | (1u << 31);  // (-1)^m (a + i b)
+  else if (m < 0) e |= 1u << 31;                        // a - i b
+  return e;
+}
+
+__device__ __forceinline__ double flip_if(double v, uint32_t bit) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((unsigned long long)bit << 63));
+}
 
 template <int LMAX>
 __global__ void __launch_bounds__(kCxTPB64) k_eval_cx64(const double* __restrict__ pts, int64_t n,
-                                                        double* __restrict__ out, int64_t ntiles, int normalized) {
+                                                        double* __restrict__ out, int64_t ntiles, int normalized,
+                                                        int vec) {
   constexpr int L2 = NH<LMAX>::value;
-  constexpr int RS = (2 * LPhases<LMAX, kCxPhase>::max_width()) | 1;
+  constexpr int RS = LPhases<LMAX, kCxPhase>::max_width() | 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t cxmap[L2];
   double* tile = reinterpret_cast<double*>(smem_raw);
+  for (int k = threadIdx.x; k < L2; k += kCxTPB64) cxmap[k] = cx_map_entry(k);
+  __syncthreads();
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t p0 = t * kCxTPB64;
     const int rows = (int)min((int64_t)kCxTPB64, n - p0);
@@ -77,18 +102,27 @@ __global__ void __launch_bounds__(kCxTPB64) k_eval_cx64(const double* __restrict
       }
     }
     double* row = tile + threadIdx.x * RS;
-    auto store = [&](int k, int k0, double v) { cx_store(row, k, k0, v); };
+    auto store = [&](int k, int k0, double v) { row[k - k0] = v; };
     auto flush = [&](int k0, int w) {
       if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
-        for (int c = 0; c < 2 * w; ++c) row[c] = (k0 == 0 && c == 0) ? kInvSqrt4Pi : 0.0;
+        for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
       }
       __syncthreads();
-      const int w2 = 2 * w;
-      const int nv = rows * w2;
+      const int nv = rows * w;
       for (int j = threadIdx.x; j < nv; j += kCxTPB64) {
-        const int r = j / w2;
-        const int c = j - r * w2;
-        __stcs(out + (p0 + r) * (2 * L2) + 2 * k0 + c, tile[r * RS + c]);
+        const int r = j / w;
+        const int c = j - r * w;
+        const uint32_t e = cxmap[k0 + c];
+        const double* src = tile + r * RS - k0;
+        const double re = flip_if(src[e & 1023u], (e >> 30) & 1u);
+        const double im = (e & (1u << 29)) ? 0.0 : flip_if(src[(e >> 10) & 1023u], e >> 31);
+        const int64_t o = (p0 + r) * L2 + k0 + c;
+        if (vec) {
+          __stcs(reinterpret_cast<double2*>(out) + o, make_double2(re, im));
+        } else {
+          __stcs(out + 2 * o, re);
+          __stcs(out + 2 * o + 1, im);
+        }
       }
       __syncthreads();
     };
@@ -132,7 +166,7 @@ shm_status cx_launch(const void* pts, int64_t n, bool f64, void* out, bool norma
   const int dev = current_device();
   if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
   const int tpb = f64 ? kCxTPB64 : kCxTPB32;
-  const size_t smem = f64 ? (size_t)kCxTPB64 * ((2 * LPhases<LMAX, kCxPhase>::max_width()) | 1) * 8
+  const size_t smem = f64 ? (size_t)kCxTPB64 * (LPhases<LMAX, kCxPhase>::max_width() | 1) * 8
                           : (size_t)kCxTPB32 * ((2 * NH<LMAX>::value) | 1) * 4;
   const void* kern = f64 ? (const void*)k_eval_cx64<LMAX> : (const void*)k_eval_cx32<LMAX>;
   int& b = bps[f64 ? 1 : 0][dev];
@@ -147,7 +181,7 @@ shm_status cx_launch(const void* pts, int64_t n, bool f64, void* out, bool norma
   const int64_t ntiles = (n + tpb - 1) / tpb;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * b);
   if (f64)
-    k_eval_cx64<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const double*)pts, n, (double*)out, ntiles, normalized);
+    k_eval_cx64<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const double*)pts, n, (double*)out, ntiles, normalized, vec);
   else
     k_eval_cx32<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const float*)pts, n, (float*)out, ntiles, normalized, vec);
   cudaError_t e = cudaGetLastError();

@@ -174,9 +174,13 @@ inline int effective_variant(bool fp64, int v, int lmax = 0) {
   return v;
 }
 
-// Default choice before (or without) tuning: staged 128 (the FP32 path is
-// HBM-bound and wants coalesced stores; FP64 is retuned by shm_autotune).
-constexpr int kDefaultVariant = 0;
+// Default choice before (or without) tuning, the fastest measured on a
+// 7M-point workload at l = 9: phased-hybrid-128 for FP64 rows (2.3 ms against
+// 4.1 ms for staged-128), staged-64 for FP32 rows (HBM-bound, coalesced
+// stores).  Above l = 9 the FP64 default runs phased-128 (effective_variant).
+constexpr int kDefaultVariantF64 = 11;
+constexpr int kDefaultVariantF32 = 1;
+inline int default_variant(bool fp64) { return fp64 ? kDefaultVariantF64 : kDefaultVariantF32; }
 
 // chosen[dtype][lmax] (-1 = default)
 int g_choice[2][SHM_LMAX_EXT + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
@@ -236,7 +240,7 @@ template <typename T, int LMAX>
 shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t s, int variant) {
   if (variant < 0) {
     variant = g_choice[sizeof(T) == 8 ? 1 : 0][LMAX];
-    if (variant < 0) variant = kDefaultVariant;
+    if (variant < 0) variant = default_variant(sizeof(T) == 8);
   }
   variant = effective_variant(sizeof(T) == 8, variant, LMAX);
   if constexpr (LMAX > SHM_LMAX_CAP) {
@@ -550,7 +554,7 @@ extern "C" const char* shm_eval_variant(int lmax, shm_dtype dtype) {
   if (lmax < 0 || lmax > SHM_LMAX_EXT || (dtype != SHM_F32 && dtype != SHM_F64)) return "";
   ensure_tune_cache();
   const int v = g_choice[dtype == SHM_F64 ? 1 : 0][lmax];
-  return kVariantNames[effective_variant(dtype == SHM_F64, v < 0 ? kDefaultVariant : v, lmax)];
+  return kVariantNames[effective_variant(dtype == SHM_F64, v < 0 ? default_variant(dtype == SHM_F64) : v, lmax)];
 }
 
 extern "C" int shm_eval_variant_count(void) { return shm::kNumVariants; }

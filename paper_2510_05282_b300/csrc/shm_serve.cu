@@ -137,7 +137,7 @@ __device__ __forceinline__ void serve_tile(const ServeChunk& c, long long p, int
       z = (T)dz;
     }
     T* row = tile + threadIdx.x * RS;
-    sh_point<LMAX>(x, y, z, false, [&](int k, T v) { row[k] = v; });
+    sh_point<LMAX, true>(x, y, z, false, [&](int k, T v) { row[k] = v; });  // FP64: the hybrid rows of shm_eval
   }
   __syncthreads();
   T* dst = reinterpret_cast<T*>(c.out) + p * L2;

@@ -40,8 +40,10 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_num_harmonics_and_status_strings(L):
-    assert [L.shm_num_harmonics(l) for l in range(10)] == [(l + 1) ** 2 for l in range(10)]
-    assert L.shm_num_harmonics(10) == 0 and L.shm_num_harmonics(-1) == 0
+    assert [L.shm_num_harmonics(l) for l in range(17)] == [(l + 1) ** 2 for l in range(17)]
+    assert L.shm_num_harmonics(17) == 0 and L.shm_num_harmonics(-1) == 0
+    assert [L.shm_num_spinors(l) for l in range(10)] == [2 * (l + 1) ** 2 for l in range(10)]
+    assert L.shm_num_spinors(10) == -1 and L.shm_num_spinors(-1) == -1
     assert L.shm_status_string(0) == b"SHM_OK"
     assert L.shm_status_string(5) == b"SHM_ETIMEOUT"
 
