@@ -328,30 +328,32 @@ __device__ __forceinline__ ff ff_from_double(double d) {
 }
 
 // float-float (normalised: |lo| <= ulp(hi)/2) -> binary64.  The double of hi
-// is assembled from its bits; lo, read from its own bits, is added in units
-// of that double's ulp directly on the bit pattern (at most 2^29 units, so
-// the significand never carries past its top bit; a borrow below a power of
-// two counts in the finer ulp there, hence the doubling).  Parts of lo below
-// one ulp of the double are truncated.  hi = 0 (or a float denormal) maps to
-// +0; NaN and infinity carry over.  Branch-free.
+// is assembled from its bits (exponent rebiased by 1023 - 127 = 896,
+// significand extended by 29 zero bits); lo is added in units of that
+// double's ulp 2^(E-179) directly on the bit pattern.  With lo = ml 2^(El-150)
+// (ml the 24-bit significand), that count is n = (ml << 5) >> (E - El - 24),
+// a right shift of 0..31 for a normalised pair (32 or more gives 0, which
+// also covers lo = 0); n < 2^29, so the significand never carries past its
+// top bit.  Below a power of two the double's ulp halves, so an opposite-sign
+// lo counts twice there.  Parts of lo below one ulp are truncated (result
+// within 1 ulp of hi + lo).  |hi| < 2^-63 (zero, denormal or tiny) maps to
+// +0 (absolute error < 1.1e-19); a NaN or infinite hi maps to NaN.
+// Branch-free, integer instructions only.
 __device__ __forceinline__ double ff_to_double(ff a) {
   const unsigned hb = __float_as_uint(a.hi);
-  const unsigned E = (hb >> 23) & 0xffu;
-  const unsigned M = hb & 0x7fffffu;
-  const unsigned Ed = E == 255u ? 2047u : E + 896u;
-  const unsigned hi32 = (hb & 0x80000000u) | (Ed << 20) | (M >> 3);
-  const long long base = (long long)(((unsigned long long)hi32 << 32) | ((unsigned long long)(M & 7u) << 29));
   const unsigned lb = __float_as_uint(a.lo);
-  const unsigned El = (lb >> 23) & 0xffu;
-  const unsigned ml = El != 0u ? ((lb & 0x7fffffu) | 0x800000u) : 0u;  // lo = ml * 2^(El-150)
-  const int sh = (int)El - (int)E + 29;                                   // lo in double ulps: ml * 2^sh
-  const unsigned up = ml << (sh > 0 ? sh : 0);
-  const unsigned dn = ml >> (sh < 0 ? (sh > -31 ? -sh : 31) : 0);
-  int n = (int)(sh >= 0 ? up : dn);
-  const bool opp = ((hb ^ lb) & 0x80000000u) != 0u;
-  n = opp ? -((M == 0u) ? 2 * n : n) : n;        // opposite signs shrink the magnitude
-  n = (E == 255u) ? 0 : n;
-  const long long bits = (E == 0u) ? 0ll : base + (long long)n;
+  const unsigned e = hb & 0x7f800000u;
+  const unsigned hi32 = (((hb & 0x7fffffffu) >> 3) + (896u << 20)) | (hb & 0x80000000u);
+  const unsigned lo32 = hb << 29;
+  const unsigned ml5 = ((lb << 5) & 0x0fffffe0u) | 0x10000000u;
+  const unsigned sh = (e >> 23) - ((lb >> 23) & 0xffu) - 24u;
+  unsigned n = __funnelshift_rc(ml5, 0u, sh);  // ml5 >> min(sh, 32)
+  const bool opp = (int)(hb ^ lb) < 0;
+  n = (opp && (hb & 0x7fffffu) == 0u) ? 2u * n : n;
+  const long long d = opp ? -(long long)n : (long long)n;
+  long long bits = (long long)(((unsigned long long)hi32 << 32) | lo32) + d;
+  bits = e < (64u << 23) ? 0ll : bits;
+  bits = e == 0x7f800000u ? 0x7ff8000000000000ll : bits;
   return __longlong_as_double(bits);
 }
 

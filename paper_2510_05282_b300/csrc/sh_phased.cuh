@@ -1,0 +1,103 @@
+// The phased FP64 evaluator kernel, shared by shm_eval (Cartesian points)
+// and shm_eval_angles (theta, phi pairs).
+//
+// l-major evaluation (sh_row_lmajor / sh_row_hybrid_lmajor) staged one phase
+// of l-shells at a time (<= 37 values per row), so a tile needs ~1/3 of the
+// shared memory of a full-row tile and ~2.5x more warps fit on an SM; every
+// l-step advances up to 10 independent m-recurrences, which feeds the FP64
+// pipe with independent work.  Rows are written phase by phase (one
+// contiguous segment of each row per phase, in 16-byte pairs when the output
+// allows).  Results are bit-identical to the full-row variants.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sh_core.cuh"
+
+namespace shm {
+
+enum { kInPoints = 0, kInAngles = 1 };
+
+// Registers are capped so that five 128-thread CTAs fit an SM (96 per
+// thread, a few bytes of spill): measured 2.01 against 2.13 ms uncapped
+// (109 registers, four CTAs) on the 192^3 grid.
+template <int LMAX, int TPB, bool HYB, int IN = kInPoints>
+__global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased(const double* __restrict__ in, int64_t n,
+                                                                double* __restrict__ out, int64_t ntiles,
+                                                                int normalized, int vec) {
+  constexpr int L2 = NH<LMAX>::value;
+  constexpr int RS = LPhases<LMAX>::max_width() | 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* tile = reinterpret_cast<double*>(smem_raw);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * TPB;
+    const int rows = (int)min((int64_t)TPB, n - p0);
+    const bool valid = (int)threadIdx.x < rows;
+    bool origin = false;
+    double xb = 0.0, yb = 0.0, zb = 1.0;
+    if constexpr (IN == kInAngles) {
+      if (valid) {  // Eq. 3-4 read backwards: the unit vector of (theta, phi)
+        const int64_t p = p0 + threadIdx.x;
+        double st, ct, sp, cp;
+        sincos(in[2 * p], &st, &ct);
+        sincos(in[2 * p + 1], &sp, &cp);
+        xb = st * cp;
+        yb = st * sp;
+        zb = ct;
+      }
+    } else {
+      double x = 0.0, y = 0.0, z = 1.0;
+      if (valid) {
+        const int64_t p = p0 + threadIdx.x;
+        x = in[3 * p];
+        y = in[3 * p + 1];
+        z = in[3 * p + 2];
+      }
+      origin = valid && is_origin(x, y, z);
+      if (valid && !origin) {
+        if (normalized) {
+          xb = x;
+          yb = y;
+          zb = z;
+        } else {
+          unit_dir(x, y, z, xb, yb, zb);
+        }
+      }
+    }
+    double* row = tile + threadIdx.x * RS;
+    auto store = [&](int k, int k0, double v) { row[k - k0] = v; };
+    auto flush = [&](int k0, int w) {
+          if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
+            for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
+          }
+          __syncthreads();
+          if (vec && L2 % 2 == 0 && ((k0 | w) & 1) == 0) {
+            // pairs: the segment of every row starts on a 16-byte boundary
+            const int hw = w >> 1;
+            const int np = rows * hw;
+            for (int j = threadIdx.x; j < np; j += TPB) {
+              const int r = j / hw;
+              const int c = 2 * (j - r * hw);
+              const double* t = tile + r * RS + c;
+              __stcs(reinterpret_cast<double2*>(out + (p0 + r) * L2 + k0 + c), make_double2(t[0], t[1]));
+            }
+          } else {
+            const int nv = rows * w;
+            for (int j = threadIdx.x; j < nv; j += TPB) {
+              const int r = j / w;
+              const int c = j - r * w;
+              __stcs(out + (p0 + r) * L2 + k0 + c, tile[r * RS + c]);
+            }
+          }
+          __syncthreads();
+        };
+    if constexpr (HYB)
+      sh_row_hybrid_lmajor<LMAX>(xb, yb, zb, store, flush);
+    else
+      sh_row_lmajor<LMAX>(xb, yb, zb, store, flush);
+  }
+}
+
+}  // namespace shm

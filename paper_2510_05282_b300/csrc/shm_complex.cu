@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "sh_core.cuh"
+#include "sh_phased.cuh"
 #include "sh_tile.cuh"
 #include "shm_internal.h"
 
@@ -69,7 +70,7 @@ __device__ __forceinline__ double flip_if(double v, uint32_t bit) {
 }
 
 template <int LMAX>
-__global__ void __launch_bounds__(kCxTPB64) k_eval_cx64(const double* __restrict__ pts, int64_t n,
+__global__ void __launch_bounds__(kCxTPB64, 5) k_eval_cx64(const double* __restrict__ pts, int64_t n,
                                                         double* __restrict__ out, int64_t ntiles, int normalized,
                                                         int vec) {
   constexpr int L2 = NH<LMAX>::value;
@@ -235,11 +236,13 @@ extern "C" shm_status shm_eval_complex(const void* points, int64_t n, int lmax, 
 
 namespace shm {
 
-constexpr int kAngTPB = 64;
+constexpr int kAngTPB = 64;     // FP32 staged kernel
+constexpr int kAngTPB64 = 128;  // FP64 phased hybrid kernel
 
 template <typename T, int LMAX>
 __global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ ang, int64_t n, T* __restrict__ out,
                                                           int64_t ntiles, int vec) {
+  static_assert(sizeof(T) == 4, "FP64 angles use k_eval_phased");
   constexpr int L2 = TileShape<LMAX>::L2;
   constexpr int RS = TileShape<LMAX>::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -249,21 +252,11 @@ __global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ a
     const int rows = (int)min((int64_t)kAngTPB, n - p0);
     if ((int)threadIdx.x < rows) {
       const int64_t p = p0 + threadIdx.x;
-      const T th = ang[2 * p], ph = ang[2 * p + 1];
       T st, ct, sp, cp;
-      if constexpr (sizeof(T) == 8) {
-        sincos(th, &st, &ct);
-        sincos(ph, &sp, &cp);
-      } else {
-        sincosf(th, &st, &ct);
-        sincosf(ph, &sp, &cp);
-      }
+      sincosf(ang[2 * p], &st, &ct);
+      sincosf(ang[2 * p + 1], &sp, &cp);
       T* row = tile + threadIdx.x * RS;
-      auto store = [&](int k, T v) { row[k] = v; };
-      if constexpr (sizeof(T) == 8)
-        sh_row_hybrid<LMAX>(st * cp, st * sp, ct, store);
-      else
-        sh_row<LMAX>(st * cp, st * sp, ct, store);
+      sh_row<LMAX>(st * cp, st * sp, ct, [&](int k, T v) { row[k] = v; });
     }
     __syncthreads();
     copy_out_tile<T, L2, RS, kAngTPB>(tile, rows, out + p0 * L2, vec != 0);
@@ -271,27 +264,36 @@ __global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ a
   }
 }
 
+// FP64 angles run the phased hybrid evaluator (sh_phased.cuh) with angle
+// input; FP32 angles the staged kernel above.
 template <typename T, int LMAX>
 shm_status ang_launch(const T* ang, int64_t n, T* out, bool vec, cudaStream_t s) {
   constexpr int MAXDEV = 64;
   static int bps[MAXDEV] = {};
   const int dev = current_device();
   if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
-  const size_t smem = (size_t)kAngTPB * TileShape<LMAX>::RS * sizeof(T);
-  auto kern = k_eval_angles<T, LMAX>;
+  constexpr int TPB = sizeof(T) == 8 ? kAngTPB64 : kAngTPB;
+  const size_t smem = sizeof(T) == 8 ? (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * 8
+                                     : (size_t)TPB * TileShape<LMAX>::RS * sizeof(T);
+  const void* kern = sizeof(T) == 8 ? (const void*)k_eval_phased<LMAX, kAngTPB64, true, kInAngles>
+                                    : (const void*)k_eval_angles<float, LMAX>;
   if (bps[dev] == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_eval_angles)");
+    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(angles)");
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kAngTPB, smem);
-    if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_eval_angles)");
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TPB, smem);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(angles)");
     bps[dev] = std::max(b, 1);
   }
-  const int64_t ntiles = (n + kAngTPB - 1) / kAngTPB;
+  const int64_t ntiles = (n + TPB - 1) / TPB;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * bps[dev]);
-  kern<<<(unsigned)grid, kAngTPB, smem, s>>>(ang, n, out, ntiles, vec ? 1 : 0);
+  if constexpr (sizeof(T) == 8)
+    k_eval_phased<LMAX, kAngTPB64, true, kInAngles><<<(unsigned)grid, TPB, smem, s>>>(ang, n, out, ntiles, 0,
+                                                                                      vec ? 1 : 0);
+  else
+    k_eval_angles<float, LMAX><<<(unsigned)grid, TPB, smem, s>>>(ang, n, out, ntiles, vec ? 1 : 0);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail_cuda(e, "k_eval_angles launch");
+  if (e != cudaSuccess) return fail_cuda(e, "angles launch");
   return SHM_OK;
 }
 

@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "sh_core.cuh"
+#include "sh_phased.cuh"
 #include "sh_tile.cuh"
 #include "shm_internal.h"
 
@@ -65,65 +66,9 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
   }
 }
 
-// kPhased (FP64): l-major evaluation (sh_row_lmajor) staged one phase of
-// l-shells at a time (<= 37 values per row), so a tile needs ~1/3 of the
-// shared memory of a full-row tile and ~2.5x more warps fit on an SM; every
-// l-step advances up to 10 independent m-recurrences, which feeds the FP64
-// pipe with independent work.  Rows are written phase by phase (one
-// contiguous segment of each row per phase).  Results are bit-identical to
-// the other variants.  For FP32 this variant is the staged path.
+// kPhased / kPhasedHybrid (FP64): k_eval_phased of sh_phased.cuh.  For FP32
+// these variants are the staged path.
 enum { kPhased = 2, kPhasedHybrid = 4 };
-
-template <int LMAX, int TPB, bool HYB>
-__global__ void __launch_bounds__(TPB) k_eval_phased(const double* __restrict__ pts, int64_t n,
-                                                     double* __restrict__ out, int64_t ntiles, int normalized) {
-  constexpr int L2 = NH<LMAX>::value;
-  constexpr int RS = LPhases<LMAX>::max_width() | 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* tile = reinterpret_cast<double*>(smem_raw);
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t p0 = t * TPB;
-    const int rows = (int)min((int64_t)TPB, n - p0);
-    const bool valid = (int)threadIdx.x < rows;
-    double x = 0.0, y = 0.0, z = 1.0;
-    if (valid) {
-      const int64_t p = p0 + threadIdx.x;
-      x = pts[3 * p];
-      y = pts[3 * p + 1];
-      z = pts[3 * p + 2];
-    }
-    const bool origin = valid && is_origin(x, y, z);
-    double xb = 0.0, yb = 0.0, zb = 1.0;
-    if (valid && !origin) {
-      if (normalized) {
-        xb = x;
-        yb = y;
-        zb = z;
-      } else {
-        unit_dir(x, y, z, xb, yb, zb);
-      }
-    }
-    double* row = tile + threadIdx.x * RS;
-    auto store = [&](int k, int k0, double v) { row[k - k0] = v; };
-    auto flush = [&](int k0, int w) {
-          if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
-            for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
-          }
-          __syncthreads();
-          const int nv = rows * w;
-          for (int j = threadIdx.x; j < nv; j += TPB) {
-            const int r = j / w;
-            const int c = j - r * w;
-            __stcs(out + (p0 + r) * L2 + k0 + c, tile[r * RS + c]);
-          }
-          __syncthreads();
-        };
-    if constexpr (HYB)
-      sh_row_hybrid_lmajor<LMAX>(xb, yb, zb, store, flush);
-    else
-      sh_row_lmajor<LMAX>(xb, yb, zb, store, flush);
-  }
-}
 
 // Launch variants the tuner chooses among (index = variant id).
 struct Variant {
@@ -227,10 +172,7 @@ shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool 
   }
   const int64_t ntiles = (n + TPB - 1) / TPB;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * blocks_per_sm[dev]);
-  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid) && sizeof(T) == 8)
-    kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0);
-  else
-    kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0, vec ? 1 : 0);
+  kern<<<(unsigned)grid, TPB, smem, stream>>>(pts, n, out, ntiles, normalized ? 1 : 0, vec ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_eval launch");
   return SHM_OK;

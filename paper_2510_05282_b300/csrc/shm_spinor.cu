@@ -157,7 +157,7 @@ __device__ __forceinline__ void spinor_copy_out32(const float* __restrict__ tile
 // FP64 rows: hybrid real rows in l-major order, staged one group of l-shells
 // at a time (as shm_eval's phased-hybrid variant).
 template <int LMAX, int TPB = kSpTPB64, int PH = kSpPhase>
-__global__ void __launch_bounds__(TPB) k_eval_spinor64(const double* __restrict__ pts, int64_t n,
+__global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_spinor64(const double* __restrict__ pts, int64_t n,
                                                        double* __restrict__ out, int64_t ntiles, int normalized,
                                                        int vec) {
   constexpr int L2 = NH<LMAX>::value;

@@ -93,14 +93,23 @@ def test_normalized_input_flag(oracle_mod):
 
 
 def test_unaligned_output_uses_scalar_path(oracle_mod):
+    """An output 8 but not 16 bytes aligned takes the scalar stores: same rows,
+    bitwise, as the 16-byte path, for every launch variant."""
     pts = inputs.random_sphere_points(1001, stream="tests", with_axes=False)
     p = torch.from_numpy(pts).cuda()
     buf = torch.empty(1001 * 100 + 1, dtype=torch.float64, device="cuda")
     out = buf[1:]                                  # 8-byte but not 16-byte aligned
     assert out.data_ptr() % 16 == 8
-    shm.eval_sh(p, 9, out=out)
-    torch.cuda.synchronize()
-    assert_normwise(out.view(1001, 100).cpu().numpy(), oracle_mod.real_sh(pts, 9), TOL_F64, "unaligned")
+    try:
+        for v in range(shm.eval_variant_count()):
+            shm.set_eval_variant(9, torch.float64, v)
+            shm.eval_sh(p, 9, out=out)
+            ref = shm.eval_sh(p, 9)
+            torch.cuda.synchronize()
+            assert torch.equal(out.view(1001, 100), ref), shm.eval_variant(9, torch.float64)
+            assert_normwise(out.view(1001, 100).cpu().numpy(), oracle_mod.real_sh(pts, 9), TOL_F64, "unaligned")
+    finally:
+        shm.set_eval_variant(9, torch.float64, -1)
 
 
 def test_bad_arguments_launch_nothing():
