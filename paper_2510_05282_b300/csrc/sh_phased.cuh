@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased(const double* __
             // pairs: the segment of every row starts on a 16-byte boundary
             const int hw = w >> 1;
             const int np = rows * hw;
+#pragma unroll 2  // two loads in flight per store: 1.94 -> 1.84 ms on the 192^3 grid (4: slower)
             for (int j = threadIdx.x; j < np; j += TPB) {
               const int r = j / hw;
               const int c = 2 * (j - r * hw);
