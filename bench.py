@@ -355,15 +355,15 @@ TRAFFIC_PER_POINT = {
     ("f64", "staged-64"): (21.318144e6 + 648.666112e6) / 884_736,
     ("f32", "staged-64"): (10.651648e6 + 294.209024e6) / 884_736,
 }
-# FP64 pipe instructions per point of the hybrid rows at lmax 9 (ncu: dadd +
-# dmul + dfma thread instructions / points of the 96^3 capture).
-HYBRID_DP_PER_POINT_L9 = 96
+# FP64 pipe instructions per point of the hybrid rows at lmax 9 (ncu
+# sass__inst_executed_per_opcode of the 96^3 capture: DMUL 54 + DFMA 20).
+HYBRID_DP_PER_POINT_L9 = 74
 
 
 def roofline_object(dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src, traffic, n):
     """The bound of the evaluator kernel: the all-FP64 rows are FP64-pipe bound
     (242 FP64 instructions per point against 824 B per point); the hybrid rows
-    (96 FP64 instructions per point) and the FP32 rows are bound by the HBM
+    (74 FP64 instructions per point) and the FP32 rows are bound by the HBM
     traffic of their output.  The other figures are given beside it."""
     fp64 = {"achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved_tflops / FP64_PEAK_TFLOPS,
