@@ -336,9 +336,13 @@ def run_gpu(args, rank, world):
                        "d2h_bytes_per_step": n * nh * es, "steps": e2e_steps,
                        "api": "shm_eval_host (pinned host in/out, 1M-point chunks double-buffered)"}
         del hin, hout, ws
-        rate, m, cores = cpu_oracle_rate(pts.astype(np.float64), LMAX, args.cpu_seconds)
+        pts64 = pts.astype(np.float64)
+        rate, m, cores = cpu_oracle_rate(pts64, LMAX, args.cpu_seconds)
+        rate1, m1, _ = cpu_oracle_rate(pts64, LMAX, min(2.0, args.cpu_seconds / 4), nthreads=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"first {m} of {n} grid points, lmax=9, FP64"}
+                                "sample": f"first {m} of {n} grid points, lmax=9, FP64",
+                                "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                                                "sample": f"first {m1} grid points, 1 thread"}}
         if args.extras:
             line["extra"] = run_extras(args, shm, torch, inputs, stream, peaks, peaks_src)
         print(json.dumps(line), flush=True)
@@ -403,8 +407,22 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
     sph = inputs.random_sphere_points(65_536)
     per, region = measure_eval(shm, torch, sph, torch.float64, LMAX, steps, 3, stream)
     ms = statistics.mean(per)
+    c_all, _, c_cores = cpu_oracle_rate(sph, LMAX, 1.0)
+    c_one, c_m1, _ = cpu_oracle_rate(sph, LMAX, 1.0, nthreads=1)
     res["random_sphere_65600_fp64_lmax9"] = {"value": sph.shape[0] * nh / (ms * 1e-3), "unit": UNIT,
-                                             "kernel_ms": ms}
+                                             "kernel_ms": ms,
+                                             "cpu_oracle": {"value": c_all, "cores": c_cores, "unit": UNIT},
+                                             "cpu_oracle_single_core": {"value": c_one, "cores": 1, "unit": UNIT,
+                                                                        "sample": f"first {c_m1} points"}}
+    # the 1M-point random-sphere set in FP32 (HBM-write bound, fits in HBM many times over)
+    sph32 = inputs.random_sphere_points(1 << 20).astype(np.float32)
+    per, region = measure_eval(shm, torch, sph32, torch.float32, LMAX, steps, 3, stream)
+    ms = statistics.mean(per)
+    gbs = sph32.shape[0] * (3 + nh) * 4 / (ms * 1e-3) / 1e9
+    res["random_sphere_1M_fp32_lmax9"] = {
+        "value": sph32.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                     "peak_source": peaks_src, "note": "420 MB out: partly absorbed by the 126 MB L2"}}
     # the all-FP64 arithmetic on the headline grid, for comparison with the tuned variant
     chosen = shm.eval_variant(LMAX, torch.float64)
     for v in range(shm.eval_variant_count()):
@@ -499,6 +517,15 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
                          "hbm_frac": gbs / hbm_peak, "unit": "GB/s", "peak_source": peaks_src,
                          "algorithmic_bytes": algo_bytes}}
         del out, ws
+    # the oracle on the same problem (all host cores): the CPU baseline of this workload
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.projectors(prob)
+    dt_cpu = time.perf_counter() - t0
+    res["projectors_512atoms_fp64"]["cpu_oracle"] = {"value": d.n_values / dt_cpu, "unit": "projector values/s",
+                                                     "cores": oracle.max_threads(0), "seconds": dt_cpu,
+                                                     "sample": "the whole problem"}
     return res
 
 

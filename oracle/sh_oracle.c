@@ -100,9 +100,11 @@ static void real_sh_from_angles(int lmax, double theta, double phi, double* row)
 
 static int check_lmax(int lmax) { return lmax >= 0 && lmax <= ORACLE_LMAX_CAP; }
 
+/* nthreads > 0: that many OpenMP threads; 0: every processor (also after an
+ * earlier call asked for fewer). */
 static void set_threads(int nthreads) {
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
 #else
   (void)nthreads;
 #endif

@@ -36,6 +36,16 @@ def per_l_max(err):
     return [float(err[:, l == ll].max()) if err.shape[0] else 0.0 for ll in range(int(l.max()) + 1)]
 
 
+def per_l_mean(err):
+    l = l_of_k(err.shape[1])
+    return [float(err[:, l == ll].mean()) if err.shape[0] else 0.0 for ll in range(int(l.max()) + 1)]
+
+
+def per_l_report(err):
+    """'l: max/mean' of a normwise error array, for the printed accuracy reports."""
+    return " ".join(f"{ll}:{a:.1e}/{b:.1e}" for ll, (a, b) in enumerate(zip(per_l_max(err), per_l_mean(err))))
+
+
 def assert_normwise(got, ref, tol, what=""):
     err = normwise_err(got, ref)
     if err.size == 0:

@@ -6,7 +6,7 @@ against the oracle at the FP32 inputs upcast exactly.
 import numpy as np
 import pytest
 
-from helpers import TOL_F32, TOL_F64, assert_normwise, normwise_err, per_l_max
+from helpers import TOL_F32, TOL_F64, assert_normwise, normwise_err, per_l_max, per_l_report
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -31,10 +31,13 @@ def gpu_eval(pts_np, lmax, dtype=torch.float64, normalized=False):
     return out.cpu().numpy()
 
 
-def test_random_sphere_fp64_all_points(oracle_mod):
+def test_random_sphere_fp64_all_points(oracle_mod, capsys):
     pts = inputs.random_sphere_points(65_536)          # 65,600 points incl. 64 on the axes
     got = gpu_eval(pts, 9)
-    assert_normwise(got, oracle_mod.real_sh(pts, 9), TOL_F64, "random sphere FP64")
+    ref = oracle_mod.real_sh(pts, 9)
+    with capsys.disabled():
+        print("\nFP64 random sphere 65,600, normwise error per l (max/mean):", per_l_report(normwise_err(got, ref)))
+    assert_normwise(got, ref, TOL_F64, "random sphere FP64")
 
 
 @pytest.mark.parametrize("lmax", list(range(10)))
@@ -210,7 +213,7 @@ def test_autotune_keeps_results_correct(oracle_mod):
     shm.set_eval_variant(9, torch.float64, -1)
 
 
-def test_dft_grid_fp64_full_size_sampled(oracle_mod):
+def test_dft_grid_fp64_full_size_sampled(oracle_mod, capsys):
     """192^3 grid (7.08M points, 5.7 GB out) in every launch configuration the
     tuner may pick for bench.py: sampled rows against the oracle; the addition
     theorem on every row."""
@@ -226,7 +229,12 @@ def test_dft_grid_fp64_full_size_sampled(oracle_mod):
             shm.set_eval_variant(9, torch.float64, v)
             out = shm.eval_sh(p, 9)
             torch.cuda.synchronize()
-            assert_normwise(out[rows_t].cpu().numpy(), ref, TOL_F64, f"192^3 grid sample, variant {v}")
+            got = out[rows_t].cpu().numpy()
+            if v == 11:  # the variant bench.py times
+                with capsys.disabled():
+                    print("\nFP64 192^3 grid sample (phased-hybrid-128), normwise error per l (max/mean):",
+                          per_l_report(normwise_err(got, ref)))
+            assert_normwise(got, ref, TOL_F64, f"192^3 grid sample, variant {v}")
             for l in range(10):
                 s = (out[:, l * l:(l + 1) ** 2] ** 2).sum(dim=1)
                 dev = (s - (2 * l + 1) / (4 * np.pi)).abs().max().item()
@@ -243,7 +251,7 @@ def test_fp32_grid_and_sphere_per_l_report(oracle_mod, capsys):
     got = gpu_eval(sph, 9, dtype=torch.float32)
     err = normwise_err(got, oracle_mod.real_sh(sph.astype(np.float64), 9))
     with capsys.disabled():
-        print("\nFP32 1M sphere, max normwise error per l:", " ".join(f"{e:.2e}" for e in per_l_max(err)))
+        print("\nFP32 1M sphere, normwise error per l (max/mean):", per_l_report(err))
     assert float(err.max()) <= TOL_F32
     grid = inputs.dft_grid_points(192).astype(np.float32)
     p = torch.from_numpy(grid).cuda()

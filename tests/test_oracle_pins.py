@@ -316,3 +316,14 @@ def test_high_l_against_40_digit_explicit_sum(oracle_mod):
                 for mm, v in vals.items():
                     worst = max(worst, abs(float(v) - O[i, l * l + l + mm]) / math.sqrt((2 * l + 1) / (4 * math.pi)))
     assert worst <= 4e-14, worst
+
+
+def test_thread_count_resets_to_all_processors(oracle_mod):
+    """nthreads = 0 means every processor, also right after a 1-thread call
+    (the CPU baselines time both)."""
+    import os
+    assert oracle_mod.max_threads(1) == 1
+    full = oracle_mod.max_threads(0)
+    assert full >= 1 and full == oracle_mod.max_threads(0)
+    if (os.cpu_count() or 1) > 1:
+        assert full > 1
