@@ -306,24 +306,37 @@ __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 // only: on a B300 the int<->float and float<->double conversion instructions
 // issue to the same narrow pipe as FP64 arithmetic.
 
-// binary64 -> float-float: hi = d with its significand truncated to 24 bits
-// (exact), lo = the remaining 29 bits truncated to a float significand
-// (relative error < 2^-24 of lo, i.e. < 2^-48 of d).  |d| below 2^-74 maps to
-// 0 (absolute error < 2^-73); NaN and |d| >= 2^128 map to a NaN/infinite hi.
-// Branch-free (selects only), so unrolled callers stay one basic block.
+// binary64 -> float-float, both parts rounded to nearest (ties away from
+// zero): hi = d rounded to a 24-bit significand (an add of half a unit to the
+// bit pattern, whose carry moves into the exponent by itself); the remainder
+// d - hi is an integer count of d's ulp below 2^29 in magnitude, of the
+// opposite sign when hi was rounded up, and lo is that count rounded to 24
+// bits.  |hi + lo - d| <= 2^-49 |d| with no bias (a truncating conversion
+// biases every coordinate towards zero, and the biases add up along the
+// recurrences: 9e-14 instead of 4e-14 normwise at l = 9).  |d| below 2^-74
+// maps to 0 (absolute error < 2^-73); NaN and |d| >= 2^128 map to a
+// NaN/infinite hi.  Branch-free (selects only).
 __device__ __forceinline__ ff ff_from_double(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const unsigned hi32 = (unsigned)(b >> 32);
-  const unsigned sign = hi32 & 0x80000000u;
-  const int e = (int)((hi32 >> 20) & 0x7ffu) - 1023;  // unbiased exponent
-  const bool tiny = e < -74, big = e > 127;
-  const unsigned ef = big ? 255u : (unsigned)(e + 127);
-  const unsigned mf = (unsigned)((b >> 29) & 0x7fffffull) | ((big && (b << 12) != 0ull) ? 0x400000u : 0u);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;         // unbiased exponent of d
+  const unsigned low = (unsigned)(b & 0x1fffffffull);      // the 29 bits below hi's significand
+  const bool up = low >= 0x10000000u;
+  const unsigned long long bh = (b & ~0x1fffffffull) + (up ? 0x20000000ull : 0ull);
+  const int eh = (int)((bh >> 52) & 0x7ffu) - 1023;        // hi's exponent (one more after a carry)
+  const bool tiny = e < -74, big = eh > 127;
+  const unsigned ef = big ? 255u : (unsigned)(eh + 127);
+  const unsigned mf = (unsigned)((bh >> 29) & 0x7fffffull) | ((big && (b << 12) != 0ull) ? 0x400000u : 0u);
   const unsigned hib = tiny ? 0u : (sign | (ef << 23) | mf);
-  const unsigned rem = (unsigned)(b & 0x1fffffffull);  // the 29 bits below hi: rem * 2^(e-52)
-  const int p = 31 - __clz(rem | 1u);                  // top set bit, 0..28
-  const unsigned m = p >= 23 ? rem >> (p - 23) : rem << (23 - p);
-  const unsigned lob = (tiny || big || rem == 0u) ? 0u : (sign | ((unsigned)(p + e + 75) << 23) | (m & 0x7fffffu));
+  const unsigned mag = up ? 0x20000000u - low : low;       // |d - hi| in units of 2^(e-52)
+  const unsigned lsign = up ? (sign ^ 0x80000000u) : sign;
+  int p = 31 - __clz(mag | 1u);                            // top set bit, 0..29
+  const int sh = p - 23;
+  unsigned m = sh > 0 ? (mag + (1u << (sh - 1))) >> sh : mag << (-sh);  // 24-bit significand, rounded
+  const bool carry = m >> 24;                              // rounding reached 2^24
+  m = carry ? m >> 1 : m;
+  p += carry ? 1 : 0;
+  const unsigned lob = (tiny || big || mag == 0u) ? 0u : (lsign | ((unsigned)(p + e + 75) << 23) | (m & 0x7fffffu));
   return {__uint_as_float(hib), __uint_as_float(lob)};
 }
 
