@@ -28,6 +28,7 @@
 #include <string>
 
 #include "sh_core.cuh"
+#include "sh_tile.cuh"
 #include "shm_internal.h"
 
 namespace shm {
@@ -103,6 +104,12 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
   __shared__ int64_t warp_sums[32];
   __shared__ int64_t carry;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (fp32) {  // FP32 radial tables, spread over every CTA of the grid
+    const int64_t nt = (int64_t)P.n_species * P.lstride * P.n_rad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < nt; i += (int64_t)gridDim.x * blockDim.x)
+      P.rad32[i] = (float)P.radial[i];
+  }
+  if (blockIdx.x != 0) return;  // the rest is one CTA's work
   if (tid == 0) {
     *P.counter = 0ull;
     *P.err = 0u;
@@ -173,8 +180,6 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
       const double I_cl = fmin(fmax(I, -2147483000.0), 2147483000.0);
       P.etab[i] = make_int2((int)I_cl, __float_as_int((float)(C - I)));
     }
-    const int64_t nt = (int64_t)P.n_species * P.lstride * P.n_rad;
-    for (int64_t i = tid; i < nt; i += blockDim.x) P.rad32[i] = (float)P.radial[i];
     for (int64_t a = tid; a < P.n_atoms; a += blockDim.x) {
       AtomF32 A;
 #pragma unroll
@@ -196,6 +201,18 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
 // integer division, int<->float conversion and float rounding-to-int issue to
 // the same narrow pipe as FP64 arithmetic; these replacements use integer and
 // FP32 instructions only.
+
+// CTAs of the set-up launch: one, plus enough to convert the FP32 radial
+// tables (float conversions issue to the narrow FP64-class pipe, so one SM
+// alone would take tens of microseconds for 80k values).
+inline unsigned setup_grid(const ProjParams& P, shm_dtype dtype) {
+  if (dtype != SHM_F32) return 1u;
+  const int64_t nt = (int64_t)P.n_species * P.lstride * P.n_rad;
+  const int64_t g = (nt + 1023) / 1024;
+  const int dev = current_device();
+  const int64_t cap = dev >= 0 ? sm_count(dev) : 1;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
 
 // floor(n / ng) for 0 <= n < 2^31 (Granlund and Montgomery, "Division by
 // invariant integers using multiplication", PLDI 1994, unsigned case: m and
@@ -399,19 +416,38 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
 // ---------------------------------------------------------------------------
 // Persistent main kernel.
 
-// Copies rows [0, rows) of a staged tile (row stride RS) to dst[rows * L2].
-// The row of element j is floor(j / L2) = umulhi(j, ceil(2^32 / L2)), exact
-// for j < 2^32 / L2^2 (here j < 128 * 100): no division instructions, which
-// on a B300 would issue conversions to the narrow FP64-class pipe.
+// Copies rows [0, rows) of a staged tile (row stride RS) to dst[rows * L2],
+// with 16-byte stores between a scalar head (up to the first 16-byte
+// boundary of dst) and a scalar tail.  For odd L2 the tile rows are
+// contiguous (RS = L2), so element j is tile[j]; otherwise its row is
+// floor(j / L2) = umulhi(j, ceil(2^32 / L2)), exact for j < 2^32 / L2^2 (here
+// j < 128 * 100): no division instructions, which on a B300 would issue
+// conversions to the narrow FP64-class pipe.
 template <typename T>
 __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int rows, int L2, int RS,
                                               T* __restrict__ dst) {
+  constexpr int E = Vec16<T>::n;
+  using V = typename Vec16<T>::type;
   const int nv = rows * L2;
   const unsigned inv = L2 > 1 ? (unsigned)((0x100000000ull + (unsigned)L2 - 1) / (unsigned)L2) : 0u;
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-    const int r = L2 > 1 ? (int)__umulhi((unsigned)j, inv) : j;
-    __stcs(dst + j, tile[r * RS + (j - r * L2)]);
+  const bool flat = RS == L2;
+  auto src = [&](int j) {
+    if (flat) return j;
+    const int r = (int)__umulhi((unsigned)j, inv);
+    return r * RS + (j - r * L2);
+  };
+  const int head = min(nv, (int)(((16u - ((unsigned)(uintptr_t)dst & 15u)) & 15u) / sizeof(T)));
+  for (int j = threadIdx.x; j < head; j += blockDim.x) __stcs(dst + j, tile[src(j)]);
+  const int nq = (nv - head) / E;
+  V* d = reinterpret_cast<V*>(dst + head);
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const int j = head + q * E;
+    T v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = tile[src(j + i)];
+    st_stream(d + q, v);
   }
+  for (int j = head + nq * E + threadIdx.x; j < nv; j += blockDim.x) __stcs(dst + j, tile[src(j)]);
 }
 
 // Atoms whose tile table a CTA keeps in shared memory (int32 entries); larger
@@ -424,35 +460,39 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
   T* tile = reinterpret_cast<T*>(smem_raw);
   int* tt = reinterpret_cast<int*>(smem_raw + tile_bytes);
   __shared__ long long s_next;
+  __shared__ int s_atom;
   const double inv_box = 1.0 / P.box, inv_rmin = 1.0 / P.r_min, inv_dlog = 1.0 / P.dlog;
   // exact tile count, from the table the set-up kernel built earlier on this stream
   const int64_t total_tiles = P.tile_offsets[P.n_atoms];
   const bool cached = P.n_atoms + 1 <= kSmemAtoms;
   if (cached)
     for (int i = threadIdx.x; i <= P.n_atoms; i += kProjTPB) tt[i] = (int)P.tile_offsets[i];
-  if (threadIdx.x == 0) s_next = (long long)atomicAdd(P.counter, 1ull);
+  __syncthreads();
+  // owning atom of tile t: the last a with tile_offsets[a] <= t (one thread
+  // searches, for the next tile while the others work on the current one)
+  auto owner = [&](int64_t t) {
+    int64_t lo = 0, hi = P.n_atoms - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if ((cached ? (int64_t)tt[mid] : P.tile_offsets[mid]) <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    return (int)lo;
+  };
+  if (threadIdx.x == 0) {
+    s_next = (long long)atomicAdd(P.counter, 1ull);
+    s_atom = s_next < total_tiles ? owner(s_next) : 0;
+  }
   __syncthreads();
   for (;;) {
     const int64_t t = s_next;
+    const int64_t a = s_atom;
     if (t >= total_tiles) break;
-    __syncthreads();  // every thread has read s_next
-    if (threadIdx.x == 0) s_next = (long long)atomicAdd(P.counter, 1ull);  // next tile, fetched early
-    // owning atom: the last a with tile_offsets[a] <= t
-    int64_t lo = 0, hi = P.n_atoms - 1;
-    if (cached) {
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if ((int64_t)tt[mid] <= t) lo = mid;
-        else hi = mid - 1;
-      }
-    } else {
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (P.tile_offsets[mid] <= t) lo = mid;
-        else hi = mid - 1;
-      }
+    __syncthreads();  // every thread has read s_next and s_atom
+    if (threadIdx.x == 0) {  // next tile and its atom, fetched early
+      s_next = (long long)atomicAdd(P.counter, 1ull);
+      s_atom = s_next < total_tiles ? owner(s_next) : 0;
     }
-    const int64_t a = lo;
     const int64_t pa0 = P.point_offsets[a], pa1 = P.point_offsets[a + 1];
     const int64_t c = t - (cached ? (int64_t)tt[a] : P.tile_offsets[a]);
     const int64_t p0 = pa0 + c * kProjTPB;
@@ -620,7 +660,7 @@ extern "C" shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dty
     if ((st = check_device_range(out, (size_t)prob->n_values * es, "out")) != SHM_OK) return st;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  k_proj_setup<<<1, 1024, 0, s>>>(P, kProjTPB, dtype == SHM_F32 ? 1 : 0);
+  k_proj_setup<<<setup_grid(P, dtype), 1024, 0, s>>>(P, kProjTPB, dtype == SHM_F32 ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
   if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
@@ -703,7 +743,7 @@ extern "C" shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_d
   }
   cudaStream_t s = (cudaStream_t)stream;
   // k_proj_setup clears the work counter and the error word before anything reads them
-  k_proj_setup<<<1, 1024, 0, s>>>(P, kProjTPB, dtype == SHM_F32 ? 1 : 0);
+  k_proj_setup<<<setup_grid(P, dtype), 1024, 0, s>>>(P, kProjTPB, dtype == SHM_F32 ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
   if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
