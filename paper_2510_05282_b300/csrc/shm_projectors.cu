@@ -292,8 +292,9 @@ __device__ __forceinline__ float interp4(const Lagrange4<float>& L, const float*
 
 // One row (lmax = LMAX): interpolate f_0..f_LMAX at the stencil, then write
 // f_l(r) R_l^m into row[0..(LMAX+1)^2).  tab points at f_{s,0}[i0].
+// (dx, dy, dz) is the displacement, or with `unit` its unit vector.
 template <int LMAX, typename T>
-__device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, const Lagrange4<T>& L,
+__device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool unit, const Lagrange4<T>& L,
                                          const T* __restrict__ tab, int n_rad, T* __restrict__ row) {
   T f[LMAX + 1];
 #pragma unroll
@@ -304,25 +305,25 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, const La
     for (int k = 1; k < NH<LMAX>::value; ++k) row[k] = (T)0;
     return;
   }
-  T xb, yb, zb;
-  unit_dir(dx, dy, dz, xb, yb, zb);
+  T xb = dx, yb = dy, zb = dz;
+  if (!unit) unit_dir(dx, dy, dz, xb, yb, zb);
   sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
 }
 
 template <typename T>
-__device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin, const Lagrange4<T>& L,
-                                                  const T* tab, int n_rad, T* row) {
+__device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin, bool unit,
+                                                  const Lagrange4<T>& L, const T* tab, int n_rad, T* row) {
   switch (lmax) {
-    case 0: proj_row<0>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    case 1: proj_row<1>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    case 2: proj_row<2>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    case 3: proj_row<3>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    case 4: proj_row<4>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    case 5: proj_row<5>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    case 6: proj_row<6>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    case 7: proj_row<7>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    case 8: proj_row<8>(dx, dy, dz, origin, L, tab, n_rad, row); break;
-    default: proj_row<9>(dx, dy, dz, origin, L, tab, n_rad, row); break;
+    case 0: proj_row<0>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 1: proj_row<1>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 2: proj_row<2>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 3: proj_row<3>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 4: proj_row<4>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 5: proj_row<5>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 6: proj_row<6>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 7: proj_row<7>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 8: proj_row<8>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    default: proj_row<9>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
   }
 }
 
@@ -342,15 +343,26 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
   for (int c = 0; c < 3; ++c) d[c] = __dsub_rn(d[c], __dmul_rn(P.box, rint(d[c] * inv_box)));
   const bool origin = is_origin(d[0], d[1], d[2]);
   double t = 0.0;
+  bool unit = false;
   if (!origin) {
-    const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2])));
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+    double r;
+    if (r2 > 1e-280) {  // one reciprocal square root gives both r (for the log) and the unit vector
+      const double ri = rsqrt(r2);
+      r = r2 * ri;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) d[c] *= ri;
+      unit = true;
+    } else {
+      r = sqrt(r2);
+    }
     t = log(r * inv_rmin) * inv_dlog;
     t = fmin(fmax(t, 0.0), (double)(P.n_rad - 1));
   }
   const double tf = floor(t);
   const Lagrange4<double> L = lagrange_at<double>((int)tf, t - tf, P.n_rad);
   const double* tab = P.radial + (int64_t)s * P.lstride * P.n_rad + L.i0;
-  proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, L, tab, P.n_rad, row);
+  proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, unit, L, tab, P.n_rad, row);
 }
 
 // FP32 row.  The displacement in grid units, (i - U) - frac with U = floor of
@@ -410,7 +422,7 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
   }
   const Lagrange4<float> L = lagrange_at<float>(it, u, P.n_rad);
   const float* tab = P.rad32 + (int64_t)s * P.lstride * P.n_rad + L.i0;
-  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, L, tab, P.n_rad, row);
+  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, false, L, tab, P.n_rad, row);
 }
 
 // ---------------------------------------------------------------------------
