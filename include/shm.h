@@ -178,8 +178,9 @@ typedef struct {
 size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dtype);
 
 /*
- * shm_projectors -- the fused projector values, one persistent launch (plus a
- * one-CTA set-up launch) on `stream`.
+ * shm_projectors -- the fused projector values, one persistent launch after a
+ * set-up launch on `stream` (one CTA; for SHM_F32 also one CTA per 1,024
+ * table values, up to the SM count, that convert the radial tables).
  *   dtype     : SHM_F64 (FP64 arithmetic, double out) or SHM_F32 (FP32
  *               arithmetic on FP32 copies of the tables, float out; grid
  *               displacements are formed exactly before rounding to float,
