@@ -292,9 +292,9 @@ shm_status shm_serve_destroy(shm_server* server);
 
 /* Point i of a generated request (points == NULL) with this seed, as double
  * x, y, z: SplitMix64 counter words 4i..4i+3 mapped with correctly rounded
- * IEEE operations only, so any binary64 implementation reproduces it
- * exactly (host function; the device uses the same arithmetic).  FP32
- * requests round these to float. */
+ * IEEE +, -, * only (on doubles assembled from the words' bits), so any
+ * binary64 implementation reproduces it exactly (host function; the device
+ * uses the same arithmetic).  FP32 requests round these to float. */
 void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3]);
 
 /*

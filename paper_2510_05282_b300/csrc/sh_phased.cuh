@@ -20,6 +20,50 @@ namespace shm {
 
 enum { kInPoints = 0, kInAngles = 1 };
 
+// Rows of one tile: every thread of the CTA calls this with the unit vector
+// of its point (xb, yb, zb; `origin` for r = 0); rows [0, rows) of the tile
+// are written to dst[r * L2 + k].  `tile` is the CTA's staging buffer of
+// TPB x (LPhases<LMAX>::max_width() | 1) doubles.  vec: dst is 16-byte
+// aligned (the copy-out then writes 16-byte pairs where L2 allows).
+template <int LMAX, int TPB, bool HYB>
+__device__ __forceinline__ void phased_rows(double xb, double yb, double zb, bool origin, int rows,
+                                            double* __restrict__ dst, bool vec, double* __restrict__ tile) {
+  constexpr int L2 = NH<LMAX>::value;
+  constexpr int RS = LPhases<LMAX>::max_width() | 1;
+  double* row = tile + threadIdx.x * RS;
+  auto store = [&](int k, int k0, double v) { row[k - k0] = v; };
+  auto flush = [&](int k0, int w) {
+    if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
+      for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
+    }
+    __syncthreads();
+    if (vec && L2 % 2 == 0 && ((k0 | w) & 1) == 0) {
+      // pairs: the segment of every row starts on a 16-byte boundary
+      const int hw = w >> 1;
+      const int np = rows * hw;
+#pragma unroll 2  // two loads in flight per store: 1.94 -> 1.84 ms on the 192^3 grid (4: slower)
+      for (int j = threadIdx.x; j < np; j += TPB) {
+        const int r = j / hw;
+        const int c = 2 * (j - r * hw);
+        const double* t = tile + r * RS + c;
+        __stcs(reinterpret_cast<double2*>(dst + (int64_t)r * L2 + k0 + c), make_double2(t[0], t[1]));
+      }
+    } else {
+      const int nv = rows * w;
+      for (int j = threadIdx.x; j < nv; j += TPB) {
+        const int r = j / w;
+        const int c = j - r * w;
+        __stcs(dst + (int64_t)r * L2 + k0 + c, tile[r * RS + c]);
+      }
+    }
+    __syncthreads();
+  };
+  if constexpr (HYB)
+    sh_row_hybrid_lmajor<LMAX>(xb, yb, zb, store, flush);
+  else
+    sh_row_lmajor<LMAX>(xb, yb, zb, store, flush);
+}
+
 // Registers are capped so that five 128-thread CTAs fit an SM (96 per
 // thread, a few bytes of spill): measured 2.01 against 2.13 ms uncapped
 // (109 registers, four CTAs) on the 192^3 grid.
@@ -28,7 +72,6 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased(const double* __
                                                                 double* __restrict__ out, int64_t ntiles,
                                                                 int normalized, int vec) {
   constexpr int L2 = NH<LMAX>::value;
-  constexpr int RS = LPhases<LMAX>::max_width() | 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* tile = reinterpret_cast<double*>(smem_raw);
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -66,38 +109,7 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased(const double* __
         }
       }
     }
-    double* row = tile + threadIdx.x * RS;
-    auto store = [&](int k, int k0, double v) { row[k - k0] = v; };
-    auto flush = [&](int k0, int w) {
-          if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
-            for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
-          }
-          __syncthreads();
-          if (vec && L2 % 2 == 0 && ((k0 | w) & 1) == 0) {
-            // pairs: the segment of every row starts on a 16-byte boundary
-            const int hw = w >> 1;
-            const int np = rows * hw;
-#pragma unroll 2  // two loads in flight per store: 1.94 -> 1.84 ms on the 192^3 grid (4: slower)
-            for (int j = threadIdx.x; j < np; j += TPB) {
-              const int r = j / hw;
-              const int c = 2 * (j - r * hw);
-              const double* t = tile + r * RS + c;
-              __stcs(reinterpret_cast<double2*>(out + (p0 + r) * L2 + k0 + c), make_double2(t[0], t[1]));
-            }
-          } else {
-            const int nv = rows * w;
-            for (int j = threadIdx.x; j < nv; j += TPB) {
-              const int r = j / w;
-              const int c = j - r * w;
-              __stcs(out + (p0 + r) * L2 + k0 + c, tile[r * RS + c]);
-            }
-          }
-          __syncthreads();
-        };
-    if constexpr (HYB)
-      sh_row_hybrid_lmajor<LMAX>(xb, yb, zb, store, flush);
-    else
-      sh_row_lmajor<LMAX>(xb, yb, zb, store, flush);
+    phased_rows<LMAX, TPB, HYB>(xb, yb, zb, origin, rows, out + p0 * L2, vec != 0, tile);
   }
 }
 

@@ -10,12 +10,14 @@
 //     batch: a round robin over the admitted, unfinished requests taking at
 //     most chunk_points points from each and batch_points in total, so large
 //     requests progress in slices while newly admitted requests join at once;
-//     the chunk descriptors go to the device with one copy from pinned memory
-//     and one k_serve launch evaluates every tile of every chunk.
-// k_serve evaluates each tile with the same per-point code and the same
-// staged store as shm_eval (sh_core.cuh, sh_tile.cuh), so a request's rows do
-// not depend on which other requests shared its batches.  The kernel never
-// waits on anything: there is no device-side polling to bound.
+//     the chunk descriptors (FP64 chunks first, then FP32) go to the device
+//     with one copy from pinned memory, and one launch per dtype present
+//     (k_serve64, k_serve32) evaluates every tile of those chunks.
+// The batch kernels evaluate each tile with the per-point code and tile
+// structure of shm_eval's default variant for the dtype (sh_phased.cuh,
+// sh_core.cuh, sh_tile.cuh), so a request's rows equal shm_eval's bit for
+// bit and do not depend on which other requests shared its batches.  The
+// kernels never wait on anything: there is no device-side polling to bound.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,12 +35,12 @@
 #include <vector>
 
 #include "sh_core.cuh"
+#include "sh_phased.cuh"
 #include "sh_tile.cuh"
 #include "shm_internal.h"
 
 namespace shm {
 
-constexpr int kServeTPB = 64;
 constexpr int kMaxChunksPerBatch = 4096;
 
 struct ServeChunk {
@@ -56,9 +58,19 @@ struct ServeChunk {
 // ---------------------------------------------------------------------------
 // Counter-based point generator (SplitMix64 of Steele, Lea and Flood 2014 as
 // a counter-based source: word(seed, c) = mix(seed + (c + 1) * golden gamma)).
-// Only correctly rounded IEEE operations, written with _rn intrinsics so no
-// FMA contraction can change a bit: any binary64 implementation reproduces
-// the points exactly.
+// Point i takes the words c = 4i .. 4i+3:
+//   s = v(w0) - 3, t = v(w1) - 3 in [-1, 1), v(w) = the double with bits
+//       (w >> 12) | 0x4000000000000000 (in [2, 4), 52 random bits: exact);
+//   direction (2s (1 - t^2), 2s 2t, (1 - s^2)(1 + t^2)), whose length is
+//       (1 + s^2)(1 + t^2) (rational parametrisations of the circle in both
+//       angles), x negated when bit 0 of w3 is 1, z when bit 1 is;
+//   radius = the double with bits ((e + 1023) << 52) | (w2 >> 12),
+//       e = -10 + ((w3 >> 32) mod 14), i.e. 2^e (1 + m 2^-52);
+//   point = direction * radius.
+// Only correctly rounded +, -, * (no division, square root or integer to
+// float conversion, which on a B300 issue to the narrow FP64-class pipe), and
+// _rn intrinsics so that no FMA contraction changes a bit: any binary64
+// implementation reproduces the points exactly.
 
 __host__ __device__ inline unsigned long long splitmix_word(unsigned long long seed, unsigned long long c) {
   unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
@@ -67,118 +79,188 @@ __host__ __device__ inline unsigned long long splitmix_word(unsigned long long s
   return z ^ (z >> 31);
 }
 
+__host__ __device__ inline unsigned long long gen_v_bits(unsigned long long w) {
+  return (w >> 12) | 0x4000000000000000ull;
+}
+__host__ __device__ inline unsigned long long gen_radius_bits(unsigned long long w2, unsigned long long w3) {
+  const unsigned long long e = (w3 >> 32) % 14ull;  // e + 10
+  return ((e + 1013ull) << 52) | (w2 >> 12);
+}
+
 __device__ inline void gen_point_dev(unsigned long long seed, long long i, double& x, double& y, double& z) {
   const unsigned long long c = 4ull * (unsigned long long)i;
   const unsigned long long w0 = splitmix_word(seed, c), w1 = splitmix_word(seed, c + 1),
                            w2 = splitmix_word(seed, c + 2), w3 = splitmix_word(seed, c + 3);
-  const double two53 = 1.0 / 9007199254740992.0;
-  const double zb = __dsub_rn(2.0 * ((double)(w0 >> 11) * two53), 1.0);
-  const double t = __dsub_rn(2.0 * ((double)(w1 >> 11) * two53), 1.0);
-  const double t2 = __dmul_rn(t, t);
-  const double den = __dadd_rn(1.0, t2);
-  double cc = __ddiv_rn(__dsub_rn(1.0, t2), den);
-  const double ss = __ddiv_rn(2.0 * t, den);
-  if (w3 & 1ull) cc = -cc;
-  const double rho = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(zb, zb)));
-  const int e = (int)((w3 >> 32) % 14ull) - 10;
-  const double radius = ldexp(1.0 + (double)(w2 >> 12) * (1.0 / 4503599627370496.0), e);
-  x = __dmul_rn(__dmul_rn(rho, cc), radius);
-  y = __dmul_rn(__dmul_rn(rho, ss), radius);
-  z = __dmul_rn(zb, radius);
+  const double s = __dsub_rn(__longlong_as_double((long long)gen_v_bits(w0)), 3.0);
+  const double t = __dsub_rn(__longlong_as_double((long long)gen_v_bits(w1)), 3.0);
+  const double s2 = __dmul_rn(s, s), t2 = __dmul_rn(t, t);
+  const double s_2 = __dadd_rn(s, s), t_2 = __dadd_rn(t, t);
+  double dx = __dmul_rn(s_2, __dsub_rn(1.0, t2));
+  const double dy = __dmul_rn(s_2, t_2);
+  double dz = __dmul_rn(__dsub_rn(1.0, s2), __dadd_rn(1.0, t2));
+  if (w3 & 1ull) dx = -dx;
+  if (w3 & 2ull) dz = -dz;
+  const double radius = __longlong_as_double((long long)gen_radius_bits(w2, w3));
+  x = __dmul_rn(dx, radius);
+  y = __dmul_rn(dy, radius);
+  z = __dmul_rn(dz, radius);
 }
 
 // Host twin of gen_point_dev (host code is compiled without FMA contraction
-// on x86-64, whose baseline ISA has no FMA).
+// on x86-64, whose baseline ISA has no FMA; the volatiles keep every
+// intermediate a rounded binary64).
+static double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, sizeof d);
+  return d;
+}
 void gen_point_host(unsigned long long seed, long long i, double* xyz) {
   const unsigned long long c = 4ull * (unsigned long long)i;
   const unsigned long long w0 = splitmix_word(seed, c), w1 = splitmix_word(seed, c + 1),
                            w2 = splitmix_word(seed, c + 2), w3 = splitmix_word(seed, c + 3);
-  const double two53 = 1.0 / 9007199254740992.0;
-  volatile double zb = 2.0 * ((double)(w0 >> 11) * two53) - 1.0;
-  volatile double t = 2.0 * ((double)(w1 >> 11) * two53) - 1.0;
-  volatile double t2 = t * t;
-  volatile double den = 1.0 + t2;
-  double cc = (1.0 - t2) / den;
-  const double ss = (2.0 * t) / den;
-  if (w3 & 1ull) cc = -cc;
-  volatile double zz = zb * zb;
-  const double rho = std::sqrt(1.0 - zz);
-  const int e = (int)((w3 >> 32) % 14ull) - 10;
-  const double radius = std::ldexp(1.0 + (double)(w2 >> 12) * (1.0 / 4503599627370496.0), e);
-  volatile double rc = rho * cc, rs = rho * ss;
-  xyz[0] = rc * radius;
-  xyz[1] = rs * radius;
-  xyz[2] = zb * radius;
+  volatile double s = bits_to_double(gen_v_bits(w0)) - 3.0;
+  volatile double t = bits_to_double(gen_v_bits(w1)) - 3.0;
+  volatile double s2 = s * s, t2 = t * t;
+  volatile double s_2 = s + s, t_2 = t + t;
+  volatile double omt = 1.0 - t2, oms = 1.0 - s2, opt = 1.0 + t2;
+  volatile double dx = s_2 * omt;
+  volatile double dy = s_2 * t_2;
+  volatile double dz = oms * opt;
+  const double ddx = (w3 & 1ull) ? -dx : dx;
+  const double ddz = (w3 & 2ull) ? -dz : dz;
+  const double radius = bits_to_double(gen_radius_bits(w2, w3));
+  xyz[0] = ddx * radius;
+  xyz[1] = dy * radius;
+  xyz[2] = ddz * radius;
 }
 
 // ---------------------------------------------------------------------------
-// Batch kernel.
+// Batch kernels: one launch per dtype of the chunks in a batch, each with the
+// tile structure of shm_eval's default variant for that dtype, so a request's
+// rows are bitwise those shm_eval gives for the same points: FP64 rows are
+// the phased hybrid rows in 128-point tiles (96 registers, five CTAs per SM),
+// FP32 rows the staged FP32 rows in 64-point tiles.
+
+constexpr int kServeTPB64 = 128;
+constexpr int kServeTPB32 = 64;
+constexpr int kServeRS64 = LPhases<SHM_LMAX_CAP>::max_width() | 1;  // staged doubles per row, any lmax
+constexpr size_t kServeSmem64 = (size_t)kServeTPB64 * kServeRS64 * 8;
+constexpr size_t kServeSmem32 = (size_t)kServeTPB32 * TileShape<SHM_LMAX_CAP>::RS * 4;
 
 __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
-template <typename T, int LMAX>
-__device__ __forceinline__ void serve_tile(const ServeChunk& c, long long p, int rows, unsigned char* smem) {
+// The chunk owning tile t (the last chunk with tile0 <= t), read by thread 0
+// into shared memory.
+__device__ __forceinline__ void serve_find_chunk(const ServeChunk* __restrict__ chunks, int nchunks, long long t,
+                                                 ServeChunk& c) {
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nchunks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (chunks[mid].tile0 <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    c = chunks[lo];
+  }
+  __syncthreads();
+}
+
+template <int LMAX>
+__device__ __forceinline__ void serve_tile64(const ServeChunk& c, long long p, int rows, double* tile) {
+  constexpr int L2 = NH<LMAX>::value;
+  const bool valid = (int)threadIdx.x < rows;
+  double x = 0.0, y = 0.0, z = 1.0;
+  if (valid) {
+    const long long pi = p + threadIdx.x;
+    if (c.pts) {
+      const double* P = reinterpret_cast<const double*>(c.pts);
+      x = P[3 * pi];
+      y = P[3 * pi + 1];
+      z = P[3 * pi + 2];
+    } else {
+      gen_point_dev(c.seed, pi, x, y, z);
+    }
+  }
+  const bool origin = valid && is_origin(x, y, z);
+  double xb = 0.0, yb = 0.0, zb = 1.0;
+  if (valid && !origin) unit_dir(x, y, z, xb, yb, zb);
+  double* dst = reinterpret_cast<double*>(c.out) + p * L2;
+  phased_rows<LMAX, kServeTPB64, true>(xb, yb, zb, origin, rows, dst, aligned16(dst), tile);
+}
+
+template <int LMAX>
+__device__ __forceinline__ void serve_tile32(const ServeChunk& c, long long p, int rows, float* tile) {
   constexpr int L2 = TileShape<LMAX>::L2;
   constexpr int RS = TileShape<LMAX>::RS;
-  T* tile = reinterpret_cast<T*>(smem);
   if ((int)threadIdx.x < rows) {
     const long long pi = p + threadIdx.x;
-    T x, y, z;
+    float x, y, z;
     if (c.pts) {
-      const T* P = reinterpret_cast<const T*>(c.pts);
+      const float* P = reinterpret_cast<const float*>(c.pts);
       x = P[3 * pi];
       y = P[3 * pi + 1];
       z = P[3 * pi + 2];
     } else {
       double dx, dy, dz;
       gen_point_dev(c.seed, pi, dx, dy, dz);
-      x = (T)dx;
-      y = (T)dy;
-      z = (T)dz;
+      x = (float)dx;
+      y = (float)dy;
+      z = (float)dz;
     }
-    T* row = tile + threadIdx.x * RS;
-    sh_point<LMAX, true>(x, y, z, false, [&](int k, T v) { row[k] = v; });  // FP64: the hybrid rows of shm_eval
+    float* row = tile + threadIdx.x * RS;
+    sh_point<LMAX>(x, y, z, false, [&](int k, float v) { row[k] = v; });
   }
   __syncthreads();
-  T* dst = reinterpret_cast<T*>(c.out) + p * L2;
-  copy_out_tile<T, L2, RS, kServeTPB>(tile, rows, dst, aligned16(dst));
+  float* dst = reinterpret_cast<float*>(c.out) + p * L2;
+  copy_out_tile<float, L2, RS, kServeTPB32>(tile, rows, dst, aligned16(dst));
 }
 
-template <typename T>
-__device__ __forceinline__ void serve_tile_l(const ServeChunk& c, long long p, int rows, unsigned char* smem) {
-  switch (c.lmax) {
-    case 0: serve_tile<T, 0>(c, p, rows, smem); break;
-    case 1: serve_tile<T, 1>(c, p, rows, smem); break;
-    case 2: serve_tile<T, 2>(c, p, rows, smem); break;
-    case 3: serve_tile<T, 3>(c, p, rows, smem); break;
-    case 4: serve_tile<T, 4>(c, p, rows, smem); break;
-    case 5: serve_tile<T, 5>(c, p, rows, smem); break;
-    case 6: serve_tile<T, 6>(c, p, rows, smem); break;
-    case 7: serve_tile<T, 7>(c, p, rows, smem); break;
-    case 8: serve_tile<T, 8>(c, p, rows, smem); break;
-    default: serve_tile<T, 9>(c, p, rows, smem); break;
+__global__ void __launch_bounds__(kServeTPB64, 5) k_serve64(const ServeChunk* __restrict__ chunks, int nchunks,
+                                                            long long ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* tile = reinterpret_cast<double*>(smem_raw);
+  __shared__ ServeChunk c;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    serve_find_chunk(chunks, nchunks, t, c);
+    const long long p = c.p0 + (t - c.tile0) * kServeTPB64;
+    const int rows = (int)min((long long)kServeTPB64, c.p0 + c.n - p);
+    switch (c.lmax) {
+      case 0: serve_tile64<0>(c, p, rows, tile); break;
+      case 1: serve_tile64<1>(c, p, rows, tile); break;
+      case 2: serve_tile64<2>(c, p, rows, tile); break;
+      case 3: serve_tile64<3>(c, p, rows, tile); break;
+      case 4: serve_tile64<4>(c, p, rows, tile); break;
+      case 5: serve_tile64<5>(c, p, rows, tile); break;
+      case 6: serve_tile64<6>(c, p, rows, tile); break;
+      case 7: serve_tile64<7>(c, p, rows, tile); break;
+      case 8: serve_tile64<8>(c, p, rows, tile); break;
+      default: serve_tile64<9>(c, p, rows, tile); break;
+    }
+    __syncthreads();  // c and the tile are free
   }
 }
 
-__global__ void __launch_bounds__(kServeTPB) k_serve(const ServeChunk* __restrict__ chunks, int nchunks,
-                                                     long long ntiles) {
+__global__ void __launch_bounds__(kServeTPB32) k_serve32(const ServeChunk* __restrict__ chunks, int nchunks,
+                                                         long long ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tile = reinterpret_cast<float*>(smem_raw);
   __shared__ ServeChunk c;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    if (threadIdx.x == 0) {  // last chunk with tile0 <= t
-      int lo = 0, hi = nchunks - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (chunks[mid].tile0 <= t) lo = mid;
-        else hi = mid - 1;
-      }
-      c = chunks[lo];
+    serve_find_chunk(chunks, nchunks, t, c);
+    const long long p = c.p0 + (t - c.tile0) * kServeTPB32;
+    const int rows = (int)min((long long)kServeTPB32, c.p0 + c.n - p);
+    switch (c.lmax) {
+      case 0: serve_tile32<0>(c, p, rows, tile); break;
+      case 1: serve_tile32<1>(c, p, rows, tile); break;
+      case 2: serve_tile32<2>(c, p, rows, tile); break;
+      case 3: serve_tile32<3>(c, p, rows, tile); break;
+      case 4: serve_tile32<4>(c, p, rows, tile); break;
+      case 5: serve_tile32<5>(c, p, rows, tile); break;
+      case 6: serve_tile32<6>(c, p, rows, tile); break;
+      case 7: serve_tile32<7>(c, p, rows, tile); break;
+      case 8: serve_tile32<8>(c, p, rows, tile); break;
+      default: serve_tile32<9>(c, p, rows, tile); break;
     }
-    __syncthreads();
-    const long long p = c.p0 + (t - c.tile0) * kServeTPB;
-    const int rows = (int)min((long long)kServeTPB, c.p0 + c.n - p);
-    if (c.dtype == SHM_F64) serve_tile_l<double>(c, p, rows, smem_raw);
-    else serve_tile_l<float>(c, p, rows, smem_raw);
     __syncthreads();
   }
 }
@@ -277,7 +359,7 @@ struct shm_server {
   double harmonics = 0, busy_ms = 0;
   std::vector<double> lat;
   std::string thread_error;
-  int smem_ok = 0, grid = 0;
+  int grid64 = 0, grid32 = 0;  // resident CTAs of the two batch kernels on the device
 
   double now_ms() const { return std::chrono::duration<double, std::milli>(shm::Clock::now() - t0).count(); }
   void run();
@@ -375,27 +457,28 @@ bool shm_server::launch_locked() {
   if (!b) return false;
   int64_t budget = cfg.batch_points;
   int nch = 0;
-  long long tiles = 0;
   const size_t na = active.size();
   size_t visited = 0;
   if (rr >= na) rr = 0;
   size_t i = rr;
+  std::vector<shm::ServeChunk> picked;
   while (budget > 0 && nch < shm::kMaxChunksPerBatch && visited < na) {
     shm::Request& R = reqs[active[i]];
     const int64_t left = R.r.n - R.next_point;
     if (left > 0) {
       const int64_t take = std::min<int64_t>({left, cfg.chunk_points, budget});
-      shm::ServeChunk& c = b->host[nch++];
+      shm::ServeChunk c;
       c.pts = R.r.points;
       c.out = R.out;
       c.seed = R.r.seed;
       c.p0 = R.next_point;
-      c.tile0 = tiles;
+      c.tile0 = 0;
       c.n = (int)take;
       c.lmax = R.r.lmax;
       c.dtype = (int)R.r.dtype;
       c.pad = 0;
-      tiles += (take + shm::kServeTPB - 1) / shm::kServeTPB;
+      picked.push_back(c);
+      ++nch;
       R.next_point += take;
       budget -= take;
       b->parts.emplace_back(active[i], take);
@@ -409,11 +492,35 @@ bool shm_server::launch_locked() {
                               [&](uint64_t t) { return reqs[t].next_point >= reqs[t].r.n; }),
                active.end());
   if (nch == 0) return false;
+  // FP64 chunks first, then FP32; tiles numbered per dtype in its kernel's tile size
+  int n64 = 0;
+  long long tiles64 = 0, tiles32 = 0;
+  for (const auto& c : picked)
+    if (c.dtype == SHM_F64) {
+      b->host[n64] = c;
+      b->host[n64].tile0 = tiles64;
+      tiles64 += (c.n + shm::kServeTPB64 - 1) / shm::kServeTPB64;
+      ++n64;
+    }
+  int k = n64;
+  for (const auto& c : picked)
+    if (c.dtype != SHM_F64) {
+      b->host[k] = c;
+      b->host[k].tile0 = tiles32;
+      tiles32 += (c.n + shm::kServeTPB32 - 1) / shm::kServeTPB32;
+      ++k;
+    }
+  const int n32 = k - n64;
   cudaError_t e = cudaMemcpyAsync(b->dev, b->host, sizeof(shm::ServeChunk) * nch, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaEventRecord(b->start, stream);
-  if (e == cudaSuccess) {
-    const long long grid_l = std::max(1LL, std::min<long long>(tiles, grid));
-    shm::k_serve<<<(unsigned)grid_l, shm::kServeTPB, (size_t)shm::kServeTPB * 101 * 8, stream>>>(b->dev, nch, tiles);
+  if (e == cudaSuccess && n64 > 0) {
+    const long long g = std::max(1LL, std::min<long long>(tiles64, grid64));
+    shm::k_serve64<<<(unsigned)g, shm::kServeTPB64, shm::kServeSmem64, stream>>>(b->dev, n64, tiles64);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && n32 > 0) {
+    const long long g = std::max(1LL, std::min<long long>(tiles32, grid32));
+    shm::k_serve32<<<(unsigned)g, shm::kServeTPB32, shm::kServeSmem32, stream>>>(b->dev + n64, n32, tiles32);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(b->end, stream);
@@ -497,13 +604,18 @@ extern "C" shm_status shm_serve_create(const shm_serve_config* cfg, shm_server**
     if ((e = cudaMalloc(&b.dev, sizeof(ServeChunk) * kMaxChunksPerBatch)) != cudaSuccess)
       return cleanup(fail(SHM_ENOMEM, "cudaMalloc for batch descriptors failed"));
   }
-  const size_t smem = (size_t)kServeTPB * 101 * 8;
-  if ((e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_serve64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kServeSmem64)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_serve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kServeSmem32)) !=
+          cudaSuccess)
     return cleanup(fail_cuda(e, "cudaFuncSetAttribute(k_serve)"));
-  int bps = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_serve, kServeTPB, smem)) != cudaSuccess)
+  int b64 = 0, b32 = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_serve64, kServeTPB64, kServeSmem64)) !=
+          cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_serve32, kServeTPB32, kServeSmem32)) != cudaSuccess)
     return cleanup(fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_serve)"));
-  S->grid = sm_count(S->device) * std::max(bps, 1);
+  S->grid64 = sm_count(S->device) * std::max(b64, 1);
+  S->grid32 = sm_count(S->device) * std::max(b32, 1);
   S->t0 = Clock::now();
   cudaSetDevice(prev);
   S->sched = std::thread([S] { S->run(); });

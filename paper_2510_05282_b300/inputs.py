@@ -237,35 +237,35 @@ def counter_points(seed: int, n: int, start: int = 0) -> np.ndarray:
     """Points start..start+n-1 of the serving request with this seed, [n, 3] float64.
 
     Point i uses the four words c = 4i .. 4i+3 of splitmix64(seed, c) and only
-    correctly rounded IEEE operations (+, -, *, /, sqrt, exact scaling by 2^e),
-    so any IEEE binary64 implementation reproduces it bit for bit:
-      u1 = (w0 >> 11) 2^-53, zb = 2 u1 - 1;   t = 2 ((w1 >> 11) 2^-53) - 1;
-      c = (1 - t^2) / (1 + t^2), s = 2 t / (1 + t^2), c negated when bit 0 of w3 is 1;
-      rho = sqrt(1 - zb^2);  direction = (rho c, rho s, zb);
-      radius = 2^e (1 + (w2 >> 12) 2^-52), e = -10 + ((w3 >> 32) mod 14).
+    correctly rounded IEEE +, -, * on doubles assembled from bits, so any IEEE
+    binary64 implementation reproduces it bit for bit:
+      s = v(w0) - 3, t = v(w1) - 3, v(w) = double with bits (w >> 12) | 0x4000000000000000;
+      direction (2s (1 - t^2), 2s 2t, (1 - s^2)(1 + t^2)) (length (1 + s^2)(1 + t^2)),
+      x negated when bit 0 of w3 is 1, z when bit 1 is;
+      radius = double with bits ((e + 1023) << 52) | (w2 >> 12), e = -10 + ((w3 >> 32) mod 14);
+      point = direction * radius.
     """
     i = np.arange(start, start + n, dtype=np.uint64)
     w0 = splitmix64(seed, np.uint64(4) * i)
     w1 = splitmix64(seed, np.uint64(4) * i + np.uint64(1))
     w2 = splitmix64(seed, np.uint64(4) * i + np.uint64(2))
     w3 = splitmix64(seed, np.uint64(4) * i + np.uint64(3))
-    two53 = 2.0 ** -53
-    u1 = (w0 >> np.uint64(11)).astype(np.float64) * two53
-    zb = 2.0 * u1 - 1.0
-    t = 2.0 * ((w1 >> np.uint64(11)).astype(np.float64) * two53) - 1.0
-    t2 = t * t
-    den = 1.0 + t2
-    c = (1.0 - t2) / den
-    s = (2.0 * t) / den
-    c = np.where((w3 & np.uint64(1)) == np.uint64(1), -c, c)
-    rho = np.sqrt(1.0 - zb * zb)
+    hi = np.uint64(0x4000000000000000)
+    s = ((w0 >> np.uint64(12)) | hi).view(np.float64) - 3.0
+    t = ((w1 >> np.uint64(12)) | hi).view(np.float64) - 3.0
+    s2, t2 = s * s, t * t
+    s_2, t_2 = s + s, t + t
+    dx = s_2 * (1.0 - t2)
+    dy = s_2 * t_2
+    dz = (1.0 - s2) * (1.0 + t2)
+    dx = np.where((w3 & np.uint64(1)) == np.uint64(1), -dx, dx)
+    dz = np.where((w3 & np.uint64(2)) == np.uint64(2), -dz, dz)
     e = (w3 >> np.uint64(32)) % np.uint64(14)
-    radius = np.ldexp(1.0 + (w2 >> np.uint64(12)).astype(np.float64) * 2.0 ** -52,
-                      e.astype(np.int64) - 10)
+    radius = (((e + np.uint64(1013)) << np.uint64(52)) | (w2 >> np.uint64(12))).view(np.float64)
     pts = np.empty((n, 3), dtype=np.float64)
-    pts[:, 0] = (rho * c) * radius
-    pts[:, 1] = (rho * s) * radius
-    pts[:, 2] = zb * radius
+    pts[:, 0] = dx * radius
+    pts[:, 1] = dy * radius
+    pts[:, 2] = dz * radius
     return pts
 
 

@@ -27,12 +27,18 @@ def test_generator_bitwise_host_vs_python(L, seed):
 
 
 def test_generator_distribution():
+    """Directions (2s(1-t^2), 4st, (1-s^2)(1+t^2)) / ((1+s^2)(1+t^2)) with s, t
+    uniform on [-1, 1): z = (1-s^2)/(1+s^2), so E[z] = 0 (random sign) and
+    E[z^2] = int_0^1 ((1-s^2)/(1+s^2))^2 ds = 2 - pi/2 (checked by
+    quadrature); radii 2^e (1+m) (1+s^2)(1+t^2) in [2^-10, 64)."""
+    from scipy.integrate import quad
     pts = inputs.counter_points(7, 200_000)
     r = np.linalg.norm(pts, axis=1)
-    assert r.min() >= 2.0 ** -10 * 0.999 and r.max() < 2.0 ** 4 * 1.001
+    assert r.min() >= 2.0 ** -10 * 0.999 and r.max() < 64.0
     u = pts / r[:, None]
-    # z uniform on [-1, 1) (Archimedes): mean ~ 0, mean of z^2 ~ 1/3
-    assert abs(u[:, 2].mean()) < 0.01 and abs((u[:, 2] ** 2).mean() - 1 / 3) < 0.01
+    ez2 = quad(lambda s: ((1 - s * s) / (1 + s * s)) ** 2, 0, 1)[0]
+    assert abs(ez2 - (2 - np.pi / 2)) < 1e-12
+    assert abs(u[:, 2].mean()) < 0.01 and abs((u[:, 2] ** 2).mean() - ez2) < 0.01
     # every octant is populated
     octs = ((u > 0) * np.array([1, 2, 4])).sum(axis=1)
     assert np.bincount(octs, minlength=8).min() > 20_000
