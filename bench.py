@@ -204,6 +204,36 @@ def timed_launches(fn, steps, stream):
     return per, region
 
 
+def graph_replay_timing(torch, shm, p, out, lmax, launches=20, replays=5):
+    """The same launch captured `launches` times into one CUDA graph and
+    replayed: median ms per launch over the replays (outside the timed region;
+    the launch overhead it removes is negligible next to a ms-scale kernel)."""
+    try:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gs):
+            for _ in range(launches):
+                shm.eval_sh(p, lmax, out=out, stream=gs)
+        cur = torch.cuda.current_stream()
+        g.replay()
+        torch.cuda.synchronize()
+        reps = []
+        for _ in range(replays):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            g.replay()
+            e1.record(cur)
+            torch.cuda.synchronize()
+            reps.append(e0.elapsed_time(e1) / launches)
+        del g
+        return {"launches_per_graph": launches, "replays": replays,
+                "median_ms_per_launch": statistics.median(reps)}
+    except Exception as e:  # reported, never silently dropped
+        return {"error": repr(e)}
+
+
 def gpu_id_for_smi(dev):
     import torch
     try:
@@ -281,6 +311,7 @@ def run_gpu(args, rank, world):
         region = max_over_ranks(region, device="cuda")
         dist.barrier()
     clk = clocks.stop() if clocks else None
+    graph = graph_replay_timing(torch, shm, p, out, LMAX) if rank == 0 else None
 
     ms_per_step = region / args.steps
     value = world * n * nh / (ms_per_step * 1e-3)
@@ -309,7 +340,9 @@ def run_gpu(args, rank, world):
                    "points": n, "lmax": LMAX, "grid": f"{args.grid}^3, h=0.3 bohr",
                    "out_bytes_per_step": n * nh * 8, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "no flush: 170 MB input and 5.66 GB output per step exceed the 126 MB L2",
-                   "launch_variant": variant, "arithmetic": arithmetic, "autotune_probe_ms": tuned_ms},
+                   "launch_variant": variant, "arithmetic": arithmetic, "autotune_probe_ms": tuned_ms,
+                   "timing": {"mean_ms_per_launch": launch_ms, "median_ms_per_launch": statistics.median(per),
+                              "cuda_graph_replay": graph}},
         "roofline": roofline_object(args.dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src,
                                     traffic, n),
         "gpu_launches": args.steps,

@@ -28,6 +28,11 @@
  *   - Output layout: row-major [n][(lmax+1)^2]; column k = l*l + l + m, m from
  *     -l to l (the App. C order).
  *   - Non-finite inputs are not special-cased: NaN propagates.
+ *   - shm_eval, shm_eval_ex, shm_eval_complex, shm_eval_spinor and
+ *     shm_eval_angles allocate nothing and only enqueue kernels on `stream`,
+ *     so they can be captured into a CUDA graph once a call of the same
+ *     (lmax, dtype) outside the capture has done the one-time per-device
+ *     kernel set-up.
  *   - shm_last_error() returns a thread-local text for the last failure.
  */
 #ifndef SHM_H
