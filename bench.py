@@ -452,8 +452,11 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
     per, region = measure_eval(shm, torch, sph32, torch.float32, LMAX, steps, 3, stream)
     ms = statistics.mean(per)
     gbs = sph32.shape[0] * (3 + nh) * 4 / (ms * 1e-3) / 1e9
+    c32, c32_m, c32_cores = cpu_oracle_rate(sph32.astype(np.float64), LMAX, 2.0)
     res["random_sphere_1M_fp32_lmax9"] = {
         "value": sph32.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+        "cpu_oracle": {"value": c32, "cores": c32_cores, "unit": UNIT,
+                       "sample": f"first {c32_m} points (FP64 oracle at the upcast FP32 inputs)"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                      "peak_source": peaks_src, "note": "420 MB out: partly absorbed by the 126 MB L2"}}
     # the all-FP64 arithmetic on the headline grid, for comparison with the tuned variant
