@@ -38,15 +38,24 @@ __device__ __forceinline__ void phased_rows(double xb, double yb, double zb, boo
     }
     __syncthreads();
     if (vec && L2 % 2 == 0 && ((k0 | w) & 1) == 0) {
-      // pairs: the segment of every row starts on a 16-byte boundary
+      // pairs: the segment of every row starts on a 16-byte boundary.  Thread
+      // (rs, cp) = divmod(threadIdx, hw) copies column pair cp of rows rs,
+      // rs + RP, rs + 2 RP, ... (RP = TPB / hw rows per pass): one division
+      // per phase and incremental addresses, instead of a division per pair
+      // (1.85 -> 1.82 ms on the 192^3 grid).
       const int hw = w >> 1;
-      const int np = rows * hw;
-#pragma unroll 2  // two loads in flight per store: 1.94 -> 1.84 ms on the 192^3 grid (4: slower)
-      for (int j = threadIdx.x; j < np; j += TPB) {
-        const int r = j / hw;
-        const int c = 2 * (j - r * hw);
-        const double* t = tile + r * RS + c;
-        __stcs(reinterpret_cast<double2*>(dst + (int64_t)r * L2 + k0 + c), make_double2(t[0], t[1]));
+      const int RP = TPB / hw;
+      const int rs = (int)threadIdx.x / hw;
+      const int cp = (int)threadIdx.x - rs * hw;
+      if (rs < RP) {
+        const double* t = tile + rs * RS + 2 * cp;
+        double2* o = reinterpret_cast<double2*>(dst + (int64_t)rs * L2 + k0 + 2 * cp);
+#pragma unroll 2  // two loads in flight per store (1.94 -> 1.84 ms before this mapping; 4: slower)
+        for (int r = rs; r < rows; r += RP) {
+          __stcs(o, make_double2(t[0], t[1]));
+          t += RP * RS;
+          o += RP * L2 / 2;
+        }
       }
     } else {
       const int nv = rows * w;
