@@ -109,20 +109,30 @@ __global__ void __launch_bounds__(kCxTPB64, 5) k_eval_cx64(const double* __restr
         for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
       }
       __syncthreads();
-      const int nv = rows * w;
-      for (int j = threadIdx.x; j < nv; j += kCxTPB64) {
-        const int r = j / w;
-        const int c = j - r * w;
+      // thread (rs, c) = divmod(threadIdx, w) writes complex slot c of rows rs,
+      // rs + RP, ... (RP = TPB / w): its map entry and source offsets are
+      // read once per phase, the addresses advance by constant steps
+      const int RP = kCxTPB64 / w;
+      const int rs = (int)threadIdx.x / w;
+      const int c = (int)threadIdx.x - rs * w;
+      if (rs < RP) {
         const uint32_t e = cxmap[k0 + c];
-        const double* src = tile + r * RS - k0;
-        const double re = flip_if(src[e & 1023u], (e >> 30) & 1u);
-        const double im = (e & (1u << 29)) ? 0.0 : flip_if(src[(e >> 10) & 1023u], e >> 31);
-        const int64_t o = (p0 + r) * L2 + k0 + c;
-        if (vec) {
-          __stcs(reinterpret_cast<double2*>(out) + o, make_double2(re, im));
-        } else {
-          __stcs(out + 2 * o, re);
-          __stcs(out + 2 * o + 1, im);
+        const int ka = (int)(e & 1023u) - k0, kb = (int)((e >> 10) & 1023u) - k0;
+        const uint32_t fa = (e >> 30) & 1u, fb = e >> 31;
+        const bool zero_im = (e & (1u << 29)) != 0u;
+        const double* src = tile + rs * RS;
+        double* o = out + 2 * ((p0 + rs) * L2 + k0 + c);
+        for (int r = rs; r < rows; r += RP) {
+          const double re = flip_if(src[ka], fa);
+          const double im = zero_im ? 0.0 : flip_if(src[kb], fb);
+          if (vec) {
+            __stcs(reinterpret_cast<double2*>(o), make_double2(re, im));
+          } else {
+            __stcs(o, re);
+            __stcs(o + 1, im);
+          }
+          src += RP * RS;
+          o += 2 * RP * L2;
         }
       }
       __syncthreads();

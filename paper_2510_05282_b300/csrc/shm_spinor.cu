@@ -123,18 +123,31 @@ __device__ __forceinline__ void spinor_copy_out64(const double* __restrict__ til
                                                   const uint32_t* __restrict__ midx,
                                                   const SpinorCoef64* __restrict__ mcoef, double* __restrict__ dst,
                                                   bool vec) {
-  const int nc = 4 * w;
-  const int nv = rows * nc;
-  for (int j = threadIdx.x; j < nv; j += TPB) {
-    const int r = j / nc;
-    const int q = 4 * k0 + (j - r * nc);
-    const uint32_t e = midx[q];
-    const SpinorCoef64 cf = mcoef[q];
-    const double* src = tile + r * RS - k0;
-    const double re = cf.re * src[e & 0x7fffu];
-    const float2 b = reinterpret_cast<const float2*>(src)[(e >> 16) & 0x7fffu];
-    const double im = (e >> 31) ? 0.0 : ff_to_double(ff_mul_c(ff{b.x, b.y}, cf.im_hi, cf.im_lo));
-    st_out(dst + 2 * ((int64_t)r * NC + q), re, im, vec);
+  // thread (rs, c) = divmod(threadIdx, w) writes the components
+  // 4 k0 + c + u w, u = 0..3, of rows rs, rs + RP, ... (RP = TPB / w): the
+  // map entries are read once per phase, the addresses advance by constant
+  // steps, and each store instruction of a warp covers adjacent components
+  const int RP = TPB / w;
+  const int rs = (int)threadIdx.x / w;
+  const int c = (int)threadIdx.x - rs * w;
+  if (rs >= RP) return;
+  const int q0 = 4 * k0 + c;
+  uint32_t e[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) e[u] = midx[q0 + u * w];
+  const double* src = tile + rs * RS - k0;
+  double* o = dst + 2 * ((int64_t)rs * NC + q0);
+  for (int r = rs; r < rows; r += RP) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const SpinorCoef64 cf = mcoef[q0 + u * w];
+      const double re = cf.re * src[e[u] & 0x7fffu];
+      const float2 b = reinterpret_cast<const float2*>(src)[(e[u] >> 16) & 0x7fffu];
+      const double im = (e[u] >> 31) ? 0.0 : ff_to_double(ff_mul_c(ff{b.x, b.y}, cf.im_hi, cf.im_lo));
+      st_out(o + 2 * u * w, re, im, vec);
+    }
+    src += RP * RS;
+    o += 2 * (int64_t)RP * NC;
   }
 }
 
