@@ -27,7 +27,10 @@
  *     launched when an error is returned.
  *   - Output layout: row-major [n][(lmax+1)^2]; column k = l*l + l + m, m from
  *     -l to l (the App. C order).
- *   - Non-finite inputs are not special-cased: NaN propagates.
+ *   - A point with a NaN or infinite coordinate (or angle) gets NaN in every
+ *     value except the constant l = 0 ones (R_0^0, Y_0^0, the l = 0
+ *     spinors); imaginary parts that are zero by construction (complex
+ *     m = 0) may stay 0.  The other points of the call are unaffected.
  *   - shm_eval, shm_eval_ex, shm_eval_complex, shm_eval_spinor and
  *     shm_eval_angles allocate nothing and only enqueue kernels on `stream`,
  *     so they can be captured into a CUDA graph once a call of the same

@@ -340,23 +340,29 @@ __device__ __forceinline__ ff ff_from_double(double d) {
   return {__uint_as_float(hib), __uint_as_float(lob)};
 }
 
-// float-float (normalised: |lo| <= ulp(hi)/2) -> binary64.  The double of hi
-// is assembled from its bits (exponent rebiased by 1023 - 127 = 896,
-// significand extended by 29 zero bits); lo is added in units of that
+// float-float (normalised: |lo| <= ulp(hi)/2, hi finite) -> binary64.  The
+// double of hi is assembled from its bits (exponent rebiased by 1023 - 127 =
+// 896, significand extended by 29 zero bits); lo is added in units of that
 // double's ulp 2^(E-179) directly on the bit pattern.  With lo = ml 2^(El-150)
 // (ml the 24-bit significand), that count is n = (ml << 5) >> (E - El - 24),
 // a right shift of 0..31 for a normalised pair (32 or more gives 0, which
 // also covers lo = 0); n < 2^29, so the significand never carries past its
 // top bit.  Below a power of two the double's ulp halves, so an opposite-sign
 // lo counts twice there.  Parts of lo below one ulp are truncated (result
-// within 1 ulp of hi + lo).  |hi| < 2^-63 (zero, denormal or tiny) maps to
-// +0 (absolute error < 1.1e-19); a NaN or infinite hi maps to NaN.
-// Branch-free, integer instructions only.
-__device__ __forceinline__ double ff_to_double(ff a) {
+// within 1 ulp of hi + lo).  hi = +-0 gives +-0; a subnormal hi (|hi| <
+// 2^-126) gives a value below 2^-1042 in magnitude, and a subnormal lo (read
+// as if normal; it matters only for |hi| < 2^-71) an absolute error below
+// 2^-126.  A NaN or infinite hi
+// gives a meaningless finite value: the row code, which only meets finite
+// values for a finite direction, uses this form, and the callers write NaN
+// rows for non-finite points.  Branch-free, integer instructions only.
+__device__ __forceinline__ double ff_to_double_finite(ff a) {
   const unsigned hb = __float_as_uint(a.hi);
   const unsigned lb = __float_as_uint(a.lo);
   const unsigned e = hb & 0x7f800000u;
-  const unsigned hi32 = (((hb & 0x7fffffffu) >> 3) + (896u << 20)) | (hb & 0x80000000u);
+  const unsigned sg = hb & 0x80000000u;
+  unsigned hi32 = (((hb & 0x7fffffffu) >> 3) + (896u << 20)) | sg;
+  hi32 = e == 0u ? sg : hi32;
   const unsigned lo32 = hb << 29;
   const unsigned ml5 = ((lb << 5) & 0x0fffffe0u) | 0x10000000u;
   const unsigned sh = (e >> 23) - ((lb >> 23) & 0xffu) - 24u;
@@ -364,10 +370,24 @@ __device__ __forceinline__ double ff_to_double(ff a) {
   const bool opp = (int)(hb ^ lb) < 0;
   n = (opp && (hb & 0x7fffffu) == 0u) ? 2u * n : n;
   const long long d = opp ? -(long long)n : (long long)n;
-  long long bits = (long long)(((unsigned long long)hi32 << 32) | lo32) + d;
-  bits = e < (64u << 23) ? 0ll : bits;
-  bits = e == 0x7f800000u ? 0x7ff8000000000000ll : bits;
+  const long long bits = (long long)(((unsigned long long)hi32 << 32) | lo32) + d;
   return __longlong_as_double(bits);
+}
+// The same with a NaN or infinite hi mapped to NaN.
+__device__ __forceinline__ double ff_to_double(ff a) {
+  const double d = ff_to_double_finite(a);
+  return (__float_as_uint(a.hi) & 0x7f800000u) == 0x7f800000u ? __longlong_as_double(0x7ff8000000000000ll) : d;
+}
+
+// True if any component is infinite or NaN.  Every evaluator gives such a
+// point a row of NaN except the constant l = 0 value.
+__device__ __forceinline__ bool nonfinite3(double x, double y, double z) {
+  const int ex = 0x7ff00000;
+  return ((__double2hiint(x) & ex) == ex) | ((__double2hiint(y) & ex) == ex) | ((__double2hiint(z) & ex) == ex);
+}
+__device__ __forceinline__ bool nonfinite3(float x, float y, float z) {
+  const unsigned ex = 0x7f800000u;
+  return ((__float_as_uint(x) & ex) == ex) | ((__float_as_uint(y) & ex) == ex) | ((__float_as_uint(z) & ex) == ex);
 }
 
 // FP64-output row with most of the arithmetic on the FP32 pipe.  1/r and the
@@ -378,7 +398,9 @@ __device__ __forceinline__ double ff_to_double(ff a) {
 // z-recurrence, the scale and the two products, then one exact conversion to
 // binary64 per value.  Normwise error against the FP64 oracle stays below
 // 5e-14 at l = 9 (the FP64 path: 1.4e-14; tolerance 1e-13) while the FP64
-// instructions per point drop from ~242 to ~75.
+// instructions per point drop from ~242 to ~75.  The direction must be
+// finite: for a non-finite one the float-float columns are meaningless
+// (callers test nonfinite3 and write a NaN row instead).
 template <int LMAX, bool CX = false, typename Store>
 __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, Store&& store) {
   store(0, Sd<CX>(0, 0));
@@ -420,21 +442,21 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
       const ff Bn = ff_add(ff_mul_u(A, Y), ff_mul_u(B, X));
       A = An;
       B = Bn;
-      store(m * m + 2 * m, ff_to_double(ff_mul_c(A, Shi<CX>(m, m), Slo<CX>(m, m))));
-      store(m * m, ff_to_double(ff_mul_c(B, Shi<CX>(m, m), Slo<CX>(m, m))));
+      store(m * m + 2 * m, ff_to_double_finite(ff_mul_c(A, Shi<CX>(m, m), Slo<CX>(m, m))));
+      store(m * m, ff_to_double_finite(ff_mul_c(B, Shi<CX>(m, m), Slo<CX>(m, m))));
       ff q2 = {1.0f, 0.0f}, q1 = Z;
       if (m + 1 <= LMAX) {
         const ff s = ff_mul_c_u(Z, Shi<CX>(m + 1, m), Slo<CX>(m + 1, m));
         const int k0 = (m + 1) * (m + 1) + (m + 1);
-        store(k0 + m, ff_to_double(ff_mul(s, A)));
-        store(k0 - m, ff_to_double(ff_mul(s, B)));
+        store(k0 + m, ff_to_double_finite(ff_mul(s, A)));
+        store(k0 - m, ff_to_double_finite(ff_mul(s, B)));
       }
 #pragma unroll
       for (int l = m + 2; l <= LMAX; ++l) {
         const ff q = ff_add(ff_mul_u(Z, q1), ff_neg(ff_mul_c_u(q2, SHM_G_HI[l][m], SHM_G_LO[l][m])));
         const ff s = ff_mul_c_u(q, Shi<CX>(l, m), Slo<CX>(l, m));
-        store(l * l + l + m, ff_to_double(ff_mul(s, A)));
-        store(l * l + l - m, ff_to_double(ff_mul(s, B)));
+        store(l * l + l + m, ff_to_double_finite(ff_mul(s, A)));
+        store(l * l + l - m, ff_to_double_finite(ff_mul(s, B)));
         q2 = q1;
         q1 = q;
       }
@@ -463,7 +485,7 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
     if constexpr (NEG_FF)
       store(k, kbase, v);
     else
-      store(k, kbase, ff_to_double(v));
+      store(k, kbase, ff_to_double_finite(v));
   };
   const ff X = ff_from_double(xb), Y = ff_from_double(yb), Z = ff_from_double(zb);
   ff A[LMAX + 1], B[LMAX + 1], q1[LMAX + 1], q2[LMAX + 1];
@@ -507,7 +529,7 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
         }
       } else {  // float-float columns
         if (l == m) {
-          store(kc + m, k0, ff_to_double(ff_mul_c(A[m], Shi<CX>(m, m), Slo<CX>(m, m))));
+          store(kc + m, k0, ff_to_double_finite(ff_mul_c(A[m], Shi<CX>(m, m), Slo<CX>(m, m))));
           store_neg_ff(kc - m, k0, ff_mul_c(B[m], Shi<CX>(m, m), Slo<CX>(m, m)));
           q2[m] = {1.0f, 0.0f};
           q1[m] = Z;
@@ -521,7 +543,7 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
             q2[m] = q1[m];
             q1[m] = q;
           }
-          store(kc + m, k0, ff_to_double(ff_mul(sv, A[m])));
+          store(kc + m, k0, ff_to_double_finite(ff_mul(sv, A[m])));
           store_neg_ff(kc - m, k0, ff_mul(sv, B[m]));
         }
       }
@@ -631,6 +653,12 @@ __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&&
   }
   T xb = x, yb = y, zb = z;
   if (!normalized) unit_dir(x, y, z, xb, yb, zb);
+  if (nonfinite3(xb, yb, zb)) {  // NaN in every value but the constant l = 0
+    store(0, (T)kInvSqrt4Pi);
+#pragma unroll
+    for (int k = 1; k < NH<LMAX>::value; ++k) store(k, (T)__longlong_as_double(0x7ff8000000000000ll));
+    return;
+  }
   if constexpr (HYBRID && sizeof(T) == 8)
     sh_row_hybrid<LMAX, CX>(xb, yb, zb, store);
   else

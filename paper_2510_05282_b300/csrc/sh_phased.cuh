@@ -31,10 +31,12 @@ __device__ __forceinline__ void phased_rows(double xb, double yb, double zb, boo
   constexpr int L2 = NH<LMAX>::value;
   constexpr int RS = LPhases<LMAX>::max_width() | 1;
   double* row = tile + threadIdx.x * RS;
+  const bool bad = nonfinite3(xb, yb, zb);  // NaN row but l = 0 (the hybrid row code needs a finite direction)
   auto store = [&](int k, int k0, double v) { row[k - k0] = v; };
   auto flush = [&](int k0, int w) {
-    if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
-      for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
+    if (origin || bad) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
+      const double fill = origin ? 0.0 : __longlong_as_double(0x7ff8000000000000ll);
+      for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : fill;
     }
     __syncthreads();
     if (vec && L2 % 2 == 0 && ((k0 | w) & 1) == 0) {

@@ -103,10 +103,12 @@ __global__ void __launch_bounds__(kCxTPB64, 5) k_eval_cx64(const double* __restr
       }
     }
     double* row = tile + threadIdx.x * RS;
+    const bool bad = nonfinite3(xb, yb, zb);  // NaN row (the hybrid row code needs a finite direction)
     auto store = [&](int k, int k0, double v) { row[k - k0] = v; };
     auto flush = [&](int k0, int w) {
-      if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
-        for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
+      if (origin || bad) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
+        const double fill = origin ? 0.0 : __longlong_as_double(0x7ff8000000000000ll);
+        for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : fill;
       }
       __syncthreads();
       // thread (rs, c) = divmod(threadIdx, w) writes complex slot c of rows rs,
@@ -161,7 +163,13 @@ __global__ void __launch_bounds__(kCxTPB32) k_eval_cx32(const float* __restrict_
       } else {
         float xb = x, yb = y, zb = z;
         if (!normalized) unit_dir(x, y, z, xb, yb, zb);
-        sh_row<LMAX, true>(xb, yb, zb, [&](int k, float v) { cx_store(row, k, 0, v); });
+        if (nonfinite3(xb, yb, zb)) {  // NaN in every value but Y_0^0 (and the zero imaginary parts of m = 0)
+          cx_store(row, 0, 0, (float)kInvSqrt4Pi);
+#pragma unroll
+          for (int k = 1; k < L2; ++k) cx_store(row, k, 0, __int_as_float(0x7fc00000));
+        } else {
+          sh_row<LMAX, true>(xb, yb, zb, [&](int k, float v) { cx_store(row, k, 0, v); });
+        }
       }
     }
     __syncthreads();
@@ -266,7 +274,12 @@ __global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ a
       sincosf(ang[2 * p], &st, &ct);
       sincosf(ang[2 * p + 1], &sp, &cp);
       T* row = tile + threadIdx.x * RS;
-      sh_row<LMAX>(st * cp, st * sp, ct, [&](int k, T v) { row[k] = v; });
+      const T xb = st * cp, yb = st * sp, zb = ct;
+      if (nonfinite3(xb, yb, zb)) {  // a non-finite angle: NaN in every value but l = 0
+        for (int k = 0; k < L2; ++k) row[k] = k == 0 ? (T)kInvSqrt4Pi : __int_as_float(0x7fc00000);
+      } else {
+        sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v; });
+      }
     }
     __syncthreads();
     copy_out_tile<T, L2, RS, kAngTPB>(tile, rows, out + p0 * L2, vec != 0);

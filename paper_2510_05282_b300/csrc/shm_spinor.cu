@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_spinor64(const double* 
     }
     double* row = tile + threadIdx.x * RS;
     float2* rowf = reinterpret_cast<float2*>(row);
+    const bool bad = nonfinite3(xb, yb, zb);  // the hybrid row code needs a finite direction
     double* dst = out + p0 * 2 * NC;
     auto store = [&](int k, int k0, auto v) {
       if constexpr (std::is_same<decltype(v), double>::value)
@@ -219,8 +220,11 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_spinor64(const double* 
         rowf[k - k0] = make_float2(v.hi, v.lo);  // m < 0: float-float
     };
     auto flush = [&](int k0, int w) {
-      if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0 (zero is 0 in both formats)
-        for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : 0.0;
+      if (origin || bad) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0 (zero is 0 in both formats)
+        // a non-finite direction: a pattern that is NaN both as binary64 and
+        // as a float pair, for the binary64 and the float-float slots alike
+        const double fill = origin ? 0.0 : __longlong_as_double(0x7ff800007fc00000ll);
+        for (int c = 0; c < w; ++c) row[c] = (k0 + c == 0) ? kInvSqrt4Pi : fill;
       }
       __syncthreads();
       spinor_copy_out64<TPB, RS, NC>(tile, rows, k0, w, midx, mcoef, dst, vec != 0);
@@ -260,7 +264,11 @@ __global__ void __launch_bounds__(kSpTPB32) k_eval_spinor32(const float* __restr
       } else {
         float xb = x, yb = y, zb = z;
         if (!normalized) unit_dir(x, y, z, xb, yb, zb);
-        sh_row<LMAX>(xb, yb, zb, [&](int k, float v) { row[k] = v; });
+        if (nonfinite3(xb, yb, zb)) {  // NaN in every value but l = 0
+          for (int c = 0; c < L2; ++c) row[c] = c == 0 ? (float)kInvSqrt4Pi : __int_as_float(0x7fc00000);
+        } else {
+          sh_row<LMAX>(xb, yb, zb, [&](int k, float v) { row[k] = v; });
+        }
       }
     }
     __syncthreads();

@@ -88,6 +88,70 @@ def test_nan_propagates():
     assert not np.isnan(got[1]).any()
 
 
+def _points_with_nonfinite(n=300):
+    """n finite points with non-finite rows at the tile edges and inside."""
+    pts = inputs.random_sphere_points(n, stream="tests", with_axes=False)
+    bad_rows = {0: [np.nan, 0.0, 1.0], 1: [np.inf, 0.0, 0.0], 127: [0.0, -np.inf, 1.0],
+                128: [1.0, 2.0, np.nan], 200: [np.inf, np.inf, -np.inf], n - 1: [np.nan, np.nan, np.nan]}
+    for i, v in bad_rows.items():
+        pts[i] = v
+    return pts, np.array(sorted(bad_rows))
+
+
+@pytest.mark.parametrize("lmax", [2, 9])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_nonfinite_points_give_nan_rows_every_variant(oracle_mod, lmax, dtype):
+    """A NaN or infinite coordinate gives NaN in every value but the constant
+    l = 0 one, on every launch variant and with the normalised-input flag;
+    the finite rows of the same launch are unaffected."""
+    pts, bad = _points_with_nonfinite()
+    good = np.setdiff1d(np.arange(pts.shape[0]), bad)
+    p = torch.from_numpy(pts).to(device="cuda", dtype=dtype)
+    ref = oracle_mod.real_sh(p[torch.from_numpy(good).cuda()].double().cpu().numpy(), lmax)
+    tol = TOL_F64 if dtype == torch.float64 else TOL_F32
+    try:
+        for v in range(shm.eval_variant_count()):
+            shm.set_eval_variant(lmax, dtype, v)
+            for normalized in (False, True):
+                got = shm.eval_sh(p, lmax, normalized=normalized).cpu().numpy()
+                what = f"{shm.eval_variant(lmax, dtype)} normalized={normalized}"
+                assert np.allclose(got[bad, 0], 0.28209479177387814347, rtol=1e-7, atol=0), what
+                assert np.all(np.isnan(got[bad, 1:])), what
+                if not normalized:
+                    assert_normwise(got[good], ref, tol, what)
+    finally:
+        shm.set_eval_variant(lmax, dtype, -1)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_nonfinite_points_complex_spinor_angles(oracle_mod, dtype):
+    pts, bad = _points_with_nonfinite()
+    good = np.setdiff1d(np.arange(pts.shape[0]), bad)
+    tol = TOL_F64 if dtype == torch.float64 else TOL_F32
+    y00 = 0.28209479177387814347
+    p = torch.from_numpy(pts).to(device="cuda", dtype=dtype)
+    cx = shm.eval_complex(p, 9).cpu().numpy()
+    assert np.allclose(cx[bad, 0], y00, rtol=1e-7, atol=0)
+    assert np.all(np.isnan(cx[bad, 1:].real))
+    assert np.all(np.isfinite(cx[good]))
+    sp = shm.eval_spinor(p, 9).cpu().numpy()           # [n, 200, 2]; spinors 0, 1 are the l = 0 block
+    assert np.all(np.isfinite(sp[bad, :2]))
+    assert np.all(np.isnan(sp[bad, 2:].real))
+    assert np.all(np.isfinite(sp[good]))
+    # angles: a NaN or infinite theta or phi
+    ang = np.stack([np.arccos(np.clip(pts[:, 2] / np.linalg.norm(pts, axis=1), -1, 1)),
+                    np.arctan2(pts[:, 1], pts[:, 0])], 1)
+    bad_a = good[:3]
+    ang[bad_a] = [[np.nan, 0.1], [0.3, np.inf], [-np.inf, np.nan]]
+    fine = good[3:]
+    a = torch.from_numpy(np.ascontiguousarray(ang)).to(device="cuda", dtype=dtype)
+    got = shm.eval_angles(a, 9).cpu().numpy()
+    assert np.allclose(got[bad_a, 0], y00, rtol=1e-7, atol=0)
+    assert np.all(np.isnan(got[bad_a, 1:]))
+    ref = oracle_mod.real_sh(pts[fine].astype(np.float32).astype(np.float64) if dtype == torch.float32 else pts[fine], 9)
+    assert_normwise(got[fine], ref, 10 * tol if dtype == torch.float32 else tol, "angles next to non-finite rows")
+
+
 def test_normalized_input_flag(oracle_mod):
     pts = inputs.random_sphere_points(5000, stream="tests", with_axes=False)
     unit = pts / np.linalg.norm(pts, axis=1, keepdims=True)
