@@ -342,36 +342,32 @@ __device__ __forceinline__ ff ff_from_double(double d) {
 
 // float-float (normalised: |lo| <= ulp(hi)/2, hi finite) -> binary64.  The
 // double of hi is assembled from its bits (exponent rebiased by 1023 - 127 =
-// 896, significand extended by 29 zero bits); lo is added in units of that
-// double's ulp 2^(E-179) directly on the bit pattern.  With lo = ml 2^(El-150)
-// (ml the 24-bit significand), that count is n = (ml << 5) >> (E - El - 24),
-// a right shift of 0..31 for a normalised pair (32 or more gives 0, which
-// also covers lo = 0); n < 2^29, so the significand never carries past its
-// top bit.  Below a power of two the double's ulp halves, so an opposite-sign
-// lo counts twice there.  Parts of lo below one ulp are truncated (result
-// within 1 ulp of hi + lo).  hi = +-0 gives +-0; a subnormal hi (|hi| <
-// 2^-126) gives a value below 2^-1042 in magnitude, and a subnormal lo (read
-// as if normal; it matters only for |hi| < 2^-71) an absolute error below
-// 2^-126.  A NaN or infinite hi
-// gives a meaningless finite value: the row code, which only meets finite
-// values for a finite direction, uses this form, and the callers write NaN
-// rows for non-finite points.  Branch-free, integer instructions only.
+// 896, significand extended by 29 zero bits); lo is then added as a signed
+// count k of units of the result's last place, directly on the bit pattern
+// (a double's bit pattern is monotonic in its magnitude, and the carry or
+// borrow moves into the exponent by itself).  k = trunc(lo * sign(hi) *
+// 2^(52 - E)), E the exponent of hi + lo: one FP32 multiply by a power of two
+// built from the exponent bits and one float -> int conversion (neither uses
+// the FP64 pipe).  E comes from hi + lo added toward zero, which differs from
+// hi's exponent exactly when hi is a power of two and lo has the opposite sign
+// -- the case where the result lies in the binade below, whose units are half
+// as large.  |k| < 2^30, so the count fits the conversion; the truncated part
+// is below one unit (result within 1 ulp of hi + lo).  hi = +-0 gives +-0.
+// For |hi| < 2^-75 the scale leaves the FP32 range and the result is off by
+// less than 2^-96 in absolute terms.  A NaN or infinite hi gives a meaningless
+// finite value: the row code, which only meets finite values for a finite
+// direction, uses this form, and the callers write NaN rows for non-finite
+// points.  Branch-free.
 __device__ __forceinline__ double ff_to_double_finite(ff a) {
   const unsigned hb = __float_as_uint(a.hi);
-  const unsigned lb = __float_as_uint(a.lo);
-  const unsigned e = hb & 0x7f800000u;
   const unsigned sg = hb & 0x80000000u;
-  unsigned hi32 = (((hb & 0x7fffffffu) >> 3) + (896u << 20)) | sg;
-  hi32 = e == 0u ? sg : hi32;
+  unsigned hi32 = ((hb >> 3) & 0x0fffffffu) + (896u << 20) + sg;
+  hi32 = (hb & 0x7f800000u) == 0u ? sg : hi32;
   const unsigned lo32 = hb << 29;
-  const unsigned ml5 = ((lb << 5) & 0x0fffffe0u) | 0x10000000u;
-  const unsigned sh = (e >> 23) - ((lb >> 23) & 0xffu) - 24u;
-  unsigned n = __funnelshift_rc(ml5, 0u, sh);  // ml5 >> min(sh, 32)
-  const bool opp = (int)(hb ^ lb) < 0;
-  n = (opp && (hb & 0x7fffffu) == 0u) ? 2u * n : n;
-  const long long d = opp ? -(long long)n : (long long)n;
-  const long long bits = (long long)(((unsigned long long)hi32 << 32) | lo32) + d;
-  return __longlong_as_double(bits);
+  const unsigned es = __float_as_uint(__fadd_rz(a.hi, a.lo)) & 0x7f800000u;  // binade of hi + lo
+  const float scale = __uint_as_float((306u << 23) - es + sg);                  // sign(hi) 2^(52 - E)
+  const int k = __float2int_rz(a.lo * scale);
+  return __longlong_as_double((long long)(((unsigned long long)hi32 << 32) | lo32) + (long long)k);
 }
 // The same with a NaN or infinite hi mapped to NaN.
 __device__ __forceinline__ double ff_to_double(ff a) {
