@@ -24,6 +24,7 @@
 #include "sh_core.cuh"
 #include "sh_phased.cuh"
 #include "sh_tile.cuh"
+#include "sh_tma.cuh"
 #include "shm_internal.h"
 
 namespace shm {
@@ -287,10 +288,18 @@ __global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ a
   }
 }
 
-// FP64 angles run the phased hybrid evaluator (sh_phased.cuh) with angle
-// input; FP32 angles the staged kernel above.
+// FP64 angles run the phased hybrid evaluator with angle input -- with TMA
+// stores (sh_tma.cuh) where they apply, else sh_phased.cuh; FP32 angles the
+// staged kernel above.
 template <typename T, int LMAX>
 shm_status ang_launch(const T* ang, int64_t n, T* out, bool vec, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (vec) {
+      bool launched = false;
+      shm_status st = launch_phased_tma<LMAX, kAngTPB64, kInAngles>(ang, n, out, false, s, &launched);
+      if (st != SHM_OK || launched) return st;
+    }
+  }
   constexpr int MAXDEV = 64;
   static int bps[MAXDEV] = {};
   const int dev = current_device();

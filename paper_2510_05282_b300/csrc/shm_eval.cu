@@ -19,6 +19,7 @@
 #include "sh_core.cuh"
 #include "sh_phased.cuh"
 #include "sh_tile.cuh"
+#include "sh_tma.cuh"
 #include "shm_internal.h"
 
 namespace shm {
@@ -66,9 +67,11 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
   }
 }
 
-// kPhased / kPhasedHybrid (FP64): k_eval_phased of sh_phased.cuh.  For FP32
-// these variants are the staged path.
-enum { kPhased = 2, kPhasedHybrid = 4 };
+// kPhased / kPhasedHybrid (FP64): k_eval_phased of sh_phased.cuh.
+// kPhasedHybridTma (FP64): k_eval_phased_tma of sh_tma.cuh (phased hybrid
+// rows leaving by TMA tensor stores).  For FP32 these variants are the
+// staged path.
+enum { kPhased = 2, kPhasedHybrid = 4, kPhasedHybridTma = 5 };
 
 // Launch variants the tuner chooses among (index = variant id).
 struct Variant {
@@ -76,7 +79,8 @@ struct Variant {
 };
 constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},  {kDirect, 128},
                                  {kDirect, 256}, {kPhased, 64}, {kPhased, 128}, {kHybrid, 64},
-                                 {kHybrid, 128}, {kHybrid, 256}, {kPhasedHybrid, 64}, {kPhasedHybrid, 128}};
+                                 {kHybrid, 128}, {kHybrid, 256}, {kPhasedHybrid, 64}, {kPhasedHybrid, 128},
+                                 {kPhasedHybridTma, 128}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // For FP32 the phased and hybrid variants run the staged-64 kernel (FP32 rows
@@ -87,14 +91,14 @@ inline size_t variant_smem(int v, int lmax, size_t es) {
   const int L2 = (lmax + 1) * (lmax + 1);
   const int p = kVariants[v].path, tpb = kVariants[v].tpb;
   if (p == kDirect) return 0;
-  if (p == kPhased || p == kPhasedHybrid) {
+  if (p == kPhased || p == kPhasedHybrid || p == kPhasedHybridTma) {
     int w = 0, mx = 0;  // LPhases<LMAX>::max_width()
     for (int l = 0; l <= lmax; ++l) {
       if (w > 0 && w + 2 * l + 1 > 37) w = 0;
       w += 2 * l + 1;
       mx = std::max(mx, w);
     }
-    return (size_t)tpb * (mx | 1) * 8;
+    return p == kPhasedHybridTma ? (size_t)tpb * mx * 8 + 128 : (size_t)tpb * (mx | 1) * 8;
   }
   return (size_t)tpb * (size_t)(L2 % 2 ? L2 : L2 + 1) * es;
 }
@@ -102,12 +106,17 @@ constexpr size_t kMaxSmemPerCta = 232448;  // B300 opt-in limit per CTA
 
 // The variant that actually runs: FP32 rows have no phased or hybrid form
 // (staged-64 runs); for l > 9 the FP64 rows are all-FP64 (a hybrid variant
-// runs its all-FP64 counterpart); a staged variant whose tile does not fit
-// in shared memory at this l runs phased-64 (FP64) or staged-64 (FP32).
+// runs its all-FP64 counterpart); the TMA variant runs phased-hybrid-128 at
+// an lmax without a TMA phase plan; a staged variant whose tile does not fit
+// in shared memory at this l runs phased-64 (FP64) or staged-64 (FP32).  (At
+// run time the TMA variant also falls back to phased-hybrid-128 for an
+// output that is not 16-byte aligned or n >= 2^31.)
 inline int effective_variant(bool fp64, int v, int lmax = 0) {
   const int p = kVariants[v].path;
   if (!fp64) {
-    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid) ? 1 : v;
+    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid || p == kPhasedHybridTma) ? 1 : v;
+  } else if (p == kPhasedHybridTma && !tma_plan_feasible(lmax)) {
+    v = lmax > SHM_LMAX_CAP ? 6 : 11;
   } else if (lmax > SHM_LMAX_CAP) {
     if (v == 7) v = 1;              // hybrid-64 -> staged-64
     else if (v == 8) v = 0;         // hybrid-128 -> staged-128
@@ -120,10 +129,12 @@ inline int effective_variant(bool fp64, int v, int lmax = 0) {
 }
 
 // Default choice before (or without) tuning, the fastest measured on a
-// 7M-point workload at l = 9: phased-hybrid-128 for FP64 rows (2.3 ms against
-// 4.1 ms for staged-128), staged-64 for FP32 rows (HBM-bound, coalesced
-// stores).  Above l = 9 the FP64 default runs phased-128 (effective_variant).
-constexpr int kDefaultVariantF64 = 11;
+// 7M-point workload at l = 9: phased-hybrid-tma-128 for FP64 rows (1.30 ms
+// against 1.42 ms for phased-hybrid-128 and 3.6 ms for staged-128),
+// staged-64 for FP32 rows (HBM-bound, coalesced stores).  At an lmax without
+// a TMA plan the FP64 default runs phased-hybrid-128, above l = 9 phased-128
+// (effective_variant).
+constexpr int kDefaultVariantF64 = 12;
 constexpr int kDefaultVariantF32 = 1;
 inline int default_variant(bool fp64) { return fp64 ? kDefaultVariantF64 : kDefaultVariantF32; }
 
@@ -133,6 +144,7 @@ int g_choice[2][SHM_LMAX_EXT + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1
 
 template <typename T, int LMAX, int TPB, int PATH>
 size_t eval_smem_bytes() {
+  if (PATH == kPhasedHybridTma) return TmaPlan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhased || PATH == kPhasedHybrid)
     return (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * sizeof(double);
   return (PATH == kStaged || PATH == kHybrid) ? (size_t)TPB * TileShape<LMAX>::RS * sizeof(T) : 0;
@@ -140,8 +152,8 @@ size_t eval_smem_bytes() {
 
 template <typename T, int LMAX, int TPB, int PATH>
 auto pick_kernel() {
-  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid) && sizeof(T) == 8) {
-    return k_eval_phased<LMAX, TPB, PATH == kPhasedHybrid>;
+  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid || PATH == kPhasedHybridTma) && sizeof(T) == 8) {
+    return k_eval_phased<LMAX, TPB, PATH != kPhased>;
   } else {
     return k_eval<T, LMAX, TPB, (PATH == kPhased || (PATH == kHybrid && sizeof(T) == 4)) ? kStaged : PATH>;
   }
@@ -153,10 +165,18 @@ template <typename T, int LMAX, int TPB, int PATH>
 shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t stream) {
   constexpr int MAXDEV = 64;
   static int blocks_per_sm[MAXDEV] = {0};
-  if constexpr (PATH == kPhased || PATH == kPhasedHybrid) {
+  if constexpr (PATH == kPhased || PATH == kPhasedHybrid || PATH == kPhasedHybridTma) {
     if constexpr (sizeof(T) == 4) {
       return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, stream);
     }
+  }
+  if constexpr (PATH == kPhasedHybridTma && sizeof(T) == 8) {
+    bool launched = false;
+    if (vec) {
+      shm_status st = launch_phased_tma<LMAX, TPB, kInPoints>(pts, n, out, normalized, stream, &launched);
+      if (st != SHM_OK || launched) return st;
+    }
+    return eval_launch_v<T, LMAX, TPB, kPhasedHybrid>(pts, n, out, normalized, vec, stream);
   }
   const int dev = current_device();
   auto kern = pick_kernel<T, LMAX, TPB, PATH>();
@@ -210,6 +230,7 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
     case 9: return eval_launch_v<T, LMAX, 256, kHybrid>(pts, n, out, normalized, vec, s);
     case 10: return eval_launch_v<T, LMAX, 64, kPhasedHybrid>(pts, n, out, normalized, vec, s);
     case 11: return eval_launch_v<T, LMAX, 128, kPhasedHybrid>(pts, n, out, normalized, vec, s);
+    case 12: return eval_launch_v<T, LMAX, 128, kPhasedHybridTma>(pts, n, out, normalized, vec, s);
   }
   return fail(SHM_EINVAL, "unknown launch variant");
 }
@@ -384,7 +405,7 @@ namespace {
 
 const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64",  "staged-256", "direct-128", "direct-256",
                                            "phased-64",  "phased-128", "hybrid-64",  "hybrid-128", "hybrid-256",
-                                           "phased-hybrid-64", "phased-hybrid-128"};
+                                           "phased-hybrid-64", "phased-hybrid-128", "phased-hybrid-tma-128"};
 
 std::mutex g_tune_mu;
 bool g_cache_loaded = false;

@@ -30,4 +30,11 @@ int sm_count(int dev);
 
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// Tensor map of a row-major FP64 matrix [n][cols] at `base` for TMA tensor
+// stores of [box_rows][box_cols] boxes (no swizzle).  False (nothing
+// launched, the caller takes its non-TMA path) when the driver entry point
+// is unavailable or the layout breaks a TMA rule: base and row pitch 16-byte
+// aligned, box width a multiple of 16 bytes, box sides <= 256, n < 2^31.
+bool encode_rows_map(CUtensorMap* map, void* base, int64_t n, int cols, int box_cols, int box_rows);
+
 }  // namespace shm

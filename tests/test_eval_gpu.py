@@ -179,6 +179,52 @@ def test_unaligned_output_uses_scalar_path(oracle_mod):
         shm.set_eval_variant(9, torch.float64, -1)
 
 
+TMA_VARIANT = 12
+COPY_OUT_VARIANT = 11
+
+
+@pytest.mark.parametrize("lmax", [1, 2, 3, 5, 7, 9, 11])
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 4099, 200_003])
+def test_tma_variant_matches_copy_out_variant(lmax, n):
+    """phased-hybrid-tma-128 (TMA tensor stores of each staged phase) writes
+    the same bits as phased-hybrid-128 (copy-out loop), ragged last tiles
+    included; at an lmax without a TMA plan (even, or above 9) it runs the
+    copy-out kernel."""
+    assert shm.eval_variant_count() > TMA_VARIANT
+    pts = inputs.random_sphere_points(n, stream="tests", with_axes=False)
+    p = torch.from_numpy(pts).cuda()
+    try:
+        shm.set_eval_variant(lmax, torch.float64, TMA_VARIANT)
+        name = shm.eval_variant(lmax, torch.float64)
+        assert name == ("phased-hybrid-tma-128" if lmax % 2 == 1 and lmax <= 9 else
+                        "phased-hybrid-128" if lmax <= 9 else "phased-128"), (lmax, name)
+        out = torch.full((n, (lmax + 1) ** 2), 7.0, dtype=torch.float64, device="cuda")
+        shm.eval_sh(p, lmax, out=out)
+        shm.set_eval_variant(lmax, torch.float64, COPY_OUT_VARIANT)
+        ref = shm.eval_sh(p, lmax)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), (lmax, n)
+    finally:
+        shm.set_eval_variant(lmax, torch.float64, -1)
+
+
+def test_tma_variant_next_to_other_allocations():
+    """The TMA stores of the last (ragged) tile stop at row n: the bytes
+    after the output, inside the same allocation, are left untouched."""
+    n = 1000
+    pts = inputs.random_sphere_points(n, stream="tests", with_axes=False)
+    p = torch.from_numpy(pts).cuda()
+    buf = torch.full((n + 300, 100), -3.0, dtype=torch.float64, device="cuda")
+    try:
+        shm.set_eval_variant(9, torch.float64, TMA_VARIANT)
+        shm.eval_sh(p, 9, out=buf[:n])
+        torch.cuda.synchronize()
+        assert torch.all(buf[n:] == -3.0)
+        assert torch.equal(buf[:n], shm.eval_sh(p, 9))
+    finally:
+        shm.set_eval_variant(9, torch.float64, -1)
+
+
 def test_bad_arguments_launch_nothing():
     from cuda.bindings import runtime as rt
     L = shm.lib()
@@ -294,9 +340,9 @@ def test_dft_grid_fp64_full_size_sampled(oracle_mod, capsys):
             out = shm.eval_sh(p, 9)
             torch.cuda.synchronize()
             got = out[rows_t].cpu().numpy()
-            if v == 11:  # the variant bench.py times
+            if shm.eval_variant(9, torch.float64) == "phased-hybrid-tma-128":  # the variant bench.py times
                 with capsys.disabled():
-                    print("\nFP64 192^3 grid sample (phased-hybrid-128), normwise error per l (max/mean):",
+                    print("\nFP64 192^3 grid sample (phased-hybrid-tma-128), normwise error per l (max/mean):",
                           per_l_report(normwise_err(got, ref)))
             assert_normwise(got, ref, TOL_F64, f"192^3 grid sample, variant {v}")
             for l in range(10):
