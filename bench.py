@@ -387,8 +387,9 @@ def run_gpu(args, rank, world):
 # variant); captures of the 96^3 grid are scaled to a full launch by the
 # number of points.
 TRAFFIC_PER_POINT = {
-    # measured on the full 192^3 launch (1-pass capture): 170.03 MB read + 5.63 GB written
-    ("f64", "phased-hybrid-128"): (170.03e6 + 5.63e9) / 7_077_888,
+    # measured on the full 192^3 launch (1-pass captures)
+    ("f64", "phased-hybrid-tma-128"): (174.86e6 + 5.75e9) / 7_077_888,
+    ("f64", "phased-hybrid-128"): (169.99e6 + 5.61e9) / 7_077_888,
     ("f64", "staged-64"): (21.318144e6 + 648.666112e6) / 884_736,
     ("f32", "staged-64"): (10.651648e6 + 294.209024e6) / 884_736,
 }
