@@ -468,7 +468,10 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
 // (type ff) instead of binary64 -- the m <= -2 ones before their conversion,
 // the m = -1 ones converted exactly to 48 bits -- for callers that keep
 // working on them with FP32 instructions.
-template <int LMAX, bool CX = false, int PHMAX = 37, bool NEG_FF = false, typename Store, typename Phase>
+// Ends: the phase plan (ends_phase(l): shell l closes a phase), by default
+// groups of whole shells of at most PHMAX values.
+template <int LMAX, bool CX = false, int PHMAX = 37, bool NEG_FF = false, typename Ends = LPhases<LMAX, PHMAX>,
+          typename Store, typename Phase>
 __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, double zb, Store&& store,
                                                      Phase&& phase) {
   auto store_neg_d = [&](int k, int kbase, double v) {
@@ -544,7 +547,7 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
         }
       }
     }
-    if (LPhases<LMAX, PHMAX>::ends_phase(l)) {
+    if (Ends::ends_phase(l)) {
       phase(k0, (l + 1) * (l + 1) - k0);
       k0 = (l + 1) * (l + 1);
     }

@@ -24,6 +24,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "sh_phased.cuh"
@@ -205,6 +206,192 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased_tma(const double
   }
   // the last stores' global writes complete before the CTA retires
   if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Double-buffered form (phased-hybrid-tma2-128).  In the kernel above every
+// phase waits for the TMA unit to read its 37 KB buffer before the next phase
+// may overwrite it; two such buffers per CTA do not fit five CTAs per SM.
+// Here phases are at most 20 values wide and alternate between two 20-column
+// buffers (41 KB per CTA), so a phase waits only for the read of the phase
+// before it, issued a whole phase earlier.  Phases (odd lmax 3..9): shells
+// 0-3 -> columns [0, 16), shells 4-5 -> [16, 36), then one shell each.  A box
+// must start on an even column, so the last value of shell 6 (k = 48) and of
+// shell 8 (k = 80) is kept in a register and sent with the next shell's box:
+// boxes [36, 48), [48, 64), [64, 80), [80, 100).  Every box is 16 or 20
+// columns (two boxes of 10 + 6 or 10 + 10 columns: pitches 2 mod 4) or 12
+// (6 + 6).
+template <int LMAX>
+struct Tma2Plan {
+  static constexpr int L2 = NH<LMAX>::value;
+  static constexpr bool feasible() { return LMAX == 3 || LMAX == 5 || LMAX == 7 || LMAX == 9; }
+  __host__ __device__ static constexpr bool ends_phase(int l) { return l == LMAX || l == 3 || l >= 5; }
+  // per row-code phase (identified by its first column k0)
+  __host__ __device__ static constexpr int index(int k0) {
+    return k0 == 0 ? 0 : (k0 == 16 ? 1 : (k0 == 36 ? 2 : (k0 == 49 ? 3 : (k0 == 64 ? 4 : 5))));
+  }
+  __host__ __device__ static constexpr int next(int k0) {
+    return k0 == 0 ? 16 : (k0 == 16 ? 36 : (k0 == 36 ? 49 : (k0 == 49 ? 64 : (k0 == 64 ? 81 : 100))));
+  }
+  __host__ __device__ static constexpr bool carried(int k) { return (k == 48 && LMAX >= 7) || (k == 80 && LMAX >= 9); }
+  __host__ __device__ static constexpr int box_x(int k0) { return (k0 == 49 || k0 == 81) ? k0 - 1 : k0; }
+  __host__ __device__ static constexpr int box_end(int k0) {
+    return (next(k0) == 49 || next(k0) == 81) ? next(k0) - 1 : next(k0);
+  }
+  __host__ __device__ static constexpr int box_w(int k0) { return box_end(k0) - box_x(k0); }
+  __host__ __device__ static constexpr int bw0(int k0) { return box_w(k0) == 12 ? 6 : 10; }
+  static constexpr int kBufCols = 20;
+  static constexpr size_t smem_bytes(int tpb) { return (size_t)2 * tpb * kBufCols * 8 + 128; }
+};
+
+// Rows of one tile, double-buffered TMA stores.  Rows of points at the
+// origin or with a non-finite coordinate are sent as computed and then
+// overwritten from registers, after the tile's stores have completed, by the
+// threads that own them (a per-tile vote; no such row in most tiles).  A fill
+// in every phase end, as the single-buffered kernel does, pushes the unrolled
+// row past the compiler's unroll limit at lmax 9 (the l loop then stays a
+// loop: 3x the instructions).
+template <int LMAX, int TPB>
+__device__ __forceinline__ void phased_rows_tma2(double xb, double yb, double zb, bool origin, int64_t p0, int rows,
+                                                 double* __restrict__ tile, double* __restrict__ out,
+                                                 const CUtensorMap* map10, const CUtensorMap* map6) {
+  using P = Tma2Plan<LMAX>;
+  const bool bad = nonfinite3(xb, yb, zb);  // NaN row but l = 0 (the hybrid row code needs a finite direction)
+  const int t = (int)threadIdx.x;
+  double carry = 0.0;
+  // staging slot of column c of the box of the phase starting at k0
+  auto at = [&](int k0, int c) -> double* {
+    const int b0 = P::bw0(k0), bw = P::box_w(k0);
+    double* buf = tile + (P::index(k0) & 1) * TPB * P::kBufCols;
+    return c < b0 ? buf + t * b0 + c : buf + TPB * b0 + t * (bw - b0) + (c - b0);
+  };
+  auto store = [&](int k, int k0, double v) {
+    if (P::carried(k))
+      carry = v;
+    else
+      *at(k0, k - P::box_x(k0)) = v;
+  };
+  auto flush = [&](int k0, int w) {
+    (void)w;
+    const int x = P::box_x(k0), bw = P::box_w(k0), b0 = P::bw0(k0);
+    if (x != k0) *at(k0, 0) = carry;  // the value carried from the previous shell
+    // the staged values (generic proxy) must be visible to the TMA unit (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      double* buf = tile + (P::index(k0) & 1) * TPB * P::kBufCols;
+      for (int j = 0; j < 2; ++j) {
+        const int xj = x + (j ? b0 : 0), wj = j ? bw - b0 : b0;
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(buf + (j ? TPB * b0 : 0));
+        const CUtensorMap* m = wj == 10 ? map10 : map6;
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                     :
+                     : "l"(reinterpret_cast<uint64_t>(m)), "r"(xj), "r"((int)p0), "r"(sa)
+                     : "memory");
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      // the next phase writes the other buffer: wait until the TMA unit has
+      // read it (its stores were issued one phase ago)
+      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    }
+    __syncthreads();
+  };
+  sh_row_hybrid_lmajor<LMAX, false, 37, false, P>(xb, yb, zb, store, flush);
+  if (__syncthreads_or((origin || bad) && (int)threadIdx.x < rows)) {
+    if (t == 0) {  // the tile's TMA writes are complete and visible before the overwrite
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
+    if ((origin || bad) && t < rows) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
+      const double fill = origin ? 0.0 : __longlong_as_double(0x7ff8000000000000ll);
+      double* row = out + (p0 + t) * P::L2;
+      for (int k = 0; k < P::L2; ++k) row[k] = k == 0 ? kInvSqrt4Pi : fill;
+    }
+  }
+}
+
+template <int LMAX, int TPB, int IN = kInPoints>
+__global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased_tma2(const double* __restrict__ in, int64_t n,
+                                                                     int64_t ntiles, int normalized,
+                                                                     double* __restrict__ out,
+                                                                     const __grid_constant__ CUtensorMap map10,
+                                                                     const __grid_constant__ CUtensorMap map6) {
+  static_assert(Tma2Plan<LMAX>::feasible(), "no double-buffered TMA plan for this lmax");
+  extern __shared__ unsigned char smem_tma[];
+  double* tile = reinterpret_cast<double*>(smem_tma + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_tma) & 127u)) & 127u));
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * TPB;
+    const int rows = (int)min((int64_t)TPB, n - p0);
+    const bool valid = (int)threadIdx.x < rows;
+    bool origin = false;
+    double xb = 0.0, yb = 0.0, zb = 1.0;
+    if constexpr (IN == kInAngles) {
+      if (valid) {  // Eq. 3-4 read backwards: the unit vector of (theta, phi)
+        const int64_t p = p0 + threadIdx.x;
+        double st, ct, sp, cp;
+        sincos(in[2 * p], &st, &ct);
+        sincos(in[2 * p + 1], &sp, &cp);
+        xb = st * cp;
+        yb = st * sp;
+        zb = ct;
+      }
+    } else {
+      double x = 0.0, y = 0.0, z = 1.0;
+      if (valid) {
+        const int64_t p = p0 + threadIdx.x;
+        x = in[3 * p];
+        y = in[3 * p + 1];
+        z = in[3 * p + 2];
+      }
+      origin = valid && is_origin(x, y, z);
+      if (valid && !origin) {
+        if (normalized) {
+          xb = x;
+          yb = y;
+          zb = z;
+        } else {
+          unit_dir(x, y, z, xb, yb, zb);
+        }
+      }
+    }
+    phased_rows_tma2<LMAX, TPB>(xb, yb, zb, origin, p0, rows, tile, out, &map10, &map6);
+  }
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Host side of the double-buffered form; as launch_phased_tma.
+template <int LMAX, int TPB, int IN>
+inline shm_status launch_phased_tma2(const double* in, int64_t n, double* out, bool normalized, cudaStream_t stream,
+                                     bool* launched) {
+  *launched = false;
+  if constexpr (Tma2Plan<LMAX>::feasible()) {
+    using Plan = Tma2Plan<LMAX>;
+    CUtensorMap m10, m6;
+    if (!encode_rows_map(&m10, out, n, Plan::L2, 10, TPB) || !encode_rows_map(&m6, out, n, Plan::L2, 6, TPB))
+      return SHM_OK;
+    constexpr int MAXDEV = 64;
+    static int blocks_per_sm[MAXDEV] = {0};
+    const int dev = current_device();
+    if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
+    auto kern = k_eval_phased_tma2<LMAX, TPB, IN>;
+    const size_t smem = Plan::smem_bytes(TPB);
+    if (blocks_per_sm[dev] == 0) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_eval_phased_tma2)");
+      int b = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TPB, smem);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_eval_phased_tma2)");
+      blocks_per_sm[dev] = std::max(b, 1);
+    }
+    const int64_t ntiles = (n + TPB - 1) / TPB;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * blocks_per_sm[dev]);
+    kern<<<(unsigned)grid, TPB, smem, stream>>>(in, n, ntiles, normalized ? 1 : 0, out, m10, m6);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "k_eval_phased_tma2 launch");
+    *launched = true;
+  }
+  return SHM_OK;
 }
 
 // Host side: encodes the two tensor maps of `out` and launches

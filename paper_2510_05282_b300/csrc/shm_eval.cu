@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
 // kPhasedHybridTma (FP64): k_eval_phased_tma of sh_tma.cuh (phased hybrid
 // rows leaving by TMA tensor stores).  For FP32 these variants are the
 // staged path.
-enum { kPhased = 2, kPhasedHybrid = 4, kPhasedHybridTma = 5 };
+enum { kPhased = 2, kPhasedHybrid = 4, kPhasedHybridTma = 5, kPhasedHybridTma2 = 6 };
 
 // Launch variants the tuner chooses among (index = variant id).
 struct Variant {
@@ -80,7 +80,7 @@ struct Variant {
 constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},  {kDirect, 128},
                                  {kDirect, 256}, {kPhased, 64}, {kPhased, 128}, {kHybrid, 64},
                                  {kHybrid, 128}, {kHybrid, 256}, {kPhasedHybrid, 64}, {kPhasedHybrid, 128},
-                                 {kPhasedHybridTma, 128}};
+                                 {kPhasedHybridTma, 128}, {kPhasedHybridTma2, 128}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // For FP32 the phased and hybrid variants run the staged-64 kernel (FP32 rows
@@ -91,6 +91,7 @@ inline size_t variant_smem(int v, int lmax, size_t es) {
   const int L2 = (lmax + 1) * (lmax + 1);
   const int p = kVariants[v].path, tpb = kVariants[v].tpb;
   if (p == kDirect) return 0;
+  if (p == kPhasedHybridTma2) return (size_t)2 * tpb * 20 * 8 + 128;
   if (p == kPhased || p == kPhasedHybrid || p == kPhasedHybridTma) {
     int w = 0, mx = 0;  // LPhases<LMAX>::max_width()
     for (int l = 0; l <= lmax; ++l) {
@@ -114,9 +115,12 @@ constexpr size_t kMaxSmemPerCta = 232448;  // B300 opt-in limit per CTA
 inline int effective_variant(bool fp64, int v, int lmax = 0) {
   const int p = kVariants[v].path;
   if (!fp64) {
-    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid || p == kPhasedHybridTma) ? 1 : v;
+    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid || p == kPhasedHybridTma || p == kPhasedHybridTma2) ? 1
+                                                                                                                : v;
   } else if (p == kPhasedHybridTma && !tma_plan_feasible(lmax)) {
     v = lmax > SHM_LMAX_CAP ? 6 : 11;
+  } else if (p == kPhasedHybridTma2 && !(lmax == 3 || lmax == 5 || lmax == 7 || lmax == 9)) {
+    v = lmax > SHM_LMAX_CAP ? 6 : (tma_plan_feasible(lmax) ? 12 : 11);
   } else if (lmax > SHM_LMAX_CAP) {
     if (v == 7) v = 1;              // hybrid-64 -> staged-64
     else if (v == 8) v = 0;         // hybrid-128 -> staged-128
@@ -134,9 +138,14 @@ inline int effective_variant(bool fp64, int v, int lmax = 0) {
 // staged-64 for FP32 rows (HBM-bound, coalesced stores).  At an lmax without
 // a TMA plan the FP64 default runs phased-hybrid-128, above l = 9 phased-128
 // (effective_variant).
+// At l = 5 and 7 the double-buffered TMA form is faster (0.63 / 0.88 ms
+// against 0.64 / 0.93 ms on the 192^3 grid); at l = 9 its six phases cost
+// more in barriers than the waits they save (1.99 against 1.30 ms).
 constexpr int kDefaultVariantF64 = 12;
 constexpr int kDefaultVariantF32 = 1;
-inline int default_variant(bool fp64) { return fp64 ? kDefaultVariantF64 : kDefaultVariantF32; }
+inline int default_variant(bool fp64, int lmax = 9) {
+  return fp64 ? ((lmax == 5 || lmax == 7) ? 13 : kDefaultVariantF64) : kDefaultVariantF32;
+}
 
 // chosen[dtype][lmax] (-1 = default)
 int g_choice[2][SHM_LMAX_EXT + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
@@ -144,6 +153,7 @@ int g_choice[2][SHM_LMAX_EXT + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1
 
 template <typename T, int LMAX, int TPB, int PATH>
 size_t eval_smem_bytes() {
+  if (PATH == kPhasedHybridTma2) return Tma2Plan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhasedHybridTma) return TmaPlan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhased || PATH == kPhasedHybrid)
     return (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * sizeof(double);
@@ -152,7 +162,8 @@ size_t eval_smem_bytes() {
 
 template <typename T, int LMAX, int TPB, int PATH>
 auto pick_kernel() {
-  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid || PATH == kPhasedHybridTma) && sizeof(T) == 8) {
+  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid || PATH == kPhasedHybridTma || PATH == kPhasedHybridTma2) &&
+                sizeof(T) == 8) {
     return k_eval_phased<LMAX, TPB, PATH != kPhased>;
   } else {
     return k_eval<T, LMAX, TPB, (PATH == kPhased || (PATH == kHybrid && sizeof(T) == 4)) ? kStaged : PATH>;
@@ -165,7 +176,7 @@ template <typename T, int LMAX, int TPB, int PATH>
 shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t stream) {
   constexpr int MAXDEV = 64;
   static int blocks_per_sm[MAXDEV] = {0};
-  if constexpr (PATH == kPhased || PATH == kPhasedHybrid || PATH == kPhasedHybridTma) {
+  if constexpr (PATH == kPhased || PATH == kPhasedHybrid || PATH == kPhasedHybridTma || PATH == kPhasedHybridTma2) {
     if constexpr (sizeof(T) == 4) {
       return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, stream);
     }
@@ -177,6 +188,14 @@ shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool 
       if (st != SHM_OK || launched) return st;
     }
     return eval_launch_v<T, LMAX, TPB, kPhasedHybrid>(pts, n, out, normalized, vec, stream);
+  }
+  if constexpr (PATH == kPhasedHybridTma2 && sizeof(T) == 8) {
+    bool launched = false;
+    if (vec) {
+      shm_status st = launch_phased_tma2<LMAX, TPB, kInPoints>(pts, n, out, normalized, stream, &launched);
+      if (st != SHM_OK || launched) return st;
+    }
+    return eval_launch_v<T, LMAX, TPB, kPhasedHybridTma>(pts, n, out, normalized, vec, stream);
   }
   const int dev = current_device();
   auto kern = pick_kernel<T, LMAX, TPB, PATH>();
@@ -202,7 +221,7 @@ template <typename T, int LMAX>
 shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t s, int variant) {
   if (variant < 0) {
     variant = g_choice[sizeof(T) == 8 ? 1 : 0][LMAX];
-    if (variant < 0) variant = default_variant(sizeof(T) == 8);
+    if (variant < 0) variant = default_variant(sizeof(T) == 8, LMAX);
   }
   variant = effective_variant(sizeof(T) == 8, variant, LMAX);
   if constexpr (LMAX > SHM_LMAX_CAP) {
@@ -231,6 +250,7 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
     case 10: return eval_launch_v<T, LMAX, 64, kPhasedHybrid>(pts, n, out, normalized, vec, s);
     case 11: return eval_launch_v<T, LMAX, 128, kPhasedHybrid>(pts, n, out, normalized, vec, s);
     case 12: return eval_launch_v<T, LMAX, 128, kPhasedHybridTma>(pts, n, out, normalized, vec, s);
+    case 13: return eval_launch_v<T, LMAX, 128, kPhasedHybridTma2>(pts, n, out, normalized, vec, s);
   }
   return fail(SHM_EINVAL, "unknown launch variant");
 }
@@ -405,7 +425,8 @@ namespace {
 
 const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64",  "staged-256", "direct-128", "direct-256",
                                            "phased-64",  "phased-128", "hybrid-64",  "hybrid-128", "hybrid-256",
-                                           "phased-hybrid-64", "phased-hybrid-128", "phased-hybrid-tma-128"};
+                                           "phased-hybrid-64", "phased-hybrid-128", "phased-hybrid-tma-128",
+                                           "phased-hybrid-tma2-128"};
 
 std::mutex g_tune_mu;
 bool g_cache_loaded = false;
@@ -517,7 +538,7 @@ extern "C" const char* shm_eval_variant(int lmax, shm_dtype dtype) {
   if (lmax < 0 || lmax > SHM_LMAX_EXT || (dtype != SHM_F32 && dtype != SHM_F64)) return "";
   ensure_tune_cache();
   const int v = g_choice[dtype == SHM_F64 ? 1 : 0][lmax];
-  return kVariantNames[effective_variant(dtype == SHM_F64, v < 0 ? default_variant(dtype == SHM_F64) : v, lmax)];
+  return kVariantNames[effective_variant(dtype == SHM_F64, v < 0 ? default_variant(dtype == SHM_F64, lmax) : v, lmax)];
 }
 
 extern "C" int shm_eval_variant_count(void) { return shm::kNumVariants; }

@@ -180,35 +180,55 @@ def test_unaligned_output_uses_scalar_path(oracle_mod):
 
 
 TMA_VARIANT = 12
+TMA2_VARIANT = 13
 COPY_OUT_VARIANT = 11
 
 
+def _tma_test_points(n):
+    """Random-sphere points with, where n allows, origin and non-finite rows
+    in the first tile, the middle and the ragged last tile."""
+    pts = inputs.random_sphere_points(n, stream="tests", with_axes=False)
+    special = {0: [0.0, 0.0, 0.0], 5: [np.nan, 1.0, 0.0], n // 2: [0.0, -0.0, 0.0], n - 1: [np.inf, 0.0, 1.0]}
+    for i, v in special.items():
+        if n > 8:
+            pts[i] = v
+    return pts
+
+
+@pytest.mark.parametrize("variant", [TMA_VARIANT, TMA2_VARIANT])
 @pytest.mark.parametrize("lmax", [1, 2, 3, 5, 7, 9, 11])
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 4099, 200_003])
-def test_tma_variant_matches_copy_out_variant(lmax, n):
-    """phased-hybrid-tma-128 (TMA tensor stores of each staged phase) writes
-    the same bits as phased-hybrid-128 (copy-out loop), ragged last tiles
-    included; at an lmax without a TMA plan (even, or above 9) it runs the
-    copy-out kernel."""
-    assert shm.eval_variant_count() > TMA_VARIANT
-    pts = inputs.random_sphere_points(n, stream="tests", with_axes=False)
+def test_tma_variants_match_copy_out_variant(variant, lmax, n):
+    """phased-hybrid-tma-128 (TMA tensor stores of each staged phase) and
+    phased-hybrid-tma2-128 (double-buffered, 20-column phases) write the same
+    bits as phased-hybrid-128 (copy-out loop), ragged last tiles, origin and
+    non-finite rows included; at an lmax without a plan they run the next
+    form down (tma2 -> tma -> copy-out)."""
+    assert shm.eval_variant_count() > TMA2_VARIANT
+    pts = _tma_test_points(n)
     p = torch.from_numpy(pts).cuda()
+    has_tma = lmax % 2 == 1 and lmax <= 9
+    has_tma2 = lmax in (3, 5, 7, 9)
+    expect = {TMA_VARIANT: "phased-hybrid-tma-128" if has_tma else "phased-hybrid-128" if lmax <= 9 else "phased-128",
+              TMA2_VARIANT: "phased-hybrid-tma2-128" if has_tma2 else "phased-hybrid-tma-128" if has_tma else
+              "phased-hybrid-128" if lmax <= 9 else "phased-128"}[variant]
     try:
-        shm.set_eval_variant(lmax, torch.float64, TMA_VARIANT)
+        shm.set_eval_variant(lmax, torch.float64, variant)
         name = shm.eval_variant(lmax, torch.float64)
-        assert name == ("phased-hybrid-tma-128" if lmax % 2 == 1 and lmax <= 9 else
-                        "phased-hybrid-128" if lmax <= 9 else "phased-128"), (lmax, name)
+        assert name == expect, (lmax, name)
         out = torch.full((n, (lmax + 1) ** 2), 7.0, dtype=torch.float64, device="cuda")
         shm.eval_sh(p, lmax, out=out)
         shm.set_eval_variant(lmax, torch.float64, COPY_OUT_VARIANT)
         ref = shm.eval_sh(p, lmax)
         torch.cuda.synchronize()
-        assert torch.equal(out, ref), (lmax, n)
+        assert torch.equal(torch.nan_to_num(out, nan=5.0), torch.nan_to_num(ref, nan=5.0)), (lmax, n)
+        assert torch.equal(torch.isnan(out), torch.isnan(ref))
     finally:
         shm.set_eval_variant(lmax, torch.float64, -1)
 
 
-def test_tma_variant_next_to_other_allocations():
+@pytest.mark.parametrize("variant", [TMA_VARIANT, TMA2_VARIANT])
+def test_tma_variant_next_to_other_allocations(variant):
     """The TMA stores of the last (ragged) tile stop at row n: the bytes
     after the output, inside the same allocation, are left untouched."""
     n = 1000
@@ -216,10 +236,11 @@ def test_tma_variant_next_to_other_allocations():
     p = torch.from_numpy(pts).cuda()
     buf = torch.full((n + 300, 100), -3.0, dtype=torch.float64, device="cuda")
     try:
-        shm.set_eval_variant(9, torch.float64, TMA_VARIANT)
+        shm.set_eval_variant(9, torch.float64, variant)
         shm.eval_sh(p, 9, out=buf[:n])
         torch.cuda.synchronize()
         assert torch.all(buf[n:] == -3.0)
+        shm.set_eval_variant(9, torch.float64, COPY_OUT_VARIANT)
         assert torch.equal(buf[:n], shm.eval_sh(p, 9))
     finally:
         shm.set_eval_variant(9, torch.float64, -1)
