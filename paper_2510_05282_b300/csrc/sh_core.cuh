@@ -375,6 +375,22 @@ __device__ __forceinline__ double ff_to_double(ff a) {
   return (__float_as_uint(a.hi) & 0x7f800000u) == 0x7f800000u ? __longlong_as_double(0x7ff8000000000000ll) : d;
 }
 
+// binary64 -> float-float, the cheap way: hi = d with its significand
+// truncated to 24 bits (integer instructions on the bit pattern), lo = the
+// remaining 29 bits as an integer, converted (one rounding to 24 bits) and
+// scaled by 2^(E-52).  hi + lo is within 2^-48 |d| of d, |lo| < ulp(hi).
+// For |d| < 2^127 only; |d| < 2^-74 gives +-0 (absolute error < 2^-74).
+__device__ __forceinline__ ff ff_from_double_fast(double d) {
+  const unsigned h = (unsigned)__double2hiint(d), l = (unsigned)__double2loint(d);
+  const unsigned sg = h & 0x80000000u;
+  const unsigned mag = h & 0x7fffffffu;
+  const bool tiny = mag < (949u << 20);
+  const unsigned hb = tiny ? sg : (__funnelshift_l(l, mag - (896u << 20), 3) | sg);
+  const float scale = __uint_as_float((((mag >> 20) - 948u) << 23) | sg);  // sign(d) 2^(E-52)
+  const float lo = tiny ? 0.0f : __uint2float_rn(l & 0x1fffffffu) * scale;
+  return {__uint_as_float(hb), lo};
+}
+
 // True if any component is infinite or NaN.  Every evaluator gives such a
 // point a row of NaN except the constant l = 0 value.
 __device__ __forceinline__ bool nonfinite3(double x, double y, double z) {
@@ -599,7 +615,39 @@ __device__ __forceinline__ void sh_column_ff(float zb, float dq, float A, float 
   }
 }
 
-template <int LMAX, bool CX = false, typename Store>
+// The m = 0, 1 columns with the plain FP32 recurrence (for short rows: at
+// l <= 4 their rounding stays far inside the FP32 tolerances).
+template <int LMAX, int M, bool CX, typename Store>
+__device__ __forceinline__ void sh_column_f32(float zb, float qq, float A, float B, Store&& store) {
+  if constexpr (M == 0) {
+    store(0, Shi<CX>(0, 0));
+  } else {
+    store(M * M + 2 * M, (float)Sd<CX>(M, M) * A);
+    store(M * M, (float)Sd<CX>(M, M) * B);
+  }
+  auto emit = [&](int l, float q) {
+    const float v = (float)Sd<CX>(l, M) * q;
+    if constexpr (M == 0) {
+      store(l * l + l, v);
+    } else {
+      store(l * l + l + M, v * A);
+      store(l * l + l - M, v * B);
+    }
+  };
+  if constexpr (M + 1 <= LMAX) emit(M + 1, zb);
+  float q2 = 1.0f, q1 = zb;
+#pragma unroll
+  for (int l = M + 2; l <= LMAX; ++l) {
+    const float q = fmaf(zb, q1, -(float)SHM_G[l][M] * (qq * q2));
+    emit(l, q);
+    q2 = q1;
+    q1 = q;
+  }
+}
+
+// FF01 = false: the m = 0, 1 columns use the plain FP32 recurrence
+// (sh_column_f32), for short rows only.
+template <int LMAX, bool CX = false, bool FF01 = true, typename Store>
 __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& store) {
   // q = xb^2 + yb^2 + zb^2 as a float-float, then dq = q - 1
   const ff px = two_prod(xb, xb), py = two_prod(yb, yb), pz = two_prod(zb, zb);
@@ -610,8 +658,13 @@ __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& sto
   const float dq = __fadd_rn(__fsub_rn(qf.hi, 1.0f), qf.lo);
   const float qq = qf.hi;
 
-  sh_column_ff<LMAX, 0, CX>(zb, dq, 0.0f, 0.0f, store);
-  if constexpr (LMAX >= 1) sh_column_ff<LMAX, 1, CX>(zb, dq, xb, yb, store);
+  if constexpr (FF01) {
+    sh_column_ff<LMAX, 0, CX>(zb, dq, 0.0f, 0.0f, store);
+    if constexpr (LMAX >= 1) sh_column_ff<LMAX, 1, CX>(zb, dq, xb, yb, store);
+  } else {
+    sh_column_f32<LMAX, 0, CX>(zb, qq, 0.0f, 0.0f, store);
+    if constexpr (LMAX >= 1) sh_column_f32<LMAX, 1, CX>(zb, qq, xb, yb, store);
+  }
   float A = xb, B = yb;
 #pragma unroll
   for (int m = 2; m <= LMAX; ++m) {

@@ -307,7 +307,10 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool uni
   }
   T xb = dx, yb = dy, zb = dz;
   if (!unit) unit_dir(dx, dy, dz, xb, yb, zb);
-  sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
+  if constexpr (sizeof(T) == 4)  // FP32: the plain recurrence for m = 0, 1 up to l = 4
+    sh_row<LMAX, false, (LMAX > 4)>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
+  else
+    sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
 }
 
 template <typename T>
@@ -395,10 +398,18 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
   if (!origin) {
     const float r2 = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     float r;
-    if (r2 < 1e-4f) {  // r < 1e-2: r in FP64
-      r = (float)sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
-    } else {
-      r = sqrtf(r2);
+    if (r2 < 1e-4f) {  // r < 1e-2: r and the unit vector in FP64
+      const double rd = sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
+      r = (float)rd;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) d[c] = (float)((double)d[c] / rd);
+    } else {  // one reciprocal square root (and a Newton step) gives r and the unit vector
+      float ri = rsqrtf(r2);
+      const float hr = r2 * ri;
+      ri = fmaf(0.5f * ri, fmaf(-hr, ri, 1.0f), ri);
+      r = r2 * ri;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) d[c] *= ri;
     }
     // r = m 2^e with m in [0.5, 1), read from the bits (r is a normal float here)
     const unsigned rb = __float_as_uint(r);
@@ -422,7 +433,7 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
   }
   const Lagrange4<float> L = lagrange_at<float>(it, u, P.n_rad);
   const float* tab = P.rad32 + (int64_t)s * P.lstride * P.n_rad + L.i0;
-  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, false, L, tab, P.n_rad, row);
+  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, true, L, tab, P.n_rad, row);
 }
 
 // ---------------------------------------------------------------------------
