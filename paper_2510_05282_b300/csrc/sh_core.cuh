@@ -413,23 +413,36 @@ __device__ __forceinline__ bool nonfinite3(float x, float y, float z) {
 // instructions per point drop from ~242 to ~75.  The direction must be
 // finite: for a non-finite one the float-float columns are meaningless
 // (callers test nonfinite3 and write a NaN row instead).
-template <int LMAX, bool CX = false, typename Store>
-__device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, Store&& store) {
-  store(0, Sd<CX>(0, 0));
+// SCALED: every value of shell l comes out multiplied by a per-l factor,
+// given as binary64 (fd[l], for the binary64 columns) and as float-float
+// (fff[l], folded into the float-float products before their conversion, so
+// the m >= 2 values need no extra binary64 multiply).  Unscaled rows are
+// bitwise unchanged.
+template <int LMAX, bool CX = false, bool SCALED = false, typename Store>
+__device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, Store&& store,
+                                              const double* fd = nullptr, const ff* fff = nullptr) {
+  auto sc = [&](int l, double v) {  // the binary64 columns' values
+    if constexpr (SCALED)
+      return v * fd[l];
+    else
+      return v;
+  };
+  store(0, sc(0, Sd<CX>(0, 0)));
   if constexpr (LMAX >= 1) {
-    store(2, Sd<CX>(1, 0) * zb);
+    store(2, sc(1, Sd<CX>(1, 0) * zb));
     double q2 = 1.0, q1 = zb;
 #pragma unroll
     for (int l = 2; l <= LMAX; ++l) {
       const double q = fma(zb, q1, -SHM_G[l][0] * q2);
-      store(l * l + l, Sd<CX>(l, 0) * q);
+      store(l * l + l, sc(l, Sd<CX>(l, 0) * q));
       q2 = q1;
       q1 = q;
     }
-    store(3, Sd<CX>(1, 1) * xb);
-    store(1, Sd<CX>(1, 1) * yb);
+    const double s1 = sc(1, Sd<CX>(1, 1));
+    store(3, s1 * xb);
+    store(1, s1 * yb);
     if constexpr (LMAX >= 2) {
-      const double s = Sd<CX>(2, 1) * zb;
+      const double s = sc(2, Sd<CX>(2, 1) * zb);
       store(7, s * xb);
       store(5, s * yb);
     }
@@ -438,7 +451,7 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
 #pragma unroll
     for (int l = 3; l <= LMAX; ++l) {
       const double q = fma(zb, q1, -SHM_G[l][1] * q2);
-      const double s = Sd<CX>(l, 1) * q;
+      const double s = sc(l, Sd<CX>(l, 1) * q);
       store(l * l + l + 1, s * xb);
       store(l * l + l - 1, s * yb);
       q2 = q1;
@@ -454,11 +467,18 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
       const ff Bn = ff_add(ff_mul_u(A, Y), ff_mul_u(B, X));
       A = An;
       B = Bn;
-      store(m * m + 2 * m, ff_to_double_finite(ff_mul_c(A, Shi<CX>(m, m), Slo<CX>(m, m))));
-      store(m * m, ff_to_double_finite(ff_mul_c(B, Shi<CX>(m, m), Slo<CX>(m, m))));
+      if constexpr (SCALED) {
+        const ff sf = ff_mul_c_u(fff[m], Shi<CX>(m, m), Slo<CX>(m, m));
+        store(m * m + 2 * m, ff_to_double_finite(ff_mul(sf, A)));
+        store(m * m, ff_to_double_finite(ff_mul(sf, B)));
+      } else {
+        store(m * m + 2 * m, ff_to_double_finite(ff_mul_c(A, Shi<CX>(m, m), Slo<CX>(m, m))));
+        store(m * m, ff_to_double_finite(ff_mul_c(B, Shi<CX>(m, m), Slo<CX>(m, m))));
+      }
       ff q2 = {1.0f, 0.0f}, q1 = Z;
       if (m + 1 <= LMAX) {
-        const ff s = ff_mul_c_u(Z, Shi<CX>(m + 1, m), Slo<CX>(m + 1, m));
+        ff s = ff_mul_c_u(Z, Shi<CX>(m + 1, m), Slo<CX>(m + 1, m));
+        if constexpr (SCALED) s = ff_mul_u(s, fff[m + 1]);
         const int k0 = (m + 1) * (m + 1) + (m + 1);
         store(k0 + m, ff_to_double_finite(ff_mul(s, A)));
         store(k0 - m, ff_to_double_finite(ff_mul(s, B)));
@@ -466,7 +486,8 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
 #pragma unroll
       for (int l = m + 2; l <= LMAX; ++l) {
         const ff q = ff_add(ff_mul_u(Z, q1), ff_neg(ff_mul_c_u(q2, SHM_G_HI[l][m], SHM_G_LO[l][m])));
-        const ff s = ff_mul_c_u(q, Shi<CX>(l, m), Slo<CX>(l, m));
+        ff s = ff_mul_c_u(q, Shi<CX>(l, m), Slo<CX>(l, m));
+        if constexpr (SCALED) s = ff_mul_u(s, fff[l]);
         store(l * l + l + m, ff_to_double_finite(ff_mul(s, A)));
         store(l * l + l - m, ff_to_double_finite(ff_mul(s, B)));
         q2 = q1;

@@ -309,8 +309,12 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool uni
   if (!unit) unit_dir(dx, dy, dz, xb, yb, zb);
   if constexpr (sizeof(T) == 4)  // FP32: the plain recurrence for m = 0, 1 up to l = 4
     sh_row<LMAX, false, (LMAX > 4)>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
-  else if constexpr (LMAX >= 2)  // FP64: the hybrid row (m >= 2 in float-float, off the FP64 pipe)
-    sh_row_hybrid<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
+  else if constexpr (LMAX >= 2) {  // FP64: the hybrid row (m >= 2 in float-float, off the FP64 pipe),
+    ff fff[LMAX + 1];              // with f_l folded into its products
+#pragma unroll
+    for (int l = 2; l <= LMAX; ++l) fff[l] = ff_from_double(f[l]);
+    sh_row_hybrid<LMAX, false, true>(xb, yb, zb, [&](int k, T v) { row[k] = v; }, f, fff);
+  }
   else
     sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
 }
