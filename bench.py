@@ -161,7 +161,9 @@ def run_reference(args, rank, world):
     from paper_2510_05282_b300 import inputs
     pts = inputs.dft_grid_points(N_SIDE)
     nh = (LMAX + 1) ** 2
-    budget = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    # about two minutes for the whole run whatever --steps and --warmup are,
+    # and at most --cpu-seconds per step
+    budget = min(args.cpu_seconds, 20.0, max(0.05, 120.0 / max(1, args.steps + args.warmup)))
     rates = []
     sample_pts = 0
     cores = 1
