@@ -391,6 +391,75 @@ __device__ __forceinline__ ff ff_from_double_fast(double d) {
   return {__uint_as_float(hb), lo};
 }
 
+// sin and cos of a (radians) as float-float, for |a| <= 800; error below
+// ~2^-47.  Argument reduction: k = nearest integer to a 2/pi, r = a - k pi/2
+// with pi/2 = P1 + P2 + P3 (P1 with 15 significant bits, so k P1 is exact for
+// |k| < 512; the three parts carry pi/2 to 2^-88): a - k P1 in binary64 is
+// exact (the operands are within a factor 2, or k = 0), and the rest runs in
+// float-float on the small remainder; |r| <= pi/4 (plus rounding of k).  Then
+// the Taylor series in z = r^2 -- sin r to r^15, cos r to r^18, truncation
+// below 2^-53 at |r| = pi/4 -- by Horner's rule in float-float, and the
+// quadrant of k.  Two FP64-pipe instructions (the subtraction and the
+// float -> binary64 conversion of k P1), the rest on the FP32 pipe.
+__device__ __forceinline__ ff ff_horner(ff p, ff z, float chi, float clo) { return ff_add(ff_mul_u(p, z), ff{chi, clo}); }
+__device__ __forceinline__ void ff_sincos(double a, ff& s, ff& c) {
+  const float kf = rintf(ff_from_double_fast(a).hi * 0x1.45f306p-1f);  // a 2/pi, rounded to an integer
+  ff r = ff_from_double(a - (double)(kf * 0x1.921cp+0f));
+  r = ff_add(r, ff_neg(two_prod(kf, 0x1.daa222p-15f)));
+  r = ff_add(r, ff{-kf * -0x1.2e7b96p-40f, 0.0f});
+  const ff z = ff_mul(r, r);
+  // sin r = r + r z (-1/3! + z/5! - z^2/7! + ... - z^6/15!)
+  ff ps = {-0x1.ae7f3ep-41f, -0x1.ccee08p-67f};              // -1/15!
+  ps = ff_horner(ps, z, 0x1.6124620p-33f, -0x1.8af25ep-58f);  // +1/13!
+  ps = ff_horner(ps, z, -0x1.ae64560p-26f, -0x1.fd5138p-52f); // -1/11!
+  ps = ff_horner(ps, z, 0x1.71de3ap-19f, 0x1.55b1ccp-45f);    // +1/9!
+  ps = ff_horner(ps, z, -0x1.a01a02p-13f, 0x1.7f97fap-39f);   // -1/7!
+  ps = ff_horner(ps, z, 0x1.111112p-7f, -0x1.dddddep-32f);    // +1/5!
+  ps = ff_horner(ps, z, -0x1.555556p-3f, 0x1.555556p-28f);    // -1/3!
+  const ff sr = ff_add(r, ff_mul_u(ff_mul_u(r, z), ps));
+  // cos r = 1 + z (-1/2! + z/4! - ... - z^8/18!)
+  ff pc = {-0x1.682786p-53f, -0x1.dcbeccp-80f};              // -1/18!
+  pc = ff_horner(pc, z, 0x1.ae7f3ep-45f, 0x1.ccee08p-71f);    // +1/16!
+  pc = ff_horner(pc, z, -0x1.93974ap-37f, -0x1.180f94p-62f);  // -1/14!
+  pc = ff_horner(pc, z, 0x1.1eed8ep-29f, 0x1.ff1b12p-54f);    // +1/12!
+  pc = ff_horner(pc, z, -0x1.27e4fcp-22f, 0x1.10ec14p-47f);   // -1/10!
+  pc = ff_horner(pc, z, 0x1.a01a02p-16f, -0x1.7f97fap-42f);   // +1/8!
+  pc = ff_horner(pc, z, -0x1.6c16c2p-10f, 0x1.27d27ep-35f);   // -1/6!
+  pc = ff_horner(pc, z, 0x1.555556p-5f, -0x1.555556p-30f);    // +1/4!
+  pc = ff_horner(pc, z, -0.5f, 0.0f);                          // -1/2!
+  const ff cr = ff_add(ff{1.0f, 0.0f}, ff_mul_u(z, pc));
+  // quadrant k mod 4: (sin, cos) = (s, c), (c, -s), (-s, -c), (-c, s)
+  const int q = (int)kf & 3;
+  const ff s1 = (q & 1) ? cr : sr, c1 = (q & 1) ? sr : cr;
+  s = (q & 2) ? ff_neg(s1) : s1;
+  c = ((q + 1) & 2) ? ff_neg(c1) : c1;
+}
+
+// Unit vector of the angles (theta, phi), Eq. 3-4 read backwards.  cos theta
+// drives the z-recurrences, whose coefficients amplify its error by up to
+// ~l^2, so theta takes the binary64 sincos; sin theta, cos phi and sin phi
+// enter only through the products x, y and the float-float powers of x + iy,
+// where 48 bits suffice, so phi takes the float-float sine/cosine (FP32 pipe)
+// when |phi| <= 800 and the binary64 one otherwise (also for non-finite phi,
+// which then gives NaN components).
+__device__ __forceinline__ void angles_to_unit(double theta, double phi, double& xb, double& yb, double& zb) {
+  double st, ct;
+  sincos(theta, &st, &ct);
+  if (fabs(phi) <= 800.0) {
+    ff sp, cp;
+    ff_sincos(phi, sp, cp);
+    const ff s = ff_from_double(st);
+    xb = ff_to_double_finite(ff_mul(s, cp));
+    yb = ff_to_double_finite(ff_mul(s, sp));
+  } else {
+    double sp, cp;
+    sincos(phi, &sp, &cp);
+    xb = st * cp;
+    yb = st * sp;
+  }
+  zb = ct;
+}
+
 // True if any component is infinite or NaN.  Every evaluator gives such a
 // point a row of NaN except the constant l = 0 value.
 __device__ __forceinline__ bool nonfinite3(double x, double y, double z) {

@@ -176,12 +176,7 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased_tma(const double
     if constexpr (IN == kInAngles) {
       if (valid) {  // Eq. 3-4 read backwards: the unit vector of (theta, phi)
         const int64_t p = p0 + threadIdx.x;
-        double st, ct, sp, cp;
-        sincos(in[2 * p], &st, &ct);
-        sincos(in[2 * p + 1], &sp, &cp);
-        xb = st * cp;
-        yb = st * sp;
-        zb = ct;
+        angles_to_unit(in[2 * p], in[2 * p + 1], xb, yb, zb);
       }
     } else {
       double x = 0.0, y = 0.0, z = 1.0;
@@ -329,12 +324,7 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased_tma2(const doubl
     if constexpr (IN == kInAngles) {
       if (valid) {  // Eq. 3-4 read backwards: the unit vector of (theta, phi)
         const int64_t p = p0 + threadIdx.x;
-        double st, ct, sp, cp;
-        sincos(in[2 * p], &st, &ct);
-        sincos(in[2 * p + 1], &sp, &cp);
-        xb = st * cp;
-        yb = st * sp;
-        zb = ct;
+        angles_to_unit(in[2 * p], in[2 * p + 1], xb, yb, zb);
       }
     } else {
       double x = 0.0, y = 0.0, z = 1.0;

@@ -65,3 +65,32 @@ def test_random_angles_against_oracle(oracle_mod, dtype, tol, lmax):
     got = shm.eval_angles(a, lmax).cpu().numpy()
     a64 = a.double().cpu().numpy()
     assert_normwise(got, oracle_mod.real_sh_angles(a64[:, 0], a64[:, 1], lmax), tol, f"angles {dtype}")
+
+
+@pytest.mark.parametrize("lmax", [3, 9])
+def test_wide_phi_range_against_oracle(oracle_mod, lmax):
+    """FP64 rows over azimuths far outside [-pi, pi]: the float-float
+    sine/cosine of phi (|phi| <= 800) with its argument reduction, the binary64
+    one beyond, and azimuths on and next to the quadrant boundaries k pi/2
+    and the switch at |phi| = 800.  The oracle evaluates cos(m phi) with m phi
+    rounded in binary64, an error of up to m |phi| 2^-53 at large |phi|; R is
+    2 pi-periodic in phi, so it is given phi reduced to [-pi, pi] in 120-bit
+    arithmetic instead (within 2^-52 of the exact reduction)."""
+    g = inputs.rng("tests", 37)
+    n = 12000
+    theta = np.arccos(g.uniform(-1, 1, n))
+    phi = g.uniform(-1000.0, 1000.0, n)
+    k = np.arange(-40, 41)
+    edges = np.concatenate([k * np.pi / 2, k * np.pi / 2 + 1e-13, k * np.pi / 2 - 1e-9, k * np.pi / 4 + 509 * np.pi / 2,
+                            [800.0, -800.0, np.nextafter(800.0, 1e3), np.nextafter(-800.0, -1e3), 0.0, -0.0, 1e-300,
+                             -3e-8, 799.9999999, -254.5 * np.pi]])
+    phi[:edges.size] = edges
+    ang = np.stack([theta, phi], axis=1)
+    a = torch.from_numpy(ang).to(device="cuda", dtype=torch.float64)
+    got = shm.eval_angles(a, lmax).cpu().numpy()
+    mpmath = pytest.importorskip("mpmath")
+    with mpmath.workprec(120):
+        two_pi = 2 * mpmath.pi
+        phi_red = np.array([float(mpmath.mpf(float(v)) - two_pi * round(v / (2 * np.pi))) for v in phi])
+    assert np.all(np.abs(phi_red) <= np.pi + 1e-9)
+    assert_normwise(got, oracle_mod.real_sh_angles(ang[:, 0], phi_red, lmax), TOL_F64, "wide phi")
