@@ -187,16 +187,20 @@ size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dty
 
 /*
  * shm_projectors -- the fused projector values, one persistent launch after a
- * set-up launch on `stream` (one CTA; for SHM_F32 also one CTA per 1,024
- * table values, up to the SM count, that convert the radial tables).
- *   dtype     : SHM_F64 (FP64 arithmetic, double out) or SHM_F32 (FP32
- *               arithmetic on FP32 copies of the tables, float out; grid
- *               displacements are formed exactly before rounding to float,
- *               1/r in FP64 for |d| < 1e-2).
+ * set-up launch on `stream` (one CTA per 1,024 table values, up to the SM
+ * count: for SHM_F32 they convert the radial tables, for SHM_F64 they write
+ * each table interval's interpolating cubic).
+ *   dtype     : SHM_F64 (FP64 arithmetic, double out; the 4-point Lagrange
+ *               interpolation evaluated as the interval's cubic in the
+ *               fractional index, the same polynomial up to rounding) or
+ *               SHM_F32 (FP32 arithmetic on FP32 copies of the tables, float
+ *               out; grid displacements are formed exactly before rounding to
+ *               float, 1/r in FP64 for |d| < 1e-2).
  *   out       : device [n_values] of dtype, caller-owned.
  *   workspace : device scratch of >= shm_projectors_workspace_size() bytes,
  *               caller-owned; it holds the work-queue counter, the per-atom
- *               tile table, an error word and (SHM_F32) the FP32 tables.  One
+ *               tile table, an error word and the FP32 tables (SHM_F32) or
+ *               the interval cubics (SHM_F64, 32 bytes per table node).  One
  *               workspace must not be shared by calls that overlap on the GPU.
  * The kernel checks every index it reads through (species, grid index, table
  * stencil, output range) against the problem's sizes; an inconsistent problem
@@ -314,7 +318,8 @@ void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3]);
  * loop with a fixed memory budget that may not grow or synchronise the device
  * through cudaMalloc/cudaFree.  They pass only the problem and the output;
  * the scratch (work counter, error word, per-atom tile table and, for
- * SHM_F32, the FP32 copies of the radial tables) lives in a static device
+ * SHM_F32, the FP32 copies of the radial tables, for SHM_F64 the cubic of
+ * each table interval, 32 bytes per node) lives in a static device
  * array of SHM_PROJ_NOALLOC_SCRATCH_BYTES bytes inside this library, which
  * every GPU that loads the library holds until the process exits.
  *   prob, dtype, out, stream : as shm_projectors.
@@ -332,7 +337,7 @@ void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3]);
  * SHM_PROJ_NOALLOC_SCRATCH_BYTES (shm_projectors_workspace_size tells how
  * much); SHM_ECUDA if the symbol lookup fails.
  */
-#define SHM_PROJ_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define SHM_PROJ_NOALLOC_SCRATCH_BYTES (1u << 23)
 shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* stream);
 
 /*

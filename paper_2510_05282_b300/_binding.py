@@ -258,7 +258,7 @@ _EXTRA_DECLS.extend([
                                 ctypes.c_int)),
 ])
 
-PROJ_NOALLOC_SCRATCH_BYTES = 1 << 20
+PROJ_NOALLOC_SCRATCH_BYTES = 1 << 23
 
 
 class DeviceProjectors:

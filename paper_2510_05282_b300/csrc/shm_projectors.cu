@@ -52,6 +52,7 @@ struct ProjWs {
   size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
   size_t atomf = 0;        // FP32: AtomF32[n_atoms] (atom coordinates in grid units)
   size_t rad32 = 0;        // FP32: float radial[n_species][lstride][n_rad]
+  size_t coef = 0;         // FP64: double {a0, a1, a2, a3}[n_species][lstride][n_rad] (cubic per interval)
   size_t total = 0;
 };
 
@@ -68,6 +69,9 @@ ProjWs proj_layout(const shm_proj_problem& p, shm_dtype dt) {
     end += round256((size_t)p.n_atoms * sizeof(AtomF32));
     w.rad32 = end;
     end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 4);
+  } else {
+    w.coef = end;
+    end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 32);
   }
   w.total = end;
   return w;
@@ -93,6 +97,7 @@ struct ProjParams {
   int2* etab;
   float* rad32;
   AtomF32* atomf;
+  double* coef;
 };
 
 enum : unsigned { kErrOffsets = 1u, kErrSpecies = 2u, kErrGrid = 4u, kErrOut = 8u };
@@ -104,10 +109,31 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
   __shared__ int64_t warp_sums[32];
   __shared__ int64_t carry;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (fp32) {  // FP32 radial tables, spread over every CTA of the grid
+  {  // FP32 radial tables, or the FP64 interval cubics, spread over every CTA of the grid
     const int64_t nt = (int64_t)P.n_species * P.lstride * P.n_rad;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < nt; i += (int64_t)gridDim.x * blockDim.x)
-      P.rad32[i] = (float)P.radial[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+      if (fp32) {
+        P.rad32[i] = (float)P.radial[i];
+      } else {
+        // 4-point Lagrange interpolation on the interval [it, it + 1] of the
+        // table (stencil i0..i0+3, i0 = clamp(it - 1, 0, n_rad - 4)) as the
+        // cubic a0 + a1 u + a2 u^2 + a3 u^3 in u = t - it: the stencil
+        // polynomial b0 + b1 x + b2 x^2 + b3 x^3 in x = t - i0 from its forward
+        // differences, shifted to x0 = it - i0.
+        const int64_t row = i / P.n_rad;
+        const int it = (int)(i - row * P.n_rad);
+        const int i0 = min(max(it - 1, 0), P.n_rad - 4);
+        const double* F = P.radial + row * P.n_rad + i0;
+        const double d1 = F[1] - F[0], d2 = F[2] - 2.0 * F[1] + F[0], d3 = F[3] - 3.0 * F[2] + 3.0 * F[1] - F[0];
+        const double b3 = d3 / 6.0, b2 = 0.5 * (d2 - d3), b1 = d1 - 0.5 * d2 + d3 / 3.0;
+        const double x0 = (double)(it - i0);
+        double* c = P.coef + 4 * i;
+        c[0] = F[it - i0];
+        c[1] = b1 + x0 * (2.0 * b2 + 3.0 * b3 * x0);
+        c[2] = b2 + 3.0 * b3 * x0;
+        c[3] = b3;
+      }
+    }
   }
   if (blockIdx.x != 0) return;  // the rest is one CTA's work
   if (tid == 0) {
@@ -206,7 +232,7 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
 // tables (float conversions issue to the narrow FP64-class pipe, so one SM
 // alone would take tens of microseconds for 80k values).
 inline unsigned setup_grid(const ProjParams& P, shm_dtype dtype) {
-  if (dtype != SHM_F32) return 1u;
+  (void)dtype;
   const int64_t nt = (int64_t)P.n_species * P.lstride * P.n_rad;
   const int64_t g = (nt + 1023) / 1024;
   const int dev = current_device();
@@ -252,6 +278,60 @@ __device__ __forceinline__ float log_unit(float m, int& e) {
   return 2.0f * z * p;
 }
 
+// ln m as a float-float (FP32 pipe) for m = 1 + f in [sqrt(1/2), sqrt(2)),
+// with f exact in binary64: ln m = 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + ...),
+// s = f / (2 + f), |s| <= 0.1716.  s by a quotient with two correction terms
+// (each the remainder times the reciprocal of the divisor); the series to
+// s^19, its terms from s^11 on (below 2^-28 of the sum) in FP32, the rest in
+// float-float.  Emulated absolute error <= 3.3e-15 (2^-48).
+__device__ __forceinline__ ff ff_log_mantissa(double f) {
+  const ff F = ff_from_double(f);
+  const ff D = ff_add(ff{2.0f, 0.0f}, F);
+  const float rc = __frcp_rn(D.hi);
+  const float q1 = F.hi * rc;
+  ff p = two_prod(q1, D.hi);
+  const ff R = ff_add(F, ff{-p.hi, -fmaf(q1, D.lo, p.lo)});
+  const float q2 = R.hi * rc;
+  p = two_prod(q2, D.hi);
+  const float R2 = __fadd_rn(__fsub_rn(__fsub_rn(R.hi, p.hi), p.lo), __fsub_rn(R.lo, q2 * D.lo));
+  const ff S = ff_add(fast_two_sum(q1, q2), ff{R2 * rc, 0.0f});
+  const ff z = ff_mul(S, S);
+  float h = 1.0f / 19.0f;
+  h = fmaf(h, z.hi, 1.0f / 17.0f);
+  h = fmaf(h, z.hi, 1.0f / 15.0f);
+  h = fmaf(h, z.hi, 1.0f / 13.0f);
+  h = fmaf(h, z.hi, 1.0f / 11.0f);
+  ff P = {h, 0.0f};
+#pragma unroll
+  for (int k = 4; k >= 1; --k) {  // 1/(2k+1) split into hi + lo
+    const float chi = (float)(1.0 / (2 * k + 1));
+    P = ff_add(ff_mul_u(P, z), ff{chi, (float)(1.0 / (2 * k + 1) - (double)chi)});
+  }
+  P = ff_add(ff_mul_u(P, z), ff{1.0f, 0.0f});
+  const ff L = ff_mul(S, P);
+  return {2.0f * L.hi, 2.0f * L.lo};
+}
+
+// Continuous log-grid index t = ln(r / r_min) / dlog from r^2 (a positive
+// normal binary64): r^2 = m 2^E with m in [sqrt(1/2), sqrt(2)), so
+// t = E K1 + K0 + ln(m) K2 with K1 = ln 2 / (2 dlog), K2 = 1 / (2 dlog),
+// K0 = -ln(r_min) / dlog.  E and m come from the bit pattern; ln m from
+// ff_log_mantissa.  Four FP64-pipe instructions (m - 1, E as a double, two
+// FMAs) instead of a binary64 logarithm.
+struct LogGrid64 {
+  double K0, K1, K2;
+};
+__device__ __forceinline__ double log_grid_index(double r2, const LogGrid64& G) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(r2);
+  int E = (int)(b >> 52) - 1023;
+  unsigned long long mb = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull;  // m in [1, 2)
+  const bool halve = mb >= 0x3ff6a09e667f3bcdull;                               // m >= sqrt(2)
+  mb -= halve ? (1ull << 52) : 0ull;
+  E += halve ? 1 : 0;
+  const ff lm = ff_log_mantissa(__longlong_as_double((long long)mb) - 1.0);
+  return fma(ff_to_double_finite(lm), G.K2, fma((double)E, G.K1, G.K0));
+}
+
 // ---------------------------------------------------------------------------
 // Per-row pieces.
 
@@ -283,22 +363,19 @@ __device__ __forceinline__ Lagrange4<T> lagrange_at(int it, T u, int n_rad) {
   return L;
 }
 
-__device__ __forceinline__ double interp4(const Lagrange4<double>& L, const double* F) {
-  return fma(L.w[3], __ldg(F + 3), fma(L.w[2], __ldg(F + 2), fma(L.w[1], __ldg(F + 1), L.w[0] * __ldg(F))));
-}
 __device__ __forceinline__ float interp4(const Lagrange4<float>& L, const float* F) {
   return fmaf(L.w[3], F[3], fmaf(L.w[2], F[2], fmaf(L.w[1], F[1], L.w[0] * F[0])));
 }
 
-// One row (lmax = LMAX): interpolate f_0..f_LMAX at the stencil, then write
-// f_l(r) R_l^m into row[0..(LMAX+1)^2).  tab points at f_{s,0}[i0].
+// One row (lmax = LMAX): f_l(r) = radial(l) for l = 0..LMAX, then write
+// f_l(r) R_l^m into row[0..(LMAX+1)^2).
 // (dx, dy, dz) is the displacement, or with `unit` its unit vector.
-template <int LMAX, typename T>
-__device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool unit, const Lagrange4<T>& L,
-                                         const T* __restrict__ tab, int n_rad, T* __restrict__ row) {
+template <int LMAX, typename T, typename Radial>
+__device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool unit, Radial&& radial,
+                                         T* __restrict__ row) {
   T f[LMAX + 1];
 #pragma unroll
-  for (int l = 0; l <= LMAX; ++l) f[l] = interp4(L, tab + (int64_t)l * n_rad);
+  for (int l = 0; l <= LMAX; ++l) f[l] = radial(l);
   if (origin) {
     row[0] = (T)kInvSqrt4Pi * f[0];
 #pragma unroll
@@ -319,20 +396,20 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool uni
     sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
 }
 
-template <typename T>
+template <typename T, typename Radial>
 __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin, bool unit,
-                                                  const Lagrange4<T>& L, const T* tab, int n_rad, T* row) {
+                                                  Radial&& L, T* row) {
   switch (lmax) {
-    case 0: proj_row<0>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    case 1: proj_row<1>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    case 2: proj_row<2>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    case 3: proj_row<3>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    case 4: proj_row<4>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    case 5: proj_row<5>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    case 6: proj_row<6>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    case 7: proj_row<7>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    case 8: proj_row<8>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
-    default: proj_row<9>(dx, dy, dz, origin, unit, L, tab, n_rad, row); break;
+    case 0: proj_row<0>(dx, dy, dz, origin, unit, L, row); break;
+    case 1: proj_row<1>(dx, dy, dz, origin, unit, L, row); break;
+    case 2: proj_row<2>(dx, dy, dz, origin, unit, L, row); break;
+    case 3: proj_row<3>(dx, dy, dz, origin, unit, L, row); break;
+    case 4: proj_row<4>(dx, dy, dz, origin, unit, L, row); break;
+    case 5: proj_row<5>(dx, dy, dz, origin, unit, L, row); break;
+    case 6: proj_row<6>(dx, dy, dz, origin, unit, L, row); break;
+    case 7: proj_row<7>(dx, dy, dz, origin, unit, L, row); break;
+    case 8: proj_row<8>(dx, dy, dz, origin, unit, L, row); break;
+    default: proj_row<9>(dx, dy, dz, origin, unit, L, row); break;
   }
 }
 
@@ -341,7 +418,7 @@ __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bo
 // contraction, so it is the correctly rounded binary64 value of each step.
 __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, double ax, double ay, double az,
                                                int s, int lmax, double inv_box, double inv_rmin,
-                                               double inv_dlog, double* row) {
+                                               double inv_dlog, const LogGrid64& G, double* row) {
   const int ng = P.ng;
   const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
   const int gi = (int)div_ng((unsigned)q1, P.ng_magic, P.ng_shift);
@@ -355,23 +432,24 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
   bool unit = false;
   if (!origin) {
     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-    double r;
-    if (r2 > 1e-280) {  // one reciprocal square root gives both r (for the log) and the unit vector
+    if (r2 > 1e-280) {  // the unit vector by one reciprocal square root; t from r^2 directly
       const double ri = rsqrt(r2);
-      r = r2 * ri;
 #pragma unroll
       for (int c = 0; c < 3; ++c) d[c] *= ri;
       unit = true;
+      t = log_grid_index(r2, G);
     } else {
-      r = sqrt(r2);
+      t = log(sqrt(r2) * inv_rmin) * inv_dlog;
     }
-    t = log(r * inv_rmin) * inv_dlog;
     t = fmin(fmax(t, 0.0), (double)(P.n_rad - 1));
   }
-  const double tf = floor(t);
-  const Lagrange4<double> L = lagrange_at<double>((int)tf, t - tf, P.n_rad);
-  const double* tab = P.radial + (int64_t)s * P.lstride * P.n_rad + L.i0;
-  proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, unit, L, tab, P.n_rad, row);
+  const double tf = floor(t), u = t - tf;
+  // f_l(r): the interval's cubic in u, two 16-byte loads and three FMAs per l
+  const double2* c = reinterpret_cast<const double2*>(P.coef + 4 * ((int64_t)s * P.lstride * P.n_rad + (int)tf));
+  proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, unit, [&](int l) {
+    const double2 a01 = __ldg(c + 2 * (int64_t)l * P.n_rad), a23 = __ldg(c + 2 * (int64_t)l * P.n_rad + 1);
+    return fma(fma(fma(a23.y, u, a23.x), u, a01.y), u, a01.x);
+  }, row);
 }
 
 // FP32 row.  The displacement in grid units, (i - U) - frac with U = floor of
@@ -439,7 +517,8 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
   }
   const Lagrange4<float> L = lagrange_at<float>(it, u, P.n_rad);
   const float* tab = P.rad32 + (int64_t)s * P.lstride * P.n_rad + L.i0;
-  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, true, L, tab, P.n_rad, row);
+  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, true,
+                           [&](int l) { return interp4(L, tab + (int64_t)l * P.n_rad); }, row);
 }
 
 // ---------------------------------------------------------------------------
@@ -491,6 +570,7 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
   __shared__ long long s_next;
   __shared__ int s_atom;
   const double inv_box = 1.0 / P.box, inv_rmin = 1.0 / P.r_min, inv_dlog = 1.0 / P.dlog;
+  const LogGrid64 G = {-log(P.r_min) * inv_dlog, 0.69314718055994530942 * 0.5 * inv_dlog, 0.5 * inv_dlog};
   // exact tile count, from the table the set-up kernel built earlier on this stream
   const int64_t total_tiles = P.tile_offsets[P.n_atoms];
   const bool cached = P.n_atoms + 1 <= kSmemAtoms;
@@ -540,7 +620,7 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
         for (int k = 0; k < L2; ++k) row[k] = (T)0;
       } else if constexpr (sizeof(T) == 8) {
         proj_point_f64(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
-                       inv_rmin, inv_dlog, reinterpret_cast<double*>(row));
+                       inv_rmin, inv_dlog, G, reinterpret_cast<double*>(row));
       } else {
         proj_point_f32(P, g, P.atomf[a], s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
       }
@@ -658,6 +738,7 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
   P->rad32 = dtype == SHM_F32 ? (float*)(ws + w.rad32) : nullptr;
   P->atomf = dtype == SHM_F32 ? (AtomF32*)(ws + w.atomf) : nullptr;
+  P->coef = dtype == SHM_F64 ? (double*)(ws + w.coef) : nullptr;
   *max_lmax = ml;
   // an upper bound of the tile count: every point of every atom in its own partial tile
   *tile_upper = p.n_points / kProjTPB + p.n_atoms;
