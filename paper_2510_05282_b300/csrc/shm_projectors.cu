@@ -38,8 +38,8 @@ constexpr int kExpLo = -160;  // FP32 log-grid exponent table covers frexpf expo
 constexpr int kExpHi = 140;
 constexpr int kExpN = kExpHi - kExpLo + 1;
 
-// An atom coordinate in grid units, q = pos / h = U + frac, frac in [0, 1)
-// held as the float-float fhi + flo (FP32 path).
+// An atom coordinate in grid units, q = pos / h = U + frac + (whole boxes),
+// U in [0, ng), frac in [0, 1) held as the float-float fhi + flo (FP32 path).
 struct AtomF32 {
   int U[3];
   float fhi[3], flo[3];
@@ -53,6 +53,7 @@ struct ProjWs {
   size_t atomf = 0;        // FP32: AtomF32[n_atoms] (atom coordinates in grid units)
   size_t rad32 = 0;        // FP32: float radial[n_species][lstride][n_rad]
   size_t coef = 0;         // FP64: double {a0, a1, a2, a3}[n_species][lstride][n_rad] (cubic per interval)
+  size_t hg = 0;           // FP64: double i * h for i < ng (grid coordinates, rounded as the definition)
   size_t total = 0;
 };
 
@@ -72,6 +73,8 @@ ProjWs proj_layout(const shm_proj_problem& p, shm_dtype dt) {
   } else {
     w.coef = end;
     end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 32);
+    w.hg = end;
+    end += round256((size_t)p.ng * 8);
   }
   w.total = end;
   return w;
@@ -98,6 +101,7 @@ struct ProjParams {
   float* rad32;
   AtomF32* atomf;
   double* coef;
+  double* hg;
 };
 
 enum : unsigned { kErrOffsets = 1u, kErrSpecies = 2u, kErrGrid = 4u, kErrOut = 8u };
@@ -196,6 +200,8 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
     __syncthreads();
   }
   if (err) atomicOr(P.err, err);
+  if (!fp32)
+    for (int i = tid; i < P.ng; i += blockDim.x) P.hg[i] = __dmul_rn((double)i, P.h);
   if (fp32) {
     // exponent table: r = m 2^e (m in [0.5, 1)), t = (e ln2 - ln r_min)/dlog + ln(m)/dlog
     //                 = I_e + c_e + ln(m)/dlog with I_e integer, c_e in [0, 1)
@@ -213,7 +219,11 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
         const double q = P.atom_pos[3 * a + c] / P.h;  // atom coordinate in grid units
         const double U = floor(q);
         const double fr = q - U;
-        A.U[c] = (int)U;
+        // U modulo ng (whole boxes do not change the minimum image), so that
+        // the point's i - U lies in (-ng, ng) and one wrap reaches the image
+        double Um = U - (double)P.ng * floor(U / (double)P.ng);
+        Um = Um < 0.0 ? Um + (double)P.ng : (Um >= (double)P.ng ? Um - (double)P.ng : Um);
+        A.U[c] = (int)Um;
         A.fhi[c] = (float)fr;
         A.flo[c] = (float)(fr - (double)A.fhi[c]);
       }
@@ -423,17 +433,30 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
   const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
   const int gi = (int)div_ng((unsigned)q1, P.ng_magic, P.ng_shift);
   const int gj = q1 - gi * ng, gk = g - q1 * ng;
-  double d[3] = {__dsub_rn(__dmul_rn((double)gi, P.h), ax), __dsub_rn(__dmul_rn((double)gj, P.h), ay),
-                 __dsub_rn(__dmul_rn((double)gk, P.h), az)};
+  // i * h from the set-up table (the same binary64 product), minus the atom
+  double d[3] = {__dsub_rn(__ldg(P.hg + gi), ax), __dsub_rn(__ldg(P.hg + gj), ay), __dsub_rn(__ldg(P.hg + gk), az)};
+  // minimum image, d - box rint(d / box): the shift is decided on the bit
+  // pattern of |d| (0 up to box/2, +-box up to 1.5 box; ties at exactly box/2
+  // go to 0 like rint's), the rounded product only beyond 1.5 box
+  const long long half_box = __double_as_longlong(0.5 * P.box), three_half_box = __double_as_longlong(1.5 * P.box);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) d[c] = __dsub_rn(d[c], __dmul_rn(P.box, rint(d[c] * inv_box)));
+  for (int c = 0; c < 3; ++c) {
+    const long long b = __double_as_longlong(d[c]);
+    const long long mag = b & 0x7fffffffffffffffll;
+    if (mag > half_box) {
+      if (mag <= three_half_box)
+        d[c] = __dsub_rn(d[c], __longlong_as_double(__double_as_longlong(P.box) | (b & (long long)0x8000000000000000ull)));
+      else
+        d[c] = __dsub_rn(d[c], __dmul_rn(P.box, rint(d[c] * inv_box)));
+    }
+  }
   const bool origin = is_origin(d[0], d[1], d[2]);
   double t = 0.0;
   bool unit = false;
   if (!origin) {
     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-    if (r2 > 1e-280) {  // the unit vector by one reciprocal square root; t from r^2 directly
-      const double ri = rsqrt(r2);
+    if (__double_as_longlong(r2) > 0x05e0000000000000ll) {  // r^2 >= 2^-929 (and inf, NaN): the unit vector
+      const double ri = rsqrt(r2);                            // by one reciprocal square root, t from r^2
 #pragma unroll
       for (int c = 0; c < 3; ++c) d[c] *= ri;
       unit = true;
@@ -441,11 +464,20 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
     } else {
       t = log(sqrt(r2) * inv_rmin) * inv_dlog;
     }
-    t = fmin(fmax(t, 0.0), (double)(P.n_rad - 1));
   }
-  const double tf = floor(t), u = t - tf;
+  // t clamped to [0, n_rad - 1] on its integer part (u = 0 at both ends)
+  const double tf = floor(t);
+  double u = t - tf;
+  int it = (int)tf;  // saturates; NaN gives 0
+  if (it >= P.n_rad - 1) {
+    it = P.n_rad - 1;
+    u = 0.0;
+  } else if (it < 0 || !((unsigned long long)__double_as_longlong(u) < 0x7ff0000000000000ull)) {
+    it = 0;  // below the grid, or t = -inf or NaN (u not finite)
+    u = 0.0;
+  }
   // f_l(r): the interval's cubic in u, two 16-byte loads and three FMAs per l
-  const double2* c = reinterpret_cast<const double2*>(P.coef + 4 * ((int64_t)s * P.lstride * P.n_rad + (int)tf));
+  const double2* c = reinterpret_cast<const double2*>(P.coef + 4 * ((int64_t)s * P.lstride * P.n_rad + it));
   proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, unit, [&](int l) {
     const double2 a01 = __ldg(c + 2 * (int64_t)l * P.n_rad), a23 = __ldg(c + 2 * (int64_t)l * P.n_rad + 1);
     return fma(fma(fma(a23.y, u, a23.x), u, a01.y), u, a01.x);
@@ -739,6 +771,7 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   P->rad32 = dtype == SHM_F32 ? (float*)(ws + w.rad32) : nullptr;
   P->atomf = dtype == SHM_F32 ? (AtomF32*)(ws + w.atomf) : nullptr;
   P->coef = dtype == SHM_F64 ? (double*)(ws + w.coef) : nullptr;
+  P->hg = dtype == SHM_F64 ? (double*)(ws + w.hg) : nullptr;
   *max_lmax = ml;
   // an upper bound of the tile count: every point of every atom in its own partial tile
   *tile_upper = p.n_points / kProjTPB + p.n_atoms;

@@ -90,14 +90,32 @@ def test_every_lmax_up_to_9(oracle_mod, dtype, tol):
     check(prob, run(prob, dtype), oracle_mod.projectors(prob), tol, f"lmax 0..9 {dtype}")
 
 
-def test_atom_on_a_grid_point_uses_origin_rule(oracle_mod):
-    prob = small_problem(3)
-    # move atom 0 exactly onto grid point (8, 9, 10): its own row is at r = 0
-    prob.atom_pos[0] = np.array([8, 9, 10], dtype=np.float64) * prob.h
+def relist(prob):
+    """Rebuild the sphere lists and output offsets after moving atoms."""
     off, idx = inputs.sphere_lists(prob.atom_pos, prob.atom_rc, prob.ng, prob.h, prob.box)
     prob.point_offsets, prob.point_index = off, idx
     nh = (prob.atom_lmax().astype(np.int64) + 1) ** 2
     prob.out_offsets = np.concatenate([[0], np.cumsum(np.diff(off) * nh)]).astype(np.int64)
+    return off, nh
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, PROJ_TOL_F64), (torch.float32, PROJ_TOL_F32)])
+def test_atoms_outside_the_primary_box(oracle_mod, dtype, tol):
+    """Atom coordinates shifted by whole boxes: raw displacements up to ~5
+    boxes, so the minimum image subtracts several boxes (and one box where
+    |d| is between half a box and 1.5 boxes)."""
+    prob = small_problem(4)
+    shifts = np.array([[2, 0, -1], [-3, 1, 0], [0, 0, 5], [1, -1, 1], [0, 0, 0], [-1, -2, 3]], dtype=np.float64)
+    prob.atom_pos = prob.atom_pos + shifts[:prob.n_atoms] * prob.box
+    relist(prob)
+    check(prob, run(prob, dtype), oracle_mod.projectors(prob), tol, f"shifted atoms {dtype}")
+
+
+def test_atom_on_a_grid_point_uses_origin_rule(oracle_mod):
+    prob = small_problem(3)
+    # move atom 0 exactly onto grid point (8, 9, 10): its own row is at r = 0
+    prob.atom_pos[0] = np.array([8, 9, 10], dtype=np.float64) * prob.h
+    off, nh = relist(prob)
     for dtype, tol in ((torch.float64, PROJ_TOL_F64), (torch.float32, PROJ_TOL_F32)):
         got = run(prob, dtype)
         ref = oracle_mod.projectors(prob)
