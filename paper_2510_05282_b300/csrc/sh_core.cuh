@@ -660,6 +660,54 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
   }
 }
 
+// Short FP64 row (LMAX <= 4) entirely in float-float, every value of shell
+// l multiplied by fff[l]: the columns m = 0, 1 too, which sh_row_hybrid keeps
+// in binary64 because their long recurrences amplify float-float rounding
+// near the poles.  Up to l = 4 the recurrences have at most three steps, so
+// the float-float rounding (2^-48) stays near 1e-14 of the shell norm while
+// the binary64 multiplies per value (scale, factor, x or y) leave the FP64
+// pipe.  The direction must be finite.
+template <int LMAX, typename Store>
+__device__ __forceinline__ void sh_row_ff_scaled(double xb, double yb, double zb, Store&& store, const ff* fff) {
+  static_assert(LMAX <= 4, "short rows only");
+  const ff X = ff_from_double(xb), Y = ff_from_double(yb), Z = ff_from_double(zb);
+  ff A = {1.0f, 0.0f}, B = {0.0f, 0.0f};
+#pragma unroll
+  for (int m = 0; m <= LMAX; ++m) {
+    if (m == 1) {
+      A = X;
+      B = Y;
+    } else if (m >= 2) {
+      const ff An = ff_add(ff_mul_u(A, X), ff_neg(ff_mul_u(B, Y)));
+      const ff Bn = ff_add(ff_mul_u(A, Y), ff_mul_u(B, X));
+      A = An;
+      B = Bn;
+    }
+    ff q2 = {1.0f, 0.0f}, q1 = Z;
+#pragma unroll
+    for (int l = m; l <= LMAX; ++l) {
+      ff s;
+      if (l == m) {
+        s = ff_mul_c_u(fff[l], Shi<false>(l, m), Slo<false>(l, m));
+      } else if (l == m + 1) {
+        s = ff_mul_u(ff_mul_c_u(Z, Shi<false>(l, m), Slo<false>(l, m)), fff[l]);
+      } else {
+        const ff q = ff_add(ff_mul_u(Z, q1), ff_neg(ff_mul_c_u(q2, SHM_G_HI[l][m], SHM_G_LO[l][m])));
+        s = ff_mul_u(ff_mul_c_u(q, Shi<false>(l, m), Slo<false>(l, m)), fff[l]);
+        q2 = q1;
+        q1 = q;
+      }
+      if (m == 0) {
+        const ff sn = fast_two_sum(s.hi, s.lo);
+        store(l * l + l, ff_to_double_finite(sn));
+      } else {
+        store(l * l + l + m, ff_to_double_finite(ff_mul(s, A)));
+        store(l * l + l - m, ff_to_double_finite(ff_mul(s, B)));
+      }
+    }
+  }
+}
+
 // FP32 row.  FP32 arithmetic throughout; two measures keep the error within
 // 2e-6 of the l-shell norm up to l = 9:
 //  * the homogeneous form q = xb^2 + yb^2 + zb^2 (1 only up to rounding in

@@ -52,7 +52,7 @@ struct ProjWs {
   size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
   size_t atomf = 0;        // FP32: AtomF32[n_atoms] (atom coordinates in grid units)
   size_t rad32 = 0;        // FP32: float radial[n_species][lstride][n_rad]
-  size_t coef = 0;         // FP64: double {a0, a1, a2, a3}[n_species][lstride][n_rad] (cubic per interval)
+  size_t coef = 0;         // FP64: float-float {a0, a1, a2, a3}[n_species][lstride][n_rad] (cubic per interval)
   size_t hg = 0;           // FP64: double i * h for i < ng (grid coordinates, rounded as the definition)
   size_t total = 0;
 };
@@ -100,7 +100,7 @@ struct ProjParams {
   int2* etab;
   float* rad32;
   AtomF32* atomf;
-  double* coef;
+  float4* coef;  // two per node: {a0.hi, a0.lo, a1.hi, a1.lo}, {a2.hi, a2.lo, a3.hi, a3.lo}
   double* hg;
 };
 
@@ -118,25 +118,27 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
       if (fp32) {
         P.rad32[i] = (float)P.radial[i];
-      } else {
-        // 4-point Lagrange interpolation on the interval [it, it + 1] of the
-        // table (stencil i0..i0+3, i0 = clamp(it - 1, 0, n_rad - 4)) as the
-        // cubic a0 + a1 u + a2 u^2 + a3 u^3 in u = t - it: the stencil
-        // polynomial b0 + b1 x + b2 x^2 + b3 x^3 in x = t - i0 from its forward
-        // differences, shifted to x0 = it - i0.
-        const int64_t row = i / P.n_rad;
-        const int it = (int)(i - row * P.n_rad);
-        const int i0 = min(max(it - 1, 0), P.n_rad - 4);
-        const double* F = P.radial + row * P.n_rad + i0;
-        const double d1 = F[1] - F[0], d2 = F[2] - 2.0 * F[1] + F[0], d3 = F[3] - 3.0 * F[2] + 3.0 * F[1] - F[0];
-        const double b3 = d3 / 6.0, b2 = 0.5 * (d2 - d3), b1 = d1 - 0.5 * d2 + d3 / 3.0;
-        const double x0 = (double)(it - i0);
-        double* c = P.coef + 4 * i;
-        c[0] = F[it - i0];
-        c[1] = b1 + x0 * (2.0 * b2 + 3.0 * b3 * x0);
-        c[2] = b2 + 3.0 * b3 * x0;
-        c[3] = b3;
+        continue;
       }
+      // 4-point Lagrange interpolation on the interval [it, it + 1] of the
+      // table (stencil i0..i0+3, i0 = clamp(it - 1, 0, n_rad - 4)) as the
+      // cubic a0 + a1 u + a2 u^2 + a3 u^3 in u = t - it: the stencil
+      // polynomial b0 + b1 x + b2 x^2 + b3 x^3 in x = t - i0 from its forward
+      // differences, shifted to x0 = it - i0, computed in binary64 and stored
+      // as float-float (the FP64 row takes f_l in float-float).  (The FP32 path keeps the
+      // weights form: its 4-byte table stays in L1, the 16-byte cubics of a
+      // species do not, and it is bound by issue and loads, not arithmetic.)
+      const int64_t row = i / P.n_rad;
+      const int it = (int)(i - row * P.n_rad);
+      const int i0 = min(max(it - 1, 0), P.n_rad - 4);
+      const double* F = P.radial + row * P.n_rad + i0;
+      const double d1 = F[1] - F[0], d2 = F[2] - 2.0 * F[1] + F[0], d3 = F[3] - 3.0 * F[2] + 3.0 * F[1] - F[0];
+      const double b3 = d3 / 6.0, b2 = 0.5 * (d2 - d3), b1 = d1 - 0.5 * d2 + d3 / 3.0;
+      const double x0 = (double)(it - i0);
+      const double c0 = F[it - i0], c1 = b1 + x0 * (2.0 * b2 + 3.0 * b3 * x0), c2 = b2 + 3.0 * b3 * x0;
+      const ff f0 = ff_from_double(c0), f1 = ff_from_double(c1), f2 = ff_from_double(c2), f3 = ff_from_double(b3);
+      P.coef[2 * i] = make_float4(f0.hi, f0.lo, f1.hi, f1.lo);
+      P.coef[2 * i + 1] = make_float4(f2.hi, f2.lo, f3.hi, f3.lo);
     }
   }
   if (blockIdx.x != 0) return;  // the rest is one CTA's work
@@ -345,65 +347,73 @@ __device__ __forceinline__ double log_grid_index(double r2, const LogGrid64& G) 
 // ---------------------------------------------------------------------------
 // Per-row pieces.
 
-template <typename T>
+// Stencil and weights of 4-point Lagrange interpolation at t = it + u
+// (already clamped to [0, n_rad - 1], 0 <= u < 1), FP32 path.
 struct Lagrange4 {
   int i0;
-  T w[4];
+  float w[4];
 };
-
-// Stencil and weights of 4-point Lagrange interpolation at continuous index t
-// (already clamped to [0, n_rad - 1]).
-template <typename T>
-__device__ __forceinline__ Lagrange4<T> lagrange_at(int it, T u, int n_rad) {
-  // t = it + u, 0 <= u < 1
-  Lagrange4<T> L;
+__device__ __forceinline__ Lagrange4 lagrange_at(int it, float u, int n_rad) {
+  Lagrange4 L;
   int i0 = it - 1;
   i0 = i0 < 0 ? 0 : (i0 > n_rad - 4 ? n_rad - 4 : i0);
-  T x;  // t - i0, in [0, 3]
-  if constexpr (sizeof(T) == 4)
-    x = small_int_to_float(it - i0) + u;
-  else
-    x = (T)(it - i0) + u;
-  const T x1 = x - (T)1, x2 = x - (T)2, x3 = x - (T)3;
+  const float x = small_int_to_float(it - i0) + u;  // t - i0, in [0, 3]
+  const float x1 = x - 1.0f, x2 = x - 2.0f, x3 = x - 3.0f;
   L.i0 = i0;
-  L.w[0] = -(x1 * x2 * x3) * (T)(1.0 / 6.0);
-  L.w[1] = (x * x2 * x3) * (T)0.5;
-  L.w[2] = -(x * x1 * x3) * (T)0.5;
-  L.w[3] = (x * x1 * x2) * (T)(1.0 / 6.0);
+  L.w[0] = -(x1 * x2 * x3) * (1.0f / 6.0f);
+  L.w[1] = (x * x2 * x3) * 0.5f;
+  L.w[2] = -(x * x1 * x3) * 0.5f;
+  L.w[3] = (x * x1 * x2) * (1.0f / 6.0f);
   return L;
 }
-
-__device__ __forceinline__ float interp4(const Lagrange4<float>& L, const float* F) {
+__device__ __forceinline__ float interp4(const Lagrange4& L, const float* F) {
   return fmaf(L.w[3], F[3], fmaf(L.w[2], F[2], fmaf(L.w[1], F[1], L.w[0] * F[0])));
 }
 
-// One row (lmax = LMAX): f_l(r) = radial(l) for l = 0..LMAX, then write
-// f_l(r) R_l^m into row[0..(LMAX+1)^2).
-// (dx, dy, dz) is the displacement, or with `unit` its unit vector.
+// One row (lmax = LMAX): f_l(r) = radial(l) for l = 0..LMAX (float for the
+// FP32 row, float-float for the FP64 row), then write f_l(r) R_l^m into
+// row[0..(LMAX+1)^2).  (dx, dy, dz) is the displacement, or with `unit` its
+// unit vector.
 template <int LMAX, typename T, typename Radial>
 __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool unit, Radial&& radial,
                                          T* __restrict__ row) {
-  T f[LMAX + 1];
-#pragma unroll
-  for (int l = 0; l <= LMAX; ++l) f[l] = radial(l);
-  if (origin) {
-    row[0] = (T)kInvSqrt4Pi * f[0];
-#pragma unroll
-    for (int k = 1; k < NH<LMAX>::value; ++k) row[k] = (T)0;
-    return;
-  }
   T xb = dx, yb = dy, zb = dz;
-  if (!unit) unit_dir(dx, dy, dz, xb, yb, zb);
-  if constexpr (sizeof(T) == 4)  // FP32: the plain recurrence for m = 0, 1 up to l = 4
-    sh_row<LMAX, false, (LMAX > 4)>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
-  else if constexpr (LMAX >= 2) {  // FP64: the hybrid row (m >= 2 in float-float, off the FP64 pipe),
-    ff fff[LMAX + 1];              // with f_l folded into its products
+  if constexpr (sizeof(T) == 4) {
+    float f[LMAX + 1];
 #pragma unroll
-    for (int l = 2; l <= LMAX; ++l) fff[l] = ff_from_double(f[l]);
-    sh_row_hybrid<LMAX, false, true>(xb, yb, zb, [&](int k, T v) { row[k] = v; }, f, fff);
+    for (int l = 0; l <= LMAX; ++l) f[l] = radial(l);
+    if (origin) {
+      row[0] = kInvSqrt4Pi * f[0];
+#pragma unroll
+      for (int k = 1; k < NH<LMAX>::value; ++k) row[k] = 0.0f;
+      return;
+    }
+    if (!unit) unit_dir(dx, dy, dz, xb, yb, zb);
+    // the plain recurrence for m = 0, 1 up to l = 4
+    sh_row<LMAX, false, (LMAX > 4)>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
+  } else {
+    ff fff[LMAX + 1];
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l) fff[l] = radial(l);
+    if (origin) {
+      row[0] = kInvSqrt4Pi * ff_to_double_finite(fff[0]);
+#pragma unroll
+      for (int k = 1; k < NH<LMAX>::value; ++k) row[k] = 0.0;
+      return;
+    }
+    if (!unit) unit_dir(dx, dy, dz, xb, yb, zb);
+    if constexpr (LMAX >= 2 && LMAX <= 4) {  // short rows: every column in float-float, f_l folded in
+      sh_row_ff_scaled<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v; }, fff);
+    } else {
+      double f[LMAX + 1];
+#pragma unroll
+      for (int l = 0; l <= LMAX; ++l) f[l] = ff_to_double_finite(fff[l]);
+      if constexpr (LMAX >= 5)  // the hybrid row (m >= 2 in float-float), f_l folded into its products
+        sh_row_hybrid<LMAX, false, true>(xb, yb, zb, [&](int k, T v) { row[k] = v; }, f, fff);
+      else
+        sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
+    }
   }
-  else
-    sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v * f[l_of_k(k)]; });
 }
 
 template <typename T, typename Radial>
@@ -476,11 +486,15 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
     it = 0;  // below the grid, or t = -inf or NaN (u not finite)
     u = 0.0;
   }
-  // f_l(r): the interval's cubic in u, two 16-byte loads and three FMAs per l
-  const double2* c = reinterpret_cast<const double2*>(P.coef + 4 * ((int64_t)s * P.lstride * P.n_rad + it));
+  // f_l(r): the interval's cubic in u by Horner's rule in float-float (FP32
+  // pipe), two 16-byte loads per l
+  const float4* c = P.coef + 2 * ((int64_t)s * P.lstride * P.n_rad + it);
+  const ff U = ff_from_double(u);
   proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, unit, [&](int l) {
-    const double2 a01 = __ldg(c + 2 * (int64_t)l * P.n_rad), a23 = __ldg(c + 2 * (int64_t)l * P.n_rad + 1);
-    return fma(fma(fma(a23.y, u, a23.x), u, a01.y), u, a01.x);
+    const float4 a01 = __ldg(c + 2 * (int64_t)l * P.n_rad), a23 = __ldg(c + 2 * (int64_t)l * P.n_rad + 1);
+    ff p = ff_add(ff_mul_u(ff{a23.z, a23.w}, U), ff{a23.x, a23.y});
+    p = ff_add(ff_mul_u(p, U), ff{a01.z, a01.w});
+    return ff_add(ff_mul_u(p, U), ff{a01.x, a01.y});
   }, row);
 }
 
@@ -547,7 +561,7 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
     }
     it = (int)itl;
   }
-  const Lagrange4<float> L = lagrange_at<float>(it, u, P.n_rad);
+  const Lagrange4 L = lagrange_at(it, u, P.n_rad);
   const float* tab = P.rad32 + (int64_t)s * P.lstride * P.n_rad + L.i0;
   proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, true,
                            [&](int l) { return interp4(L, tab + (int64_t)l * P.n_rad); }, row);
@@ -768,9 +782,9 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   P->err = (unsigned*)(ws + w.counter + 8);
   P->tile_offsets = (int64_t*)(ws + w.tiles);
   P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
-  P->rad32 = dtype == SHM_F32 ? (float*)(ws + w.rad32) : nullptr;
   P->atomf = dtype == SHM_F32 ? (AtomF32*)(ws + w.atomf) : nullptr;
-  P->coef = dtype == SHM_F64 ? (double*)(ws + w.coef) : nullptr;
+  P->rad32 = dtype == SHM_F32 ? (float*)(ws + w.rad32) : nullptr;
+  P->coef = dtype == SHM_F64 ? (float4*)(ws + w.coef) : nullptr;
   P->hg = dtype == SHM_F64 ? (double*)(ws + w.hg) : nullptr;
   *max_lmax = ml;
   // an upper bound of the tile count: every point of every atom in its own partial tile
