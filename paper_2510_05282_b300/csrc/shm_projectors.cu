@@ -3,12 +3,17 @@
 // motivates: projectors of pseudopotential / PAW methods on a 3-D grid).
 //
 // Launch structure (both on the caller's stream):
-//  1. k_proj_setup (one CTA): validates every atom's offsets and species,
-//     builds the tile table (tiles = TPB consecutive sphere points of one
-//     atom; tile_offsets[a] = number of tiles of atoms before a, 0 tiles for
-//     an atom that failed validation), zeroes the work counter and the error
-//     word, and for FP32 converts the radial tables and builds the exponent
-//     table of the log-grid index.
+//  1. k_proj_setup (CTA 0): orders the atoms by the lmax of their species,
+//     largest first (atom_order), validates every atom's offsets and
+//     species, builds the tile table in that order (tiles = TPB consecutive
+//     sphere points of one atom; tile_offsets[j] = number of tiles of the
+//     atoms before atom_order[j], 0 tiles for an atom that failed
+//     validation), zeroes the work counter and the error word; with the
+//     other CTAs it converts the radial tables (FP32: float copies and the
+//     exponent table of the log-grid index; FP64: the interval cubics).
+//     Tiles of one lmax then run together, so the SMs execute one row code
+//     path at a time (instruction-cache locality); the output layout, by
+//     atom, is unchanged.
 //  2. k_proj (persistent: SMs x resident CTAs): each CTA takes the next tile
 //     from an atomic work counter, evaluates its rows -- minimum-image
 //     displacement, 1/r, log-grid index, 4-point Lagrange interpolation of the
@@ -49,6 +54,7 @@ struct AtomF32 {
 struct ProjWs {
   size_t counter = 0;      // unsigned long long work counter, uint32 error word at +8
   size_t tiles = 256;      // int64 tile_offsets[n_atoms + 1]
+  size_t order = 0;        // int32 atom_order[n_atoms]
   size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
   size_t atomf = 0;        // FP32: AtomF32[n_atoms] (atom coordinates in grid units)
   size_t rad32 = 0;        // FP32: float radial[n_species][lstride][n_rad]
@@ -63,6 +69,8 @@ ProjWs proj_layout(const shm_proj_problem& p, shm_dtype dt) {
   ProjWs w;
   w.tiles = 256;
   size_t end = w.tiles + round256((size_t)(p.n_atoms + 1) * 8);
+  w.order = end;
+  end += round256((size_t)std::max<int64_t>(p.n_atoms, 1) * 4);
   if (dt == SHM_F32) {
     w.etab = end;
     end += round256((size_t)kExpN * 8);
@@ -97,6 +105,7 @@ struct ProjParams {
   unsigned long long* counter;
   unsigned* err;
   int64_t* tile_offsets;
+  int32_t* atom_order;
   int2* etab;
   float* rad32;
   AtomF32* atomf;
@@ -148,12 +157,33 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
     carry = 0;
     P.tile_offsets[0] = 0;
   }
+  // atom_order: a counting sort of the atoms by the lmax of their species
+  // (invalid species count as lmax 0), largest lmax first
+  __shared__ int key_count[SHM_LMAX_CAP + 1], key_next[SHM_LMAX_CAP + 1];
+  auto key_of = [&](int64_t a) {
+    const int s = P.atom_species[a];
+    return (s >= 0 && s < P.n_species) ? (int)P.lmax[s] : 0;
+  };
+  if (tid <= SHM_LMAX_CAP) key_count[tid] = 0;
+  __syncthreads();
+  for (int64_t a = tid; a < P.n_atoms; a += blockDim.x) atomicAdd(&key_count[key_of(a)], 1);
+  __syncthreads();
+  if (tid == 0) {
+    int start = 0;
+    for (int k = SHM_LMAX_CAP; k >= 0; --k) {
+      key_next[k] = start;
+      start += key_count[k];
+    }
+  }
+  __syncthreads();
+  for (int64_t a = tid; a < P.n_atoms; a += blockDim.x) P.atom_order[atomicAdd(&key_next[key_of(a)], 1)] = (int)a;
   __syncthreads();
   unsigned err = 0;
   for (int64_t base = 0; base < P.n_atoms; base += blockDim.x) {
-    const int64_t a = base + tid;
+    const int64_t j = base + tid;
     int64_t ntiles = 0;
-    if (a < P.n_atoms) {
+    if (j < P.n_atoms) {
+      const int64_t a = P.atom_order[j];
       const int64_t p0 = P.point_offsets[a], p1 = P.point_offsets[a + 1];
       const int s = P.atom_species[a];
       bool ok = true;
@@ -196,7 +226,7 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
     }
     __syncthreads();
     const int64_t incl = v + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
-    if (a < P.n_atoms) P.tile_offsets[a + 1] = incl;
+    if (j < P.n_atoms) P.tile_offsets[j + 1] = incl;
     __syncthreads();
     if (tid == blockDim.x - 1) carry = incl;
     __syncthreads();
@@ -623,8 +653,9 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
   if (cached)
     for (int i = threadIdx.x; i <= P.n_atoms; i += kProjTPB) tt[i] = (int)P.tile_offsets[i];
   __syncthreads();
-  // owning atom of tile t: the last a with tile_offsets[a] <= t (one thread
-  // searches, for the next tile while the others work on the current one)
+  // owning atom of tile t: atom_order[j] for the last j with tile_offsets[j]
+  // <= t (one thread searches, for the next tile while the others work on
+  // the current one)
   auto owner = [&](int64_t t) {
     int64_t lo = 0, hi = P.n_atoms - 1;
     while (lo < hi) {
@@ -641,15 +672,16 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
   __syncthreads();
   for (;;) {
     const int64_t t = s_next;
-    const int64_t a = s_atom;
+    const int64_t j = s_atom;
     if (t >= total_tiles) break;
     __syncthreads();  // every thread has read s_next and s_atom
     if (threadIdx.x == 0) {  // next tile and its atom, fetched early
       s_next = (long long)atomicAdd(P.counter, 1ull);
       s_atom = s_next < total_tiles ? owner(s_next) : 0;
     }
+    const int64_t a = P.atom_order[j];
     const int64_t pa0 = P.point_offsets[a], pa1 = P.point_offsets[a + 1];
-    const int64_t c = t - (cached ? (int64_t)tt[a] : P.tile_offsets[a]);
+    const int64_t c = t - (cached ? (int64_t)tt[j] : P.tile_offsets[j]);
     const int64_t p0 = pa0 + c * kProjTPB;
     const int rows = (int)min((int64_t)kProjTPB, pa1 - p0);
     const int s = P.atom_species[a];
@@ -781,6 +813,7 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   P->counter = (unsigned long long*)(ws + w.counter);
   P->err = (unsigned*)(ws + w.counter + 8);
   P->tile_offsets = (int64_t*)(ws + w.tiles);
+  P->atom_order = (int32_t*)(ws + w.order);
   P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
   P->atomf = dtype == SHM_F32 ? (AtomF32*)(ws + w.atomf) : nullptr;
   P->rad32 = dtype == SHM_F32 ? (float*)(ws + w.rad32) : nullptr;
