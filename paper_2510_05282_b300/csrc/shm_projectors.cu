@@ -600,6 +600,28 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
 // ---------------------------------------------------------------------------
 // Persistent main kernel.
 
+// Copies nv contiguous staged values to dst: the part between dst's first
+// and last 16-byte boundaries by one bulk copy (cp.async.bulk) issued by
+// thread 0, which waits until the copy has read the staging buffer; the
+// scalar head and tail by plain stores.  stage must have dst's address
+// modulo 16, and the writers must have fenced their shared-memory stores for
+// the async proxy before the barrier that precedes this call.
+template <typename T>
+__device__ __forceinline__ void bulk_rows_out(const T* stage, int nv, T* __restrict__ dst) {
+  const int head = min(nv, (int)(((16u - ((unsigned)(uintptr_t)dst & 15u)) & 15u) / sizeof(T)));
+  const int nbody = (int)((((size_t)(nv - head) * sizeof(T)) & ~(size_t)15) / sizeof(T));
+  const int tail = nv - head - nbody;
+  if (threadIdx.x == 0 && nbody > 0) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst + head),
+                 "r"((unsigned)__cvta_generic_to_shared(stage + head)), "r"((unsigned)(nbody * sizeof(T)))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  }
+  if ((int)threadIdx.x < head) __stcs(dst + threadIdx.x, stage[threadIdx.x]);
+  if ((int)threadIdx.x < tail) __stcs(dst + head + nbody + threadIdx.x, stage[head + nbody + threadIdx.x]);
+}
+
 // Copies rows [0, rows) of a staged tile (row stride RS) to dst[rows * L2],
 // with 16-byte stores between a scalar head (up to the first 16-byte
 // boundary of dst) and a scalar tail.  For odd L2 the tile rows are
@@ -689,10 +711,16 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
     const int L2 = (lmax + 1) * (lmax + 1);
     const int RS = L2 | 1;
     const int64_t o0 = P.out_offsets[a] + c * kProjTPB * (int64_t)L2;
+    // odd row widths: the tile is staged contiguously (RS = L2), shifted so
+    // that it has the 16-byte phase of its place in the output, and leaves by
+    // one bulk copy
+    const bool flat = (L2 & 1) != 0;
+    T* const dst = out + o0;
+    T* const stage = tile + (flat ? (int)(((uintptr_t)dst & 15u) / sizeof(T)) : 0);
     if ((int)threadIdx.x < rows) {
       const int64_t p = p0 + threadIdx.x;
       const int g = P.point_index[p];
-      T* row = tile + threadIdx.x * RS;
+      T* row = stage + threadIdx.x * RS;
       if (g < 0 || g >= P.ng * P.ng * P.ng) {
         atomicOr(P.err, kErrGrid);
         for (int k = 0; k < L2; ++k) row[k] = (T)0;
@@ -703,10 +731,17 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
         proj_point_f32(P, g, P.atomf[a], s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
       }
     }
-    __syncthreads();
-    copy_rows_out<T>(tile, rows, L2, RS, out + o0);
+    if (flat) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the rows, visible to the bulk copy
+      __syncthreads();
+      bulk_rows_out<T>(stage, rows * L2, dst);
+    } else {
+      __syncthreads();
+      copy_rows_out<T>(tile, rows, L2, RS, dst);
+    }
     __syncthreads();  // the tile buffer is free and s_next holds the next tile
   }
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 template <typename T>
@@ -716,12 +751,12 @@ shm_status launch_proj(const ProjParams& P, int max_lmax, T* out, int64_t tile_u
   const int dev = current_device();
   if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
   const int RS = ((max_lmax + 1) * (max_lmax + 1)) | 1;
-  const size_t tile_bytes = ((size_t)kProjTPB * RS * sizeof(T) + 15) / 16 * 16;
+  const size_t tile_bytes = ((size_t)kProjTPB * RS * sizeof(T) + 15) / 16 * 16 + 16;  // + the staging shift
   const size_t smem = tile_bytes + (P.n_atoms + 1 <= kSmemAtoms ? (size_t)(P.n_atoms + 1) * 4 : 0);
   auto kern = k_proj<T>;
   if (bps[dev][max_lmax] == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)kProjTPB * 101 * sizeof(T) + kSmemAtoms * 4));
+                                         (int)((size_t)kProjTPB * 101 * sizeof(T) + 16 + kSmemAtoms * 4));
     if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_proj)");
     int b = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kProjTPB, smem);
