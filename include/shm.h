@@ -162,7 +162,7 @@ shm_status shm_eval_set_variant(int lmax, shm_dtype dtype, int variant);
 #define SHM_PROJ_MAX_SPECIES 64
 
 typedef struct {
-  int64_t n_atoms;               /* >= 0 */
+  int64_t n_atoms;               /* 0 <= n_atoms < 2^31 */
   const double* atom_pos;        /* device [n_atoms][3], bohr */
   const int32_t* atom_species;   /* device [n_atoms], 0 <= s < n_species */
   int32_t n_species;             /* 1..SHM_PROJ_MAX_SPECIES */

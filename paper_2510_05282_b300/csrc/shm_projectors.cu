@@ -786,6 +786,7 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   const shm_proj_problem& p = *prob;
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
   if (p.n_atoms < 0 || p.n_points < 0 || p.n_values < 0) return fail(SHM_EINVAL, "negative size");
+  if (p.n_atoms > INT32_MAX) return fail(SHM_EINVAL, "n_atoms must be below 2^31");
   if (p.n_species < 1 || p.n_species > SHM_PROJ_MAX_SPECIES) return fail(SHM_EINVAL, "n_species must be 1..64");
   if (!p.species_lmax) return fail(SHM_EINVAL, "species_lmax (host) is null");
   if (p.n_rad < 4) return fail(SHM_EINVAL, "n_rad must be >= 4");

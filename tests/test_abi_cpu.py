@@ -82,3 +82,14 @@ def test_binding_errors_carry_text(L):
     with pytest.raises(shm.ShmError) as ei:
         shm.check(L.shm_eval(None, 3, 17, 1, None, None))
     assert ei.value.status == 1 and "lmax" in str(ei.value)
+
+
+def test_projector_sizes_rejected_on_the_host(L):
+    """Atom counts the projector tables cannot index (the tile order holds
+    atoms as int32) and negative sizes fail before any device call."""
+    p = _binding._ProjProblem()
+    p.n_species = 1
+    for n_atoms, msg in ((1 << 31, "2^31"), (-1, "negative")):
+        p.n_atoms = n_atoms
+        assert L.shm_projectors(ctypes.byref(p), 1, None, None, 0, None) == 1
+        assert msg in L.shm_last_error().decode()
