@@ -45,9 +45,9 @@ constexpr int kExpN = kExpHi - kExpLo + 1;
 
 // An atom coordinate in grid units, q = pos / h = U + frac + (whole boxes),
 // U in [0, ng), frac in [0, 1) held as the float-float fhi + flo (FP32 path).
-struct AtomF32 {
-  int U[3];
-  float fhi[3], flo[3];
+struct __align__(16) AtomF32 {  // 48 bytes: three 16-byte loads
+  int U[4];
+  float fhi[4], flo[4];
 };
 
 // Workspace layout (byte offsets; every block 256-byte aligned).
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
       P.etab[i] = make_int2((int)I_cl, __float_as_int((float)(C - I)));
     }
     for (int64_t a = tid; a < P.n_atoms; a += blockDim.x) {
-      AtomF32 A;
+      AtomF32 A = {};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double q = P.atom_pos[3 * a + c] / P.h;  // atom coordinate in grid units
@@ -728,7 +728,12 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
         proj_point_f64(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
                        inv_rmin, inv_dlog, G, reinterpret_cast<double*>(row));
       } else {
-        proj_point_f32(P, g, P.atomf[a], s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
+        const int4* ap = reinterpret_cast<const int4*>(P.atomf + a);
+        const int4 u4 = __ldg(ap), fh4 = __ldg(ap + 1), fl4 = __ldg(ap + 2);
+        const AtomF32 A = {{u4.x, u4.y, u4.z, 0},
+                           {__int_as_float(fh4.x), __int_as_float(fh4.y), __int_as_float(fh4.z), 0.0f},
+                           {__int_as_float(fl4.x), __int_as_float(fl4.y), __int_as_float(fl4.z), 0.0f}};
+        proj_point_f32(P, g, A, s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
       }
     }
     if (flat) {
