@@ -90,6 +90,16 @@ def test_every_lmax_up_to_9(oracle_mod, dtype, tol):
     check(prob, run(prob, dtype), oracle_mod.projectors(prob), tol, f"lmax 0..9 {dtype}")
 
 
+@pytest.mark.parametrize("n_rad", [4, 5])
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, PROJ_TOL_F64), (torch.float32, PROJ_TOL_F32)])
+def test_shortest_radial_tables(oracle_mod, n_rad, dtype, tol):
+    """Tables of 4 and 5 nodes: every interval's stencil is clamped at an end
+    (the stencil start i0 is 0 or n_rad - 4 throughout), so each offset of
+    the interval within its stencil, 0 to 3, occurs."""
+    prob = small_problem(11, n_rad=n_rad, r_min=0.05, r_max=2.5)
+    check(prob, run(prob, dtype), oracle_mod.projectors(prob), tol, f"n_rad {n_rad} {dtype}")
+
+
 def relist(prob):
     """Rebuild the sphere lists and output offsets after moving atoms."""
     off, idx = inputs.sphere_lists(prob.atom_pos, prob.atom_rc, prob.ng, prob.h, prob.box)
