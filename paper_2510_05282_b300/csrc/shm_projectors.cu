@@ -494,7 +494,9 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
   double t = 0.0;
   bool unit = false;
   if (!origin) {
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+    // r^2 by two FMAs (within an ulp of the unfused sum; it feeds 1/r and
+    // the log-grid index, where an ulp moves t by ~1e-14)
+    const double r2 = fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
     if (__double_as_longlong(r2) > 0x05e0000000000000ll) {  // r^2 >= 2^-929 (and inf, NaN): the unit vector
       const double ri = rsqrt(r2);                            // by one reciprocal square root, t from r^2
 #pragma unroll
