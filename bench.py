@@ -5,9 +5,12 @@
 
 One step = one pass of the evaluator over the whole workload: all R_l^m,
 l <= 9, at the 7,077,888 points of a 192^3 grid (spacing 0.3 bohr, centred on
-a seeded off-grid atom), FP64 in and out (5.66 GB of output per step).  Inputs
-are resident in HBM when the timed region starts; input (170 MB) and output
-(5.66 GB) both exceed the 126 MB L2, so no L2 flush is needed between steps.
+a seeded off-grid atom), FP64 in and out (5.66 GB of output per step), every
+value computed in binary64 arithmetic (SHM_STRICT_FP64: the paper's precision;
+the float-float hybrid rows are reported beside it as an extra, labelled).
+Inputs are resident in HBM when the timed region starts; input (170 MB) and
+output (5.66 GB) both exceed the 126 MB L2, so no L2 flush is needed between
+steps.
 
 Prints one JSON line (rank 0).  N > 1 runs one process per GPU (torchrun);
 each rank evaluates its own copy of the grid (weak scaling, no collective on
@@ -41,33 +44,14 @@ LMAX = 9
 N_SIDE = 192
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 pipe peak: the nominal 1.25 TFLOP/s dense FP64 of a B300 (148 SMs at
-# up to 2032 MHz), i.e. 0.625e12 FP64 pipe instructions per second (one DFMA,
-# DMUL or DADD each).  No measured FP64 figure is provided for this machine.
-FP64_PEAK_TFLOPS = 1.25
+# FP64 pipe peak: measured in every run by shm_probe_fp64_rate (independent
+# DFMA chains on every SM, CUDA events); the nominal 1.25 TFLOP/s dense FP64
+# of a B300 (0.625e12 FP64 pipe instructions per second) only if that fails.
+FP64_NOMINAL_TFLOPS = 1.25
 HBM_FALLBACK_GBS = 6400.0
-
-
-def dp_instr_per_point(lmax: int) -> int:
-    """FP64 pipe instructions per point of the FP64 evaluator (sh_core.cuh).
-
-    normalisation: r^2 (3), x/r, y/r, z/r (3), rsqrt (one MUFU seed refined by
-    Newton steps in FP64; counted as 6);
-    m = 0: S*z for l = 1 (1), l = 2 one FMA with a constant and one scale (2),
-    l >= 3 two for the recurrence and one scale (3);
-    m >= 1: (x+iy)^m update (4, m >= 2), l = m: 2 products, l = m+1: 3,
-    l = m+2: one FMA + scale + 2 products (4), l >= m+3: 5."""
-    n = 12
-    for l in range(1, lmax + 1):
-        n += 1 if l == 1 else (2 if l == 2 else 3)
-    for m in range(1, lmax + 1):
-        n += 4 if m >= 2 else 0
-        n += 2
-        if m + 1 <= lmax:
-            n += 3
-        for l in range(m + 2, lmax + 1):
-            n += 4 if l == m + 2 else 5
-    return n
+# FP64 pipe instructions per point of the all-binary64 rows at lmax 9
+# (sh_row: DMUL + DFMA, counted by ncu sass__inst_executed_per_opcode).
+STRICT_DP_PER_POINT_L9 = 242
 
 
 def load_peaks():
@@ -139,20 +123,33 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- reference arm
 
-def cpu_oracle_rate(points: np.ndarray, lmax: int, budget_s: float, nthreads: int = 0):
-    """Y/s of the oracle on a bounded prefix of `points` (about budget_s of CPU work)."""
+def oracle_timing(points: np.ndarray, lmax: int, step_s: float, steps: int, warmup: int, nthreads: int = 0):
+    """The one protocol by which this file times the oracle (the GPU line's
+    cpu_baseline and the reference arm alike): size a prefix of `points` so
+    that one call takes about step_s (a probe call on up to 20,000 points),
+    make `warmup` untimed calls on it, then `steps` timed calls.  Returns the
+    median Y/s over the timed calls, the prefix size and the thread count."""
     import oracle
     oracle.build()
     probe = min(points.shape[0], 20000)
     t0 = time.perf_counter()
     oracle.real_sh(points[:probe], lmax, nthreads=nthreads)
     dt = max(time.perf_counter() - t0, 1e-6)
-    m = int(min(points.shape[0], max(probe, probe * budget_s / dt)))
-    t0 = time.perf_counter()
-    oracle.real_sh(points[:m], lmax, nthreads=nthreads)
-    dt = time.perf_counter() - t0
+    m = int(min(points.shape[0], max(probe, probe * step_s / dt)))
     nh = (lmax + 1) ** 2
-    return m * nh / dt, m, oracle.max_threads(nthreads)
+    rates = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        oracle.real_sh(points[:m], lmax, nthreads=nthreads)
+        if i >= warmup:
+            rates.append(m * nh / (time.perf_counter() - t0))
+    return statistics.median(rates), m, oracle.max_threads(nthreads)
+
+
+def cpu_oracle_rate(points: np.ndarray, lmax: int, budget_s: float, nthreads: int = 0):
+    """Y/s of the oracle on a bounded prefix of `points`: oracle_timing with
+    one warm-up and three timed calls of about budget_s / 4 each."""
+    return oracle_timing(points, lmax, budget_s / 4, 3, 1, nthreads)
 
 
 def run_reference(args, rank, world):
@@ -162,17 +159,10 @@ def run_reference(args, rank, world):
     pts = inputs.dft_grid_points(N_SIDE)
     nh = (LMAX + 1) ** 2
     # about two minutes for the whole run whatever --steps and --warmup are,
-    # and at most --cpu-seconds per step
+    # and at most --cpu-seconds per step; the same protocol as the GPU arm's
+    # cpu_baseline (oracle_timing), with one call per step
     budget = min(args.cpu_seconds, 20.0, max(0.05, 120.0 / max(1, args.steps + args.warmup)))
-    rates = []
-    sample_pts = 0
-    cores = 1
-    for i in range(args.warmup + args.steps):
-        r, m, cores = cpu_oracle_rate(pts, LMAX, budget)
-        sample_pts = m
-        if i >= args.warmup:
-            rates.append(r)
-    value = statistics.median(rates)
+    value, sample_pts, cores = oracle_timing(pts, LMAX, budget, args.steps, args.warmup)
     ms = pts.shape[0] * nh / value * 1e3
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -182,7 +172,8 @@ def run_reference(args, rank, world):
                    "note": "each step times the oracle on a prefix of the grid; ms_per_step is "
                            "extrapolated to the full grid"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"first {sample_pts} of {pts.shape[0]} grid points per step"},
+                         "sample": f"first {sample_pts} of {pts.shape[0]} grid points per step",
+                         "protocol": "oracle_timing: median of the timed calls after warm-up calls"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -206,18 +197,19 @@ def timed_launches(fn, steps, stream):
     return per, region
 
 
-def graph_replay_timing(torch, shm, p, out, lmax, launches=20, replays=5):
-    """The same launch captured `launches` times into one CUDA graph and
-    replayed: median ms per launch over the replays (outside the timed region;
-    the launch overhead it removes is negligible next to a ms-scale kernel)."""
+def graph_replay_timing(torch, fn, launches=20, replays=5, stream=None):
+    """fn (one launch on `stream`) captured `launches` times into one CUDA
+    graph and replayed: median ms per launch over the replays (outside the
+    timed region; the launch overhead it removes is negligible next to a
+    ms-scale kernel)."""
     try:
-        gs = torch.cuda.Stream()
+        gs = stream if stream is not None else torch.cuda.Stream()
         gs.wait_stream(torch.cuda.current_stream())
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=gs):
             for _ in range(launches):
-                shm.eval_sh(p, lmax, out=out, stream=gs)
+                fn(gs)
         cur = torch.cuda.current_stream()
         g.replay()
         torch.cuda.synchronize()
@@ -245,16 +237,29 @@ def gpu_id_for_smi(dev):
         return None
 
 
-def measure_eval(shm, torch, pts_np, dtype, lmax, steps, warmup, stream):
+def measure_eval(shm, torch, pts_np, dtype, lmax, steps, warmup, stream, strict=False):
     p = torch.from_numpy(pts_np).to(device="cuda", dtype=dtype)
     out = torch.empty((p.shape[0], (lmax + 1) ** 2), dtype=dtype, device="cuda")
     with torch.cuda.stream(stream):
         for _ in range(warmup):
-            shm.eval_sh(p, lmax, out=out, stream=stream)
+            shm.eval_sh(p, lmax, out=out, stream=stream, strict=strict)
     torch.cuda.synchronize()
-    per, region = timed_launches(lambda: shm.eval_sh(p, lmax, out=out, stream=stream), steps, stream)
+    per, region = timed_launches(lambda: shm.eval_sh(p, lmax, out=out, stream=stream, strict=strict), steps, stream)
     del out, p
     return per, region
+
+
+def measure_fp64_peak(shm, reps=3):
+    """The FP64 pipe rate of this GPU (shm_probe_fp64_rate: DFMA chains on
+    every SM): best of `reps` launches, as TFLOP/s (2 flops per DFMA)."""
+    try:
+        rates = [shm.probe_fp64_rate(1 << 14)[0] for _ in range(reps)]
+        return {"tflops": 2.0 * max(rates) / 1e12, "dfma_per_s": max(rates), "runs": rates,
+                "source": "measured: shm_probe_fp64_rate (8 independent DFMA chains per thread, 2048 threads "
+                          "per SM, CUDA events), best of 3"}
+    except Exception as e:  # the nominal figure, said so
+        return {"tflops": FP64_NOMINAL_TFLOPS, "dfma_per_s": FP64_NOMINAL_TFLOPS * 0.5e12,
+                "source": f"nominal 1.25 TFLOP/s (probe failed: {e!r})"}
 
 
 def run_gpu(args, rank, world):
@@ -273,28 +278,34 @@ def run_gpu(args, rank, world):
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     peaks, peaks_src = load_peaks()
+    fp64 = measure_fp64_peak(shm)
     nh = (LMAX + 1) ** 2
 
     tdt = torch.float64 if args.dtype == "f64" else torch.float32
     es = 8 if args.dtype == "f64" else 4
+    strict = args.dtype == "f64" and args.arith == "strict"
     tuned_ms = None
     if args.variant:
         for v in range(shm.eval_variant_count()):
-            shm.set_eval_variant(LMAX, tdt, v)
-            if shm.eval_variant(LMAX, tdt) == args.variant:
+            try:
+                shm.set_eval_variant(LMAX, tdt, v, strict=strict)
+            except shm.ShmError:
+                continue
+            if shm.eval_variant(LMAX, tdt, strict=strict) == args.variant:
                 break
         else:
             raise SystemExit(f"unknown launch variant {args.variant}")
     pts = inputs.dft_grid_points(args.grid)
     if not args.variant and args.tune:  # tune on the workload's own size
-        tuned_ms = shm.autotune(LMAX, tdt, min(pts.shape[0], 1 << 23))
+        tuned_ms = shm.autotune(LMAX, tdt, min(pts.shape[0], 1 << 23), strict=strict)
     if args.dtype == "f32":
         pts = pts.astype(np.float32)
     n = pts.shape[0]
     p = torch.from_numpy(pts).cuda()
     out = torch.empty((n, nh), dtype=tdt, device="cuda")
+    launch = lambda st: shm.eval_sh(p, LMAX, out=out, stream=st, strict=strict)  # noqa: E731
     for _ in range(args.warmup):
-        shm.eval_sh(p, LMAX, out=out, stream=stream)
+        launch(stream)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(gpu_id_for_smi(dev)) if rank == 0 else None
@@ -304,7 +315,7 @@ def run_gpu(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    per, region = timed_launches(lambda: shm.eval_sh(p, LMAX, out=out, stream=stream), args.steps, stream)
+    per, region = timed_launches(lambda: launch(stream), args.steps, stream)
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
@@ -313,26 +324,22 @@ def run_gpu(args, rank, world):
         region = max_over_ranks(region, device="cuda")
         dist.barrier()
     clk = clocks.stop() if clocks else None
-    graph = graph_replay_timing(torch, shm, p, out, LMAX) if rank == 0 else None
+    graph = graph_replay_timing(torch, launch, stream=stream) if rank == 0 else None
 
     ms_per_step = region / args.steps
     value = world * n * nh / (ms_per_step * 1e-3)
     launch_ms = statistics.mean(per)
 
     # roofline of the (single) kernel
-    variant = shm.eval_variant(LMAX, tdt)
+    variant = shm.eval_variant(LMAX, tdt, strict=strict)
     hybrid = args.dtype == "f64" and "hybrid" in variant
-    dp_pp = HYBRID_DP_PER_POINT_L9 if hybrid else dp_instr_per_point(LMAX)
+    dp_pp = HYBRID_DP_PER_POINT_L9 if hybrid else STRICT_DP_PER_POINT_L9
     achieved_tflops = 2.0 * dp_pp * n / (launch_ms * 1e-3) / 1e12
     bytes_per_launch = n * (3 + nh) * es
     achieved_gbs = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     tpp = TRAFFIC_PER_POINT.get((args.dtype, variant))
     traffic = tpp * n if tpp else None
-    arithmetic = ("FP64 (1/r and the m = 0, 1 columns) + float-float 2xFP32 (m >= 2 columns), FP64 output; "
-                  "max normwise error vs the FP64 oracle <= 5e-14 (tolerance 1e-13)"
-                  if (args.dtype == "f64" and "hybrid" in variant) else
-                  ("FP64" if args.dtype == "f64" else "FP32 (FP64 1/r for r < 1e-2; float-float m = 0, 1)"))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -340,13 +347,14 @@ def run_gpu(args, rank, world):
         "config": {"workload": (WORKLOAD if args.grid == N_SIDE else f"dft_grid_{args.grid}cubed_fp64_lmax9")
                    .replace("fp64", "fp32" if args.dtype == "f32" else "fp64"),
                    "points": n, "lmax": LMAX, "grid": f"{args.grid}^3, h=0.3 bohr",
-                   "out_bytes_per_step": n * nh * 8, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "out_bytes_per_step": n * nh * es, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "no flush: 170 MB input and 5.66 GB output per step exceed the 126 MB L2",
-                   "launch_variant": variant, "arithmetic": arithmetic, "autotune_probe_ms": tuned_ms,
+                   "launch_variant": variant, "arithmetic": ARITHMETIC[(args.dtype, hybrid)],
+                   "autotune_probe_ms": tuned_ms,
                    "timing": {"mean_ms_per_launch": launch_ms, "median_ms_per_launch": statistics.median(per),
                               "cuda_graph_replay": graph}},
         "roofline": roofline_object(args.dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src,
-                                    traffic, n),
+                                    traffic, fp64),
         "gpu_launches": args.steps,
         "clocks": clk,
         "kernel_ms": launch_ms,
@@ -360,29 +368,41 @@ def run_gpu(args, rank, world):
         hin = torch.from_numpy(pts).pin_memory()
         hout = torch.empty((n, nh), dtype=tdt).pin_memory()
         ws = torch.empty(shm.eval_host_workspace_size(LMAX, tdt, 1 << 20), dtype=torch.uint8, device="cuda")
-        shm.eval_host(hin, LMAX, hout, ws, stream=stream)
+        shm.eval_host(hin, LMAX, hout, ws, stream=stream, strict=strict)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            shm.eval_host(hin, LMAX, hout, ws, stream=stream)
+            shm.eval_host(hin, LMAX, hout, ws, stream=stream, strict=strict)
             stream.synchronize()
         dt = (time.perf_counter() - t0) / e2e_steps
         line["e2e"] = {"value": n * nh / dt, "unit": UNIT, "h2d_bytes_per_step": n * 3 * es,
                        "d2h_bytes_per_step": n * nh * es, "steps": e2e_steps,
-                       "api": "shm_eval_host (pinned host in/out, 1M-point chunks double-buffered)"}
+                       "api": "shm_eval_host_ex (pinned host in/out, 1M-point chunks double-buffered)"
+                              + (", SHM_STRICT_FP64" if strict else "")}
         del hin, hout, ws
         pts64 = pts.astype(np.float64)
         rate, m, cores = cpu_oracle_rate(pts64, LMAX, args.cpu_seconds)
-        rate1, m1, _ = cpu_oracle_rate(pts64, LMAX, min(2.0, args.cpu_seconds / 4), nthreads=1)
+        rate1, m1, _ = cpu_oracle_rate(pts64, LMAX, min(4.0, args.cpu_seconds / 2), nthreads=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"first {m} of {n} grid points, lmax=9, FP64",
+                                "protocol": "oracle_timing: median of 3 timed calls after 1 warm-up call",
                                 "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
                                                 "sample": f"first {m1} grid points, 1 thread"}}
         if args.extras:
-            line["extra"] = run_extras(args, shm, torch, inputs, stream, peaks, peaks_src)
+            line["extra"] = run_extras(args, shm, torch, inputs, stream, peaks, peaks_src, fp64)
         print(json.dumps(line), flush=True)
     return 0
 
+
+ARITHMETIC = {
+    ("f64", False): "binary64 throughout (SHM_STRICT_FP64): IEEE double multiply and fused multiply-add, CUDA's "
+                    "binary64 rsqrt",
+    ("f64", True): "FP64 out, float-float arithmetic: binary64 for 1/r and the m = 0, 1 columns, float-float "
+                   "(2 x FP32, ~48-bit significand) for the m >= 2 columns (72 of 100 values); within 1e-13 of "
+                   "the l-shell norm of the FP64 oracle",
+    ("f32", False): "FP32 (FP64 1/r for r < 1e-2; float-float m = 0, 1)",
+    ("f32", True): "FP32 (FP64 1/r for r < 1e-2; float-float m = 0, 1)",
+}
 
 # DRAM bytes per point (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # evaluator at lmax 9 from ncu captures (profiles/), keyed by (dtype, launch
@@ -400,35 +420,58 @@ TRAFFIC_PER_POINT = {
 HYBRID_DP_PER_POINT_L9 = 74
 
 
-def roofline_object(dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src, traffic, n):
-    """The bound of the evaluator kernel: the all-FP64 rows are FP64-pipe bound
-    (242 FP64 instructions per point against 824 B per point); the hybrid rows
-    (74 FP64 instructions per point) and the FP32 rows are bound by the HBM
-    traffic of their output.  The other figures are given beside it."""
-    fp64 = {"achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-            "def": f"{dp_pp} FP64 pipe instructions per point x 2 (FMA-equivalent flops) / mean launch time",
-            "peak_source": "recipe nominal FP64 1.25 TFLOP/s (0.625e12 FP64 pipe instr/s)"}
+def roofline_object(dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src, traffic, fp64):
+    """The bound of the evaluator kernel: the all-binary64 rows are FP64-pipe
+    bound (242 FP64 instructions per point against 824 B per point: 3.1 ms
+    at the measured FP64 rate against 0.9 ms of HBM); the hybrid rows (74 FP64
+    instructions per point) and the FP32 rows are bound by the HBM traffic of
+    their output.  The other figure is given beside it."""
+    fp = {"achieved": achieved_tflops, "peak": fp64["tflops"], "unit": "TFLOP/s",
+          "frac": achieved_tflops / fp64["tflops"],
+          "def": f"{dp_pp} FP64 pipe instructions per point x 2 (FMA-equivalent flops) x points / mean launch time",
+          "peak_source": fp64["source"]}
     hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
            "def": "algorithmic bytes (points in + rows out) / mean launch time", "peak_source": peaks_src}
     if dtype == "f64" and not hybrid:
-        return {"bound": "alu", "pipe": "fp64", **{k: fp64[k] for k in ("achieved", "peak", "unit", "frac")},
-                "traffic": traffic, "achieved_def": fp64["def"], "peak_source": fp64["peak_source"], "hbm": hbm}
+        return {"bound": "alu", "pipe": "fp64", **{k: fp[k] for k in ("achieved", "peak", "unit", "frac")},
+                "traffic": traffic, "achieved_def": fp["def"], "peak_source": fp["peak_source"], "hbm": hbm}
     out = {"bound": "hbm", **{k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}, "traffic": traffic,
            "achieved_def": hbm["def"], "peak_source": peaks_src}
     if dtype == "f64":
-        out["fp64_pipe"] = fp64
+        out["fp64_pipe"] = fp
     return out
 
 
-def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
+def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src, fp64):
     """Other workloads, reported beside the headline (not part of `value`)."""
     res = {}
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     nh = (LMAX + 1) ** 2
     steps = max(5, min(args.steps, 50))
+    g64 = inputs.dft_grid_points(N_SIDE)
+    # the same grid with the default FP64 rows: float-float for m >= 2 (not binary64 arithmetic)
+    if args.tune:
+        shm.autotune(LMAX, torch.float64, g64.shape[0])
+    per, region = measure_eval(shm, torch, g64, torch.float64, LMAX, steps, 3, stream)
+    ms = statistics.mean(per)
+    variant = shm.eval_variant(LMAX, torch.float64)
+    hyb = "hybrid" in variant
+    gbs = g64.shape[0] * (3 + nh) * 8 / (ms * 1e-3) / 1e9
+    dp_pp = HYBRID_DP_PER_POINT_L9 if hyb else STRICT_DP_PER_POINT_L9
+    tf = 2.0 * dp_pp * g64.shape[0] / (ms * 1e-3) / 1e12
+    tpp = TRAFFIC_PER_POINT.get(("f64", variant))
+    res["dft_grid_192cubed_f64out_ffarith_lmax9"] = {
+        "value": g64.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "launch_variant": variant,
+        "dtype": "f64-out/ff-arith" if hyb else "f64", "arithmetic": ARITHMETIC[("f64", hyb)],
+        "accuracy": "max normwise error 4.9e-14 on a 20,000-row sample of this grid (GPU tests; all-binary64 "
+                    "rows: 1.4e-14; tolerance 1e-13)",
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                     "peak_source": peaks_src, "traffic": tpp * g64.shape[0] if tpp else None,
+                     "fp64_pipe": {"achieved": tf, "peak": fp64["tflops"], "unit": "TFLOP/s",
+                                   "frac": tf / fp64["tflops"], "peak_source": fp64["source"],
+                                   "def": f"{dp_pp} FP64 pipe instructions per point"}}}
     # FP32 on the same grid: HBM-write bound
-    g32 = inputs.dft_grid_points(N_SIDE).astype(np.float32)
+    g32 = g64.astype(np.float32)
     if args.tune:
         shm.autotune(LMAX, torch.float32, g32.shape[0])
     per, region = measure_eval(shm, torch, g32, torch.float32, LMAX, steps, 3, stream)
@@ -439,17 +482,19 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
         "launch_variant": shm.eval_variant(LMAX, torch.float32),
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": gbs / hbm_peak, "peak_source": peaks_src}}
-    # the plain random-sphere set (65,600 points): latency-sized
+    # the plain random-sphere set (65,600 points): latency-sized; binary64 and default rows
     sph = inputs.random_sphere_points(65_536)
-    per, region = measure_eval(shm, torch, sph, torch.float64, LMAX, steps, 3, stream)
-    ms = statistics.mean(per)
-    c_all, _, c_cores = cpu_oracle_rate(sph, LMAX, 1.0)
-    c_one, c_m1, _ = cpu_oracle_rate(sph, LMAX, 1.0, nthreads=1)
-    res["random_sphere_65600_fp64_lmax9"] = {"value": sph.shape[0] * nh / (ms * 1e-3), "unit": UNIT,
-                                             "kernel_ms": ms,
-                                             "cpu_oracle": {"value": c_all, "cores": c_cores, "unit": UNIT},
-                                             "cpu_oracle_single_core": {"value": c_one, "cores": 1, "unit": UNIT,
-                                                                        "sample": f"first {c_m1} points"}}
+    c_all, _, c_cores = cpu_oracle_rate(sph, LMAX, 2.0)
+    c_one, c_m1, _ = cpu_oracle_rate(sph, LMAX, 2.0, nthreads=1)
+    for strict, key in ((True, "random_sphere_65600_fp64_lmax9"), (False, "random_sphere_65600_f64out_ffarith_lmax9")):
+        per, region = measure_eval(shm, torch, sph, torch.float64, LMAX, steps, 3, stream, strict=strict)
+        ms = statistics.mean(per)
+        res[key] = {"value": sph.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+                    "launch_variant": shm.eval_variant(LMAX, torch.float64, strict=strict),
+                    "arithmetic": ARITHMETIC[("f64", not strict)],
+                    "cpu_oracle": {"value": c_all, "cores": c_cores, "unit": UNIT},
+                    "cpu_oracle_single_core": {"value": c_one, "cores": 1, "unit": UNIT,
+                                               "sample": f"first {c_m1} points"}}
     # the 1M-point random-sphere set in FP32 (HBM-write bound, fits in HBM many times over)
     sph32 = inputs.random_sphere_points(1 << 20).astype(np.float32)
     per, region = measure_eval(shm, torch, sph32, torch.float32, LMAX, steps, 3, stream)
@@ -462,29 +507,12 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src):
                        "sample": f"first {c32_m} points (FP64 oracle at the upcast FP32 inputs)"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                      "peak_source": peaks_src, "note": "420 MB out: partly absorbed by the 126 MB L2"}}
-    # the all-FP64 arithmetic on the headline grid, for comparison with the tuned variant
-    chosen = shm.eval_variant(LMAX, torch.float64)
-    for v in range(shm.eval_variant_count()):
-        shm.set_eval_variant(LMAX, torch.float64, v)
-        if shm.eval_variant(LMAX, torch.float64) == "staged-64":
-            break
-    g64 = inputs.dft_grid_points(N_SIDE)
-    per, region = measure_eval(shm, torch, g64, torch.float64, LMAX, steps, 3, stream)
-    ms = statistics.mean(per)
-    tf = 2.0 * dp_instr_per_point(LMAX) * g64.shape[0] / (ms * 1e-3) / 1e12
-    res["dft_grid_192cubed_fp64_lmax9_all_fp64_arithmetic"] = {
-        "value": g64.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, "launch_variant": "staged-64",
-        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": tf / FP64_PEAK_TFLOPS}}
-    for v in range(shm.eval_variant_count()):
-        shm.set_eval_variant(LMAX, torch.float64, v)
-        if shm.eval_variant(LMAX, torch.float64) == chosen:
-            break
     for fn in EXTRA_WORKLOADS:
         try:
             res.update(fn(args, shm, torch, inputs, stream, peaks, peaks_src))
         except Exception as e:  # reported, never silently dropped
             res[getattr(fn, "__name__", "extra")] = {"error": repr(e)}
+    res["fp64_peak_probe"] = fp64
     return res
 
 
@@ -570,15 +598,36 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
 
 def extra_serving(args, shm, torch, inputs, stream, peaks, peaks_src):
     """Serving: Poisson request streams (sizes log-uniform in [1e3, 4e6] points,
-    lmax uniform in 0..9, dtype 50/50 FP32/FP64, points generated on the device
-    from each request's seed), continuous batching, per-rate throughput and
-    submit-to-done latency percentiles.  Requests are submitted with
-    SHM_REQ_DISCARD (the client does not read rows back)."""
+    lmax uniform in 0..9, dtype 50/50 FP32/FP64 -- FP64 requests with
+    all-binary64 rows unless --serve-fp64 hybrid --, points generated on the
+    device from each request's seed), continuous batching, per-rate throughput
+    and latency percentiles.  A client thread collects every request as it
+    completes (shm_serve_wait_any) and releases its rows; the client latency
+    is submit -> that wait returning, the scheduler latency submit -> the
+    scheduler seeing the request's last batch finish."""
     res = {}
+    strict = args.serve_fp64 == "strict"
     for rate in args.serve_rates:
         reqs = inputs.serving_requests(rate, args.serve_seconds)
         with shm.Server(pool_bytes=48 << 30, max_slots=256, queue_capacity=2048, batch_points=8 << 20,
                         chunk_points=1 << 20, inflight_batches=3) as srv:
+            stop = threading.Event()
+            errors = []
+
+            def collect():
+                while True:
+                    st, t, r = srv.wait_any(timeout_ms=20)
+                    if st == 0:
+                        srv.release(t)
+                    elif st == 5:
+                        if stop.is_set():
+                            return
+                    else:
+                        errors.append(st)
+                        srv.release(t)
+
+            th = threading.Thread(target=collect, daemon=True)
+            th.start()
             t0 = time.perf_counter()
             for r in reqs:
                 while True:
@@ -587,23 +636,29 @@ def extra_serving(args, shm, torch, inputs, stream, peaks, peaks_src):
                         break
                     if dt > 2e-3:
                         time.sleep(dt - 1e-3)
-                srv.submit(r.n, r.lmax, r.dtype, seed=r.seed, discard=True)
+                srv.submit(r.n, r.lmax, r.dtype, seed=r.seed, strict=strict)
             t_sub = time.perf_counter() - t0
             deadline = time.perf_counter() + 300
             while time.perf_counter() < deadline:
                 st = srv.stats()
-                if st["completed"] + st["rejected"] >= st["submitted"]:
+                if st["completed"] + st["rejected"] >= st["submitted"] and st["collected"] >= st["completed"]:
                     break
                 time.sleep(0.001)
             wall = time.perf_counter() - t0
+            stop.set()
+            th.join(timeout=10)
             st = srv.stats()
-        res[f"serve_poisson_{rate}_per_s"] = {
+        res[f"serve_poisson_{rate:g}_per_s"] = {
             "offered_req_per_s": rate, "submitted": st["submitted"], "submit_rate_achieved": len(reqs) / t_sub,
-            "completed": st["completed"], "rejected_busy": st["rejected"],
+            "completed": st["completed"], "collected": st["collected"], "rejected_busy": st["rejected"],
             "completed_req_per_s": st["completed"] / wall, "value": st["harmonics_done"] / wall, "unit": UNIT,
-            "lat_p50_ms": st["lat_p50_ms"], "lat_p99_ms": st["lat_p99_ms"], "lat_max_ms": st["lat_max_ms"],
+            "client_lat_p50_ms": st["client_lat_p50_ms"], "client_lat_p99_ms": st["client_lat_p99_ms"],
+            "client_lat_max_ms": st["client_lat_max_ms"],
+            "sched_lat_p50_ms": st["lat_p50_ms"], "sched_lat_p99_ms": st["lat_p99_ms"],
             "batches": st["batches"], "gpu_busy_frac": st["busy_ms"] / (wall * 1e3), "wall_s": wall,
-            "duration_s": args.serve_seconds, "pool_peak_bytes": st["pool_peak"]}
+            "duration_s": args.serve_seconds, "pool_peak_bytes": st["pool_peak"],
+            "fp64_rows": "all-binary64 (SHM_REQ_STRICT_FP64)" if strict else "hybrid (float-float m >= 2)",
+            "request_errors": len(errors)}
     return res
 
 
@@ -646,13 +701,18 @@ def main():
     ap.add_argument("--grid", type=int, default=N_SIDE, help="grid side (192 = the benchmark workload; "
                     "smaller sides only for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
-                    help="length of each Poisson request stream of the serving extra (30 for the full run)")
+    ap.add_argument("--serve-seconds", type=float, default=30.0,
+                    help="length of each Poisson request stream of the serving extra")
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")],
-                    default=[1000.0, 5000.0, 20000.0, 50000.0])
+                    default=[1000.0, 2000.0, 5000.0, 10000.0, 20000.0, 50000.0])
+    ap.add_argument("--serve-fp64", choices=["strict", "hybrid"], default="strict",
+                    help="rows of the FP64 requests of the serving extra")
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64",
                     help="f64 is the benchmark workload; f32 only for profiling captures")
     ap.add_argument("--variant", default=None, help="pin a launch variant by name (skips the autotuner)")
+    ap.add_argument("--arith", choices=["strict", "hybrid"], default="strict",
+                    help="FP64 rows: strict = binary64 throughout (the benchmark workload), hybrid = the "
+                         "default rows with float-float m >= 2 columns (profiling captures only)")
     ap.add_argument("--no-tune", dest="tune", action="store_false", default=True,
                     help="skip shm_autotune (use the library's default launch variant)")
     ap.add_argument("--extras", dest="extras", action="store_true", default=True)

@@ -49,8 +49,15 @@ extern "C" {
 #endif
 
 typedef enum {
-  SHM_F32 = 0, /* float  in, float  out, FP32 arithmetic (FP64 for 1/r when r < 1e-2) */
-  SHM_F64 = 1  /* double in, double out, FP64 arithmetic */
+  SHM_F32 = 0, /* float in, float out: FP32 arithmetic (FP64 for 1/r when r < 1e-2, float-float for the
+                  m = 0, 1 recurrences) */
+  SHM_F64 = 1  /* double in, double out.  Default arithmetic for l <= 9: binary64 for 1/r and the m = 0, 1
+                  columns, float-float (two FP32 numbers, a ~48-bit significand, on the FP32 pipe) for the
+                  m >= 2 columns, converted to binary64 once per value; within 1e-13 of the l-shell norm
+                  sqrt((2l+1)/4pi) (measured <= 5.4e-14 at l = 9, all-binary64 rows: 1.4e-14).  With the
+                  flag SHM_STRICT_FP64 every operation is binary64 (IEEE double add, multiply, fused
+                  multiply-add; CUDA's binary64 rsqrt and sincos).  Rows above l = 9 are always
+                  all-binary64. */
 } shm_dtype;
 
 typedef enum {
@@ -71,12 +78,23 @@ typedef enum {
 
 /* shm_eval_ex flags */
 #define SHM_NORMALIZED_INPUT 0x1u /* points are already x/r, y/r, z/r: skip the r work */
+#define SHM_STRICT_FP64 0x2u      /* SHM_F64 only (ignored for SHM_F32): compute every value in binary64
+                                     arithmetic -- no float-float -- with the same formulas (Sec. II
+                                     Eq. 5-6 via the recurrence of the rows), as the paper does (Sec. IV:
+                                     machine precision in double).  Accepted by shm_eval_ex,
+                                     shm_eval_host_ex, shm_eval_complex, shm_eval_spinor,
+                                     shm_eval_angles_ex and the tuner (shm_autotune_ex).  The all-binary64
+                                     rows are bound by the FP64 pipe (about 2.4 FP64 instructions per
+                                     harmonic at l = 9, against 0.74 for the default rows). */
 
 /* Number of harmonics for lmax: (lmax+1)^2 (0 for lmax outside 0..16). */
 int shm_num_harmonics(int lmax);
 
 /*
- * shm_eval -- all R_l^m, 0 <= l <= lmax, at n points.
+ * shm_eval -- all R_l^m, 0 <= l <= lmax, at n points, in the default
+ * arithmetic of the dtype (see shm_dtype: for SHM_F64 the hybrid
+ * binary64/float-float rows at l <= 9; shm_eval_ex with SHM_STRICT_FP64 for
+ * all-binary64 rows).
  *   points : device, [n][3] x, y, z (AoS) relative to the centre, element type
  *            per dtype, aligned to its element size.
  *   n      : number of points, >= 0 (0: returns SHM_OK, launches nothing).
@@ -90,7 +108,7 @@ int shm_num_harmonics(int lmax);
  */
 shm_status shm_eval(const void* points, int64_t n, int lmax, shm_dtype dtype, void* out, void* stream);
 
-/* shm_eval with flags (SHM_NORMALIZED_INPUT). Unknown flag bits: SHM_EINVAL. */
+/* shm_eval with flags (SHM_NORMALIZED_INPUT, SHM_STRICT_FP64). Unknown flag bits: SHM_EINVAL. */
 shm_status shm_eval_ex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
                        void* out, void* stream);
 
@@ -115,6 +133,10 @@ shm_status shm_eval_ex(const void* points, int64_t n, int lmax, shm_dtype dtype,
 shm_status shm_eval_host(const void* points_host, int64_t n, int lmax, shm_dtype dtype, void* out_host,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* shm_eval_host with flags (SHM_NORMALIZED_INPUT, SHM_STRICT_FP64); unknown bits: SHM_EINVAL. */
+shm_status shm_eval_host_ex(const void* points_host, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
+                            void* out_host, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Device workspace bytes shm_eval_host needs for chunks of `chunk_points` points. */
 size_t shm_eval_host_workspace_size(int lmax, shm_dtype dtype, int64_t chunk_points);
 
@@ -131,15 +153,26 @@ size_t shm_eval_host_workspace_size(int lmax, shm_dtype dtype, int64_t chunk_poi
  */
 shm_status shm_autotune(int lmax, shm_dtype dtype, int64_t n_probe, double* best_ms);
 
+/* shm_autotune for the rows a flag selects: with SHM_STRICT_FP64 (SHM_F64)
+ * only the all-binary64 variants are timed and the choice is kept for calls
+ * that pass that flag (a separate entry of the cache file).  Other bits:
+ * SHM_EINVAL. */
+shm_status shm_autotune_ex(int lmax, shm_dtype dtype, unsigned flags, int64_t n_probe, double* best_ms);
+
 /* Text naming the launch variant shm_eval uses for (lmax, dtype) (always succeeds
- * for valid arguments; "" otherwise). */
+ * for valid arguments; "" otherwise); _ex: for calls with these flags
+ * (SHM_STRICT_FP64 selects the all-binary64 choice). */
 const char* shm_eval_variant(int lmax, shm_dtype dtype);
+const char* shm_eval_variant_ex(int lmax, shm_dtype dtype, unsigned flags);
 
 /* Number of launch variants, and pinning one of them (0 .. count-1) for
  * (lmax, dtype) in this process; variant -1 restores the default choice.
+ * _ex with SHM_STRICT_FP64 pins the choice of strict calls and accepts only
+ * all-binary64 variants (staged-*, direct-*, phased-64/128, rows-tma-*).
  * Errors: SHM_EINVAL. */
 int shm_eval_variant_count(void);
 shm_status shm_eval_set_variant(int lmax, shm_dtype dtype, int variant);
+shm_status shm_eval_set_variant_ex(int lmax, shm_dtype dtype, unsigned flags, int variant);
 
 /* ------------------------------------------------------------------------
  * Fused non-local projectors.  Sec. I of the paper motivates the method by
@@ -168,8 +201,8 @@ typedef struct {
   int32_t n_species;             /* 1..SHM_PROJ_MAX_SPECIES */
   const int32_t* species_lmax;   /* HOST [n_species], each 0..9 */
   const double* radial;          /* device [n_species][radial_lstride][n_rad] */
-  int32_t radial_lstride;        /* >= 1 + max species lmax */
-  int32_t n_rad;                 /* >= 4 */
+  int32_t radial_lstride;        /* 1 + max species lmax .. 64 */
+  int32_t n_rad;                 /* 4 .. 2^26 */
   double r_min;                  /* > 0 */
   double dlog;                   /* > 0 */
   double box;                    /* > 0, = ng * h */
@@ -178,11 +211,15 @@ typedef struct {
   const int64_t* point_offsets;  /* device [n_atoms+1], non-decreasing, [0] = 0 */
   const int32_t* point_index;    /* device [n_points], each in [0, ng^3) */
   const int64_t* out_offsets;    /* device [n_atoms+1], out_offsets[a+1] - out_offsets[a] = n_a (L_a+1)^2 */
-  int64_t n_points;              /* host copy of point_offsets[n_atoms] */
-  int64_t n_values;              /* host copy of out_offsets[n_atoms] */
+  int64_t n_points;              /* host copy of point_offsets[n_atoms], <= 2^40 */
+  int64_t n_values;              /* host copy of out_offsets[n_atoms], <= 2^44 */
 } shm_proj_problem;
 
-/* Device workspace bytes shm_projectors needs for this problem and dtype. */
+/* Device workspace bytes shm_projectors needs for this problem and dtype; 0
+ * for a problem shm_projectors would reject on its host-side checks (the
+ * reason is then in shm_last_error()).  Host-side limits: n_rad 4..2^26,
+ * radial_lstride (1 + max species lmax)..64, n_points <= 2^40, n_values <=
+ * 2^44, n_atoms < 2^31 -- so no size product can overflow. */
 size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dtype);
 
 /*
@@ -243,7 +280,8 @@ typedef struct {
   int32_t device;           /* CUDA device ordinal */
 } shm_serve_config;
 
-#define SHM_REQ_DISCARD 0x1u /* free the output as soon as the request completes (no result rows) */
+#define SHM_REQ_DISCARD 0x1u     /* free the output as soon as the request completes (no result rows) */
+#define SHM_REQ_STRICT_FP64 0x2u /* SHM_F64 requests: all-binary64 rows (as SHM_STRICT_FP64 for shm_eval_ex) */
 
 typedef struct {
   const void* points;       /* device [n][3] of dtype, kept alive by the caller until the request
@@ -253,7 +291,7 @@ typedef struct {
   int32_t lmax;             /* 0..9 */
   shm_dtype dtype;
   uint64_t seed;
-  uint32_t flags;           /* SHM_REQ_DISCARD */
+  uint32_t flags;           /* SHM_REQ_DISCARD, SHM_REQ_STRICT_FP64 */
 } shm_request;
 
 typedef struct {
@@ -273,8 +311,13 @@ typedef struct {
   uint64_t queued_now, active_now;
   double harmonics_done;    /* sum over completed requests of n (lmax+1)^2 */
   double busy_ms;           /* sum of batch GPU times (CUDA events) */
-  double lat_p50_ms, lat_p99_ms, lat_max_ms;   /* submit -> done, over completed requests */
+  double lat_p50_ms, lat_p99_ms, lat_max_ms;   /* submit -> done (as the scheduler saw it), over completed
+                                                  requests */
   size_t pool_bytes, pool_in_use, pool_peak;
+  uint64_t collected;                          /* requests a wait has returned to the client */
+  double client_lat_p50_ms, client_lat_p99_ms, client_lat_max_ms;  /* submit -> the first shm_serve_wait or
+                                                  shm_serve_wait_any returning the request, over collected
+                                                  requests: the latency the client sees */
 } shm_serve_stats;
 
 /* Creates a server: allocates the pool and starts the scheduler thread.
@@ -290,6 +333,15 @@ shm_status shm_serve_submit(shm_server* server, const shm_request* req, uint64_t
  * SHM_ETIMEOUT when it is still running; SHM_ENOTFOUND for an unknown or
  * released ticket. */
 shm_status shm_serve_wait(shm_server* server, uint64_t ticket, int timeout_ms, shm_result* result);
+
+/* Waits up to timeout_ms (< 0: no limit) for any request that has completed
+ * and that no wait has returned yet, oldest completion first, and returns
+ * its ticket and result (requests submitted with SHM_REQ_DISCARD are never
+ * returned).  A client that collects its requests this way sees each one as
+ * soon as it completes, whatever order they were submitted in.  SHM_ETIMEOUT
+ * when none completed in time; SHM_ECUDA for a request whose batch failed
+ * (ticket and result are still filled in). */
+shm_status shm_serve_wait_any(shm_server* server, int timeout_ms, uint64_t* ticket, shm_result* result);
 
 /* Returns a completed request's output memory to the pool and forgets the
  * ticket.  SHM_EBUSY if it has not completed. */
@@ -349,8 +401,9 @@ shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_dtype dtype,
  *   points, n, lmax, dtype, flags, stream : as shm_eval_ex.
  *   out : device, [n][(lmax+1)^2][2] of dtype: (Re, Im) at k = l*l + l + m.
  * FP64 rows use binary64 for 1/r and the m = 0, 1 columns and float-float
- * arithmetic for m >= 2 (within 1e-13 of the l-shell norm); FP32 rows as
- * shm_eval.  Nothing is allocated.  Errors: as shm_eval.
+ * arithmetic for m >= 2 (within 1e-13 of the l-shell norm), or binary64
+ * throughout with SHM_STRICT_FP64; FP32 rows as shm_eval.  Nothing is
+ * allocated.  Errors: as shm_eval.
  */
 shm_status shm_eval_complex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags, void* out,
                             void* stream);
@@ -362,11 +415,18 @@ shm_status shm_eval_complex(const void* points, int64_t n, int lmax, shm_dtype d
  *   angles : device, [n][2] (theta, phi) in radians, theta from +z (Eq. 3),
  *            phi = atan2(y, x) (Eq. 4), element type per dtype.
  *   out    : device, [n][(lmax+1)^2] of dtype, as shm_eval.
- * The unit vector (sin t cos p, sin t sin p, cos t) is formed with CUDA's
- * sincos, then the rows are those of shm_eval (FP64: the hybrid rows).
- * Nothing is allocated.  Errors: as shm_eval.
+ * The unit vector (sin t cos p, sin t sin p, cos t): for SHM_F64, theta by
+ * CUDA's binary64 sincos and phi by a float-float sine and cosine on the FP32
+ * pipe (|phi| <= 800; binary64 sincos beyond), then the hybrid rows of
+ * shm_eval; for SHM_F32, sincosf and the FP32 rows.  Nothing is allocated.
+ * Errors: as shm_eval.
  */
 shm_status shm_eval_angles(const void* angles, int64_t n, int lmax, shm_dtype dtype, void* out, void* stream);
+
+/* shm_eval_angles with flags: SHM_STRICT_FP64 (SHM_F64) takes binary64 sincos
+ * of both angles and the all-binary64 rows.  Other bits: SHM_EINVAL. */
+shm_status shm_eval_angles_ex(const void* angles, int64_t n, int lmax, shm_dtype dtype, unsigned flags, void* out,
+                              void* stream);
 
 /*
  * shm_eval_spinor -- the spin-1/2 spinor harmonics (Sec. II Eq. 7) for every
@@ -381,15 +441,28 @@ shm_status shm_eval_angles(const void* angles, int64_t n, int lmax, shm_dtype dt
  *         each l first j = l - 1/2, then j = l + 1/2; m_j ascending, i.e.
  *         q = 2 l^2 + (s < 0 ? 0 : 2l) + (m_j + j).  16-byte (FP64) or
  *         8-byte (FP32) alignment of out enables the vector store path.
- * FP64 rows: the hybrid real rows times binary64 coefficients (within 1e-13
- * of the l-shell norm sqrt((2l+1)/4pi)); FP32 rows as shm_eval.  Nothing is
- * allocated.  Errors: as shm_eval (lmax outside 0..9: SHM_EINVAL).
+ * FP64 rows: the hybrid real rows times the coupling coefficients, real
+ * parts by binary64 products and imaginary parts by float-float products
+ * (within 1e-13 of the l-shell norm sqrt((2l+1)/4pi)); with SHM_STRICT_FP64
+ * the all-binary64 rows and binary64 products throughout.  FP32 rows as
+ * shm_eval.  Nothing is allocated.  Errors: as shm_eval (lmax outside 0..9:
+ * SHM_EINVAL).
  */
 shm_status shm_eval_spinor(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags, void* out,
                            void* stream);
 
 /* Spinor harmonics per point for lmax: 2 (lmax+1)^2 (-1 for lmax outside 0..9). */
 int shm_num_spinors(int lmax);
+
+/* Diagnostics (not part of the method).  The FP64 pipe's rate on the current
+ * device, measured: a kernel of independent DFMA chains (8 per thread, the
+ * resident maximum of 256-thread CTAs per SM, `iters` DFMAs per chain) timed
+ * with CUDA events after a warm-up launch.  *dfma_per_s receives the DFMA
+ * instructions per second summed over the GPU's lanes (x 2 = FP64 flop/s),
+ * *ms (may be NULL) the timed launch.  It synchronises on a private stream,
+ * so it must not run during stream capture; nothing is allocated.
+ * Errors: SHM_EINVAL (iters outside 1..2^24, null result), SHM_ECUDA. */
+shm_status shm_probe_fp64_rate(int64_t iters, double* dfma_per_s, double* ms);
 
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* shm_last_error(void);

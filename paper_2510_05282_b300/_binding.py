@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(PKG, "libshm.so")
 
 SHM_F32, SHM_F64 = 0, 1
 SHM_NORMALIZED_INPUT = 0x1
+SHM_STRICT_FP64 = 0x2
 LMAX_CAP = 9
 
 STATUS = {0: "SHM_OK", 1: "SHM_EINVAL", 2: "SHM_ENOMEM", 3: "SHM_ECUDA", 4: "SHM_EBUSY",
@@ -71,6 +72,18 @@ def _declare(L):
     L.shm_eval_complex.restype = i32
     L.shm_eval_angles.argtypes = [vp, i64, i32, i32, vp, vp]
     L.shm_eval_angles.restype = i32
+    L.shm_eval_angles_ex.argtypes = [vp, i64, i32, i32, u32, vp, vp]
+    L.shm_eval_angles_ex.restype = i32
+    L.shm_eval_host_ex.argtypes = [vp, i64, i32, i32, u32, vp, vp, sz, vp]
+    L.shm_eval_host_ex.restype = i32
+    L.shm_autotune_ex.argtypes = [i32, i32, u32, i64, ctypes.POINTER(ctypes.c_double)]
+    L.shm_autotune_ex.restype = i32
+    L.shm_eval_variant_ex.argtypes = [i32, i32, u32]
+    L.shm_eval_variant_ex.restype = ctypes.c_char_p
+    L.shm_eval_set_variant_ex.argtypes = [i32, i32, u32, i32]
+    L.shm_eval_set_variant_ex.restype = i32
+    L.shm_probe_fp64_rate.argtypes = [i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.shm_probe_fp64_rate.restype = i32
     L.shm_eval_spinor.argtypes = [vp, i64, i32, i32, u32, vp, vp]
     L.shm_eval_spinor.restype = i32
     L.shm_num_spinors.argtypes = [i32]
@@ -116,9 +129,14 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
 
 
-def eval_sh(points, lmax: int, out=None, normalized: bool = False, stream=None):
+def _flags(normalized: bool = False, strict: bool = False) -> int:
+    return (SHM_NORMALIZED_INPUT if normalized else 0) | (SHM_STRICT_FP64 if strict else 0)
+
+
+def eval_sh(points, lmax: int, out=None, normalized: bool = False, stream=None, strict: bool = False):
     """All R_l^m, l <= lmax, at device points [n, 3] (float32 or float64 CUDA
-    tensor) -> [n, (lmax+1)^2] of the same dtype, column k = l*l + l + m."""
+    tensor) -> [n, (lmax+1)^2] of the same dtype, column k = l*l + l + m.
+    strict: all-binary64 rows for float64 (SHM_STRICT_FP64)."""
     import torch
     if not (isinstance(points, torch.Tensor) and points.is_cuda):
         raise TypeError("points must be a CUDA tensor")
@@ -130,12 +148,12 @@ def eval_sh(points, lmax: int, out=None, normalized: bool = False, stream=None):
         out = torch.empty((n, num_harmonics(lmax)), dtype=points.dtype, device=points.device)
     elif out.dtype != points.dtype or not out.is_contiguous() or out.numel() != n * num_harmonics(lmax):
         raise ValueError("out must be contiguous, of the points dtype and [n, (lmax+1)^2]")
-    flags = SHM_NORMALIZED_INPUT if normalized else 0
-    check(lib().shm_eval_ex(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
+    check(lib().shm_eval_ex(points.data_ptr(), n, int(lmax), code, _flags(normalized, strict), out.data_ptr(),
+                            _stream_ptr(stream)))
     return out
 
 
-def eval_complex(points, lmax: int, out=None, normalized: bool = False, stream=None):
+def eval_complex(points, lmax: int, out=None, normalized: bool = False, stream=None, strict: bool = False):
     """Complex Y_l^m, l <= lmax, at device points [n, 3] -> complex CUDA tensor
     [n, (lmax+1)^2] (complex128 for float64 points, complex64 for float32)."""
     import torch
@@ -149,8 +167,8 @@ def eval_complex(points, lmax: int, out=None, normalized: bool = False, stream=N
         out = torch.empty((n, num_harmonics(lmax), 2), dtype=points.dtype, device=points.device)
     elif out.dtype != points.dtype or not out.is_contiguous() or out.numel() != 2 * n * num_harmonics(lmax):
         raise ValueError("out must be a contiguous [n, (lmax+1)^2, 2] tensor of the points dtype")
-    flags = SHM_NORMALIZED_INPUT if normalized else 0
-    check(lib().shm_eval_complex(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
+    check(lib().shm_eval_complex(points.data_ptr(), n, int(lmax), code, _flags(normalized, strict), out.data_ptr(),
+                                 _stream_ptr(stream)))
     return torch.view_as_complex(out.view(n, num_harmonics(lmax), 2))
 
 
@@ -162,7 +180,7 @@ def num_spinors(lmax: int) -> int:
     return n
 
 
-def eval_spinor(points, lmax: int, out=None, normalized: bool = False, stream=None):
+def eval_spinor(points, lmax: int, out=None, normalized: bool = False, stream=None, strict: bool = False):
     """Spin-1/2 spinor harmonics (Eq. 7) for l <= lmax at device points [n, 3]
     -> complex CUDA tensor [n, 2 (lmax+1)^2, 2]: spinor q (l ascending, j = l - 1/2
     before j = l + 1/2, m_j ascending), component (upper, lower)."""
@@ -178,12 +196,12 @@ def eval_spinor(points, lmax: int, out=None, normalized: bool = False, stream=No
         out = torch.empty((n, ns, 2, 2), dtype=points.dtype, device=points.device)
     elif out.dtype != points.dtype or not out.is_contiguous() or out.numel() != 4 * n * ns:
         raise ValueError("out must be a contiguous [n, 2 (lmax+1)^2, 2, 2] tensor of the points dtype")
-    flags = SHM_NORMALIZED_INPUT if normalized else 0
-    check(lib().shm_eval_spinor(points.data_ptr(), n, int(lmax), code, flags, out.data_ptr(), _stream_ptr(stream)))
+    check(lib().shm_eval_spinor(points.data_ptr(), n, int(lmax), code, _flags(normalized, strict), out.data_ptr(),
+                                _stream_ptr(stream)))
     return torch.view_as_complex(out.view(n, ns, 2, 2))
 
 
-def eval_angles(angles, lmax: int, out=None, stream=None):
+def eval_angles(angles, lmax: int, out=None, stream=None, strict: bool = False):
     """All R_l^m, l <= lmax, at directions given as a device tensor [n, 2] of
     (theta, phi) -> [n, (lmax+1)^2] of the same dtype."""
     import torch
@@ -194,24 +212,34 @@ def eval_angles(angles, lmax: int, out=None, stream=None):
     n = angles.shape[0]
     if out is None:
         out = torch.empty((n, num_harmonics(lmax)), dtype=angles.dtype, device=angles.device)
-    check(lib().shm_eval_angles(angles.data_ptr(), n, int(lmax), _dtype_code(angles.dtype), out.data_ptr(),
-                                _stream_ptr(stream)))
+    check(lib().shm_eval_angles_ex(angles.data_ptr(), n, int(lmax), _dtype_code(angles.dtype),
+                                   _flags(False, strict), out.data_ptr(), _stream_ptr(stream)))
     return out
 
 
-def autotune(lmax: int, dtype, n_probe: int = 1 << 20) -> float:
-    """Time every launch variant for (lmax, dtype); keep the fastest. Returns its ms."""
+def autotune(lmax: int, dtype, n_probe: int = 1 << 20, strict: bool = False) -> float:
+    """Time every launch variant for (lmax, dtype) (the all-binary64 ones only
+    with strict); keep the fastest. Returns its ms."""
     best = ctypes.c_double(0.0)
-    check(lib().shm_autotune(int(lmax), _dtype_code(dtype), int(n_probe), ctypes.byref(best)))
+    check(lib().shm_autotune_ex(int(lmax), _dtype_code(dtype), _flags(False, strict), int(n_probe),
+                                ctypes.byref(best)))
     return best.value
 
 
-def eval_variant(lmax: int, dtype) -> str:
-    return lib().shm_eval_variant(int(lmax), _dtype_code(dtype)).decode()
+def eval_variant(lmax: int, dtype, strict: bool = False) -> str:
+    return lib().shm_eval_variant_ex(int(lmax), _dtype_code(dtype), _flags(False, strict)).decode()
 
 
-def set_eval_variant(lmax: int, dtype, variant: int) -> None:
-    check(lib().shm_eval_set_variant(int(lmax), _dtype_code(dtype), int(variant)))
+def set_eval_variant(lmax: int, dtype, variant: int, strict: bool = False) -> None:
+    check(lib().shm_eval_set_variant_ex(int(lmax), _dtype_code(dtype), _flags(False, strict), int(variant)))
+
+
+def probe_fp64_rate(iters: int = 1 << 14):
+    """Measured FP64 pipe rate of the current device: (DFMA instructions per
+    second, ms of the timed launch)."""
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(lib().shm_probe_fp64_rate(int(iters), ctypes.byref(rate), ctypes.byref(ms)))
+    return rate.value, ms.value
 
 
 def eval_variant_count() -> int:
@@ -222,7 +250,7 @@ def eval_host_workspace_size(lmax: int, dtype, chunk_points: int) -> int:
     return int(lib().shm_eval_host_workspace_size(int(lmax), _dtype_code(dtype), int(chunk_points)))
 
 
-def eval_host(points_host, lmax: int, out_host, workspace, stream=None) -> None:
+def eval_host(points_host, lmax: int, out_host, workspace, stream=None, strict: bool = False) -> None:
     """shm_eval_host: host (ideally pinned) points -> host rows, through a device
     workspace.  Enqueued on `stream`; synchronise it before reading out_host.
     points_host / out_host are CPU torch tensors or numpy arrays."""
@@ -234,8 +262,9 @@ def eval_host(points_host, lmax: int, out_host, workspace, stream=None) -> None:
     dt = points_host.dtype
     code = _dtype_code(dt)
     n = points_host.shape[0]
-    check(lib().shm_eval_host(ptr(points_host), n, int(lmax), code, ptr(out_host), workspace.data_ptr(),
-                              workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
+    check(lib().shm_eval_host_ex(ptr(points_host), n, int(lmax), code, _flags(False, strict), ptr(out_host),
+                                 workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                 _stream_ptr(stream)))
 
 
 # --------------------------------------------------------------------------- projectors
@@ -326,6 +355,7 @@ def projectors_noalloc(dprob: DeviceProjectors, dtype, out, stream=None):
 # --------------------------------------------------------------------------- serving
 
 SHM_REQ_DISCARD = 0x1
+SHM_REQ_STRICT_FP64 = 0x2
 
 
 class ServeConfig(ctypes.Structure):
@@ -350,7 +380,9 @@ class ServeStats(ctypes.Structure):
                 ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("queued_now", ctypes.c_uint64),
                 ("active_now", ctypes.c_uint64), ("harmonics_done", ctypes.c_double), ("busy_ms", ctypes.c_double),
                 ("lat_p50_ms", ctypes.c_double), ("lat_p99_ms", ctypes.c_double), ("lat_max_ms", ctypes.c_double),
-                ("pool_bytes", ctypes.c_size_t), ("pool_in_use", ctypes.c_size_t), ("pool_peak", ctypes.c_size_t)]
+                ("pool_bytes", ctypes.c_size_t), ("pool_in_use", ctypes.c_size_t), ("pool_peak", ctypes.c_size_t),
+                ("collected", ctypes.c_uint64), ("client_lat_p50_ms", ctypes.c_double),
+                ("client_lat_p99_ms", ctypes.c_double), ("client_lat_max_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -361,6 +393,8 @@ _EXTRA_DECLS.extend([
     ("shm_serve_create", ([ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)], ctypes.c_int)),
     ("shm_serve_submit", ([_vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int)),
     ("shm_serve_wait", ([_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ServeResult)], ctypes.c_int)),
+    ("shm_serve_wait_any", ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ServeResult)],
+                            ctypes.c_int)),
     ("shm_serve_release", ([_vp, ctypes.c_uint64], ctypes.c_int)),
     ("shm_serve_stats_get", ([_vp, ctypes.POINTER(ServeStats)], ctypes.c_int)),
     ("shm_serve_stats_reset", ([_vp], ctypes.c_int)),
@@ -392,11 +426,13 @@ class Server:
         self.h = h
         self._keep = {}
 
-    def submit(self, n: int, lmax: int, dtype, seed: int = 0, points=None, discard: bool = False):
-        """Returns a ticket, or None when the server answered SHM_EBUSY."""
+    def submit(self, n: int, lmax: int, dtype, seed: int = 0, points=None, discard: bool = False,
+               strict: bool = False):
+        """Returns a ticket, or None when the server answered SHM_EBUSY.
+        strict: all-binary64 rows for a float64 request."""
         req = _Request(points=points.data_ptr() if points is not None else None, n=int(n), lmax=int(lmax),
                        dtype=_dtype_code(dtype), seed=int(seed) & 0xFFFFFFFFFFFFFFFF,
-                       flags=SHM_REQ_DISCARD if discard else 0)
+                       flags=(SHM_REQ_DISCARD if discard else 0) | (SHM_REQ_STRICT_FP64 if strict else 0))
         t = ctypes.c_uint64(0)
         st = lib().shm_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t))
         if st == 4:
@@ -410,6 +446,14 @@ class Server:
         r = ServeResult()
         check(lib().shm_serve_wait(self.h, int(ticket), int(timeout_ms), ctypes.byref(r)))
         return r
+
+    def wait_any(self, timeout_ms: int = -1):
+        """(status, ticket, result) of the oldest completed request no wait has
+        returned yet; status SHM_ETIMEOUT (5) when none completed in time."""
+        r = ServeResult()
+        t = ctypes.c_uint64(0)
+        st = lib().shm_serve_wait_any(self.h, int(timeout_ms), ctypes.byref(t), ctypes.byref(r))
+        return st, t.value, r
 
     def wait_status(self, ticket: int, timeout_ms: int = 0):
         r = ServeResult()

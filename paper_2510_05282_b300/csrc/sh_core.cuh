@@ -441,11 +441,13 @@ __device__ __forceinline__ void ff_sincos(double a, ff& s, ff& c) {
 // enter only through the products x, y and the float-float powers of x + iy,
 // where 48 bits suffice, so phi takes the float-float sine/cosine (FP32 pipe)
 // when |phi| <= 800 and the binary64 one otherwise (also for non-finite phi,
-// which then gives NaN components).
+// which then gives NaN components).  STRICT: binary64 sincos for phi too, and
+// x, y as binary64 products (for the all-binary64 rows).
+template <bool STRICT = false>
 __device__ __forceinline__ void angles_to_unit(double theta, double phi, double& xb, double& yb, double& zb) {
   double st, ct;
   sincos(theta, &st, &ct);
-  if (fabs(phi) <= 800.0) {
+  if (!STRICT && fabs(phi) <= 800.0) {
     ff sp, cp;
     ff_sincos(phi, sp, cp);
     const ff s = ff_from_double(st);

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased(const double* __
     if constexpr (IN == kInAngles) {
       if (valid) {  // Eq. 3-4 read backwards: the unit vector of (theta, phi)
         const int64_t p = p0 + threadIdx.x;
-        angles_to_unit(in[2 * p], in[2 * p + 1], xb, yb, zb);
+        angles_to_unit<!HYB>(in[2 * p], in[2 * p + 1], xb, yb, zb);
       }
     } else {
       double x = 0.0, y = 0.0, z = 1.0;

@@ -422,4 +422,153 @@ inline shm_status launch_phased_tma(const double* in, int64_t n, double* out, bo
   }
   return SHM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// All-binary64 rows with TMA stores (rows-tma-TPB, the SHM_STRICT_FP64 path).
+// sh_row<LMAX>(double...) produces a row in m-major order with few live
+// registers (~40), so a whole row is staged: the tile [TPB rows][L2 columns]
+// is held as column boxes of kBW = 10 columns (the last one narrower when L2
+// is not a multiple of 10), each box dense [TPB][width] in shared memory.  A
+// pitch of 10 doubles is 2 mod 4, so the 32 rows a warp writes at once are
+// 4-way bank-conflicted, the least an even pitch allows.  Once the tile is
+// complete one thread sends the boxes by cp.async.bulk.tensor; the next tile
+// waits for the TMA unit to have read the buffer only after its points' unit
+// vectors are formed, so the wait overlaps FP64 work.  These rows are bound
+// by the FP64 pipe (~242 FP64 instructions per point at l = 9, against 824
+// bytes of HBM traffic); the TMA store takes the copy-out loop and its
+// second barrier off the SM, so the FP64 pipe idles only at the barrier.
+// Odd lmax (the row pitch (lmax+1)^2 * 8 bytes must be a multiple of 16).
+template <int LMAX>
+struct RowsTmaPlan {
+  static constexpr int L2 = NH<LMAX>::value;
+  static constexpr int kBW = 10;
+  static constexpr int nfull = L2 / kBW;
+  static constexpr int rem = L2 - nfull * kBW;
+  static constexpr int nbox = nfull + (rem ? 1 : 0);
+  static constexpr bool feasible() { return L2 % 2 == 0; }
+  // box widths of the two tensor maps (the second unused when rem == 0)
+  static constexpr int width_a() { return nfull > 0 ? kBW : rem; }
+  static constexpr int width_b() { return rem > 0 ? rem : kBW; }
+  static constexpr size_t smem_bytes(int tpb) { return (size_t)tpb * L2 * 8 + 128; }
+};
+
+// Odd lmax up to SHM_LMAX_EXT (run-time mirror for the host's variant choice).
+inline bool rows_tma_feasible(int lmax) { return lmax >= 1 && lmax <= SHM_LMAX_EXT && (lmax & 1) == 1; }
+
+template <int LMAX, int TPB, int IN = kInPoints>
+__global__ void __launch_bounds__(TPB) k_eval_rows_tma(const double* __restrict__ in, int64_t n, int64_t ntiles,
+                                                       int normalized, const __grid_constant__ CUtensorMap map_a,
+                                                       const __grid_constant__ CUtensorMap map_b) {
+  using Plan = RowsTmaPlan<LMAX>;
+  static_assert(Plan::feasible(), "rows-tma needs an even row width (odd lmax)");
+  constexpr int BW = Plan::kBW;
+  extern __shared__ unsigned char smem_rt[];
+  double* tile = reinterpret_cast<double*>(smem_rt + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_rt) & 127u)) & 127u));
+  const int t = (int)threadIdx.x;
+  bool pending = false;  // a previous tile's boxes may still be read from the buffer
+  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    const int64_t p0 = tt * TPB;
+    const bool valid = (int64_t)t < n - p0;
+    double xb = 0.0, yb = 0.0, zb = 1.0;  // rows past n: a dummy direction (the TMA unit clips them)
+    bool origin = false;
+    if constexpr (IN == kInAngles) {
+      if (valid) angles_to_unit<true>(in[2 * (p0 + t)], in[2 * (p0 + t) + 1], xb, yb, zb);
+    } else {
+      double x = 0.0, y = 0.0, z = 1.0;
+      if (valid) {
+        x = in[3 * (p0 + t)];
+        y = in[3 * (p0 + t) + 1];
+        z = in[3 * (p0 + t) + 2];
+      }
+      origin = valid && is_origin(x, y, z);
+      if (valid && !origin) {
+        if (normalized) {
+          xb = x;
+          yb = y;
+          zb = z;
+        } else {
+          unit_dir(x, y, z, xb, yb, zb);
+        }
+      }
+    }
+    if (pending) {  // the buffer is reused: wait until the TMA unit has read the last tile
+      if (t == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      __syncthreads();
+    }
+    auto store = [&](int k, double v) {
+      const int b = k / BW;
+      const int w = b < Plan::nfull ? BW : Plan::rem;
+      tile[b * TPB * BW + t * w + (k - b * BW)] = v;
+    };
+    if (origin) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
+      store(0, kInvSqrt4Pi);
+#pragma unroll
+      for (int k = 1; k < Plan::L2; ++k) store(k, 0.0);
+    } else if (nonfinite3(xb, yb, zb)) {  // NaN in every value but the constant l = 0
+      store(0, kInvSqrt4Pi);
+#pragma unroll
+      for (int k = 1; k < Plan::L2; ++k) store(k, __longlong_as_double(0x7ff8000000000000ll));
+    } else {
+      sh_row<LMAX>(xb, yb, zb, store);
+    }
+    // the staged values (generic proxy) must be visible to the TMA unit (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+#pragma unroll
+      for (int b = 0; b < Plan::nbox; ++b) {
+        const CUtensorMap* m = b < Plan::nfull ? &map_a : &map_b;
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(tile + b * TPB * BW);
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                     :
+                     : "l"(reinterpret_cast<uint64_t>(m)), "r"(b * BW), "r"((int)p0), "r"(sa)
+                     : "memory");
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    pending = true;
+  }
+  // the last stores' global writes complete before the CTA retires
+  if (t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Host side: encodes the tensor maps of `out` and launches k_eval_rows_tma
+// (grid = SMs x resident CTAs, CTAs loop over tiles).  *launched = false with
+// SHM_OK when TMA does not apply (even lmax, output not 16-byte aligned,
+// n >= 2^31, or no driver entry point): the caller then runs a copy-out
+// kernel with the same rows.
+template <int LMAX, int TPB, int IN>
+inline shm_status launch_rows_tma(const double* in, int64_t n, double* out, bool normalized, cudaStream_t stream,
+                                  bool* launched) {
+  *launched = false;
+  if constexpr (RowsTmaPlan<LMAX>::feasible()) {
+    using Plan = RowsTmaPlan<LMAX>;
+    CUtensorMap ma, mb;
+    if (!encode_rows_map(&ma, out, n, Plan::L2, Plan::width_a(), TPB) ||
+        !encode_rows_map(&mb, out, n, Plan::L2, Plan::width_b(), TPB))
+      return SHM_OK;
+    constexpr int MAXDEV = 64;
+    static int blocks_per_sm[MAXDEV] = {0};
+    const int dev = current_device();
+    if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
+    auto kern = k_eval_rows_tma<LMAX, TPB, IN>;
+    const size_t smem = Plan::smem_bytes(TPB);
+    if (blocks_per_sm[dev] == 0) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_eval_rows_tma)");
+      int b = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TPB, smem);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_eval_rows_tma)");
+      blocks_per_sm[dev] = std::max(b, 1);
+    }
+    const int64_t ntiles = (n + TPB - 1) / TPB;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * blocks_per_sm[dev]);
+    kern<<<(unsigned)grid, TPB, smem, stream>>>(in, n, ntiles, normalized ? 1 : 0, ma, mb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "k_eval_rows_tma launch");
+    *launched = true;
+  }
+  return SHM_OK;
+}
+
 }  // namespace shm

@@ -1,5 +1,6 @@
 // Error reporting, pointer checks and device queries shared by libshm.
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -114,6 +115,34 @@ int current_device() {
     return 0;
   }
   return d;
+}
+
+// Allocation-failure injection: SHM_FAIL_ALLOC names the allocation sites
+// that fail ("serve_pool", "serve_pinned", "serve_batch", "autotune",
+// comma-separated, or "all"), read at every allocation.
+bool alloc_fail_injected(const char* site) {
+  const char* v = getenv("SHM_FAIL_ALLOC");
+  if (!v || !*v) return false;
+  const std::string list = std::string(",") + v + ",";
+  return list.find(",all,") != std::string::npos || list.find(std::string(",") + site + ",") != std::string::npos;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes, const char* site) {
+  *p = nullptr;
+  if (alloc_fail_injected(site)) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_malloc(void** p, size_t bytes, const char* site) {
+  *p = nullptr;
+  if (alloc_fail_injected(site)) return cudaErrorMemoryAllocation;
+  return cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+}
+
+shm_status fail_alloc(cudaError_t e, const char* site, const std::string& what) {
+  if (alloc_fail_injected(site)) return fail(SHM_ENOMEM, what + " (failure injected by SHM_FAIL_ALLOC)");
+  cudaGetLastError();
+  return fail(SHM_ENOMEM, what + ": " + cudaGetErrorString(e));
 }
 
 int sm_count(int dev) {

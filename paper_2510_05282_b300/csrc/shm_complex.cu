@@ -12,7 +12,8 @@
 // FP64 rows use the hybrid arithmetic in l-major order (binary64 for 1/r and
 // m = 0, 1, float-float for m >= 2), staged as real values one group of
 // l-shells at a time; the copy-out pairs them into (re, im) with a per-CTA map
-// and writes 16-byte complex values.  (Scattering the values into complex
+// and writes 16-byte complex values.  With SHM_STRICT_FP64 the FP64 rows are
+// the all-binary64 m-major rows (sh_row), staged whole and paired the same way.  (Scattering the values into complex
 // slots as they are produced raised the row code's register use from 96 to
 // 162 and cut the resident warps.)  FP32 rows use the FP32 row code, staged a
 // full row at a time in complex layout.
@@ -144,6 +145,51 @@ __global__ void __launch_bounds__(kCxTPB64, 5) k_eval_cx64(const double* __restr
   }
 }
 
+// All-binary64 complex rows (SHM_STRICT_FP64): the m-major real row of
+// sh_row<LMAX, CX> (scale constants divided by sqrt2 for m != 0), staged
+// whole with an odd row stride, then paired into (re, im) slots by the map.
+constexpr int kCxTPBs = 64;
+
+template <int LMAX>
+__global__ void __launch_bounds__(kCxTPBs) k_eval_cx64s(const double* __restrict__ pts, int64_t n,
+                                                       double* __restrict__ out, int64_t ntiles, int normalized,
+                                                       int vec) {
+  constexpr int L2 = NH<LMAX>::value;
+  constexpr int RS = L2 | 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t cxmap[L2];
+  double* tile = reinterpret_cast<double*>(smem_raw);
+  for (int k = threadIdx.x; k < L2; k += kCxTPBs) cxmap[k] = cx_map_entry(k);
+  __syncthreads();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * kCxTPBs;
+    const int rows = (int)min((int64_t)kCxTPBs, n - p0);
+    if ((int)threadIdx.x < rows) {
+      const int64_t p = p0 + threadIdx.x;
+      double* row = tile + threadIdx.x * RS;
+      sh_point<LMAX, false, true>(pts[3 * p], pts[3 * p + 1], pts[3 * p + 2], normalized != 0,
+                                  [&](int k, double v) { row[k] = v; });
+    }
+    __syncthreads();
+    const int nv = rows * L2;
+    double* o = out + 2 * p0 * L2;
+    for (int j = threadIdx.x; j < nv; j += kCxTPBs) {
+      const int r = j / L2, c = j - r * L2;
+      const uint32_t e = cxmap[c];
+      const double* src = tile + r * RS;
+      const double re = flip_if(src[e & 1023u], (e >> 30) & 1u);
+      const double im = (e & (1u << 29)) ? 0.0 : flip_if(src[(e >> 10) & 1023u], e >> 31);
+      if (vec) {
+        __stcs(reinterpret_cast<double2*>(o + 2 * j), make_double2(re, im));
+      } else {
+        __stcs(o + 2 * j, re);
+        __stcs(o + 2 * j + 1, im);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <int LMAX>
 __global__ void __launch_bounds__(kCxTPB32) k_eval_cx32(const float* __restrict__ pts, int64_t n,
                                                         float* __restrict__ out, int64_t ntiles, int normalized,
@@ -180,16 +226,21 @@ __global__ void __launch_bounds__(kCxTPB32) k_eval_cx32(const float* __restrict_
 }
 
 template <int LMAX>
-shm_status cx_launch(const void* pts, int64_t n, bool f64, void* out, bool normalized, bool vec, cudaStream_t s) {
+shm_status cx_launch(const void* pts, int64_t n, bool f64, void* out, bool normalized, bool vec, cudaStream_t s,
+                     bool strict) {
   constexpr int MAXDEV = 64;
-  static int bps[2][MAXDEV] = {};
+  static int bps[3][MAXDEV] = {};
   const int dev = current_device();
   if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
-  const int tpb = f64 ? kCxTPB64 : kCxTPB32;
-  const size_t smem = f64 ? (size_t)kCxTPB64 * (LPhases<LMAX, kCxPhase>::max_width() | 1) * 8
-                          : (size_t)kCxTPB32 * ((2 * NH<LMAX>::value) | 1) * 4;
-  const void* kern = f64 ? (const void*)k_eval_cx64<LMAX> : (const void*)k_eval_cx32<LMAX>;
-  int& b = bps[f64 ? 1 : 0][dev];
+  strict = strict && f64;
+  const int tpb = strict ? kCxTPBs : (f64 ? kCxTPB64 : kCxTPB32);
+  const size_t smem = strict ? (size_t)kCxTPBs * (NH<LMAX>::value | 1) * 8
+                      : f64  ? (size_t)kCxTPB64 * (LPhases<LMAX, kCxPhase>::max_width() | 1) * 8
+                             : (size_t)kCxTPB32 * ((2 * NH<LMAX>::value) | 1) * 4;
+  const void* kern = strict ? (const void*)k_eval_cx64s<LMAX>
+                     : f64  ? (const void*)k_eval_cx64<LMAX>
+                            : (const void*)k_eval_cx32<LMAX>;
+  int& b = bps[strict ? 2 : (f64 ? 1 : 0)][dev];
   if (b == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_eval_cx)");
@@ -200,7 +251,10 @@ shm_status cx_launch(const void* pts, int64_t n, bool f64, void* out, bool norma
   }
   const int64_t ntiles = (n + tpb - 1) / tpb;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * b);
-  if (f64)
+  if (strict)
+    k_eval_cx64s<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const double*)pts, n, (double*)out, ntiles, normalized,
+                                                          vec);
+  else if (f64)
     k_eval_cx64<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const double*)pts, n, (double*)out, ntiles, normalized, vec);
   else
     k_eval_cx32<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const float*)pts, n, (float*)out, ntiles, normalized, vec);
@@ -214,11 +268,12 @@ shm_status cx_launch(const void* pts, int64_t n, bool f64, void* out, bool norma
 extern "C" shm_status shm_eval_complex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
                                        void* out, void* stream) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_eval_complex");
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
   if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
   if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
-  if (flags & ~SHM_NORMALIZED_INPUT) return fail(SHM_EINVAL, "unknown flag bits");
+  if (flags & ~(SHM_NORMALIZED_INPUT | SHM_STRICT_FP64)) return fail(SHM_EINVAL, "unknown flag bits");
   if (n == 0) return SHM_OK;
   const size_t es = dtype == SHM_F64 ? 8 : 4;
   const int64_t L2 = (int64_t)(lmax + 1) * (lmax + 1);
@@ -232,36 +287,39 @@ extern "C" shm_status shm_eval_complex(const void* points, int64_t n, int lmax, 
   if (st != SHM_OK) return st;
   if ((st = check_device_range(out, out_bytes, "out")) != SHM_OK) return st;
   const bool f64 = dtype == SHM_F64, norm = (flags & SHM_NORMALIZED_INPUT) != 0, vec = aligned(out, 16);
+  const bool strict = (flags & SHM_STRICT_FP64) != 0;
   cudaStream_t s = (cudaStream_t)stream;
   switch (lmax) {
-    case 0: return cx_launch<0>(points, n, f64, out, norm, vec, s);
-    case 1: return cx_launch<1>(points, n, f64, out, norm, vec, s);
-    case 2: return cx_launch<2>(points, n, f64, out, norm, vec, s);
-    case 3: return cx_launch<3>(points, n, f64, out, norm, vec, s);
-    case 4: return cx_launch<4>(points, n, f64, out, norm, vec, s);
-    case 5: return cx_launch<5>(points, n, f64, out, norm, vec, s);
-    case 6: return cx_launch<6>(points, n, f64, out, norm, vec, s);
-    case 7: return cx_launch<7>(points, n, f64, out, norm, vec, s);
-    case 8: return cx_launch<8>(points, n, f64, out, norm, vec, s);
-    default: return cx_launch<9>(points, n, f64, out, norm, vec, s);
+    case 0: return cx_launch<0>(points, n, f64, out, norm, vec, s, strict);
+    case 1: return cx_launch<1>(points, n, f64, out, norm, vec, s, strict);
+    case 2: return cx_launch<2>(points, n, f64, out, norm, vec, s, strict);
+    case 3: return cx_launch<3>(points, n, f64, out, norm, vec, s, strict);
+    case 4: return cx_launch<4>(points, n, f64, out, norm, vec, s, strict);
+    case 5: return cx_launch<5>(points, n, f64, out, norm, vec, s, strict);
+    case 6: return cx_launch<6>(points, n, f64, out, norm, vec, s, strict);
+    case 7: return cx_launch<7>(points, n, f64, out, norm, vec, s, strict);
+    case 8: return cx_launch<8>(points, n, f64, out, norm, vec, s, strict);
+    default: return cx_launch<9>(points, n, f64, out, norm, vec, s, strict);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Angular interface: (theta, phi) per point (Sec. II Eq. 3-4 read backwards:
 // x/r = sin(theta) cos(phi), y/r = sin(theta) sin(phi), z/r = cos(theta)),
-// then the rows of shm_eval.  The sines and cosines are CUDA's sincos
-// (binary64 on the FP64 pipe for FP64 rows, sincosf for FP32).
+// then the rows of shm_eval.  FP64: CUDA's binary64 sincos of theta and the
+// float-float sine and cosine of phi (angles_to_unit), then the hybrid rows;
+// with SHM_STRICT_FP64 binary64 sincos of both angles and the all-binary64
+// rows (rows-tma-64, or the staged kernel below).  FP32: sincosf.
 
 namespace shm {
 
 constexpr int kAngTPB = 64;     // FP32 staged kernel
 constexpr int kAngTPB64 = 128;  // FP64 phased hybrid kernel
 
+// FP32, and FP64 with SHM_STRICT_FP64 where TMA does not apply.
 template <typename T, int LMAX>
 __global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ ang, int64_t n, T* __restrict__ out,
                                                           int64_t ntiles, int vec) {
-  static_assert(sizeof(T) == 4, "FP64 angles use k_eval_phased");
   constexpr int L2 = TileShape<LMAX>::L2;
   constexpr int RS = TileShape<LMAX>::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -271,13 +329,20 @@ __global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ a
     const int rows = (int)min((int64_t)kAngTPB, n - p0);
     if ((int)threadIdx.x < rows) {
       const int64_t p = p0 + threadIdx.x;
-      T st, ct, sp, cp;
-      sincosf(ang[2 * p], &st, &ct);
-      sincosf(ang[2 * p + 1], &sp, &cp);
+      T xb, yb, zb;
+      if constexpr (sizeof(T) == 8) {
+        angles_to_unit<true>(ang[2 * p], ang[2 * p + 1], xb, yb, zb);
+      } else {
+        T st, ct, sp, cp;
+        sincosf(ang[2 * p], &st, &ct);
+        sincosf(ang[2 * p + 1], &sp, &cp);
+        xb = st * cp;
+        yb = st * sp;
+        zb = ct;
+      }
       T* row = tile + threadIdx.x * RS;
-      const T xb = st * cp, yb = st * sp, zb = ct;
       if (nonfinite3(xb, yb, zb)) {  // a non-finite angle: NaN in every value but l = 0
-        for (int k = 0; k < L2; ++k) row[k] = k == 0 ? (T)kInvSqrt4Pi : __int_as_float(0x7fc00000);
+        for (int k = 0; k < L2; ++k) row[k] = k == 0 ? (T)kInvSqrt4Pi : (T)__longlong_as_double(0x7ff8000000000000ll);
       } else {
         sh_row<LMAX>(xb, yb, zb, [&](int k, T v) { row[k] = v; });
       }
@@ -292,68 +357,74 @@ __global__ void __launch_bounds__(kAngTPB) k_eval_angles(const T* __restrict__ a
 // stores (sh_tma.cuh) where they apply, else sh_phased.cuh; FP32 angles the
 // staged kernel above.
 template <typename T, int LMAX>
-shm_status ang_launch(const T* ang, int64_t n, T* out, bool vec, cudaStream_t s) {
+shm_status ang_launch(const T* ang, int64_t n, T* out, bool vec, cudaStream_t s, bool strict) {
+  strict = strict && sizeof(T) == 8;
   if constexpr (sizeof(T) == 8) {
     if (vec) {
       bool launched = false;
-      shm_status st = launch_phased_tma<LMAX, kAngTPB64, kInAngles>(ang, n, out, false, s, &launched);
+      shm_status st = strict ? launch_rows_tma<LMAX, 64, kInAngles>(ang, n, out, false, s, &launched)
+                             : launch_phased_tma<LMAX, kAngTPB64, kInAngles>(ang, n, out, false, s, &launched);
       if (st != SHM_OK || launched) return st;
     }
   }
   constexpr int MAXDEV = 64;
-  static int bps[MAXDEV] = {};
+  static int bps[2][MAXDEV] = {};
   const int dev = current_device();
   if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
-  constexpr int TPB = sizeof(T) == 8 ? kAngTPB64 : kAngTPB;
-  const size_t smem = sizeof(T) == 8 ? (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * 8
-                                     : (size_t)TPB * TileShape<LMAX>::RS * sizeof(T);
-  const void* kern = sizeof(T) == 8 ? (const void*)k_eval_phased<LMAX, kAngTPB64, true, kInAngles>
-                                    : (const void*)k_eval_angles<float, LMAX>;
-  if (bps[dev] == 0) {
+  const bool phased = sizeof(T) == 8 && !strict;  // the FP64 hybrid rows
+  const int TPB = phased ? kAngTPB64 : kAngTPB;
+  const size_t smem = phased ? (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * 8
+                             : (size_t)TPB * TileShape<LMAX>::RS * sizeof(T);
+  const void* kern = phased ? (const void*)k_eval_phased<LMAX, kAngTPB64, true, kInAngles>
+                            : (const void*)k_eval_angles<T, LMAX>;
+  int& bb = bps[phased ? 1 : 0][dev];
+  if (bb == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(angles)");
     int b = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TPB, smem);
     if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(angles)");
-    bps[dev] = std::max(b, 1);
+    bb = std::max(b, 1);
   }
   const int64_t ntiles = (n + TPB - 1) / TPB;
-  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * bps[dev]);
-  if constexpr (sizeof(T) == 8)
-    k_eval_phased<LMAX, kAngTPB64, true, kInAngles><<<(unsigned)grid, TPB, smem, s>>>(ang, n, out, ntiles, 0,
-                                                                                      vec ? 1 : 0);
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * bb);
+  if (phased)
+    k_eval_phased<LMAX, kAngTPB64, true, kInAngles><<<(unsigned)grid, TPB, smem, s>>>(
+        reinterpret_cast<const double*>(ang), n, reinterpret_cast<double*>(out), ntiles, 0, vec ? 1 : 0);
   else
-    k_eval_angles<float, LMAX><<<(unsigned)grid, TPB, smem, s>>>(ang, n, out, ntiles, vec ? 1 : 0);
+    k_eval_angles<T, LMAX><<<(unsigned)grid, TPB, smem, s>>>(ang, n, out, ntiles, vec ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "angles launch");
   return SHM_OK;
 }
 
 template <typename T>
-shm_status ang_dispatch(const T* ang, int64_t n, int lmax, T* out, bool vec, cudaStream_t s) {
+shm_status ang_dispatch(const T* ang, int64_t n, int lmax, T* out, bool vec, cudaStream_t s, bool strict) {
   switch (lmax) {
-    case 0: return ang_launch<T, 0>(ang, n, out, vec, s);
-    case 1: return ang_launch<T, 1>(ang, n, out, vec, s);
-    case 2: return ang_launch<T, 2>(ang, n, out, vec, s);
-    case 3: return ang_launch<T, 3>(ang, n, out, vec, s);
-    case 4: return ang_launch<T, 4>(ang, n, out, vec, s);
-    case 5: return ang_launch<T, 5>(ang, n, out, vec, s);
-    case 6: return ang_launch<T, 6>(ang, n, out, vec, s);
-    case 7: return ang_launch<T, 7>(ang, n, out, vec, s);
-    case 8: return ang_launch<T, 8>(ang, n, out, vec, s);
-    default: return ang_launch<T, 9>(ang, n, out, vec, s);
+    case 0: return ang_launch<T, 0>(ang, n, out, vec, s, strict);
+    case 1: return ang_launch<T, 1>(ang, n, out, vec, s, strict);
+    case 2: return ang_launch<T, 2>(ang, n, out, vec, s, strict);
+    case 3: return ang_launch<T, 3>(ang, n, out, vec, s, strict);
+    case 4: return ang_launch<T, 4>(ang, n, out, vec, s, strict);
+    case 5: return ang_launch<T, 5>(ang, n, out, vec, s, strict);
+    case 6: return ang_launch<T, 6>(ang, n, out, vec, s, strict);
+    case 7: return ang_launch<T, 7>(ang, n, out, vec, s, strict);
+    case 8: return ang_launch<T, 8>(ang, n, out, vec, s, strict);
+    default: return ang_launch<T, 9>(ang, n, out, vec, s, strict);
   }
 }
 
 }  // namespace shm
 
-extern "C" shm_status shm_eval_angles(const void* angles, int64_t n, int lmax, shm_dtype dtype, void* out,
-                                      void* stream) {
+extern "C" shm_status shm_eval_angles_ex(const void* angles, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
+                                         void* out, void* stream) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_eval_angles_ex");
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
   if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
   if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
+  if (flags & ~SHM_STRICT_FP64) return fail(SHM_EINVAL, "unknown flag bits");
   if (n == 0) return SHM_OK;
   const size_t es = dtype == SHM_F64 ? 8 : 4;
   const int64_t L2 = (int64_t)(lmax + 1) * (lmax + 1);
@@ -367,7 +438,13 @@ extern "C" shm_status shm_eval_angles(const void* angles, int64_t n, int lmax, s
   if (st != SHM_OK) return st;
   if ((st = check_device_range(out, out_bytes, "out")) != SHM_OK) return st;
   const bool vec = aligned(out, 16);
+  const bool strict = (flags & SHM_STRICT_FP64) != 0;
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == SHM_F64) return ang_dispatch<double>((const double*)angles, n, lmax, (double*)out, vec, s);
-  return ang_dispatch<float>((const float*)angles, n, lmax, (float*)out, vec, s);
+  if (dtype == SHM_F64) return ang_dispatch<double>((const double*)angles, n, lmax, (double*)out, vec, s, strict);
+  return ang_dispatch<float>((const float*)angles, n, lmax, (float*)out, vec, s, false);
+}
+
+extern "C" shm_status shm_eval_angles(const void* angles, int64_t n, int lmax, shm_dtype dtype, void* out,
+                                      void* stream) {
+  return shm_eval_angles_ex(angles, n, lmax, dtype, 0u, out, stream);
 }

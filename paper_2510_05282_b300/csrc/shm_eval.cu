@@ -69,9 +69,14 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
 
 // kPhased / kPhasedHybrid (FP64): k_eval_phased of sh_phased.cuh.
 // kPhasedHybridTma (FP64): k_eval_phased_tma of sh_tma.cuh (phased hybrid
-// rows leaving by TMA tensor stores).  For FP32 these variants are the
-// staged path.
-enum { kPhased = 2, kPhasedHybrid = 4, kPhasedHybridTma = 5, kPhasedHybridTma2 = 6 };
+// rows leaving by TMA tensor stores).  kRowsTma (FP64): k_eval_rows_tma of
+// sh_tma.cuh (all-binary64 rows, whole rows staged and sent by TMA tensor
+// stores).  For FP32 these variants are the staged path.
+enum { kPhased = 2, kPhasedHybrid = 4, kPhasedHybridTma = 5, kPhasedHybridTma2 = 6, kRowsTma = 7 };
+
+// Store paths whose FP64 rows are computed entirely in binary64 (sh_row,
+// sh_row_lmajor): the variants SHM_STRICT_FP64 may run.
+constexpr bool strict_path(int p) { return p == kStaged || p == kDirect || p == kPhased || p == kRowsTma; }
 
 // Launch variants the tuner chooses among (index = variant id).
 struct Variant {
@@ -80,7 +85,8 @@ struct Variant {
 constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},  {kDirect, 128},
                                  {kDirect, 256}, {kPhased, 64}, {kPhased, 128}, {kHybrid, 64},
                                  {kHybrid, 128}, {kHybrid, 256}, {kPhasedHybrid, 64}, {kPhasedHybrid, 128},
-                                 {kPhasedHybridTma, 128}, {kPhasedHybridTma2, 128}};
+                                 {kPhasedHybridTma, 128}, {kPhasedHybridTma2, 128}, {kRowsTma, 64},
+                                 {kRowsTma, 32}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // For FP32 the phased and hybrid variants run the staged-64 kernel (FP32 rows
@@ -92,6 +98,7 @@ inline size_t variant_smem(int v, int lmax, size_t es) {
   const int p = kVariants[v].path, tpb = kVariants[v].tpb;
   if (p == kDirect) return 0;
   if (p == kPhasedHybridTma2) return (size_t)2 * tpb * 20 * 8 + 128;
+  if (p == kRowsTma) return (size_t)tpb * L2 * 8 + 128;
   if (p == kPhased || p == kPhasedHybrid || p == kPhasedHybridTma) {
     int w = 0, mx = 0;  // LPhases<LMAX>::max_width()
     for (int l = 0; l <= lmax; ++l) {
@@ -115,8 +122,12 @@ constexpr size_t kMaxSmemPerCta = 232448;  // B300 opt-in limit per CTA
 inline int effective_variant(bool fp64, int v, int lmax = 0) {
   const int p = kVariants[v].path;
   if (!fp64) {
-    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid || p == kPhasedHybridTma || p == kPhasedHybridTma2) ? 1
-                                                                                                                : v;
+    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid || p == kPhasedHybridTma || p == kPhasedHybridTma2 ||
+         p == kRowsTma)
+            ? 1
+            : v;
+  } else if (p == kRowsTma && !rows_tma_feasible(lmax)) {
+    v = 1;  // staged-64: the same all-binary64 rows with the copy-out loop
   } else if (p == kPhasedHybridTma && !tma_plan_feasible(lmax)) {
     v = lmax > SHM_LMAX_CAP ? 6 : 11;
   } else if (p == kPhasedHybridTma2 && !(lmax == 3 || lmax == 5 || lmax == 7 || lmax == 9)) {
@@ -141,18 +152,30 @@ inline int effective_variant(bool fp64, int v, int lmax = 0) {
 // At l = 5 and 7 the double-buffered TMA form is faster (0.63 / 0.88 ms
 // against 0.64 / 0.93 ms on the 192^3 grid); at l = 9 its six phases cost
 // more in barriers than the waits they save (1.99 against 1.30 ms).
+// With SHM_STRICT_FP64 the FP64 rows are all-binary64: rows-tma-32 by
+// default (staged-64 at even lmax, where the row pitch rules TMA out);
+// measured on the 192^3 grid at l = 9: rows-tma-32 3.41 ms, rows-tma-64
+// 3.47, phased-64 3.48, staged-64 3.63, staged-128 4.08, direct-128 17.6.
 constexpr int kDefaultVariantF64 = 12;
 constexpr int kDefaultVariantF32 = 1;
-inline int default_variant(bool fp64, int lmax = 9) {
+constexpr int kDefaultVariantStrict = 15;
+inline int default_variant(bool fp64, int lmax = 9, bool strict = false) {
+  if (fp64 && strict) return kDefaultVariantStrict;
   return fp64 ? ((lmax == 5 || lmax == 7) ? 13 : kDefaultVariantF64) : kDefaultVariantF32;
 }
 
-// chosen[dtype][lmax] (-1 = default)
-int g_choice[2][SHM_LMAX_EXT + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
+// The choice table a call reads: 0 = FP32, 1 = FP64, 2 = FP64 with
+// SHM_STRICT_FP64 (strict is ignored for FP32).
+inline int choice_slot(bool fp64, bool strict) { return fp64 ? (strict ? 2 : 1) : 0; }
+
+// chosen[slot][lmax] (-1 = default)
+int g_choice[3][SHM_LMAX_EXT + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
+                                     {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
                                      {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
 
 template <typename T, int LMAX, int TPB, int PATH>
 size_t eval_smem_bytes() {
+  if (PATH == kRowsTma) return RowsTmaPlan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhasedHybridTma2) return Tma2Plan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhasedHybridTma) return TmaPlan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhased || PATH == kPhasedHybrid)
@@ -197,6 +220,17 @@ shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool 
     }
     return eval_launch_v<T, LMAX, TPB, kPhasedHybridTma>(pts, n, out, normalized, vec, stream);
   }
+  if constexpr (PATH == kRowsTma) {
+    if constexpr (sizeof(T) == 8) {
+      bool launched = false;
+      if (vec) {
+        shm_status st = launch_rows_tma<LMAX, TPB, kInPoints>(pts, n, out, normalized, stream, &launched);
+        if (st != SHM_OK || launched) return st;
+      }
+    }
+    // the same all-binary64 rows with the copy-out loop
+    return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, stream);
+  }
   const int dev = current_device();
   auto kern = pick_kernel<T, LMAX, TPB, PATH>();
   const size_t smem = eval_smem_bytes<T, LMAX, TPB, PATH>();
@@ -218,10 +252,11 @@ shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool 
 }
 
 template <typename T, int LMAX>
-shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t s, int variant) {
+shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t s, int variant,
+                       bool strict) {
   if (variant < 0) {
-    variant = g_choice[sizeof(T) == 8 ? 1 : 0][LMAX];
-    if (variant < 0) variant = default_variant(sizeof(T) == 8, LMAX);
+    variant = g_choice[choice_slot(sizeof(T) == 8, strict)][LMAX];
+    if (variant < 0) variant = default_variant(sizeof(T) == 8, LMAX, strict);
   }
   variant = effective_variant(sizeof(T) == 8, variant, LMAX);
   if constexpr (LMAX > SHM_LMAX_CAP) {
@@ -233,6 +268,8 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
       case 4: return eval_launch_v<T, LMAX, 256, kDirect>(pts, n, out, normalized, vec, s);
       case 5: return eval_launch_v<T, LMAX, 64, kPhased>(pts, n, out, normalized, vec, s);
       case 6: return eval_launch_v<T, LMAX, 128, kPhased>(pts, n, out, normalized, vec, s);
+      case 14: return eval_launch_v<T, LMAX, 64, kRowsTma>(pts, n, out, normalized, vec, s);
+      case 15: return eval_launch_v<T, LMAX, 32, kRowsTma>(pts, n, out, normalized, vec, s);
     }
     return fail(SHM_EINVAL, "unknown launch variant");
   }
@@ -251,31 +288,33 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
     case 11: return eval_launch_v<T, LMAX, 128, kPhasedHybrid>(pts, n, out, normalized, vec, s);
     case 12: return eval_launch_v<T, LMAX, 128, kPhasedHybridTma>(pts, n, out, normalized, vec, s);
     case 13: return eval_launch_v<T, LMAX, 128, kPhasedHybridTma2>(pts, n, out, normalized, vec, s);
+    case 14: return eval_launch_v<T, LMAX, 64, kRowsTma>(pts, n, out, normalized, vec, s);
+    case 15: return eval_launch_v<T, LMAX, 32, kRowsTma>(pts, n, out, normalized, vec, s);
   }
   return fail(SHM_EINVAL, "unknown launch variant");
 }
 
 template <typename T>
 shm_status eval_dispatch(const T* pts, int64_t n, int lmax, T* out, bool normalized, bool vec, cudaStream_t s,
-                         int variant = -1) {
+                         int variant = -1, bool strict = false) {
   switch (lmax) {
-    case 0: return eval_launch<T, 0>(pts, n, out, normalized, vec, s, variant);
-    case 1: return eval_launch<T, 1>(pts, n, out, normalized, vec, s, variant);
-    case 2: return eval_launch<T, 2>(pts, n, out, normalized, vec, s, variant);
-    case 3: return eval_launch<T, 3>(pts, n, out, normalized, vec, s, variant);
-    case 4: return eval_launch<T, 4>(pts, n, out, normalized, vec, s, variant);
-    case 5: return eval_launch<T, 5>(pts, n, out, normalized, vec, s, variant);
-    case 6: return eval_launch<T, 6>(pts, n, out, normalized, vec, s, variant);
-    case 7: return eval_launch<T, 7>(pts, n, out, normalized, vec, s, variant);
-    case 8: return eval_launch<T, 8>(pts, n, out, normalized, vec, s, variant);
-    case 9: return eval_launch<T, 9>(pts, n, out, normalized, vec, s, variant);
-    case 10: return eval_launch<T, 10>(pts, n, out, normalized, vec, s, variant);
-    case 11: return eval_launch<T, 11>(pts, n, out, normalized, vec, s, variant);
-    case 12: return eval_launch<T, 12>(pts, n, out, normalized, vec, s, variant);
-    case 13: return eval_launch<T, 13>(pts, n, out, normalized, vec, s, variant);
-    case 14: return eval_launch<T, 14>(pts, n, out, normalized, vec, s, variant);
-    case 15: return eval_launch<T, 15>(pts, n, out, normalized, vec, s, variant);
-    case 16: return eval_launch<T, 16>(pts, n, out, normalized, vec, s, variant);
+    case 0: return eval_launch<T, 0>(pts, n, out, normalized, vec, s, variant, strict);
+    case 1: return eval_launch<T, 1>(pts, n, out, normalized, vec, s, variant, strict);
+    case 2: return eval_launch<T, 2>(pts, n, out, normalized, vec, s, variant, strict);
+    case 3: return eval_launch<T, 3>(pts, n, out, normalized, vec, s, variant, strict);
+    case 4: return eval_launch<T, 4>(pts, n, out, normalized, vec, s, variant, strict);
+    case 5: return eval_launch<T, 5>(pts, n, out, normalized, vec, s, variant, strict);
+    case 6: return eval_launch<T, 6>(pts, n, out, normalized, vec, s, variant, strict);
+    case 7: return eval_launch<T, 7>(pts, n, out, normalized, vec, s, variant, strict);
+    case 8: return eval_launch<T, 8>(pts, n, out, normalized, vec, s, variant, strict);
+    case 9: return eval_launch<T, 9>(pts, n, out, normalized, vec, s, variant, strict);
+    case 10: return eval_launch<T, 10>(pts, n, out, normalized, vec, s, variant, strict);
+    case 11: return eval_launch<T, 11>(pts, n, out, normalized, vec, s, variant, strict);
+    case 12: return eval_launch<T, 12>(pts, n, out, normalized, vec, s, variant, strict);
+    case 13: return eval_launch<T, 13>(pts, n, out, normalized, vec, s, variant, strict);
+    case 14: return eval_launch<T, 14>(pts, n, out, normalized, vec, s, variant, strict);
+    case 15: return eval_launch<T, 15>(pts, n, out, normalized, vec, s, variant, strict);
+    case 16: return eval_launch<T, 16>(pts, n, out, normalized, vec, s, variant, strict);
   }
   return fail(SHM_EINVAL, "lmax must be in 0..16");
 }
@@ -287,11 +326,12 @@ void ensure_tune_cache();
 extern "C" shm_status shm_eval_ex(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
                                   void* out, void* stream) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_eval_ex");
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
   if (lmax < 0 || lmax > SHM_LMAX_EXT) return fail(SHM_EINVAL, "lmax must be in 0..16");
   if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
-  if (flags & ~SHM_NORMALIZED_INPUT) return fail(SHM_EINVAL, "unknown flag bits");
+  if (flags & ~(SHM_NORMALIZED_INPUT | SHM_STRICT_FP64)) return fail(SHM_EINVAL, "unknown flag bits");
   if (n == 0) return SHM_OK;
   const size_t es = dtype == SHM_F64 ? 8 : 4;
   const int64_t L2 = (int64_t)(lmax + 1) * (lmax + 1);
@@ -307,10 +347,11 @@ extern "C" shm_status shm_eval_ex(const void* points, int64_t n, int lmax, shm_d
   if (st != SHM_OK) return st;
   const bool vec = aligned(out, 16);
   const bool norm = (flags & SHM_NORMALIZED_INPUT) != 0;
+  const bool strict = (flags & SHM_STRICT_FP64) != 0;
   ensure_tune_cache();
   cudaStream_t s = (cudaStream_t)stream;
   if (dtype == SHM_F64)
-    return eval_dispatch<double>((const double*)points, n, lmax, (double*)out, norm, vec, s);
+    return eval_dispatch<double>((const double*)points, n, lmax, (double*)out, norm, vec, s, -1, strict);
   return eval_dispatch<float>((const float*)points, n, lmax, (float*)out, norm, vec, s);
 }
 
@@ -364,13 +405,17 @@ extern "C" size_t shm_eval_host_workspace_size(int lmax, shm_dtype dtype, int64_
   return 2 * (((size_t)chunk_points * 3 * es + 255) / 256 * 256 + ((size_t)chunk_points * per + 255) / 256 * 256);
 }
 
-extern "C" shm_status shm_eval_host(const void* points_host, int64_t n, int lmax, shm_dtype dtype, void* out_host,
-                                    void* workspace, size_t workspace_bytes, void* stream) {
+extern "C" shm_status shm_eval_host_ex(const void* points_host, int64_t n, int lmax, shm_dtype dtype,
+                                       unsigned flags, void* out_host, void* workspace, size_t workspace_bytes,
+                                       void* stream) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_eval_host_ex");
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
   if (lmax < 0 || lmax > SHM_LMAX_EXT) return fail(SHM_EINVAL, "lmax must be in 0..16");
   if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
+  if (flags & ~(SHM_NORMALIZED_INPUT | SHM_STRICT_FP64)) return fail(SHM_EINVAL, "unknown flag bits");
+  const bool norm = (flags & SHM_NORMALIZED_INPUT) != 0, strict = (flags & SHM_STRICT_FP64) != 0;
   if (n == 0) return SHM_OK;
   if (!points_host || !out_host) return fail(SHM_EINVAL, "points_host and out_host must be non-null");
   const size_t es = dtype == SHM_F64 ? 8 : 4;
@@ -404,8 +449,9 @@ extern "C" shm_status shm_eval_host(const void* points_host, int64_t n, int lmax
     e = cudaMemcpyAsync(bin[b], (const char*)points_host + (size_t)p0 * 3 * es, (size_t)m * 3 * es,
                         cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync H2D");
-    st = dtype == SHM_F64 ? eval_dispatch<double>((const double*)bin[b], m, lmax, (double*)bout[b], false, true, s)
-                          : eval_dispatch<float>((const float*)bin[b], m, lmax, (float*)bout[b], false, true, s);
+    st = dtype == SHM_F64
+             ? eval_dispatch<double>((const double*)bin[b], m, lmax, (double*)bout[b], norm, true, s, -1, strict)
+             : eval_dispatch<float>((const float*)bin[b], m, lmax, (float*)bout[b], norm, true, s);
     if (st != SHM_OK) return st;
     e = cudaMemcpyAsync((char*)out_host + (size_t)p0 * L2 * es, bout[b], (size_t)m * L2 * es, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync D2H");
@@ -417,6 +463,11 @@ extern "C" shm_status shm_eval_host(const void* points_host, int64_t n, int lmax
   return SHM_OK;
 }
 
+extern "C" shm_status shm_eval_host(const void* points_host, int64_t n, int lmax, shm_dtype dtype, void* out_host,
+                                    void* workspace, size_t workspace_bytes, void* stream) {
+  return shm_eval_host_ex(points_host, n, lmax, dtype, 0u, out_host, workspace, workspace_bytes, stream);
+}
+
 // ---------------------------------------------------------------------------
 // Autotuner.
 
@@ -426,7 +477,7 @@ namespace {
 const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64",  "staged-256", "direct-128", "direct-256",
                                            "phased-64",  "phased-128", "hybrid-64",  "hybrid-128", "hybrid-256",
                                            "phased-hybrid-64", "phased-hybrid-128", "phased-hybrid-tma-128",
-                                           "phased-hybrid-tma2-128"};
+                                           "phased-hybrid-tma2-128", "rows-tma-64", "rows-tma-32"};
 
 std::mutex g_tune_mu;
 bool g_cache_loaded = false;
@@ -438,9 +489,12 @@ void load_tune_cache_locked() {
   if (!path || !*path) return;
   FILE* f = fopen(path, "r");
   if (!f) return;
+  // lines "slot lmax variant": slot 0 = FP32, 1 = FP64, 2 = FP64 with SHM_STRICT_FP64
   int dt, l, v;
   while (fscanf(f, "%d %d %d", &dt, &l, &v) == 3)
-    if (dt >= 0 && dt <= 1 && l >= 0 && l <= SHM_LMAX_EXT && v >= 0 && v < kNumVariants) g_choice[dt][l] = v;
+    if (dt >= 0 && dt <= 2 && l >= 0 && l <= SHM_LMAX_EXT && v >= 0 && v < kNumVariants &&
+        (dt != 2 || strict_path(kVariants[v].path)))
+      g_choice[dt][l] = v;
   fclose(f);
 }
 
@@ -457,15 +511,15 @@ __global__ void k_probe_points(T* pts, int64_t n) {
 }
 
 template <typename T>
-shm_status autotune_t(int lmax, int64_t n, double* best_ms) {
+shm_status autotune_t(int lmax, int64_t n, double* best_ms, bool strict) {
   T *pts = nullptr, *out = nullptr;
   const size_t nh = (size_t)(lmax + 1) * (lmax + 1);
-  cudaError_t e = cudaMalloc(&pts, (size_t)n * 3 * sizeof(T));
-  if (e != cudaSuccess) return fail(SHM_ENOMEM, "autotune: cudaMalloc of probe points failed");
-  e = cudaMalloc(&out, (size_t)n * nh * sizeof(T));
+  cudaError_t e = dev_malloc((void**)&pts, (size_t)n * 3 * sizeof(T), "autotune");
+  if (e != cudaSuccess) return fail_alloc(e, "autotune", "autotune: cudaMalloc of probe points failed");
+  e = dev_malloc((void**)&out, (size_t)n * nh * sizeof(T), "autotune");
   if (e != cudaSuccess) {
     cudaFree(pts);
-    return fail(SHM_ENOMEM, "autotune: cudaMalloc of probe output failed");
+    return fail_alloc(e, "autotune", "autotune: cudaMalloc of probe output failed");
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -476,10 +530,11 @@ shm_status autotune_t(int lmax, int64_t n, double* best_ms) {
   shm_status st = SHM_OK;
   for (int v = 0; v < kNumVariants && st == SHM_OK; ++v) {
     if (effective_variant(sizeof(T) == 8, v, lmax) != v) continue;
+    if (strict && !strict_path(kVariants[v].path)) continue;
     float tv = 1e30f;
     for (int rep = 0; rep < 4 && st == SHM_OK; ++rep) {  // first repetition is a warm-up
       cudaEventRecord(e0, 0);
-      st = eval_dispatch<T>(pts, n, lmax, out, false, true, 0, v);
+      st = eval_dispatch<T>(pts, n, lmax, out, false, true, 0, v, strict);
       cudaEventRecord(e1, 0);
       if (st != SHM_OK) break;
       if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
@@ -500,13 +555,14 @@ shm_status autotune_t(int lmax, int64_t n, double* best_ms) {
   cudaFree(pts);
   cudaFree(out);
   if (st != SHM_OK) return st;
-  g_choice[sizeof(T) == 8 ? 1 : 0][lmax] = best;
+  const int slot = choice_slot(sizeof(T) == 8, strict);
+  g_choice[slot][lmax] = best;
   if (best_ms) *best_ms = best_t;
   const char* path = getenv("SHM_TUNE_CACHE");
   if (path && *path) {
     FILE* f = fopen(path, "a");
     if (f) {
-      fprintf(f, "%d %d %d\n", sizeof(T) == 8 ? 1 : 0, lmax, best);
+      fprintf(f, "%d %d %d\n", slot, lmax, best);
       fclose(f);
     }
   }
@@ -522,34 +578,54 @@ void ensure_tune_cache() {
 
 }  // namespace shm
 
-extern "C" shm_status shm_autotune(int lmax, shm_dtype dtype, int64_t n_probe, double* best_ms) {
+extern "C" shm_status shm_autotune_ex(int lmax, shm_dtype dtype, unsigned flags, int64_t n_probe, double* best_ms) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_autotune_ex");
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
   if (lmax < 0 || lmax > SHM_LMAX_EXT) return fail(SHM_EINVAL, "lmax must be in 0..16");
   if (n_probe <= 0 || n_probe > (int64_t)1 << 26) return fail(SHM_EINVAL, "n_probe must be in 1..2^26");
+  if (flags & ~SHM_STRICT_FP64) return fail(SHM_EINVAL, "unknown flag bits");
+  const bool strict = dtype == SHM_F64 && (flags & SHM_STRICT_FP64) != 0;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   load_tune_cache_locked();
-  return dtype == SHM_F64 ? autotune_t<double>(lmax, n_probe, best_ms) : autotune_t<float>(lmax, n_probe, best_ms);
+  return dtype == SHM_F64 ? autotune_t<double>(lmax, n_probe, best_ms, strict)
+                          : autotune_t<float>(lmax, n_probe, best_ms, false);
 }
 
-extern "C" const char* shm_eval_variant(int lmax, shm_dtype dtype) {
+extern "C" shm_status shm_autotune(int lmax, shm_dtype dtype, int64_t n_probe, double* best_ms) {
+  return shm_autotune_ex(lmax, dtype, 0u, n_probe, best_ms);
+}
+
+extern "C" const char* shm_eval_variant_ex(int lmax, shm_dtype dtype, unsigned flags) {
   using namespace shm;
   if (lmax < 0 || lmax > SHM_LMAX_EXT || (dtype != SHM_F32 && dtype != SHM_F64)) return "";
   ensure_tune_cache();
-  const int v = g_choice[dtype == SHM_F64 ? 1 : 0][lmax];
-  return kVariantNames[effective_variant(dtype == SHM_F64, v < 0 ? default_variant(dtype == SHM_F64, lmax) : v, lmax)];
+  const bool fp64 = dtype == SHM_F64, strict = fp64 && (flags & SHM_STRICT_FP64) != 0;
+  const int v = g_choice[choice_slot(fp64, strict)][lmax];
+  return kVariantNames[effective_variant(fp64, v < 0 ? default_variant(fp64, lmax, strict) : v, lmax)];
 }
+
+extern "C" const char* shm_eval_variant(int lmax, shm_dtype dtype) { return shm_eval_variant_ex(lmax, dtype, 0u); }
 
 extern "C" int shm_eval_variant_count(void) { return shm::kNumVariants; }
 
-extern "C" shm_status shm_eval_set_variant(int lmax, shm_dtype dtype, int variant) {
+extern "C" shm_status shm_eval_set_variant_ex(int lmax, shm_dtype dtype, unsigned flags, int variant) {
   using namespace shm;
   clear_error();
   if (lmax < 0 || lmax > SHM_LMAX_EXT || (dtype != SHM_F32 && dtype != SHM_F64))
     return fail(SHM_EINVAL, "bad lmax or dtype");
+  if (flags & ~SHM_STRICT_FP64) return fail(SHM_EINVAL, "unknown flag bits");
   if (variant < -1 || variant >= kNumVariants) return fail(SHM_EINVAL, "variant out of range");
+  const bool fp64 = dtype == SHM_F64, strict = fp64 && (flags & SHM_STRICT_FP64) != 0;
+  if (strict && variant >= 0 && !strict_path(kVariants[variant].path))
+    return fail(SHM_EINVAL, "variant computes part of its rows in float-float; SHM_STRICT_FP64 takes only "
+                            "all-binary64 variants");
   ensure_tune_cache();
-  g_choice[dtype == SHM_F64 ? 1 : 0][lmax] = variant;
+  g_choice[choice_slot(fp64, strict)][lmax] = variant;
   return SHM_OK;
+}
+
+extern "C" shm_status shm_eval_set_variant(int lmax, shm_dtype dtype, int variant) {
+  return shm_eval_set_variant_ex(lmax, dtype, 0u, variant);
 }

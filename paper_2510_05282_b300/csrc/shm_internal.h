@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -27,6 +28,27 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb);
 
 int current_device();
 int sm_count(int dev);
+
+// The library's own device and pinned allocations (serve pool and batch
+// descriptors, tuner probe buffers) go through these, so that a test can make
+// any of them fail without exhausting memory: the environment variable
+// SHM_FAIL_ALLOC lists the failing sites ("serve_pool", "serve_pinned",
+// "serve_batch", "autotune", comma-separated, or "all").  A failing site
+// returns cudaErrorMemoryAllocation without calling CUDA; fail_alloc turns
+// either kind of failure into SHM_ENOMEM with a message that says which.
+bool alloc_fail_injected(const char* site);
+cudaError_t dev_malloc(void** p, size_t bytes, const char* site);
+cudaError_t pinned_malloc(void** p, size_t bytes, const char* site);
+shm_status fail_alloc(cudaError_t e, const char* site, const std::string& what);
+
+// NVTX range around an entry point (header-only NVTX 3: inert unless a
+// profiler injects its library).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 

@@ -65,6 +65,49 @@ struct ProjWs {
 
 inline size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Host-side bounds that keep every size product below 2^63 (so no byte count
+// of the layout or of a range check can wrap): tables of at most 2^26 nodes
+// per function and 64 functions per species, so n_species x lstride x n_rad
+// x 32 bytes < 2^43; at most 2^40 points and 2^44 values.
+constexpr int32_t kProjMaxNRad = 1 << 26;
+constexpr int32_t kProjMaxLstride = 64;
+constexpr int64_t kProjMaxPoints = (int64_t)1 << 40;
+constexpr int64_t kProjMaxValues = (int64_t)1 << 44;
+
+// Validates the host-visible scalars and the host species table of a
+// problem without touching the device (no CUDA call); *max_lmax receives the
+// largest species lmax.  Every size the layout and the range checks multiply
+// is bounded here first.
+shm_status proj_validate(const shm_proj_problem* prob, shm_dtype dtype, int* max_lmax) {
+  if (!prob) return fail(SHM_EINVAL, "prob is null");
+  const shm_proj_problem& p = *prob;
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (p.n_atoms < 0 || p.n_points < 0 || p.n_values < 0) return fail(SHM_EINVAL, "negative size");
+  if (p.n_atoms > INT32_MAX) return fail(SHM_EINVAL, "n_atoms must be below 2^31");
+  if (p.n_points > kProjMaxPoints) return fail(SHM_EINVAL, "n_points must be at most 2^40");
+  if (p.n_values > kProjMaxValues) return fail(SHM_EINVAL, "n_values must be at most 2^44");
+  if (p.n_species < 1 || p.n_species > SHM_PROJ_MAX_SPECIES) return fail(SHM_EINVAL, "n_species must be 1..64");
+  if (!p.species_lmax) return fail(SHM_EINVAL, "species_lmax (host) is null");
+  if (p.n_rad < 4 || p.n_rad > kProjMaxNRad) return fail(SHM_EINVAL, "n_rad must be in 4..2^26");
+  if (p.ng < 1 || p.ng > 1290) return fail(SHM_EINVAL, "ng must be in 1..1290");
+  if (!(p.r_min > 0) || !(p.dlog > 0) || !(p.box > 0) || !(p.h > 0) || !std::isfinite(p.r_min) ||
+      !std::isfinite(p.dlog) || !std::isfinite(p.box) || !std::isfinite(p.h))
+    return fail(SHM_EINVAL, "r_min, dlog, box and h must be finite and > 0");
+  if (std::fabs(p.ng * p.h - p.box) > 1e-9 * p.box) return fail(SHM_EINVAL, "box must equal ng * h");
+  int ml = 0;
+  for (int s = 0; s < p.n_species; ++s) {
+    const int l = p.species_lmax[s];
+    if (l < 0 || l > SHM_LMAX_CAP) return fail(SHM_EINVAL, "species_lmax must be in 0..9");
+    ml = std::max(ml, l);
+  }
+  if (p.radial_lstride < ml + 1 || p.radial_lstride > kProjMaxLstride)
+    return fail(SHM_EINVAL, "radial_lstride must be in (1 + max species lmax)..64");
+  *max_lmax = ml;
+  return SHM_OK;
+}
+
+// Workspace layout of a problem that passed proj_validate (its products
+// cannot overflow).
 ProjWs proj_layout(const shm_proj_problem& p, shm_dtype dt) {
   ProjWs w;
   w.tiles = 256;
@@ -789,26 +832,10 @@ shm_status launch_proj(const ProjParams& P, int max_lmax, T* out, int64_t tile_u
 // parameters; the device-side arrays are validated by k_proj_setup.
 shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* workspace, size_t ws_bytes,
                         ProjParams* P, int* max_lmax, int64_t* tile_upper) {
-  if (!prob) return fail(SHM_EINVAL, "prob is null");
-  const shm_proj_problem& p = *prob;
-  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
-  if (p.n_atoms < 0 || p.n_points < 0 || p.n_values < 0) return fail(SHM_EINVAL, "negative size");
-  if (p.n_atoms > INT32_MAX) return fail(SHM_EINVAL, "n_atoms must be below 2^31");
-  if (p.n_species < 1 || p.n_species > SHM_PROJ_MAX_SPECIES) return fail(SHM_EINVAL, "n_species must be 1..64");
-  if (!p.species_lmax) return fail(SHM_EINVAL, "species_lmax (host) is null");
-  if (p.n_rad < 4) return fail(SHM_EINVAL, "n_rad must be >= 4");
-  if (p.ng < 1 || p.ng > 1290) return fail(SHM_EINVAL, "ng must be in 1..1290");
-  if (!(p.r_min > 0) || !(p.dlog > 0) || !(p.box > 0) || !(p.h > 0) || !std::isfinite(p.r_min) ||
-      !std::isfinite(p.dlog) || !std::isfinite(p.box) || !std::isfinite(p.h))
-    return fail(SHM_EINVAL, "r_min, dlog, box and h must be finite and > 0");
-  if (std::fabs(p.ng * p.h - p.box) > 1e-9 * p.box) return fail(SHM_EINVAL, "box must equal ng * h");
   int ml = 0;
-  for (int s = 0; s < p.n_species; ++s) {
-    const int l = p.species_lmax[s];
-    if (l < 0 || l > SHM_LMAX_CAP) return fail(SHM_EINVAL, "species_lmax must be in 0..9");
-    ml = std::max(ml, l);
-  }
-  if (p.radial_lstride < ml + 1) return fail(SHM_EINVAL, "radial_lstride < 1 + max species lmax");
+  shm_status vst = proj_validate(prob, dtype, &ml);
+  if (vst != SHM_OK) return vst;
+  const shm_proj_problem& p = *prob;
   const ProjWs w = proj_layout(p, dtype);
   if (!workspace) return fail(SHM_EINVAL, "workspace is null");
   if (ws_bytes < w.total) return fail(SHM_EINVAL, "workspace too small (see shm_projectors_workspace_size)");
@@ -872,14 +899,16 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
 }  // namespace shm
 
 extern "C" size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dtype) {
-  if (!prob || prob->n_atoms < 0 || prob->n_species < 1 || prob->n_rad < 1 || prob->radial_lstride < 1) return 0;
-  if (dtype != SHM_F32 && dtype != SHM_F64) return 0;
-  return shm::proj_layout(*prob, dtype).total;
+  using namespace shm;
+  int ml = 0;
+  if (proj_validate(prob, dtype, &ml) != SHM_OK) return 0;  // the reason is in shm_last_error()
+  return proj_layout(*prob, dtype).total;
 }
 
 extern "C" shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
                                      size_t workspace_bytes, void* stream) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_projectors");
   clear_error();
   ProjParams P;
   int max_lmax = 0;
@@ -949,12 +978,11 @@ shm_status noalloc_scratch(void** ptr) {
 extern "C" shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_dtype dtype, void* out,
                                               void* stream) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_projectors_noalloc");
   clear_error();
-  if (!prob) return fail(SHM_EINVAL, "prob is null");
-  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
-  if (prob->n_atoms < 0 || prob->n_species < 1 || prob->n_species > SHM_PROJ_MAX_SPECIES || prob->n_rad < 4 ||
-      prob->radial_lstride < 1)
-    return fail(SHM_EINVAL, "bad problem sizes");
+  int ml = 0;
+  shm_status vst = proj_validate(prob, dtype, &ml);  // the problem's fields first, then its scratch need
+  if (vst != SHM_OK) return vst;
   const size_t need = proj_layout(*prob, dtype).total;
   if (need > SHM_PROJ_NOALLOC_SCRATCH_BYTES)
     return fail(SHM_EINVAL, "problem needs " + std::to_string(need) + " bytes of scratch; the allocation-free "

@@ -10,9 +10,14 @@
 //     batch: a round robin over the admitted, unfinished requests taking at
 //     most chunk_points points from each and batch_points in total, so large
 //     requests progress in slices while newly admitted requests join at once;
-//     the chunk descriptors (FP64 chunks first, then FP32) go to the device
-//     with one copy from pinned memory, and one launch per dtype present
-//     (k_serve64, k_serve32) evaluates every tile of those chunks.
+//     the chunk descriptors (FP64 chunks first, then all-binary64 FP64
+//     chunks, then FP32) go to the device with one copy from pinned memory,
+//     and one launch per kind present (k_serve64, k_serve64s, k_serve32)
+//     evaluates every tile of those chunks.
+// Clients either wait for one ticket (shm_serve_wait) or collect requests in
+// completion order (shm_serve_wait_any); the first successful return of
+// either for a request records its client-side latency (submit -> the wait
+// returning), reported beside the scheduler's submit -> done latency.
 // The batch kernels evaluate each tile with the per-point code and tile
 // structure of shm_eval's default variant for the dtype (sh_phased.cuh,
 // sh_core.cuh, sh_tile.cuh), so a request's rows equal shm_eval's bit for
@@ -52,7 +57,7 @@ struct ServeChunk {
   int n;                    // points in the chunk
   int lmax;
   int dtype;                // SHM_F32 / SHM_F64
-  int pad;
+  int strict;               // 1: all-binary64 rows (SHM_REQ_STRICT_FP64)
 };
 
 // ---------------------------------------------------------------------------
@@ -143,8 +148,10 @@ void gen_point_host(unsigned long long seed, long long i, double* xyz) {
 
 constexpr int kServeTPB64 = 128;
 constexpr int kServeTPB32 = 64;
+constexpr int kServeTPB64s = 64;  // all-binary64 rows: the staged-64 tile of shm_eval
 constexpr int kServeRS64 = LPhases<SHM_LMAX_CAP>::max_width() | 1;  // staged doubles per row, any lmax
 constexpr size_t kServeSmem64 = (size_t)kServeTPB64 * kServeRS64 * 8;
+constexpr size_t kServeSmem64s = (size_t)kServeTPB64s * TileShape<SHM_LMAX_CAP>::RS * 8;
 constexpr size_t kServeSmem32 = (size_t)kServeTPB32 * TileShape<SHM_LMAX_CAP>::RS * 4;
 
 __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
@@ -186,6 +193,32 @@ __device__ __forceinline__ void serve_tile64(const ServeChunk& c, long long p, i
   if (valid && !origin) unit_dir(x, y, z, xb, yb, zb);
   double* dst = reinterpret_cast<double*>(c.out) + p * L2;
   phased_rows<LMAX, kServeTPB64, true>(xb, yb, zb, origin, rows, dst, aligned16(dst), tile);
+}
+
+// All-binary64 rows (SHM_REQ_STRICT_FP64): shm_eval's staged-64 tile (the
+// m-major rows of sh_row staged whole, coalesced copy-out), bitwise the rows
+// of shm_eval_ex with SHM_STRICT_FP64.
+template <int LMAX>
+__device__ __forceinline__ void serve_tile64s(const ServeChunk& c, long long p, int rows, double* tile) {
+  constexpr int L2 = TileShape<LMAX>::L2;
+  constexpr int RS = TileShape<LMAX>::RS;
+  if ((int)threadIdx.x < rows) {
+    const long long pi = p + threadIdx.x;
+    double x, y, z;
+    if (c.pts) {
+      const double* P = reinterpret_cast<const double*>(c.pts);
+      x = P[3 * pi];
+      y = P[3 * pi + 1];
+      z = P[3 * pi + 2];
+    } else {
+      gen_point_dev(c.seed, pi, x, y, z);
+    }
+    double* row = tile + threadIdx.x * RS;
+    sh_point<LMAX>(x, y, z, false, [&](int k, double v) { row[k] = v; });
+  }
+  __syncthreads();
+  double* dst = reinterpret_cast<double*>(c.out) + p * L2;
+  copy_out_tile<double, L2, RS, kServeTPB64s>(tile, rows, dst, aligned16(dst));
 }
 
 template <int LMAX>
@@ -237,6 +270,31 @@ __global__ void __launch_bounds__(kServeTPB64, 5) k_serve64(const ServeChunk* __
       default: serve_tile64<9>(c, p, rows, tile); break;
     }
     __syncthreads();  // c and the tile are free
+  }
+}
+
+__global__ void __launch_bounds__(kServeTPB64s) k_serve64s(const ServeChunk* __restrict__ chunks, int nchunks,
+                                                           long long ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* tile = reinterpret_cast<double*>(smem_raw);
+  __shared__ ServeChunk c;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    serve_find_chunk(chunks, nchunks, t, c);
+    const long long p = c.p0 + (t - c.tile0) * kServeTPB64s;
+    const int rows = (int)min((long long)kServeTPB64s, c.p0 + c.n - p);
+    switch (c.lmax) {
+      case 0: serve_tile64s<0>(c, p, rows, tile); break;
+      case 1: serve_tile64s<1>(c, p, rows, tile); break;
+      case 2: serve_tile64s<2>(c, p, rows, tile); break;
+      case 3: serve_tile64s<3>(c, p, rows, tile); break;
+      case 4: serve_tile64s<4>(c, p, rows, tile); break;
+      case 5: serve_tile64s<5>(c, p, rows, tile); break;
+      case 6: serve_tile64s<6>(c, p, rows, tile); break;
+      case 7: serve_tile64s<7>(c, p, rows, tile); break;
+      case 8: serve_tile64s<8>(c, p, rows, tile); break;
+      default: serve_tile64s<9>(c, p, rows, tile); break;
+    }
+    __syncthreads();
   }
 }
 
@@ -320,7 +378,8 @@ struct Request {
   void* out = nullptr;
   int64_t next_point = 0, done_points = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
-  bool failed = false;  // a batch holding part of it failed to launch or run
+  bool failed = false;     // a batch holding part of it failed to launch or run
+  bool collected = false;  // a wait has returned it (client latency recorded)
 };
 
 struct Batch {
@@ -357,9 +416,11 @@ struct shm_server {
   // stats
   uint64_t submitted = 0, rejected = 0, admitted = 0, completed = 0, nbatches = 0;
   double harmonics = 0, busy_ms = 0;
-  std::vector<double> lat;
+  std::vector<double> lat;         // submit -> the scheduler seeing the request done
+  std::vector<double> lat_client;  // submit -> a wait returning the request to the client
+  std::deque<uint64_t> done_q;     // completed, not yet collected (shm_serve_wait_any)
   std::string thread_error;
-  int grid64 = 0, grid32 = 0;  // resident CTAs of the two batch kernels on the device
+  int grid64 = 0, grid64s = 0, grid32 = 0;  // resident CTAs of the batch kernels on the device
 
   double now_ms() const { return std::chrono::duration<double, std::milli>(shm::Clock::now() - t0).count(); }
   void run();
@@ -409,6 +470,8 @@ bool shm_server::retire_locked() {
         if (R.r.flags & SHM_REQ_DISCARD) {
           alloc.release(R.pool_off, R.out_bytes);
           reqs.erase(it);
+        } else {
+          done_q.push_back(pr.first);
         }
       }
     }
@@ -448,6 +511,7 @@ bool shm_server::admit_locked() {
 
 bool shm_server::launch_locked() {
   if (active.empty()) return false;
+  shm::NvtxRange nvtx_range("shm_serve_batch");
   shm::Batch* b = nullptr;
   int inflight = 0;
   for (auto& x : batches) {
@@ -476,7 +540,7 @@ bool shm_server::launch_locked() {
       c.n = (int)take;
       c.lmax = R.r.lmax;
       c.dtype = (int)R.r.dtype;
-      c.pad = 0;
+      c.strict = (R.r.dtype == SHM_F64 && (R.r.flags & SHM_REQ_STRICT_FP64)) ? 1 : 0;
       picked.push_back(c);
       ++nch;
       R.next_point += take;
@@ -492,17 +556,26 @@ bool shm_server::launch_locked() {
                               [&](uint64_t t) { return reqs[t].next_point >= reqs[t].r.n; }),
                active.end());
   if (nch == 0) return false;
-  // FP64 chunks first, then FP32; tiles numbered per dtype in its kernel's tile size
-  int n64 = 0;
-  long long tiles64 = 0, tiles32 = 0;
+  // FP64 chunks first, then all-binary64 FP64 chunks, then FP32; tiles
+  // numbered per kind in its kernel's tile size
+  int k = 0;
+  long long tiles64 = 0, tiles64s = 0, tiles32 = 0;
   for (const auto& c : picked)
-    if (c.dtype == SHM_F64) {
-      b->host[n64] = c;
-      b->host[n64].tile0 = tiles64;
+    if (c.dtype == SHM_F64 && !c.strict) {
+      b->host[k] = c;
+      b->host[k].tile0 = tiles64;
       tiles64 += (c.n + shm::kServeTPB64 - 1) / shm::kServeTPB64;
-      ++n64;
+      ++k;
     }
-  int k = n64;
+  const int n64 = k;
+  for (const auto& c : picked)
+    if (c.dtype == SHM_F64 && c.strict) {
+      b->host[k] = c;
+      b->host[k].tile0 = tiles64s;
+      tiles64s += (c.n + shm::kServeTPB64s - 1) / shm::kServeTPB64s;
+      ++k;
+    }
+  const int n64s = k - n64;
   for (const auto& c : picked)
     if (c.dtype != SHM_F64) {
       b->host[k] = c;
@@ -510,7 +583,7 @@ bool shm_server::launch_locked() {
       tiles32 += (c.n + shm::kServeTPB32 - 1) / shm::kServeTPB32;
       ++k;
     }
-  const int n32 = k - n64;
+  const int n32 = k - n64 - n64s;
   cudaError_t e = cudaMemcpyAsync(b->dev, b->host, sizeof(shm::ServeChunk) * nch, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaEventRecord(b->start, stream);
   if (e == cudaSuccess && n64 > 0) {
@@ -518,9 +591,15 @@ bool shm_server::launch_locked() {
     shm::k_serve64<<<(unsigned)g, shm::kServeTPB64, shm::kServeSmem64, stream>>>(b->dev, n64, tiles64);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && n64s > 0) {
+    const long long g = std::max(1LL, std::min<long long>(tiles64s, grid64s));
+    shm::k_serve64s<<<(unsigned)g, shm::kServeTPB64s, shm::kServeSmem64s, stream>>>(b->dev + n64, n64s, tiles64s);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && n32 > 0) {
     const long long g = std::max(1LL, std::min<long long>(tiles32, grid32));
-    shm::k_serve32<<<(unsigned)g, shm::kServeTPB32, shm::kServeSmem32, stream>>>(b->dev + n64, n32, tiles32);
+    shm::k_serve32<<<(unsigned)g, shm::kServeTPB32, shm::kServeSmem32, stream>>>(b->dev + n64 + n64s, n32,
+                                                                                 tiles32);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(b->end, stream);
@@ -560,6 +639,7 @@ extern "C" void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3
 
 extern "C" shm_status shm_serve_create(const shm_serve_config* cfg, shm_server** server) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_serve_create");
   clear_error();
   if (!cfg || !server) return fail(SHM_EINVAL, "null argument");
   if (cfg->pool_bytes < 256 || cfg->max_slots < 1 || cfg->queue_capacity < 1 || cfg->batch_points < 1 ||
@@ -590,31 +670,35 @@ extern "C" shm_status shm_serve_create(const shm_serve_config* cfg, shm_server**
   };
   if ((e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking)) != cudaSuccess)
     return cleanup(fail_cuda(e, "cudaStreamCreateWithFlags"));
-  if ((e = cudaMalloc(&S->pool, cfg->pool_bytes)) != cudaSuccess) {
-    cudaGetLastError();
-    return cleanup(fail(SHM_ENOMEM, "cannot allocate the serve pool of " + std::to_string(cfg->pool_bytes) + " bytes"));
-  }
+  if ((e = dev_malloc((void**)&S->pool, cfg->pool_bytes, "serve_pool")) != cudaSuccess)
+    return cleanup(fail_alloc(e, "serve_pool",
+                              "cannot allocate the serve pool of " + std::to_string(cfg->pool_bytes) + " bytes"));
   S->alloc.init(cfg->pool_bytes);
   S->batches.resize(cfg->inflight_batches);
   for (auto& b : S->batches) {
     if ((e = cudaEventCreate(&b.start)) != cudaSuccess || (e = cudaEventCreate(&b.end)) != cudaSuccess)
       return cleanup(fail_cuda(e, "cudaEventCreate"));
-    if ((e = cudaHostAlloc(&b.host, sizeof(ServeChunk) * kMaxChunksPerBatch, cudaHostAllocDefault)) != cudaSuccess)
-      return cleanup(fail(SHM_ENOMEM, "cudaHostAlloc for batch descriptors failed"));
-    if ((e = cudaMalloc(&b.dev, sizeof(ServeChunk) * kMaxChunksPerBatch)) != cudaSuccess)
-      return cleanup(fail(SHM_ENOMEM, "cudaMalloc for batch descriptors failed"));
+    if ((e = pinned_malloc((void**)&b.host, sizeof(ServeChunk) * kMaxChunksPerBatch, "serve_pinned")) != cudaSuccess)
+      return cleanup(fail_alloc(e, "serve_pinned", "pinned batch descriptors"));
+    if ((e = dev_malloc((void**)&b.dev, sizeof(ServeChunk) * kMaxChunksPerBatch, "serve_batch")) != cudaSuccess)
+      return cleanup(fail_alloc(e, "serve_batch", "device batch descriptors"));
   }
   if ((e = cudaFuncSetAttribute(k_serve64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kServeSmem64)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_serve64s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kServeSmem64s)) !=
           cudaSuccess ||
       (e = cudaFuncSetAttribute(k_serve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kServeSmem32)) !=
           cudaSuccess)
     return cleanup(fail_cuda(e, "cudaFuncSetAttribute(k_serve)"));
-  int b64 = 0, b32 = 0;
+  int b64 = 0, b64s = 0, b32 = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_serve64, kServeTPB64, kServeSmem64)) !=
+          cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64s, k_serve64s, kServeTPB64s, kServeSmem64s)) !=
           cudaSuccess ||
       (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_serve32, kServeTPB32, kServeSmem32)) != cudaSuccess)
     return cleanup(fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_serve)"));
   S->grid64 = sm_count(S->device) * std::max(b64, 1);
+  S->grid64s = sm_count(S->device) * std::max(b64s, 1);
   S->grid32 = sm_count(S->device) * std::max(b32, 1);
   S->t0 = Clock::now();
   cudaSetDevice(prev);
@@ -625,12 +709,13 @@ extern "C" shm_status shm_serve_create(const shm_serve_config* cfg, shm_server**
 
 extern "C" shm_status shm_serve_submit(shm_server* S, const shm_request* req, uint64_t* ticket) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_serve_submit");
   clear_error();
   if (!S || !req || !ticket) return fail(SHM_EINVAL, "null argument");
   if (req->n < 1) return fail(SHM_EINVAL, "n must be >= 1");
   if (req->lmax < 0 || req->lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
   if (req->dtype != SHM_F32 && req->dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
-  if (req->flags & ~SHM_REQ_DISCARD) return fail(SHM_EINVAL, "unknown request flags");
+  if (req->flags & ~(SHM_REQ_DISCARD | SHM_REQ_STRICT_FP64)) return fail(SHM_EINVAL, "unknown request flags");
   Request R;
   R.r = *req;
   R.es = req->dtype == SHM_F64 ? 8 : 4;
@@ -675,8 +760,17 @@ static void fill_result(const shm::Request& R, shm_result* res) {
   res->t_done_ms = R.t_done;
 }
 
+// Records the client-side latency of a completed request the first time a
+// wait returns it (caller holds S->mu).
+static void collect_locked(shm_server* S, shm::Request& R) {
+  if (R.collected) return;
+  R.collected = true;
+  S->lat_client.push_back(S->now_ms() - R.t_submit);
+}
+
 extern "C" shm_status shm_serve_wait(shm_server* S, uint64_t ticket, int timeout_ms, shm_result* res) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_serve_wait");
   clear_error();
   if (!S || !res) return fail(SHM_EINVAL, "null argument");
   std::unique_lock<std::mutex> lk(S->mu);
@@ -692,12 +786,45 @@ extern "C" shm_status shm_serve_wait(shm_server* S, uint64_t ticket, int timeout
   if (it == S->reqs.end()) return fail(SHM_ENOTFOUND, "unknown or released ticket");
   fill_result(it->second, res);
   if (it->second.state != kDone) return fail(SHM_ETIMEOUT, "request not complete");
+  collect_locked(S, it->second);
   if (it->second.failed) return fail(SHM_ECUDA, "a batch holding this request failed: " + S->thread_error);
+  return SHM_OK;
+}
+
+extern "C" shm_status shm_serve_wait_any(shm_server* S, int timeout_ms, uint64_t* ticket, shm_result* res) {
+  using namespace shm;
+  NvtxRange nvtx_range("shm_serve_wait_any");
+  clear_error();
+  if (!S || !ticket || !res) return fail(SHM_EINVAL, "null argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  // the oldest completed request no wait has returned yet (released or
+  // already collected tickets are skipped)
+  auto next = [&]() -> shm::Request* {
+    while (!S->done_q.empty()) {
+      auto it = S->reqs.find(S->done_q.front());
+      if (it != S->reqs.end() && !it->second.collected) return &it->second;
+      S->done_q.pop_front();
+    }
+    return nullptr;
+  };
+  auto ready = [&] { return next() != nullptr; };
+  if (timeout_ms < 0)
+    S->cv_done.wait(lk, ready);
+  else
+    S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+  shm::Request* R = next();
+  if (!R) return fail(SHM_ETIMEOUT, "no request completed in time");
+  *ticket = S->done_q.front();
+  S->done_q.pop_front();
+  fill_result(*R, res);
+  collect_locked(S, *R);
+  if (R->failed) return fail(SHM_ECUDA, "a batch holding this request failed: " + S->thread_error);
   return SHM_OK;
 }
 
 extern "C" shm_status shm_serve_release(shm_server* S, uint64_t ticket) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_serve_release");
   clear_error();
   if (!S) return fail(SHM_EINVAL, "null server");
   std::lock_guard<std::mutex> lk(S->mu);
@@ -714,7 +841,7 @@ extern "C" shm_status shm_serve_stats_get(shm_server* S, shm_serve_stats* st) {
   using namespace shm;
   clear_error();
   if (!S || !st) return fail(SHM_EINVAL, "null argument");
-  std::vector<double> lat;
+  std::vector<double> lat, latc;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     st->submitted = S->submitted;
@@ -730,17 +857,22 @@ extern "C" shm_status shm_serve_stats_get(shm_server* S, shm_serve_stats* st) {
     st->pool_in_use = S->alloc.in_use;
     st->pool_peak = S->alloc.peak;
     lat = S->lat;
+    latc = S->lat_client;
     if (!S->thread_error.empty()) return fail(SHM_ECUDA, S->thread_error);
   }
-  auto pct = [&](double q) {
-    if (lat.empty()) return 0.0;
-    const size_t k = std::min(lat.size() - 1, (size_t)(q * (double)(lat.size() - 1) + 0.5));
-    std::nth_element(lat.begin(), lat.begin() + k, lat.end());
-    return lat[k];
+  auto pct = [](std::vector<double>& v, double q) {
+    if (v.empty()) return 0.0;
+    const size_t k = std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5));
+    std::nth_element(v.begin(), v.begin() + k, v.end());
+    return v[k];
   };
-  st->lat_p50_ms = pct(0.50);
-  st->lat_p99_ms = pct(0.99);
+  st->lat_p50_ms = pct(lat, 0.50);
+  st->lat_p99_ms = pct(lat, 0.99);
   st->lat_max_ms = lat.empty() ? 0.0 : *std::max_element(lat.begin(), lat.end());
+  st->collected = latc.size();
+  st->client_lat_p50_ms = pct(latc, 0.50);
+  st->client_lat_p99_ms = pct(latc, 0.99);
+  st->client_lat_max_ms = latc.empty() ? 0.0 : *std::max_element(latc.begin(), latc.end());
   return SHM_OK;
 }
 
@@ -752,12 +884,14 @@ extern "C" shm_status shm_serve_stats_reset(shm_server* S) {
   S->submitted = S->rejected = S->admitted = S->completed = S->nbatches = 0;
   S->harmonics = S->busy_ms = 0;
   S->lat.clear();
+  S->lat_client.clear();
   S->alloc.peak = S->alloc.in_use;
   return SHM_OK;
 }
 
 extern "C" shm_status shm_serve_destroy(shm_server* S) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_serve_destroy");
   clear_error();
   if (!S) return fail(SHM_EINVAL, "null server");
   {

@@ -11,6 +11,9 @@
 // products are split between the FP64 pipe (real parts) and float-float
 // arithmetic on the FP32 pipe (imaginary parts): 800 binary64 products per
 // point at l = 9 would make the kernel FP64-bound well above its HBM time.
+// With SHM_STRICT_FP64 (k_eval_spinor64s) the rows are the all-binary64
+// m-major rows, staged whole, and both parts are binary64 products: the
+// arithmetic of the definition, FP64-pipe bound.
 // Output [n][2 (lmax+1)^2 spinors][upper, lower][re, im].
 #include <cuda_runtime.h>
 
@@ -238,6 +241,53 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_spinor64(const double* 
   }
 }
 
+// All-binary64 spinors (SHM_STRICT_FP64): real rows of sh_row<LMAX>, staged
+// whole with an odd row stride; every component part is one binary64
+// product coefficient x real value.
+constexpr int kSpTPBs = 64;
+
+template <int LMAX>
+__global__ void __launch_bounds__(kSpTPBs) k_eval_spinor64s(const double* __restrict__ pts, int64_t n,
+                                                           double* __restrict__ out, int64_t ntiles, int normalized,
+                                                           int vec) {
+  constexpr int L2 = NH<LMAX>::value;
+  constexpr int NC = 4 * L2;
+  constexpr int RS = L2 | 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t midx[NC];
+  __shared__ double2 mcoef[NC];
+  double* tile = reinterpret_cast<double*>(smem_raw);
+  for (int q = threadIdx.x; q < NC; q += kSpTPBs) {
+    const SpinorTerm t = spinor_term(q);
+    midx[q] = spinor_idx(t);
+    mcoef[q] = make_double2(t.cre, t.cim);
+  }
+  __syncthreads();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t p0 = t * kSpTPBs;
+    const int rows = (int)min((int64_t)kSpTPBs, n - p0);
+    if ((int)threadIdx.x < rows) {
+      const int64_t p = p0 + threadIdx.x;
+      double* row = tile + threadIdx.x * RS;
+      sh_point<LMAX>(pts[3 * p], pts[3 * p + 1], pts[3 * p + 2], normalized != 0,
+                     [&](int k, double v) { row[k] = v; });
+    }
+    __syncthreads();
+    const int nv = rows * NC;
+    double* dst = out + p0 * 2 * NC;
+    for (int j = threadIdx.x; j < nv; j += kSpTPBs) {
+      const int r = j / NC, q = j - r * NC;
+      const uint32_t e = midx[q];
+      const double2 cf = mcoef[q];
+      const double* src = tile + r * RS;
+      const double re = cf.x * src[e & 0x7fffu];
+      const double im = (e >> 31) ? 0.0 : cf.y * src[(e >> 16) & 0x7fffu];
+      st_out(dst + 2 * (int64_t)j, re, im, vec != 0);
+    }
+    __syncthreads();
+  }
+}
+
 // FP32 rows: the FP32 row code, staged a full row at a time.
 template <int LMAX>
 __global__ void __launch_bounds__(kSpTPB32) k_eval_spinor32(const float* __restrict__ pts, int64_t n,
@@ -283,16 +333,20 @@ __global__ void __launch_bounds__(kSpTPB32) k_eval_spinor32(const float* __restr
 
 template <int LMAX>
 shm_status spinor_launch(const void* pts, int64_t n, bool f64, void* out, bool normalized, bool vec,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool strict) {
   constexpr int MAXDEV = 64;
-  static int bps[2][MAXDEV] = {};
+  static int bps[3][MAXDEV] = {};
   const int dev = current_device();
   if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
-  const int tpb = f64 ? kSpTPB64 : kSpTPB32;
-  const size_t smem = f64 ? (size_t)kSpTPB64 * (LPhases<LMAX, kSpPhase>::max_width() | 1) * 8
-                          : (size_t)kSpTPB32 * TileShape<LMAX>::RS * 4;
-  const void* kern = f64 ? (const void*)k_eval_spinor64<LMAX> : (const void*)k_eval_spinor32<LMAX>;
-  int& b = bps[f64 ? 1 : 0][dev];
+  strict = strict && f64;
+  const int tpb = strict ? kSpTPBs : (f64 ? kSpTPB64 : kSpTPB32);
+  const size_t smem = strict ? (size_t)kSpTPBs * (NH<LMAX>::value | 1) * 8
+                      : f64  ? (size_t)kSpTPB64 * (LPhases<LMAX, kSpPhase>::max_width() | 1) * 8
+                             : (size_t)kSpTPB32 * TileShape<LMAX>::RS * 4;
+  const void* kern = strict ? (const void*)k_eval_spinor64s<LMAX>
+                     : f64  ? (const void*)k_eval_spinor64<LMAX>
+                            : (const void*)k_eval_spinor32<LMAX>;
+  int& b = bps[strict ? 2 : (f64 ? 1 : 0)][dev];
   if (b == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_eval_spinor)");
@@ -303,7 +357,10 @@ shm_status spinor_launch(const void* pts, int64_t n, bool f64, void* out, bool n
   }
   const int64_t ntiles = (n + tpb - 1) / tpb;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * b);
-  if (f64)
+  if (strict)
+    k_eval_spinor64s<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const double*)pts, n, (double*)out, ntiles,
+                                                              normalized, vec);
+  else if (f64)
     k_eval_spinor64<LMAX><<<(unsigned)grid, tpb, smem, s>>>((const double*)pts, n, (double*)out, ntiles,
                                                              normalized, vec);
   else
@@ -323,11 +380,12 @@ extern "C" int shm_num_spinors(int lmax) {
 extern "C" shm_status shm_eval_spinor(const void* points, int64_t n, int lmax, shm_dtype dtype, unsigned flags,
                                       void* out, void* stream) {
   using namespace shm;
+  NvtxRange nvtx_range("shm_eval_spinor");
   clear_error();
   if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
   if (lmax < 0 || lmax > SHM_LMAX_CAP) return fail(SHM_EINVAL, "lmax must be in 0..9");
   if (n < 0) return fail(SHM_EINVAL, "n must be >= 0");
-  if (flags & ~SHM_NORMALIZED_INPUT) return fail(SHM_EINVAL, "unknown flag bits");
+  if (flags & ~(SHM_NORMALIZED_INPUT | SHM_STRICT_FP64)) return fail(SHM_EINVAL, "unknown flag bits");
   if (n == 0) return SHM_OK;
   const size_t es = dtype == SHM_F64 ? 8 : 4;
   const int64_t L2 = (int64_t)(lmax + 1) * (lmax + 1);
@@ -341,17 +399,18 @@ extern "C" shm_status shm_eval_spinor(const void* points, int64_t n, int lmax, s
   if (st != SHM_OK) return st;
   if ((st = check_device_range(out, out_bytes, "out")) != SHM_OK) return st;
   const bool f64 = dtype == SHM_F64, norm = (flags & SHM_NORMALIZED_INPUT) != 0, vec = aligned(out, 2 * es);
+  const bool strict = (flags & SHM_STRICT_FP64) != 0;
   cudaStream_t s = (cudaStream_t)stream;
   switch (lmax) {
-    case 0: return spinor_launch<0>(points, n, f64, out, norm, vec, s);
-    case 1: return spinor_launch<1>(points, n, f64, out, norm, vec, s);
-    case 2: return spinor_launch<2>(points, n, f64, out, norm, vec, s);
-    case 3: return spinor_launch<3>(points, n, f64, out, norm, vec, s);
-    case 4: return spinor_launch<4>(points, n, f64, out, norm, vec, s);
-    case 5: return spinor_launch<5>(points, n, f64, out, norm, vec, s);
-    case 6: return spinor_launch<6>(points, n, f64, out, norm, vec, s);
-    case 7: return spinor_launch<7>(points, n, f64, out, norm, vec, s);
-    case 8: return spinor_launch<8>(points, n, f64, out, norm, vec, s);
-    default: return spinor_launch<9>(points, n, f64, out, norm, vec, s);
+    case 0: return spinor_launch<0>(points, n, f64, out, norm, vec, s, strict);
+    case 1: return spinor_launch<1>(points, n, f64, out, norm, vec, s, strict);
+    case 2: return spinor_launch<2>(points, n, f64, out, norm, vec, s, strict);
+    case 3: return spinor_launch<3>(points, n, f64, out, norm, vec, s, strict);
+    case 4: return spinor_launch<4>(points, n, f64, out, norm, vec, s, strict);
+    case 5: return spinor_launch<5>(points, n, f64, out, norm, vec, s, strict);
+    case 6: return spinor_launch<6>(points, n, f64, out, norm, vec, s, strict);
+    case 7: return spinor_launch<7>(points, n, f64, out, norm, vec, s, strict);
+    case 8: return spinor_launch<8>(points, n, f64, out, norm, vec, s, strict);
+    default: return spinor_launch<9>(points, n, f64, out, norm, vec, s, strict);
   }
 }
