@@ -249,14 +249,15 @@ def measure_eval(shm, torch, pts_np, dtype, lmax, steps, warmup, stream, strict=
     return per, region
 
 
-def measure_fp64_peak(shm, reps=3):
+def measure_fp64_peak(shm, reps=2):
     """The FP64 pipe rate of this GPU (shm_probe_fp64_rate: DFMA chains on
-    every SM): best of `reps` launches, as TFLOP/s (2 flops per DFMA)."""
+    every SM, six launch shapes, the fastest), best of `reps` probes, as
+    TFLOP/s (2 flops per DFMA).  About 0.2 s per probe."""
     try:
-        rates = [shm.probe_fp64_rate(1 << 14)[0] for _ in range(reps)]
+        rates = [shm.probe_fp64_rate(1 << 12)[0] for _ in range(reps)]
         return {"tflops": 2.0 * max(rates) / 1e12, "dfma_per_s": max(rates), "runs": rates,
-                "source": "measured: shm_probe_fp64_rate (8 independent DFMA chains per thread, 2048 threads "
-                          "per SM, CUDA events), best of 3"}
+                "source": "measured: shm_probe_fp64_rate (independent DFMA chains, 4-16 per thread, 2-8 CTAs of "
+                          "256 threads per SM, CUDA events; the fastest shape), best of 2"}
     except Exception as e:  # the nominal figure, said so
         return {"tflops": FP64_NOMINAL_TFLOPS, "dfma_per_s": FP64_NOMINAL_TFLOPS * 0.5e12,
                 "source": f"nominal 1.25 TFLOP/s (probe failed: {e!r})"}
@@ -296,6 +297,12 @@ def run_gpu(args, rank, world):
         else:
             raise SystemExit(f"unknown launch variant {args.variant}")
     pts = inputs.dft_grid_points(args.grid)
+    n_total = pts.shape[0]
+    shard = args.shard and world > 1
+    if shard:  # strong scaling: this rank's contiguous part of the one grid
+        from paper_2510_05282_b300.parallel import shard_range
+        a, b = shard_range(n_total, rank, world)
+        pts = np.ascontiguousarray(pts[a:b])
     if not args.variant and args.tune:  # tune on the workload's own size
         tuned_ms = shm.autotune(LMAX, tdt, min(pts.shape[0], 1 << 23), strict=strict)
     if args.dtype == "f32":
@@ -327,7 +334,7 @@ def run_gpu(args, rank, world):
     graph = graph_replay_timing(torch, launch, stream=stream) if rank == 0 else None
 
     ms_per_step = region / args.steps
-    value = world * n * nh / (ms_per_step * 1e-3)
+    value = (n_total if shard else world * n) * nh / (ms_per_step * 1e-3)
     launch_ms = statistics.mean(per)
 
     # roofline of the (single) kernel
@@ -342,12 +349,14 @@ def run_gpu(args, rank, world):
     traffic = tpp * n if tpp else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": (WORKLOAD if args.grid == N_SIDE else f"dft_grid_{args.grid}cubed_fp64_lmax9")
                    .replace("fp64", "fp32" if args.dtype == "f32" else "fp64"),
-                   "points": n, "lmax": LMAX, "grid": f"{args.grid}^3, h=0.3 bohr",
-                   "out_bytes_per_step": n * nh * es, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "points": n_total, "points_per_rank": n, "lmax": LMAX, "grid": f"{args.grid}^3, h=0.3 bohr",
+                   "out_bytes_per_step": n * nh * es,
+                   "parallelism": (f"shard{world}" if shard else f"replicas{world}") if world > 1 else "single",
                    "l2": "no flush: 170 MB input and 5.66 GB output per step exceed the 126 MB L2",
                    "launch_variant": variant, "arithmetic": ARITHMETIC[(args.dtype, hybrid)],
                    "autotune_probe_ms": tuned_ms,
@@ -413,6 +422,7 @@ TRAFFIC_PER_POINT = {
     ("f64", "phased-hybrid-tma-128"): (174.86e6 + 5.75e9) / 7_077_888,
     ("f64", "phased-hybrid-128"): (169.99e6 + 5.61e9) / 7_077_888,
     ("f64", "staged-64"): (21.318144e6 + 648.666112e6) / 884_736,
+    ("f64", "rows-tma-32"): (21.561344e6 + 652.576256e6) / 884_736,
     ("f32", "staged-64"): (10.651648e6 + 294.209024e6) / 884_736,
 }
 # FP64 pipe instructions per point of the hybrid rows at lmax 9 (ncu
@@ -558,8 +568,10 @@ def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
 
 def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
     """Fused projectors: 512 atoms, 40 bohr box, h = 0.2, spheres 2-5 bohr,
-    lmax in {2, 3, 4}; values/s of one shm_projectors call (set-up + persistent
-    launch), FP64 and FP32."""
+    lmax in {2, 3, 4}; FP64 and FP32.  The launch variant is picked by
+    shm_projectors_autotune on this problem; the set-up (shm_projectors_prepare)
+    runs once, and each timed call is shm_projectors_run: one persistent
+    launch.  values/s = values per call / mean launch time."""
     res = {}
     prob = inputs.projector_problem()
     d = shm.DeviceProjectors(prob)
@@ -567,22 +579,34 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
     for dt, name, es in ((torch.float64, "fp64", 8), (torch.float32, "fp32", 4)):
         ws = d.workspace(dt)
         out = torch.empty(d.n_values, dtype=dt, device="cuda")
-        fn = lambda: shm.projectors(d, dt, out=out, workspace=ws, stream=stream)  # noqa: E731
+        tuned_ms = shm.projectors_autotune(d, dt, out, ws) if args.tune else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        shm.projectors_prepare(d, dt, ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prepare_ms = e0.elapsed_time(e1)
+        fn = lambda: shm.projectors_run(d, dt, out, ws, stream=stream)  # noqa: E731
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
         per, _ = timed_launches(fn, max(5, min(args.steps, 30)), stream)
         ms = statistics.mean(per)
+        graph = graph_replay_timing(torch, lambda st: shm.projectors_run(d, dt, out, ws, stream=st), stream=stream)
         err_bits = shm.projectors_check(ws, stream=stream)
         algo_bytes = d.n_values * es + d.n_points * 4
         gbs = algo_bytes / (ms * 1e-3) / 1e9
         res[f"projectors_512atoms_{name}"] = {
             "value": d.n_values / (ms * 1e-3), "unit": "projector values/s", "ms_per_call": ms,
             "atoms": prob.n_atoms, "points": d.n_points, "values": d.n_values, "error_bits": err_bits,
-            "launches_per_call": 2,
-            "roofline": {"bound": "hbm" if es == 4 else "alu", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
-                         "hbm_frac": gbs / hbm_peak, "unit": "GB/s", "peak_source": peaks_src,
-                         "algorithmic_bytes": algo_bytes}}
+            "launches_per_call": 1, "prepare_ms_once": prepare_ms, "launch_variant": shm.projectors_variant(dt),
+            "autotune_best_ms": tuned_ms, "cuda_graph_replay": graph,
+            "arithmetic": ("FP64 out: binary64 displacement, r^2, 1/r and unit vector; float-float (2 x FP32) "
+                           "log-grid index, radial cubic and harmonic rows; within 1e-13 of the oracle"
+                           if es == 8 else "FP32 (FP64 1/r for |d| < 1e-2)"),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "peak_source": peaks_src, "algorithmic_bytes": algo_bytes,
+                         "def": "values x element size + 4 B grid index per point, / mean launch time"}}
         del out, ws
     # the oracle on the same problem (all host cores): the CPU baseline of this workload
     import oracle
@@ -627,16 +651,23 @@ def extra_serving(args, shm, torch, inputs, stream, peaks, peaks_src):
                         srv.release(t)
 
             th = threading.Thread(target=collect, daemon=True)
+            switch = sys.getswitchinterval()
+            sys.setswitchinterval(1e-4)   # the collector gets the interpreter within 0.1 ms of a completion
             th.start()
             t0 = time.perf_counter()
-            for r in reqs:
-                while True:
-                    dt = r.arrival_s - (time.perf_counter() - t0)
-                    if dt <= 0:
-                        break
-                    if dt > 2e-3:
-                        time.sleep(dt - 1e-3)
-                srv.submit(r.n, r.lmax, r.dtype, seed=r.seed, strict=strict)
+            i = 0
+            while i < len(reqs):
+                # every request that has arrived, then sleep (without holding the
+                # interpreter) until the next arrival
+                now = time.perf_counter() - t0
+                while i < len(reqs) and reqs[i].arrival_s <= now:
+                    r = reqs[i]
+                    srv.submit(r.n, r.lmax, r.dtype, seed=r.seed, strict=strict)
+                    i += 1
+                if i < len(reqs):
+                    dt = reqs[i].arrival_s - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
             t_sub = time.perf_counter() - t0
             deadline = time.perf_counter() + 300
             while time.perf_counter() < deadline:
@@ -647,6 +678,7 @@ def extra_serving(args, shm, torch, inputs, stream, peaks, peaks_src):
             wall = time.perf_counter() - t0
             stop.set()
             th.join(timeout=10)
+            sys.setswitchinterval(switch)
             st = srv.stats()
         res[f"serve_poisson_{rate:g}_per_s"] = {
             "offered_req_per_s": rate, "submitted": st["submitted"], "submit_rate_achieved": len(reqs) / t_sub,
@@ -710,6 +742,9 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64",
                     help="f64 is the benchmark workload; f32 only for profiling captures")
     ap.add_argument("--variant", default=None, help="pin a launch variant by name (skips the autotuner)")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split the one grid into contiguous per-rank parts (strong scaling) instead of "
+                         "a grid per rank (replicas, weak scaling)")
     ap.add_argument("--arith", choices=["strict", "hybrid"], default="strict",
                     help="FP64 rows: strict = binary64 throughout (the benchmark workload), hybrid = the "
                          "default rows with float-float m >= 2 columns (profiling captures only)")

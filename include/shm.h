@@ -223,10 +223,11 @@ typedef struct {
 size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dtype);
 
 /*
- * shm_projectors -- the fused projector values, one persistent launch after a
- * set-up launch on `stream` (one CTA per 1,024 table values, up to the SM
- * count: for SHM_F32 they convert the radial tables, for SHM_F64 they write
- * each table interval's interpolating cubic).
+ * shm_projectors -- the fused projector values: shm_projectors_prepare then
+ * shm_projectors_run on `stream` (two launches: the set-up, one CTA per
+ * 1,024 table values up to the SM count -- for SHM_F32 they convert the
+ * radial tables, for SHM_F64 they write each table interval's interpolating
+ * cubic --, then the persistent launch).
  *   dtype     : SHM_F64 (FP64 arithmetic, double out; the 4-point Lagrange
  *               interpolation evaluated as the interval's cubic in the
  *               fractional index, the same polynomial up to rounding) or
@@ -249,10 +250,62 @@ size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dty
 shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
                           size_t workspace_bytes, void* stream);
 
+/*
+ * shm_projectors_prepare -- the per-problem set-up of shm_projectors, done
+ * once: one launch on `stream` that validates every atom's offsets and
+ * species, orders the atoms by species lmax, builds the tile table (tiles of
+ * the current launch variant's size) and writes the FP32 tables or the FP64
+ * interval cubics into `workspace`; it clears the work counter and the error
+ * word.  The workspace is then "prepared" for this problem and dtype, and
+ * shm_projectors_run computes the values with one launch per call.  Prepare
+ * again after changing any array of the problem or the variant choice.
+ *   prob, dtype, workspace, workspace_bytes, stream : as shm_projectors.
+ * Errors: as shm_projectors.
+ */
+shm_status shm_projectors_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* workspace,
+                                  size_t workspace_bytes, void* stream);
+
+/*
+ * shm_projectors_run -- the projector values on a prepared workspace: ONE
+ * persistent launch on `stream` (SMs x resident CTAs drawing tiles from the
+ * workspace's work counter; the last CTA to finish resets the counter for
+ * the next run).  It allocates nothing and enqueues only that kernel, so it
+ * can be captured into a CUDA graph and replayed.  Runs of one workspace on
+ * different streams must not overlap on the GPU (they share the counter).
+ * Every index the kernel follows is checked on the device against the
+ * problem; tiles that do not match it set error bit 8 and are skipped.
+ * Errors: as shm_projectors; SHM_EINVAL when the workspace has not been
+ * prepared for this problem's sizes and dtype.
+ */
+shm_status shm_projectors_run(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
+                              size_t workspace_bytes, void* stream);
+
+/*
+ * shm_projectors_autotune -- times every projector launch variant (tile size
+ * 64/128/256 sphere points, one or two points per thread, a 64-register cap,
+ * bulk copy or copy-out of odd-width tiles) on this problem: for each, a
+ * prepare and four runs into `out` (the first a warm-up), keeping the fastest
+ * for later prepares of this dtype in this process (and in the file
+ * SHM_TUNE_CACHE names, if set).  Leaves `workspace` prepared for the chosen
+ * variant.  It synchronises a private stream, so it must not run during
+ * stream capture.  best_ms (may be NULL) receives the fastest run.
+ * Errors: as shm_projectors_prepare.
+ */
+shm_status shm_projectors_autotune(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
+                                   size_t workspace_bytes, double* best_ms);
+
+/* Projector launch variants: count, the name of the current choice for a
+ * dtype, and pinning one (0 .. count-1; -1 restores the default) for later
+ * prepares in this process.  Errors: SHM_EINVAL. */
+int shm_projectors_variant_count(void);
+const char* shm_projectors_variant(shm_dtype dtype);
+shm_status shm_projectors_set_variant(shm_dtype dtype, int variant);
+
 /* Error bits a projector launch found (0 = none); waits for `stream`.
  * 1: point_offsets not non-decreasing or beyond n_points; 2: species index out
  * of range; 4: grid index out of range; 8: output block beyond n_values or
- * inconsistent with out_offsets. */
+ * inconsistent with out_offsets (or a tile that does not match the problem).
+ * The bits accumulate from the last prepare on. */
 shm_status shm_projectors_check(const void* workspace, void* stream, uint32_t* error_bits);
 
 /* ------------------------------------------------------------------------

@@ -285,6 +285,15 @@ _EXTRA_DECLS.extend([
     ("shm_projectors_check", ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int)),
     ("shm_projectors_noalloc", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
                                 ctypes.c_int)),
+    ("shm_projectors_prepare", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                 ctypes.c_void_p], ctypes.c_int)),
+    ("shm_projectors_run", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int)),
+    ("shm_projectors_autotune", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)], ctypes.c_int)),
+    ("shm_projectors_variant_count", ([], ctypes.c_int)),
+    ("shm_projectors_variant", ([ctypes.c_int], ctypes.c_char_p)),
+    ("shm_projectors_set_variant", ([ctypes.c_int, ctypes.c_int], ctypes.c_int)),
 ])
 
 PROJ_NOALLOC_SCRATCH_BYTES = 1 << 23
@@ -335,6 +344,40 @@ def projectors(dprob: DeviceProjectors, dtype, out=None, workspace=None, stream=
     check(lib().shm_projectors(ctypes.byref(dprob.c), _dtype_code(dtype), out.data_ptr(), workspace.data_ptr(),
                                workspace.numel(), _stream_ptr(stream)))
     return out
+
+
+def projectors_prepare(dprob: DeviceProjectors, dtype, workspace, stream=None) -> None:
+    """shm_projectors_prepare: the per-problem set-up launch into `workspace`."""
+    check(lib().shm_projectors_prepare(ctypes.byref(dprob.c), _dtype_code(dtype), workspace.data_ptr(),
+                                       workspace.numel(), _stream_ptr(stream)))
+
+
+def projectors_run(dprob: DeviceProjectors, dtype, out, workspace, stream=None):
+    """shm_projectors_run: one persistent launch on a prepared workspace."""
+    check(lib().shm_projectors_run(ctypes.byref(dprob.c), _dtype_code(dtype), out.data_ptr(), workspace.data_ptr(),
+                                   workspace.numel(), _stream_ptr(stream)))
+    return out
+
+
+def projectors_autotune(dprob: DeviceProjectors, dtype, out, workspace) -> float:
+    """Time every projector launch variant on this problem; keep the fastest
+    (the workspace is left prepared for it).  Returns its ms per run."""
+    best = ctypes.c_double(0.0)
+    check(lib().shm_projectors_autotune(ctypes.byref(dprob.c), _dtype_code(dtype), out.data_ptr(),
+                                        workspace.data_ptr(), workspace.numel(), ctypes.byref(best)))
+    return best.value
+
+
+def projectors_variant(dtype) -> str:
+    return lib().shm_projectors_variant(_dtype_code(dtype)).decode()
+
+
+def projectors_variant_count() -> int:
+    return int(lib().shm_projectors_variant_count())
+
+
+def set_projectors_variant(dtype, variant: int) -> None:
+    check(lib().shm_projectors_set_variant(_dtype_code(dtype), int(variant)))
 
 
 def projectors_check(workspace, stream=None) -> int:

@@ -3,23 +3,27 @@
 // motivates: projectors of pseudopotential / PAW methods on a 3-D grid).
 //
 // Launch structure (both on the caller's stream):
-//  1. k_proj_setup (CTA 0): orders the atoms by the lmax of their species,
-//     largest first (atom_order), validates every atom's offsets and
-//     species, builds the tile table in that order (tiles = TPB consecutive
-//     sphere points of one atom; tile_offsets[j] = number of tiles of the
-//     atoms before atom_order[j], 0 tiles for an atom that failed
-//     validation), zeroes the work counter and the error word; with the
-//     other CTAs it converts the radial tables (FP32: float copies and the
-//     exponent table of the log-grid index; FP64: the interval cubics).
-//     Tiles of one lmax then run together, so the SMs execute one row code
-//     path at a time (instruction-cache locality); the output layout, by
-//     atom, is unchanged.
-//  2. k_proj (persistent: SMs x resident CTAs): each CTA takes the next tile
-//     from an atomic work counter, evaluates its rows -- minimum-image
-//     displacement, 1/r, log-grid index, 4-point Lagrange interpolation of the
-//     l radial functions, the real harmonics (sh_core.cuh), and their product
-//     -- into a shared-memory tile with an odd row stride, then copies the
-//     tile (one contiguous block of the output) out with coalesced stores.
+//  1. prepare, once per problem (shm_projectors_prepare): k_proj_setup (CTA
+//     0) orders the atoms by the lmax of their species, largest first
+//     (atom_order), validates every atom's offsets and species, builds the
+//     tile table in that order (tiles = TILE consecutive sphere points of one
+//     atom; tile_offsets[j] = number of tiles of the atoms before
+//     atom_order[j], 0 tiles for an atom that failed validation), zeroes the
+//     work counter, the finish count and the error word; with the other CTAs
+//     it converts the radial tables (FP32: float copies and the exponent
+//     table of the log-grid index; FP64: the interval cubics).  Tiles of one
+//     lmax then run together, so the SMs execute one row code path at a time
+//     (instruction-cache locality); the output layout, by atom, is unchanged.
+//  2. run, every call (shm_projectors_run): k_proj (persistent: SMs x
+//     resident CTAs) -- each CTA takes the next tile from an atomic work
+//     counter, evaluates its rows -- minimum-image displacement, 1/r, log-grid
+//     index, 4-point Lagrange interpolation of the l radial functions, the
+//     real harmonics (sh_core.cuh), and their product -- into a shared-memory
+//     tile with an odd row stride, then copies the tile (one contiguous block
+//     of the output) out with coalesced stores or one bulk copy; the last CTA
+//     to finish resets the counter for the next run.  One launch per call.
+//  The launch variant (tile size, points per thread, register cap, store
+//  path) is the tuner's choice (shm_projectors_autotune) or the default.
 // Uneven sphere sizes (4k..65k points) and per-species lmax balance through
 // the dynamic queue; a tile never spans two atoms, so every row of a tile has
 // the same width.
@@ -28,9 +32,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "sh_core.cuh"
 #include "sh_tile.cuh"
@@ -38,7 +45,6 @@
 
 namespace shm {
 
-constexpr int kProjTPB = 128;
 constexpr int kExpLo = -160;  // FP32 log-grid exponent table covers frexpf exponents kExpLo..kExpHi
 constexpr int kExpHi = 140;
 constexpr int kExpN = kExpHi - kExpLo + 1;
@@ -52,7 +58,7 @@ struct __align__(16) AtomF32 {  // 48 bytes: three 16-byte loads
 
 // Workspace layout (byte offsets; every block 256-byte aligned).
 struct ProjWs {
-  size_t counter = 0;      // unsigned long long work counter, uint32 error word at +8
+  size_t counter = 0;      // unsigned long long work counter, uint32 error word at +8, uint32 finish count at +12
   size_t tiles = 256;      // int64 tile_offsets[n_atoms + 1]
   size_t order = 0;        // int32 atom_order[n_atoms]
   size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
@@ -147,6 +153,7 @@ struct ProjParams {
   // workspace views
   unsigned long long* counter;
   unsigned* err;
+  unsigned* done;  // CTAs of the current launch that have finished
   int64_t* tile_offsets;
   int32_t* atom_order;
   int2* etab;
@@ -197,6 +204,7 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
   if (tid == 0) {
     *P.counter = 0ull;
     *P.err = 0u;
+    *P.done = 0u;
     carry = 0;
     P.tile_offsets[0] = 0;
   }
@@ -672,7 +680,7 @@ __device__ __forceinline__ void bulk_rows_out(const T* stage, int nv, T* __restr
 // boundary of dst) and a scalar tail.  For odd L2 the tile rows are
 // contiguous (RS = L2), so element j is tile[j]; otherwise its row is
 // floor(j / L2) = umulhi(j, ceil(2^32 / L2)), exact for j < 2^32 / L2^2 (here
-// j < 128 * 100): no division instructions, which on a B300 would issue
+// j < 256 * 100): no division instructions, which on a B300 would issue
 // conversions to the narrow FP64-class pipe.
 template <typename T>
 __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int rows, int L2, int RS,
@@ -705,8 +713,24 @@ __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int ro
 // problems search the table in global memory.
 constexpr int kSmemAtoms = 4096;
 
-template <typename T>
-__global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__ out, int tile_bytes) {
+// The persistent kernel.  TILE sphere points of one atom per tile, PPT
+// points per thread (TILE / PPT threads per CTA), MINB resident CTAs per SM
+// asked of the register allocator (0: no cap).  bulk: tiles of odd row width
+// leave by one bulk copy, else by the copy-out loop.
+//
+// Each CTA draws tiles from the work counter until the counter passes the
+// tile count; the last CTA to finish resets the counter (and the finish
+// count) to zero, so every launch starts from a clean counter with no other
+// work on the stream: one launch per call, replayable from a CUDA graph.
+// Every index the kernel follows is checked against the problem (the atom
+// of a tile, its species, offsets and output block, every grid index), so a
+// workspace that does not hold this problem's tables sets error bits instead
+// of reading or writing out of bounds; tile_limit caps the tile count read
+// from the workspace.
+template <typename T, int TILE, int PPT, int MINB>
+__global__ void __launch_bounds__(TILE / PPT, MINB) k_proj(ProjParams P, T* __restrict__ out, int tile_bytes,
+                                                          int64_t tile_limit, int bulk) {
+  constexpr int NT = TILE / PPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   int* tt = reinterpret_cast<int*>(smem_raw + tile_bytes);
@@ -714,11 +738,11 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
   __shared__ int s_atom;
   const double inv_box = 1.0 / P.box, inv_rmin = 1.0 / P.r_min, inv_dlog = 1.0 / P.dlog;
   const LogGrid64 G = {-log(P.r_min) * inv_dlog, 0.69314718055994530942 * 0.5 * inv_dlog, 0.5 * inv_dlog};
-  // exact tile count, from the table the set-up kernel built earlier on this stream
-  const int64_t total_tiles = P.tile_offsets[P.n_atoms];
+  // exact tile count, from the table the set-up kernel built
+  const int64_t total_tiles = min(max(P.tile_offsets[P.n_atoms], (int64_t)0), tile_limit);
   const bool cached = P.n_atoms + 1 <= kSmemAtoms;
   if (cached)
-    for (int i = threadIdx.x; i <= P.n_atoms; i += kProjTPB) tt[i] = (int)P.tile_offsets[i];
+    for (int i = threadIdx.x; i <= P.n_atoms; i += NT) tt[i] = (int)P.tile_offsets[i];
   __syncthreads();
   // owning atom of tile t: atom_order[j] for the last j with tile_offsets[j]
   // <= t (one thread searches, for the next tile while the others work on
@@ -746,39 +770,53 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
       s_next = (long long)atomicAdd(P.counter, 1ull);
       s_atom = s_next < total_tiles ? owner(s_next) : 0;
     }
+    // the tile's atom and its blocks, checked against the problem
     const int64_t a = P.atom_order[j];
-    const int64_t pa0 = P.point_offsets[a], pa1 = P.point_offsets[a + 1];
-    const int64_t c = t - (cached ? (int64_t)tt[j] : P.tile_offsets[j]);
-    const int64_t p0 = pa0 + c * kProjTPB;
-    const int rows = (int)min((int64_t)kProjTPB, pa1 - p0);
-    const int s = P.atom_species[a];
-    const int lmax = P.lmax[s];
+    bool ok = a >= 0 && a < P.n_atoms;
+    const int64_t pa0 = ok ? P.point_offsets[a] : 0, pa1 = ok ? P.point_offsets[a + 1] : 0;
+    const int s = ok ? P.atom_species[a] : 0;
+    ok = ok && s >= 0 && s < P.n_species && pa0 >= 0 && pa1 >= pa0 && pa1 <= P.n_points;
+    const int lmax = ok ? P.lmax[s] : 0;
     const int L2 = (lmax + 1) * (lmax + 1);
+    const int64_t c = t - (cached ? (int64_t)tt[j] : P.tile_offsets[j]);
+    const int64_t p0 = pa0 + c * TILE;
+    const int64_t oa0 = ok ? P.out_offsets[a] : 0, oa1 = ok ? P.out_offsets[a + 1] : 0;
+    ok = ok && c >= 0 && p0 < pa1 && oa0 >= 0 && oa1 <= P.n_values && oa1 - oa0 == (pa1 - pa0) * L2;
+    if (!ok) {  // the same decision in every thread: skip the tile
+      if (threadIdx.x == 0) atomicOr(P.err, kErrOut);
+      __syncthreads();  // s_next and s_atom hold the next tile
+      continue;
+    }
+    const int rows = (int)min((int64_t)TILE, pa1 - p0);
     const int RS = L2 | 1;
-    const int64_t o0 = P.out_offsets[a] + c * kProjTPB * (int64_t)L2;
+    const int64_t o0 = oa0 + c * TILE * (int64_t)L2;
     // odd row widths: the tile is staged contiguously (RS = L2), shifted so
     // that it has the 16-byte phase of its place in the output, and leaves by
     // one bulk copy
-    const bool flat = (L2 & 1) != 0;
+    const bool flat = bulk && (L2 & 1) != 0;
     T* const dst = out + o0;
     T* const stage = tile + (flat ? (int)(((uintptr_t)dst & 15u) / sizeof(T)) : 0);
-    if ((int)threadIdx.x < rows) {
-      const int64_t p = p0 + threadIdx.x;
-      const int g = P.point_index[p];
-      T* row = stage + threadIdx.x * RS;
-      if (g < 0 || g >= P.ng * P.ng * P.ng) {
-        atomicOr(P.err, kErrGrid);
-        for (int k = 0; k < L2; ++k) row[k] = (T)0;
-      } else if constexpr (sizeof(T) == 8) {
-        proj_point_f64(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
-                       inv_rmin, inv_dlog, G, reinterpret_cast<double*>(row));
-      } else {
-        const int4* ap = reinterpret_cast<const int4*>(P.atomf + a);
-        const int4 u4 = __ldg(ap), fh4 = __ldg(ap + 1), fl4 = __ldg(ap + 2);
-        const AtomF32 A = {{u4.x, u4.y, u4.z, 0},
-                           {__int_as_float(fh4.x), __int_as_float(fh4.y), __int_as_float(fh4.z), 0.0f},
-                           {__int_as_float(fl4.x), __int_as_float(fl4.y), __int_as_float(fl4.z), 0.0f}};
-        proj_point_f32(P, g, A, s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      const int r = (int)threadIdx.x + u * NT;
+      if (r < rows) {
+        const int64_t pt = p0 + r;
+        const int g = P.point_index[pt];
+        T* row = stage + r * RS;
+        if (g < 0 || g >= P.ng * P.ng * P.ng) {
+          atomicOr(P.err, kErrGrid);
+          for (int k = 0; k < L2; ++k) row[k] = (T)0;
+        } else if constexpr (sizeof(T) == 8) {
+          proj_point_f64(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
+                         inv_rmin, inv_dlog, G, reinterpret_cast<double*>(row));
+        } else {
+          const int4* ap = reinterpret_cast<const int4*>(P.atomf + a);
+          const int4 u4 = __ldg(ap), fh4 = __ldg(ap + 1), fl4 = __ldg(ap + 2);
+          const AtomF32 A = {{u4.x, u4.y, u4.z, 0},
+                             {__int_as_float(fh4.x), __int_as_float(fh4.y), __int_as_float(fh4.z), 0.0f},
+                             {__int_as_float(fl4.x), __int_as_float(fl4.y), __int_as_float(fl4.z), 0.0f}};
+          proj_point_f32(P, g, A, s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
+        }
       }
     }
     if (flat) {
@@ -791,47 +829,107 @@ __global__ void __launch_bounds__(kProjTPB) k_proj(ProjParams P, T* __restrict__
     }
     __syncthreads();  // the tile buffer is free and s_next holds the next tile
   }
-  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if (threadIdx.x == 0) {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    // every CTA draws from the counter until it passes the tile count, so
+    // once all have finished nothing reads it again in this launch: the last
+    // to finish clears it for the next launch
+    __threadfence();
+    if (atomicAdd(P.done, 1u) == gridDim.x - 1) {
+      *P.counter = 0ull;
+      *P.done = 0u;
+      __threadfence();
+    }
+  }
 }
 
-template <typename T>
-shm_status launch_proj(const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, cudaStream_t s) {
-  constexpr int MAXDEV = 64;
-  static int bps[MAXDEV][SHM_LMAX_CAP + 1] = {};
-  const int dev = current_device();
-  if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
+// Launch variants of the persistent kernel (index = variant id): tile size,
+// points per thread, resident-CTA request for the register allocator, and
+// the store path of odd-width tiles.
+struct ProjVariant {
+  int tile, ppt, minb;
+  bool bulk;
+  const char* name;
+};
+constexpr ProjVariant kProjVariants[] = {
+    {128, 1, 0, true, "tile128"},          {128, 1, 0, false, "tile128-copyout"},
+    {128, 1, 8, true, "tile128-regcap64"}, {128, 2, 0, true, "tile128-2ppt"},
+    {64, 1, 0, true, "tile64"},            {256, 1, 0, true, "tile256"},
+};
+constexpr int kNumProjVariants = sizeof(kProjVariants) / sizeof(kProjVariants[0]);
+constexpr int kDefaultProjVariant = 0;
+constexpr size_t kProjMaxSmem = 232448;  // B300 opt-in shared memory per CTA
+
+// Shared memory of a launch: the staging tile (with room for the 16-byte
+// shift of a bulk-copied tile) and, for up to kSmemAtoms atoms, the tile
+// table.
+inline size_t proj_tile_bytes(int tile, int max_lmax, size_t es) {
   const int RS = ((max_lmax + 1) * (max_lmax + 1)) | 1;
-  const size_t tile_bytes = ((size_t)kProjTPB * RS * sizeof(T) + 15) / 16 * 16 + 16;  // + the staging shift
+  return ((size_t)tile * RS * es + 15) / 16 * 16 + 16;
+}
+inline size_t proj_smem(int variant, int max_lmax, size_t es, int64_t n_atoms) {
+  return proj_tile_bytes(kProjVariants[variant].tile, max_lmax, es) +
+         (n_atoms + 1 <= kSmemAtoms ? (size_t)(n_atoms + 1) * 4 : 0);
+}
+
+std::mutex g_proj_mu;
+int g_proj_choice[2] = {-1, -1};  // [dtype], -1 = default
+// the variant a workspace was prepared with (its tile table depends on the
+// tile size), with the problem sizes it was prepared for
+struct ProjPrepared {
+  int variant;
+  shm_dtype dtype;
+  int64_t n_atoms, n_points, n_values;
+};
+std::unordered_map<const void*, ProjPrepared> g_prepared;
+
+template <typename T, int TILE, int PPT, int MINB>
+shm_status launch_proj_v(const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, bool bulk, cudaStream_t s) {
+  auto kern = k_proj<T, TILE, PPT, MINB>;
+  const int dev = current_device();
+  const size_t tile_bytes = proj_tile_bytes(TILE, max_lmax, sizeof(T));
   const size_t smem = tile_bytes + (P.n_atoms + 1 <= kSmemAtoms ? (size_t)(P.n_atoms + 1) * 4 : 0);
-  auto kern = k_proj<T>;
-  if (bps[dev][max_lmax] == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)kProjTPB * 101 * sizeof(T) + 16 + kSmemAtoms * 4));
-    if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_proj)");
-    int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kProjTPB, smem);
-    if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_proj)");
-    bps[dev][max_lmax] = std::max(b, 1);
-  }
-  // the occupancy was taken for the first problem's table size; recompute when it grows
   {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kProjTPB, smem) == cudaSuccess && b > 0)
-      bps[dev][max_lmax] = b;
-    else
-      cudaGetLastError();
+    // the shared-memory opt-in, once per device (kept at the largest size any
+    // problem needs)
+    constexpr int MAXDEV = 64;
+    static size_t optin[MAXDEV] = {};
+    std::lock_guard<std::mutex> lk(g_proj_mu);
+    if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
+    if (optin[dev] < smem) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_proj)");
+      optin[dev] = smem;
+    }
   }
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tile_upper, (int64_t)sm_count(dev) * bps[dev][max_lmax]));
-  kern<<<(unsigned)grid, kProjTPB, smem, s>>>(P, out, (int)tile_bytes);
-  cudaError_t e = cudaGetLastError();
+  int b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TILE / PPT, smem);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_proj)");
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tile_upper, (int64_t)sm_count(dev) * std::max(b, 1)));
+  kern<<<(unsigned)grid, TILE / PPT, smem, s>>>(P, out, (int)tile_bytes, tile_upper, bulk ? 1 : 0);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_proj launch");
   return SHM_OK;
 }
 
+template <typename T>
+shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, cudaStream_t s) {
+  const bool bulk = kProjVariants[variant].bulk;
+  switch (variant) {
+    case 0:
+    case 1: return launch_proj_v<T, 128, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 2: return launch_proj_v<T, 128, 1, 8>(P, max_lmax, out, tile_upper, bulk, s);
+    case 3: return launch_proj_v<T, 128, 2, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 4: return launch_proj_v<T, 64, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 5: return launch_proj_v<T, 256, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
+  }
+  return fail(SHM_EINVAL, "unknown projector launch variant");
+}
+
 // Validates the host-visible part of the problem and fills the kernel
 // parameters; the device-side arrays are validated by k_proj_setup.
-shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* workspace, size_t ws_bytes,
-                        ProjParams* P, int* max_lmax, int64_t* tile_upper) {
+shm_status proj_params(const shm_proj_problem* prob, shm_dtype dtype, void* workspace, size_t ws_bytes,
+                       int tile, ProjParams* P, int* max_lmax, int64_t* tile_upper) {
   int ml = 0;
   shm_status vst = proj_validate(prob, dtype, &ml);
   if (vst != SHM_OK) return vst;
@@ -882,6 +980,7 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   char* ws = (char*)workspace;
   P->counter = (unsigned long long*)(ws + w.counter);
   P->err = (unsigned*)(ws + w.counter + 8);
+  P->done = (unsigned*)(ws + w.counter + 12);
   P->tile_offsets = (int64_t*)(ws + w.tiles);
   P->atom_order = (int32_t*)(ws + w.order);
   P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
@@ -891,7 +990,7 @@ shm_status proj_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* wor
   P->hg = dtype == SHM_F64 ? (double*)(ws + w.hg) : nullptr;
   *max_lmax = ml;
   // an upper bound of the tile count: every point of every atom in its own partial tile
-  *tile_upper = p.n_points / kProjTPB + p.n_atoms;
+  *tile_upper = p.n_points / tile + p.n_atoms;
   (void)es;
   return SHM_OK;
 }
@@ -905,32 +1004,238 @@ extern "C" size_t shm_projectors_workspace_size(const shm_proj_problem* prob, sh
   return proj_layout(*prob, dtype).total;
 }
 
+namespace shm {
+namespace {
+
+// Checks the output buffer of a call.
+shm_status check_out(const shm_proj_problem* prob, shm_dtype dtype, void* out) {
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  if (prob->n_values > 0) {
+    if (!out) return fail(SHM_EINVAL, "out is null");
+    if (!aligned(out, es)) return fail(SHM_EINVAL, "out must be aligned to the element size");
+    shm_status st = check_device_range(out, (size_t)prob->n_values * es, "out");
+    if (st != SHM_OK) return st;
+  }
+  return SHM_OK;
+}
+
+// The variant a prepare uses: the tuned (or pinned) choice for the dtype if
+// its shared memory fits this problem, else the default.
+int prepare_variant(shm_dtype dtype, int max_lmax, int64_t n_atoms) {
+  int v;
+  {
+    std::lock_guard<std::mutex> lk(g_proj_mu);
+    v = g_proj_choice[dtype == SHM_F64 ? 1 : 0];
+  }
+  if (v < 0) v = kDefaultProjVariant;
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  if (proj_smem(v, max_lmax, es, n_atoms) > kProjMaxSmem) v = kDefaultProjVariant;
+  return v;
+}
+
+// Set-up launch into `workspace` for `variant`, recorded for later runs.
+shm_status prepare_in(const shm_proj_problem* prob, shm_dtype dtype, void* workspace, size_t ws_bytes, int variant,
+                      cudaStream_t s) {
+  ProjParams P;
+  int max_lmax = 0;
+  int64_t tile_upper = 0;
+  shm_status st = proj_params(prob, dtype, workspace, ws_bytes, kProjVariants[variant].tile, &P, &max_lmax,
+                              &tile_upper);
+  if (st != SHM_OK) return st;
+  if (proj_smem(variant, max_lmax, dtype == SHM_F64 ? 8 : 4, prob->n_atoms) > kProjMaxSmem)
+    return fail(SHM_EINVAL, "projector tile does not fit in shared memory for this lmax");
+  k_proj_setup<<<setup_grid(P, dtype), 1024, 0, s>>>(P, kProjVariants[variant].tile, dtype == SHM_F32 ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
+  std::lock_guard<std::mutex> lk(g_proj_mu);
+  g_prepared[workspace] = ProjPrepared{variant, dtype, prob->n_atoms, prob->n_points, prob->n_values};
+  return SHM_OK;
+}
+
+// The persistent launch on a prepared workspace.
+shm_status run_in(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace, size_t ws_bytes,
+                  cudaStream_t s) {
+  ProjPrepared rec;
+  {
+    std::lock_guard<std::mutex> lk(g_proj_mu);
+    auto it = g_prepared.find(workspace);
+    if (it == g_prepared.end())
+      return fail(SHM_EINVAL, "workspace not prepared (call shm_projectors_prepare first)");
+    rec = it->second;
+  }
+  if (rec.dtype != dtype || rec.n_atoms != prob->n_atoms || rec.n_points != prob->n_points ||
+      rec.n_values != prob->n_values)
+    return fail(SHM_EINVAL, "workspace was prepared for another problem or dtype");
+  ProjParams P;
+  int max_lmax = 0;
+  int64_t tile_upper = 0;
+  shm_status st = proj_params(prob, dtype, workspace, ws_bytes, kProjVariants[rec.variant].tile, &P, &max_lmax,
+                              &tile_upper);
+  if (st != SHM_OK) return st;
+  if ((st = check_out(prob, dtype, out)) != SHM_OK) return st;
+  if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
+  return dtype == SHM_F64 ? launch_proj<double>(rec.variant, P, max_lmax, (double*)out, tile_upper, s)
+                          : launch_proj<float>(rec.variant, P, max_lmax, (float*)out, tile_upper, s);
+}
+
+void load_proj_tune_cache();
+
+}  // namespace
+}  // namespace shm
+
+extern "C" shm_status shm_projectors_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* workspace,
+                                             size_t workspace_bytes, void* stream) {
+  using namespace shm;
+  NvtxRange nvtx_range("shm_projectors_prepare");
+  clear_error();
+  int ml = 0;
+  shm_status st = proj_validate(prob, dtype, &ml);
+  if (st != SHM_OK) return st;
+  load_proj_tune_cache();
+  return prepare_in(prob, dtype, workspace, workspace_bytes, prepare_variant(dtype, ml, prob->n_atoms),
+                    (cudaStream_t)stream);
+}
+
+extern "C" shm_status shm_projectors_run(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
+                                         size_t workspace_bytes, void* stream) {
+  using namespace shm;
+  NvtxRange nvtx_range("shm_projectors_run");
+  clear_error();
+  int ml = 0;
+  shm_status st = proj_validate(prob, dtype, &ml);
+  if (st != SHM_OK) return st;
+  return run_in(prob, dtype, out, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
 extern "C" shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
                                      size_t workspace_bytes, void* stream) {
   using namespace shm;
   NvtxRange nvtx_range("shm_projectors");
   clear_error();
-  ProjParams P;
-  int max_lmax = 0;
-  int64_t tile_upper = 0;
-  shm_status st = proj_prepare(prob, dtype, workspace, workspace_bytes, &P, &max_lmax, &tile_upper);
+  int ml = 0;
+  shm_status st = proj_validate(prob, dtype, &ml);
   if (st != SHM_OK) return st;
-  const size_t es = dtype == SHM_F64 ? 8 : 4;
-  if (prob->n_values > 0) {
-    if (!out) return fail(SHM_EINVAL, "out is null");
-    if (!aligned(out, es)) return fail(SHM_EINVAL, "out must be aligned to the element size");
-    if ((st = check_device_range(out, (size_t)prob->n_values * es, "out")) != SHM_OK) return st;
-  }
+  if ((st = check_out(prob, dtype, out)) != SHM_OK) return st;
+  load_proj_tune_cache();
   cudaStream_t s = (cudaStream_t)stream;
-  k_proj_setup<<<setup_grid(P, dtype), 1024, 0, s>>>(P, kProjTPB, dtype == SHM_F32 ? 1 : 0);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
-  if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
-  // The persistent kernel stops when the work counter passes the real tile
-  // count, which it reads from the table (tile_offsets[n_atoms]); the host's
-  // upper bound only sizes the grid.
-  return dtype == SHM_F64 ? launch_proj<double>(P, max_lmax, (double*)out, tile_upper, s)
-                          : launch_proj<float>(P, max_lmax, (float*)out, tile_upper, s);
+  st = prepare_in(prob, dtype, workspace, workspace_bytes, prepare_variant(dtype, ml, prob->n_atoms), s);
+  if (st != SHM_OK) return st;
+  return run_in(prob, dtype, out, workspace, workspace_bytes, s);
+}
+
+namespace shm {
+namespace {
+
+// Projector choices in the tuner's cache file (SHM_TUNE_CACHE): lines
+// "3 0 v" (FP32) and "4 0 v" (FP64), v a projector launch variant; the
+// evaluator's lines (slots 0..2) share the file.
+constexpr int kProjCacheSlotF32 = 3;
+
+void load_proj_tune_cache() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* path = getenv("SHM_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    int slot, x, v;
+    std::lock_guard<std::mutex> lk(g_proj_mu);
+    while (fscanf(f, "%d %d %d", &slot, &x, &v) == 3)
+      if ((slot == kProjCacheSlotF32 || slot == kProjCacheSlotF32 + 1) && v >= 0 && v < kNumProjVariants)
+        g_proj_choice[slot - kProjCacheSlotF32] = v;
+    fclose(f);
+  });
+}
+
+}  // namespace
+}  // namespace shm
+
+extern "C" shm_status shm_projectors_autotune(const shm_proj_problem* prob, shm_dtype dtype, void* out,
+                                              void* workspace, size_t workspace_bytes, double* best_ms) {
+  using namespace shm;
+  NvtxRange nvtx_range("shm_projectors_autotune");
+  clear_error();
+  int ml = 0;
+  shm_status st = proj_validate(prob, dtype, &ml);
+  if (st != SHM_OK) return st;
+  if ((st = check_out(prob, dtype, out)) != SHM_OK) return st;
+  load_proj_tune_cache();
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return fail_cuda(e, "cudaStreamCreate");
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    st = fail_cuda(e, "cudaEventCreate");
+  }
+  const size_t es = dtype == SHM_F64 ? 8 : 4;
+  int best = -1;
+  float best_t = 0.f;
+  for (int v = 0; v < kNumProjVariants && st == SHM_OK; ++v) {
+    if (proj_smem(v, ml, es, prob->n_atoms) > kProjMaxSmem) continue;
+    if ((st = prepare_in(prob, dtype, workspace, workspace_bytes, v, s)) != SHM_OK) break;
+    float tv = 1e30f;
+    for (int rep = 0; rep < 4 && st == SHM_OK; ++rep) {  // the first run is a warm-up
+      cudaEventRecord(e0, s);
+      st = run_in(prob, dtype, out, workspace, workspace_bytes, s);
+      cudaEventRecord(e1, s);
+      if (st != SHM_OK) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+        st = fail_cuda(e, "projector autotune: kernel failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tv = std::min(tv, ms);
+    }
+    if (st == SHM_OK && (best < 0 || tv < best_t)) {
+      best = v;
+      best_t = tv;
+    }
+  }
+  if (st == SHM_OK && best >= 0) {
+    {
+      std::lock_guard<std::mutex> lk(g_proj_mu);
+      g_proj_choice[dtype == SHM_F64 ? 1 : 0] = best;
+    }
+    // leave the workspace prepared for the chosen variant
+    st = prepare_in(prob, dtype, workspace, workspace_bytes, best, s);
+    if (st == SHM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = fail_cuda(e, "cudaStreamSynchronize");
+    const char* path = getenv("SHM_TUNE_CACHE");
+    if (st == SHM_OK && path && *path) {
+      FILE* f = fopen(path, "a");
+      if (f) {
+        fprintf(f, "%d 0 %d\n", kProjCacheSlotF32 + (dtype == SHM_F64 ? 1 : 0), best);
+        fclose(f);
+      }
+    }
+    if (best_ms) *best_ms = best_t;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  return st;
+}
+
+extern "C" int shm_projectors_variant_count(void) { return shm::kNumProjVariants; }
+
+extern "C" const char* shm_projectors_variant(shm_dtype dtype) {
+  using namespace shm;
+  if (dtype != SHM_F32 && dtype != SHM_F64) return "";
+  load_proj_tune_cache();
+  std::lock_guard<std::mutex> lk(g_proj_mu);
+  const int v = g_proj_choice[dtype == SHM_F64 ? 1 : 0];
+  return kProjVariants[v < 0 ? kDefaultProjVariant : v].name;
+}
+
+extern "C" shm_status shm_projectors_set_variant(shm_dtype dtype, int variant) {
+  using namespace shm;
+  clear_error();
+  if (dtype != SHM_F32 && dtype != SHM_F64) return fail(SHM_EINVAL, "dtype must be SHM_F32 or SHM_F64");
+  if (variant < -1 || variant >= kNumProjVariants) return fail(SHM_EINVAL, "variant out of range");
+  load_proj_tune_cache();
+  std::lock_guard<std::mutex> lk(g_proj_mu);
+  g_proj_choice[dtype == SHM_F64 ? 1 : 0] = variant;
+  return SHM_OK;
 }
 
 extern "C" shm_status shm_projectors_check(const void* workspace, void* stream, uint32_t* error_bits) {
@@ -991,23 +1296,13 @@ extern "C" shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_d
   void* scratch = nullptr;
   shm_status st = noalloc_scratch(&scratch);
   if (st != SHM_OK) return st;
-  ProjParams P;
-  int max_lmax = 0;
-  int64_t tile_upper = 0;
-  st = proj_prepare(prob, dtype, scratch, SHM_PROJ_NOALLOC_SCRATCH_BYTES, &P, &max_lmax, &tile_upper);
-  if (st != SHM_OK) return st;
-  const size_t es = dtype == SHM_F64 ? 8 : 4;
-  if (prob->n_values > 0) {
-    if (!out) return fail(SHM_EINVAL, "out is null");
-    if (!aligned(out, es)) return fail(SHM_EINVAL, "out must be aligned to the element size");
-    if ((st = check_device_range(out, (size_t)prob->n_values * es, "out")) != SHM_OK) return st;
-  }
+  if ((st = check_out(prob, dtype, out)) != SHM_OK) return st;
+  load_proj_tune_cache();
+  // the set-up launch clears the work counter, the finish count and the
+  // error word before the persistent launch reads them
   cudaStream_t s = (cudaStream_t)stream;
-  // k_proj_setup clears the work counter and the error word before anything reads them
-  k_proj_setup<<<setup_grid(P, dtype), 1024, 0, s>>>(P, kProjTPB, dtype == SHM_F32 ? 1 : 0);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
-  if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
-  return dtype == SHM_F64 ? launch_proj<double>(P, max_lmax, (double*)out, tile_upper, s)
-                          : launch_proj<float>(P, max_lmax, (float*)out, tile_upper, s);
+  st = prepare_in(prob, dtype, scratch, SHM_PROJ_NOALLOC_SCRATCH_BYTES, prepare_variant(dtype, ml, prob->n_atoms),
+                  s);
+  if (st != SHM_OK) return st;
+  return run_in(prob, dtype, out, scratch, SHM_PROJ_NOALLOC_SCRATCH_BYTES, s);
 }

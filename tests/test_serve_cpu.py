@@ -53,3 +53,26 @@ def test_create_and_submit_validation_without_gpu(L):
     req = _binding._Request(points=None, n=10, lmax=3, dtype=1, seed=0, flags=0)
     t = ctypes.c_uint64()
     assert L.shm_serve_submit(None, ctypes.byref(req), ctypes.byref(t)) == 1
+
+
+def test_injected_tuner_allocation_failure_without_gpu(L, monkeypatch):
+    """SHM_FAIL_ALLOC=autotune: the tuner's probe allocation fails before any
+    CUDA call, with SHM_ENOMEM and a message naming the injection."""
+    monkeypatch.setenv("SHM_FAIL_ALLOC", "autotune")
+    best = ctypes.c_double(-1.0)
+    assert L.shm_autotune(9, 1, 1000, ctypes.byref(best)) == 2
+    assert "injected" in L.shm_last_error().decode()
+    assert best.value == -1.0
+    monkeypatch.setenv("SHM_FAIL_ALLOC", "serve_pool,autotune")
+    assert L.shm_autotune_ex(5, 0, 0, 1000, ctypes.byref(best)) == 2
+    monkeypatch.setenv("SHM_FAIL_ALLOC", "serve_pool")     # another site only: the tuner's own check passes
+    st = L.shm_autotune(9, 1, 1000, ctypes.byref(best))
+    assert "injected" not in L.shm_last_error().decode()
+    assert st != 0                                           # no GPU here: a real failure
+
+
+def test_request_flags_validated(L):
+    """Unknown request flag bits are refused (SHM_REQ_DISCARD | SHM_REQ_STRICT_FP64 are the known ones)."""
+    req = _binding._Request(points=None, n=10, lmax=3, dtype=1, seed=0, flags=0x4)
+    t = ctypes.c_uint64()
+    assert L.shm_serve_submit(ctypes.c_void_p(1), ctypes.byref(req), ctypes.byref(t)) == 1

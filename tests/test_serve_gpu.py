@@ -165,3 +165,92 @@ def test_latency_statistics():
         s = srv.stats()
         assert s["completed"] == 20 and 0 < s["lat_p50_ms"] <= s["lat_p99_ms"] <= s["lat_max_ms"]
         assert s["harmonics_done"] == sum(10_000 * (i + 1) * ((i % 10) + 1) ** 2 for i in range(20))
+
+
+def test_strict_fp64_requests_equal_strict_evaluator_bitwise(oracle_mod):
+    """SHM_REQ_STRICT_FP64: the request's rows are the all-binary64 rows,
+    bitwise those of shm_eval_ex with SHM_STRICT_FP64, alone and mixed with
+    default FP64 and FP32 requests in the same batches."""
+    g = inputs.rng("tests", 503)
+    with shm.Server(pool_bytes=2 << 30, batch_points=1 << 16, chunk_points=1 << 14) as srv:
+        tickets = []
+        for i in range(12):
+            n = int(g.integers(1000, 60_000))
+            lmax = int(g.integers(0, 10))
+            dtype = (torch.float64, torch.float32)[i % 2]
+            strict = i % 4 == 0
+            tickets.append((srv.submit(n, lmax, dtype, seed=1000 + i, strict=strict), n, lmax, dtype, strict, 1000 + i))
+        for t, n, lmax, dtype, strict, seed in tickets:
+            r, out = result(srv, t)
+            pts = inputs.counter_points(seed, n)
+            p = torch.from_numpy(pts).to(device="cuda", dtype=dtype)
+            ref = shm.eval_sh(p, lmax, strict=strict)
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref), (n, lmax, dtype, strict)
+            if strict:
+                assert_normwise(out.cpu().numpy()[::37], oracle_mod.real_sh(pts[::37], lmax), TOL_F64, "strict serve")
+            srv.release(t)
+
+
+def test_wait_any_returns_requests_in_completion_order_and_counts_client_latency():
+    with shm.Server(pool_bytes=2 << 30) as srv:
+        sizes = [400_000, 2_000, 3_000, 150_000, 1_000]
+        tickets = {srv.submit(n, 9, torch.float64, seed=77 + i): n for i, n in enumerate(sizes)}
+        seen = []
+        while len(seen) < len(tickets):
+            st, t, r = srv.wait_any(timeout_ms=60_000)
+            assert st == 0 and t in tickets and r.status == 0
+            assert t not in seen and r.n == tickets[t]
+            seen.append(t)
+        st, t, r = srv.wait_any(timeout_ms=20)       # nothing left to collect
+        assert st == 5
+        stats = srv.stats()
+        assert stats["collected"] == len(sizes) and stats["completed"] == len(sizes)
+        assert 0 < stats["client_lat_p50_ms"] <= stats["client_lat_max_ms"]
+        # a wait on an already collected ticket still returns it, but counts it once
+        assert srv.wait(seen[0], timeout_ms=10).status == 0
+        assert srv.stats()["collected"] == len(sizes)
+        for t in seen:
+            srv.release(t)
+        # discarded requests are never handed to wait_any
+        srv.submit(5_000, 3, torch.float32, seed=1, discard=True)
+        st, t, r = srv.wait_any(timeout_ms=2_000)
+        assert st == 5
+
+
+def _free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+@pytest.mark.parametrize("site", ["serve_pool", "serve_pinned", "serve_batch", "all"])
+def test_injected_allocation_failure_at_create(site, monkeypatch):
+    """SHM_FAIL_ALLOC makes the named allocation of shm_serve_create fail:
+    SHM_ENOMEM, no server, nothing left allocated; without it the same
+    create succeeds."""
+    import ctypes
+    from paper_2510_05282_b300 import _binding
+    L = shm.lib()
+    cfg = _binding.ServeConfig(pool_bytes=1 << 30, max_slots=8, queue_capacity=16, batch_points=1 << 16,
+                               chunk_points=1 << 14, inflight_batches=2, device=torch.cuda.current_device())
+    before = _free_bytes()
+    monkeypatch.setenv("SHM_FAIL_ALLOC", site)
+    h = ctypes.c_void_p(0)
+    assert L.shm_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == 2
+    assert h.value is None
+    assert "injected" in L.shm_last_error().decode()
+    assert _free_bytes() >= before - (64 << 20)
+    monkeypatch.delenv("SHM_FAIL_ALLOC")
+    assert L.shm_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    assert L.shm_serve_destroy(h) == 0
+
+
+def test_injected_allocation_failure_in_the_tuner(monkeypatch):
+    """The tuner's probe allocation fails: SHM_ENOMEM, the variant choice is
+    unchanged and no probe kernel has run (the choice would otherwise move)."""
+    before = shm.eval_variant(7, torch.float64)
+    monkeypatch.setenv("SHM_FAIL_ALLOC", "autotune")
+    with pytest.raises(shm.ShmError) as ei:
+        shm.autotune(7, torch.float64, 1 << 14)
+    assert ei.value.status == 2 and "injected" in str(ei.value)
+    assert shm.eval_variant(7, torch.float64) == before
