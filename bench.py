@@ -52,6 +52,10 @@ HBM_FALLBACK_GBS = 6400.0
 # FP64 pipe instructions per point of the all-binary64 rows at lmax 9
 # (sh_row: DMUL + DFMA, counted by ncu sass__inst_executed_per_opcode).
 STRICT_DP_PER_POINT_L9 = 242
+# binary64 products per point that the rows-tma-emu variants compute on the
+# integer pipes instead (dmul_int, bitwise the DMUL results): the 90 output
+# products s A, s B at lmax 9, and with the scales s = S q another 36.
+EMU_PRODUCTS_L9 = {"rows-tma-emu-o-32": 90, "rows-tma-emu-os-32": 126}
 
 
 def load_peaks():
@@ -340,7 +344,8 @@ def run_gpu(args, rank, world):
     # roofline of the (single) kernel
     variant = shm.eval_variant(LMAX, tdt, strict=strict)
     hybrid = args.dtype == "f64" and "hybrid" in variant
-    dp_pp = HYBRID_DP_PER_POINT_L9 if hybrid else STRICT_DP_PER_POINT_L9
+    emu = EMU_PRODUCTS_L9.get(variant, 0)
+    dp_pp = HYBRID_DP_PER_POINT_L9 if hybrid else STRICT_DP_PER_POINT_L9 - emu
     achieved_tflops = 2.0 * dp_pp * n / (launch_ms * 1e-3) / 1e12
     bytes_per_launch = n * (3 + nh) * es
     achieved_gbs = bytes_per_launch / (launch_ms * 1e-3) / 1e9
@@ -363,7 +368,7 @@ def run_gpu(args, rank, world):
                    "timing": {"mean_ms_per_launch": launch_ms, "median_ms_per_launch": statistics.median(per),
                               "cuda_graph_replay": graph}},
         "roofline": roofline_object(args.dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src,
-                                    traffic, fp64),
+                                    traffic, fp64, emu, n, launch_ms),
         "gpu_launches": args.steps,
         "clocks": clk,
         "kernel_ms": launch_ms,
@@ -405,7 +410,8 @@ def run_gpu(args, rank, world):
 
 ARITHMETIC = {
     ("f64", False): "binary64 throughout (SHM_STRICT_FP64): IEEE double multiply and fused multiply-add, CUDA's "
-                    "binary64 rsqrt",
+                    "binary64 rsqrt; with a rows-tma-emu variant part of the binary64 products are computed on the "
+                    "integer pipes, bitwise equal to the DMUL results (shm_probe_dmul; GPU tests)",
     ("f64", True): "FP64 out, float-float arithmetic: binary64 for 1/r and the m = 0, 1 columns, float-float "
                    "(2 x FP32, ~48-bit significand) for the m >= 2 columns (72 of 100 values); within 1e-13 of "
                    "the l-shell norm of the FP64 oracle",
@@ -430,12 +436,15 @@ TRAFFIC_PER_POINT = {
 HYBRID_DP_PER_POINT_L9 = 74
 
 
-def roofline_object(dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src, traffic, fp64):
+def roofline_object(dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_peak, peaks_src, traffic, fp64,
+                    emu=0, n=0, launch_ms=0.0):
     """The bound of the evaluator kernel: the all-binary64 rows are FP64-pipe
-    bound (242 FP64 instructions per point against 824 B per point: 3.1 ms
-    at the measured FP64 rate against 0.9 ms of HBM); the hybrid rows (74 FP64
-    instructions per point) and the FP32 rows are bound by the HBM traffic of
-    their output.  The other figure is given beside it."""
+    bound (242 FP64 instructions per point against 824 B per point: 3.4 ms
+    at the measured FP64 rate against 0.9 ms of HBM); `achieved` counts the
+    FP64 instructions the kernel executes (242 less the products it moves to
+    the integer pipes).  The hybrid rows (74 FP64 instructions per point) and
+    the FP32 rows are bound by the HBM traffic of their output.  The other
+    figure is given beside it."""
     fp = {"achieved": achieved_tflops, "peak": fp64["tflops"], "unit": "TFLOP/s",
           "frac": achieved_tflops / fp64["tflops"],
           "def": f"{dp_pp} FP64 pipe instructions per point x 2 (FMA-equivalent flops) x points / mean launch time",
@@ -443,8 +452,15 @@ def roofline_object(dtype, hybrid, dp_pp, achieved_tflops, achieved_gbs, hbm_pea
     hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
            "def": "algorithmic bytes (points in + rows out) / mean launch time", "peak_source": peaks_src}
     if dtype == "f64" and not hybrid:
-        return {"bound": "alu", "pipe": "fp64", **{k: fp[k] for k in ("achieved", "peak", "unit", "frac")},
-                "traffic": traffic, "achieved_def": fp["def"], "peak_source": fp["peak_source"], "hbm": hbm}
+        out = {"bound": "alu", "pipe": "fp64", **{k: fp[k] for k in ("achieved", "peak", "unit", "frac")},
+               "traffic": traffic, "achieved_def": fp["def"], "peak_source": fp["peak_source"], "hbm": hbm}
+        if emu:
+            eq = 2.0 * STRICT_DP_PER_POINT_L9 * n / (launch_ms * 1e-3) / 1e12
+            out["integer_pipe_products"] = {
+                "per_point": emu, "note": "binary64 products computed on the integer pipes (dmul_int), bitwise the "
+                                          "DMUL results; not counted in `achieved`",
+                "binary64_equivalent_tflops": eq, "binary64_equivalent_frac_of_fp64_peak": eq / fp64["tflops"]}
+        return out
     out = {"bound": "hbm", **{k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}, "traffic": traffic,
            "achieved_def": hbm["def"], "peak_source": peaks_src}
     if dtype == "f64":

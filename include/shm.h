@@ -168,7 +168,9 @@ const char* shm_eval_variant_ex(int lmax, shm_dtype dtype, unsigned flags);
 /* Number of launch variants, and pinning one of them (0 .. count-1) for
  * (lmax, dtype) in this process; variant -1 restores the default choice.
  * _ex with SHM_STRICT_FP64 pins the choice of strict calls and accepts only
- * all-binary64 variants (staged-*, direct-*, phased-64/128, rows-tma-*).
+ * all-binary64 variants (staged-*, direct-*, phased-64/128, rows-tma-*; the
+ * rows-tma-emu-* ones compute part of their binary64 products on the integer
+ * pipes, bitwise the FP64 instructions' results, see shm_probe_dmul).
  * Errors: SHM_EINVAL. */
 int shm_eval_variant_count(void);
 shm_status shm_eval_set_variant(int lmax, shm_dtype dtype, int variant);
@@ -516,6 +518,19 @@ int shm_num_spinors(int lmax);
  * so it must not run during stream capture; nothing is allocated.
  * Errors: SHM_EINVAL (iters outside 1..2^24, null result), SHM_ECUDA. */
 shm_status shm_probe_fp64_rate(int64_t iters, double* dfma_per_s, double* ms);
+
+/* Diagnostics: checks the library's binary64 multiplication on the integer
+ * pipes (used by the rows-tma-emu-* variants of SHM_STRICT_FP64) against the
+ * GPU's DMUL instruction on n operand pairs generated from `seed` (random
+ * significands over most of the normal range, exact ties, all-ones
+ * significands, products at the edges of the normal range, zeros and
+ * subnormals).  *mismatches receives the pairs where the two results differ
+ * in any bit (0 expected), *declined the pairs outside the emulation's range
+ * (zero, subnormal or non-finite operands or results), which the row code
+ * hands to the FP64 instructions.  Synchronises the device; nothing is
+ * allocated.  Errors: SHM_EINVAL (n outside 0..2^40, null results),
+ * SHM_ECUDA. */
+shm_status shm_probe_dmul(int64_t n, uint64_t seed, int64_t* mismatches, int64_t* declined);
 
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* shm_last_error(void);

@@ -8,7 +8,7 @@ from ._binding import (LMAX_CAP, SHM_F32, SHM_F64, ShmError, autotune, check, ev
                        eval_complex, eval_spinor, num_spinors, eval_host,
                        eval_host_workspace_size, eval_sh, eval_variant, eval_variant_count, lib,
                        num_harmonics, set_eval_variant, DeviceProjectors, projectors, projectors_check,
-                       projectors_noalloc, Server, serve_generated_point, probe_fp64_rate,
+                       projectors_noalloc, Server, serve_generated_point, probe_fp64_rate, probe_dmul,
                        SHM_STRICT_FP64, projectors_prepare, projectors_run, projectors_autotune,
                        projectors_variant, projectors_variant_count, set_projectors_variant)
 from . import inputs  # noqa: F401

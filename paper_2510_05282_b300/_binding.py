@@ -84,6 +84,8 @@ def _declare(L):
     L.shm_eval_set_variant_ex.restype = i32
     L.shm_probe_fp64_rate.argtypes = [i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.shm_probe_fp64_rate.restype = i32
+    L.shm_probe_dmul.argtypes = [i64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.shm_probe_dmul.restype = i32
     L.shm_eval_spinor.argtypes = [vp, i64, i32, i32, u32, vp, vp]
     L.shm_eval_spinor.restype = i32
     L.shm_num_spinors.argtypes = [i32]
@@ -232,6 +234,14 @@ def eval_variant(lmax: int, dtype, strict: bool = False) -> str:
 
 def set_eval_variant(lmax: int, dtype, variant: int, strict: bool = False) -> None:
     check(lib().shm_eval_set_variant_ex(int(lmax), _dtype_code(dtype), _flags(False, strict), int(variant)))
+
+
+def probe_dmul(n: int, seed: int = 1):
+    """(mismatches, declined) of the integer-pipe binary64 multiply against
+    the DMUL instruction on n generated operand pairs."""
+    mm, dec = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    check(lib().shm_probe_dmul(int(n), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(mm), ctypes.byref(dec)))
+    return mm.value, dec.value
 
 
 def probe_fp64_rate(iters: int = 1 << 14):

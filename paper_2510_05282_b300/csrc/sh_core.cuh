@@ -155,6 +155,112 @@ __device__ __forceinline__ void sh_row(double xb, double yb, double zb, Store&& 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Binary64 multiplication on the integer pipes.
+//
+// The all-binary64 rows are bound by the FP64 pipe of a B300 (about 2
+// instructions per SM-cycle) while its integer pipes idle.  dmul_int returns
+// the IEEE-754 binary64 product a*b rounded to nearest-even -- the value the
+// DMUL instruction returns, bit for bit -- computed with 32-bit integer
+// multiply-adds, shifts and adds: the exact 106-bit product of the 53-bit
+// significands, then the rounding of IEEE 754-2008 Sec. 4.3.1.  It covers
+// normal operands with a normal product, and sets `bad` for anything else
+// (a zero, subnormal, infinite or NaN operand, or a product that would
+// overflow or be subnormal) without giving a meaningful value: the callers
+// then compute the whole row again with the FP64 instructions.
+//
+// With ma, mb the significands (2^52 <= ma, mb < 2^53) split into 21 + 32
+// bits, P = ma mb (2^104 <= P < 2^106) is accumulated in three 64-bit partial
+// sums (four 32x32 -> 64-bit multiply-adds): P = t3 2^64 + lo(t2) 2^32 +
+// lo(p0).  The significand of the result is P >> s, s = 52 + (P >= 2^105);
+// the round bit is bit s-1 of P, the sticky bit the OR of the bits below it;
+// round up when round && (sticky || the significand is odd).  The biased
+// exponent is ea + eb - 1023 + (s - 52); adding the significand (with its
+// implicit bit 52) and the round-up to (exponent - 1) << 52 carries into the
+// exponent by itself when the rounding reaches 2^53.
+__device__ __forceinline__ double dmul_int(double a, double b, unsigned& bad) {
+  const unsigned ah = (unsigned)__double2hiint(a), al = (unsigned)__double2loint(a);
+  const unsigned bh = (unsigned)__double2hiint(b), bl = (unsigned)__double2loint(b);
+  const unsigned ea = (ah >> 20) & 0x7ffu, eb = (bh >> 20) & 0x7ffu;
+  const unsigned mah = (ah & 0xfffffu) | 0x100000u, mbh = (bh & 0xfffffu) | 0x100000u;
+  const unsigned long long p0 = (unsigned long long)al * bl;
+  const unsigned long long t1 = (unsigned long long)mah * bl + (p0 >> 32);
+  const unsigned long long t2 = (unsigned long long)al * mbh + (t1 & 0xffffffffull);
+  const unsigned long long t3 = (unsigned long long)mah * mbh + (t1 >> 32) + (t2 >> 32);
+  const unsigned mid = (unsigned)t2, low = (unsigned)p0;
+  const unsigned top = (unsigned)(t3 >> 41);  // 1 when P >= 2^105
+  const unsigned sh = 20u + top;               // s - 32: the shift of the middle word
+  const unsigned long long M = (t3 << (32u - sh)) | (unsigned long long)(mid >> sh);
+  const unsigned round = (mid >> (sh - 1u)) & 1u;
+  const unsigned sticky = (mid & ((1u << (sh - 1u)) - 1u)) | low;
+  const unsigned inc = round & (((sticky != 0u) ? 1u : 0u) | (unsigned)(M & 1ull));
+  const int e = (int)ea + (int)eb - 1023 + (int)top;  // biased exponent of the result
+  bad |= ((ea - 1u) >= 2046u) | ((eb - 1u) >= 2046u) | ((unsigned)(e - 1) >= 2045u);
+  const unsigned long long r = ((unsigned long long)(unsigned)(e - 1) << 52) + M + inc;
+  return __longlong_as_double((long long)(r | ((unsigned long long)((ah ^ bh) & 0x80000000u) << 32)));
+}
+
+// sh_row<LMAX>(double...) with some of its products computed by dmul_int:
+// the same binary64 operations on the same operands, so the same bits when
+// `bad` stays 0.  EMU selects the products by role (bit mask):
+//   kEmuOut   -- the products that leave as harmonics: s A, s B and S A, S B;
+//   kEmuScale -- the scales s = S_lm Qh (and S zb at l = m + 1), m >= 1;
+//   kEmuRec   -- G_lm Qh_{l-2} inside the recurrences, m >= 1;
+//   kEmuM0    -- the products of the m = 0 column (its scales and G Qh).
+// Every product dmul_int cannot do exactly raises `bad`; the caller then
+// recomputes the row with sh_row (a point with a zero or subnormal power of
+// x + iy, for instance on an axis, takes that path).
+enum : int { kEmuOut = 1, kEmuScale = 2, kEmuRec = 4, kEmuM0 = 8 };
+
+template <int LMAX, int EMU, typename Store>
+__device__ __forceinline__ unsigned sh_row_emu(double xb, double yb, double zb, Store&& store) {
+  unsigned bad = 0u;
+  auto mul = [&](bool emu, double a, double b) { return emu ? dmul_int(a, b, bad) : a * b; };
+  constexpr bool OUT = (EMU & kEmuOut) != 0, SCL = (EMU & kEmuScale) != 0, REC = (EMU & kEmuRec) != 0,
+                 M0 = (EMU & kEmuM0) != 0;
+  store(0, Sd<false>(0, 0));
+  if constexpr (LMAX >= 1) {
+    store(2, mul(M0, Sd<false>(1, 0), zb));
+    double q2 = 1.0, q1 = zb;
+#pragma unroll
+    for (int l = 2; l <= LMAX; ++l) {
+      const double q = fma(zb, q1, -mul(M0, SHM_G[l][0], q2));
+      store(l * l + l, mul(M0, Sd<false>(l, 0), q));
+      q2 = q1;
+      q1 = q;
+    }
+  }
+  double A = xb, B = yb;
+#pragma unroll
+  for (int m = 1; m <= LMAX; ++m) {
+    if (m > 1) {
+      const double An = fma(A, xb, -B * yb);
+      const double Bn = fma(A, yb, B * xb);
+      A = An;
+      B = Bn;
+    }
+    store(m * m + 2 * m, mul(OUT, Sd<false>(m, m), A));
+    store(m * m, mul(OUT, Sd<false>(m, m), B));
+    if (m + 1 <= LMAX) {
+      const double s = mul(SCL, Sd<false>(m + 1, m), zb);
+      const int k0 = (m + 1) * (m + 1) + (m + 1);
+      store(k0 + m, mul(OUT, s, A));
+      store(k0 - m, mul(OUT, s, B));
+    }
+    double q2 = 1.0, q1 = zb;
+#pragma unroll
+    for (int l = m + 2; l <= LMAX; ++l) {
+      const double q = fma(zb, q1, -mul(REC, SHM_G[l][m], q2));
+      const double s = mul(SCL, Sd<false>(l, m), q);
+      store(l * l + l + m, mul(OUT, s, A));
+      store(l * l + l - m, mul(OUT, s, B));
+      q2 = q1;
+      q1 = q;
+    }
+  }
+  return bad;
+}
+
 // FP64 row in l-major order: same arithmetic as sh_row<LMAX>(double...) (the
 // same operations on the same operands, so bit-identical results), but the
 // values come out l by l: all (x+iy)^m first, then for each l the next step of

@@ -455,7 +455,11 @@ struct RowsTmaPlan {
 // Odd lmax up to SHM_LMAX_EXT (run-time mirror for the host's variant choice).
 inline bool rows_tma_feasible(int lmax) { return lmax >= 1 && lmax <= SHM_LMAX_EXT && (lmax & 1) == 1; }
 
-template <int LMAX, int TPB, int IN = kInPoints>
+// EMU != 0 (rows-tma-emu-*): the rows of sh_row_emu<LMAX, EMU> -- part of
+// the binary64 products on the integer pipes (dmul_int), bitwise the same
+// values -- and, for a point where dmul_int declines a product, the rows of
+// sh_row written over them.
+template <int LMAX, int TPB, int IN = kInPoints, int EMU = 0>
 __global__ void __launch_bounds__(TPB) k_eval_rows_tma(const double* __restrict__ in, int64_t n, int64_t ntiles,
                                                        int normalized, const __grid_constant__ CUtensorMap map_a,
                                                        const __grid_constant__ CUtensorMap map_b) {
@@ -508,6 +512,8 @@ __global__ void __launch_bounds__(TPB) k_eval_rows_tma(const double* __restrict_
       store(0, kInvSqrt4Pi);
 #pragma unroll
       for (int k = 1; k < Plan::L2; ++k) store(k, __longlong_as_double(0x7ff8000000000000ll));
+    } else if constexpr (EMU != 0) {
+      if (sh_row_emu<LMAX, EMU>(xb, yb, zb, store)) sh_row<LMAX>(xb, yb, zb, store);
     } else {
       sh_row<LMAX>(xb, yb, zb, store);
     }
@@ -537,7 +543,7 @@ __global__ void __launch_bounds__(TPB) k_eval_rows_tma(const double* __restrict_
 // SHM_OK when TMA does not apply (even lmax, output not 16-byte aligned,
 // n >= 2^31, or no driver entry point): the caller then runs a copy-out
 // kernel with the same rows.
-template <int LMAX, int TPB, int IN>
+template <int LMAX, int TPB, int IN, int EMU = 0>
 inline shm_status launch_rows_tma(const double* in, int64_t n, double* out, bool normalized, cudaStream_t stream,
                                   bool* launched) {
   *launched = false;
@@ -551,7 +557,7 @@ inline shm_status launch_rows_tma(const double* in, int64_t n, double* out, bool
     static int blocks_per_sm[MAXDEV] = {0};
     const int dev = current_device();
     if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
-    auto kern = k_eval_rows_tma<LMAX, TPB, IN>;
+    auto kern = k_eval_rows_tma<LMAX, TPB, IN, EMU>;
     const size_t smem = Plan::smem_bytes(TPB);
     if (blocks_per_sm[dev] == 0) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

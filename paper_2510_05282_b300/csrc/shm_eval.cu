@@ -72,11 +72,26 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
 // rows leaving by TMA tensor stores).  kRowsTma (FP64): k_eval_rows_tma of
 // sh_tma.cuh (all-binary64 rows, whole rows staged and sent by TMA tensor
 // stores).  For FP32 these variants are the staged path.
-enum { kPhased = 2, kPhasedHybrid = 4, kPhasedHybridTma = 5, kPhasedHybridTma2 = 6, kRowsTma = 7 };
+// kRowsTmaEmu* (FP64): k_eval_rows_tma with part of the binary64 products on
+// the integer pipes (dmul_int: bitwise the FP64 instruction's results).
+enum {
+  kPhased = 2,
+  kPhasedHybrid = 4,
+  kPhasedHybridTma = 5,
+  kPhasedHybridTma2 = 6,
+  kRowsTma = 7,
+  kRowsTmaEmuO = 8,  // output products
+  kRowsTmaEmuOS = 9  // + scales
+};
 
-// Store paths whose FP64 rows are computed entirely in binary64 (sh_row,
-// sh_row_lmajor): the variants SHM_STRICT_FP64 may run.
-constexpr bool strict_path(int p) { return p == kStaged || p == kDirect || p == kPhased || p == kRowsTma; }
+constexpr bool rows_tma_path(int p) { return p == kRowsTma || p == kRowsTmaEmuO || p == kRowsTmaEmuOS; }
+constexpr int emu_mask(int p) {
+  return p == kRowsTmaEmuO ? kEmuOut : (p == kRowsTmaEmuOS ? (kEmuOut | kEmuScale) : 0);
+}
+
+// Store paths whose FP64 rows are computed entirely in binary64 arithmetic
+// (sh_row, sh_row_lmajor, sh_row_emu): the variants SHM_STRICT_FP64 may run.
+constexpr bool strict_path(int p) { return p == kStaged || p == kDirect || p == kPhased || rows_tma_path(p); }
 
 // Launch variants the tuner chooses among (index = variant id).
 struct Variant {
@@ -86,7 +101,7 @@ constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},
                                  {kDirect, 256}, {kPhased, 64}, {kPhased, 128}, {kHybrid, 64},
                                  {kHybrid, 128}, {kHybrid, 256}, {kPhasedHybrid, 64}, {kPhasedHybrid, 128},
                                  {kPhasedHybridTma, 128}, {kPhasedHybridTma2, 128}, {kRowsTma, 64},
-                                 {kRowsTma, 32}};
+                                 {kRowsTma, 32}, {kRowsTmaEmuO, 32}, {kRowsTmaEmuOS, 32}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // For FP32 the phased and hybrid variants run the staged-64 kernel (FP32 rows
@@ -98,7 +113,7 @@ inline size_t variant_smem(int v, int lmax, size_t es) {
   const int p = kVariants[v].path, tpb = kVariants[v].tpb;
   if (p == kDirect) return 0;
   if (p == kPhasedHybridTma2) return (size_t)2 * tpb * 20 * 8 + 128;
-  if (p == kRowsTma) return (size_t)tpb * L2 * 8 + 128;
+  if (rows_tma_path(p)) return (size_t)tpb * L2 * 8 + 128;
   if (p == kPhased || p == kPhasedHybrid || p == kPhasedHybridTma) {
     int w = 0, mx = 0;  // LPhases<LMAX>::max_width()
     for (int l = 0; l <= lmax; ++l) {
@@ -123,11 +138,12 @@ inline int effective_variant(bool fp64, int v, int lmax = 0) {
   const int p = kVariants[v].path;
   if (!fp64) {
     v = (p == kPhased || p == kHybrid || p == kPhasedHybrid || p == kPhasedHybridTma || p == kPhasedHybridTma2 ||
-         p == kRowsTma)
+         rows_tma_path(p))
             ? 1
             : v;
-  } else if (p == kRowsTma && !rows_tma_feasible(lmax)) {
+  } else if (rows_tma_path(p) && !rows_tma_feasible(lmax)) {
     v = 1;  // staged-64: the same all-binary64 rows with the copy-out loop
+
   } else if (p == kPhasedHybridTma && !tma_plan_feasible(lmax)) {
     v = lmax > SHM_LMAX_CAP ? 6 : 11;
   } else if (p == kPhasedHybridTma2 && !(lmax == 3 || lmax == 5 || lmax == 7 || lmax == 9)) {
@@ -152,13 +168,15 @@ inline int effective_variant(bool fp64, int v, int lmax = 0) {
 // At l = 5 and 7 the double-buffered TMA form is faster (0.63 / 0.88 ms
 // against 0.64 / 0.93 ms on the 192^3 grid); at l = 9 its six phases cost
 // more in barriers than the waits they save (1.99 against 1.30 ms).
-// With SHM_STRICT_FP64 the FP64 rows are all-binary64: rows-tma-32 by
-// default (staged-64 at even lmax, where the row pitch rules TMA out);
-// measured on the 192^3 grid at l = 9: rows-tma-32 3.41 ms, rows-tma-64
-// 3.47, phased-64 3.48, staged-64 3.63, staged-128 4.08, direct-128 17.6.
+// With SHM_STRICT_FP64 the FP64 rows are all-binary64: rows-tma-emu-o-32 by
+// default (the output products on the integer pipes; staged-64 at even
+// lmax, where the row pitch rules TMA out); measured on the 192^3 grid at
+// l = 9: rows-tma-emu-o-32 2.57 ms, rows-tma-emu-os-32 2.91, rows-tma-32
+// 3.41, rows-tma-64 3.47, phased-64 3.48, staged-64 3.63, staged-128 4.08,
+// direct-128 17.6.
 constexpr int kDefaultVariantF64 = 12;
 constexpr int kDefaultVariantF32 = 1;
-constexpr int kDefaultVariantStrict = 15;
+constexpr int kDefaultVariantStrict = 16;
 inline int default_variant(bool fp64, int lmax = 9, bool strict = false) {
   if (fp64 && strict) return kDefaultVariantStrict;
   return fp64 ? ((lmax == 5 || lmax == 7) ? 13 : kDefaultVariantF64) : kDefaultVariantF32;
@@ -175,7 +193,7 @@ int g_choice[3][SHM_LMAX_EXT + 1] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1
 
 template <typename T, int LMAX, int TPB, int PATH>
 size_t eval_smem_bytes() {
-  if (PATH == kRowsTma) return RowsTmaPlan<LMAX>::smem_bytes(TPB);
+  if (rows_tma_path(PATH)) return RowsTmaPlan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhasedHybridTma2) return Tma2Plan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhasedHybridTma) return TmaPlan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhased || PATH == kPhasedHybrid)
@@ -220,11 +238,12 @@ shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool 
     }
     return eval_launch_v<T, LMAX, TPB, kPhasedHybridTma>(pts, n, out, normalized, vec, stream);
   }
-  if constexpr (PATH == kRowsTma) {
+  if constexpr (rows_tma_path(PATH)) {
     if constexpr (sizeof(T) == 8) {
       bool launched = false;
       if (vec) {
-        shm_status st = launch_rows_tma<LMAX, TPB, kInPoints>(pts, n, out, normalized, stream, &launched);
+        shm_status st =
+            launch_rows_tma<LMAX, TPB, kInPoints, emu_mask(PATH)>(pts, n, out, normalized, stream, &launched);
         if (st != SHM_OK || launched) return st;
       }
     }
@@ -270,6 +289,8 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
       case 6: return eval_launch_v<T, LMAX, 128, kPhased>(pts, n, out, normalized, vec, s);
       case 14: return eval_launch_v<T, LMAX, 64, kRowsTma>(pts, n, out, normalized, vec, s);
       case 15: return eval_launch_v<T, LMAX, 32, kRowsTma>(pts, n, out, normalized, vec, s);
+      case 16: return eval_launch_v<T, LMAX, 32, kRowsTmaEmuO>(pts, n, out, normalized, vec, s);
+      case 17: return eval_launch_v<T, LMAX, 32, kRowsTmaEmuOS>(pts, n, out, normalized, vec, s);
     }
     return fail(SHM_EINVAL, "unknown launch variant");
   }
@@ -290,6 +311,8 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
     case 13: return eval_launch_v<T, LMAX, 128, kPhasedHybridTma2>(pts, n, out, normalized, vec, s);
     case 14: return eval_launch_v<T, LMAX, 64, kRowsTma>(pts, n, out, normalized, vec, s);
     case 15: return eval_launch_v<T, LMAX, 32, kRowsTma>(pts, n, out, normalized, vec, s);
+    case 16: return eval_launch_v<T, LMAX, 32, kRowsTmaEmuO>(pts, n, out, normalized, vec, s);
+    case 17: return eval_launch_v<T, LMAX, 32, kRowsTmaEmuOS>(pts, n, out, normalized, vec, s);
   }
   return fail(SHM_EINVAL, "unknown launch variant");
 }
@@ -477,7 +500,8 @@ namespace {
 const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64",  "staged-256", "direct-128", "direct-256",
                                            "phased-64",  "phased-128", "hybrid-64",  "hybrid-128", "hybrid-256",
                                            "phased-hybrid-64", "phased-hybrid-128", "phased-hybrid-tma-128",
-                                           "phased-hybrid-tma2-128", "rows-tma-64", "rows-tma-32"};
+                                           "phased-hybrid-tma2-128", "rows-tma-64", "rows-tma-32",
+                                           "rows-tma-emu-o-32", "rows-tma-emu-os-32"};
 
 std::mutex g_tune_mu;
 bool g_cache_loaded = false;

@@ -145,7 +145,7 @@ def test_projector_noalloc_reports_the_bad_field_first(L):
 def test_strict_flag_host_side(L):
     """SHM_STRICT_FP64 selects a separate choice of launch variant: only the
     all-binary64 ones may be pinned for it; unknown flag bits are refused."""
-    assert L.shm_eval_variant_ex(9, 1, 2).decode() == "rows-tma-32"
+    assert L.shm_eval_variant_ex(9, 1, 2).decode() == "rows-tma-emu-o-32"
     assert L.shm_eval_variant_ex(8, 1, 2).decode() == "staged-64"       # even lmax: no TMA row pitch
     assert "hybrid" in L.shm_eval_variant_ex(9, 1, 0).decode()
     assert L.shm_eval_variant_ex(9, 0, 2).decode() == "staged-64"       # FP32 ignores the flag

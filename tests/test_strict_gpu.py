@@ -19,7 +19,7 @@ from paper_2510_05282_b300 import inputs  # noqa: E402
 
 STAGED_128 = 0
 STRICT_VARIANTS = ("staged-128", "staged-64", "staged-256", "direct-128", "direct-256", "phased-64", "phased-128",
-                   "rows-tma-64", "rows-tma-32")
+                   "rows-tma-64", "rows-tma-32", "rows-tma-emu-o-32", "rows-tma-emu-os-32")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -93,7 +93,7 @@ def test_every_strict_variant_is_bitwise_the_same(lmax):
             assert _same(out, ref), name
     finally:
         shm.set_eval_variant(lmax, torch.float64, -1, strict=True)
-    assert "staged-64" in seen and len(seen) >= 7
+    assert "staged-64" in seen and len(seen) >= (9 if lmax % 2 else 7)
 
 
 def test_strict_flag_does_not_change_the_default_rows():
@@ -243,3 +243,43 @@ def test_strict_angles(oracle_mod, lmax):
     shm.eval_angles(torch.from_numpy(ang).cuda(), lmax, out=out, strict=True)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), got)
+
+
+def test_integer_pipe_multiply_is_bitwise_dmul():
+    """dmul_int, the binary64 product on the integer pipes, against the DMUL
+    instruction on 2^26 generated pairs (ties, all-ones significands, the
+    edges of the normal range, zeros and subnormals among them): every
+    product it returns is DMUL's bit for bit, and it declines the operands
+    outside its range (which the rows then compute with DMUL)."""
+    mismatches, declined = shm.probe_dmul(1 << 26, seed=2025)
+    assert mismatches == 0
+    assert 0 < declined < (1 << 26) // 4
+
+
+@pytest.mark.parametrize("lmax", [1, 3, 5, 7, 9, 11, 15])
+def test_emulated_product_variants_on_awkward_points(oracle_mod, lmax):
+    """The rows-tma-emu variants on points whose rows contain exact zeros
+    (axes, x = y diagonals), tiny and huge radii and powers of x + iy that
+    underflow (y ~ 1e-200): bitwise the all-FP64 rows, through the per-point
+    fallback where the integer multiply declines."""
+    pts = np.concatenate([_points(5000), inputs.edge_points(),
+                          np.array([[1.0, 1.0, 0.3], [2.0, -2.0, 1.0], [1.0, 1e-200, 0.5], [1e-160, 1.0, 1e-170],
+                                    [3.0, 0.0, 0.0], [0.0, 0.0, 7.0], [1e-300, 1e-300, 1e-300]])])
+    p = torch.from_numpy(pts).cuda()
+    ref = _staged128(p, lmax)
+    try:
+        for name in ("rows-tma-emu-o-32", "rows-tma-emu-os-32"):
+            for i in range(shm.eval_variant_count()):
+                try:
+                    shm.set_eval_variant(lmax, torch.float64, i, strict=True)
+                except shm.ShmError:
+                    continue
+                if shm.eval_variant(lmax, torch.float64, strict=True) == name:
+                    break
+            assert shm.eval_variant(lmax, torch.float64, strict=True) == name
+            out = torch.full_like(ref, 3.0)
+            shm.eval_sh(p, lmax, out=out, strict=True)
+            torch.cuda.synchronize()
+            assert _same(out, ref), name
+    finally:
+        shm.set_eval_variant(lmax, torch.float64, -1, strict=True)
