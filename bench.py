@@ -643,6 +643,26 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
                          "frac": gbs / hbm_peak, "peak_source": peaks_src, "algorithmic_bytes": algo_bytes,
                          "def": "values x element size + 4 B grid index per point, / mean launch time"}}
         del out, ws
+    # FP64 with SHM_STRICT_FP64: binary64 tables, log-grid index and rows
+    ws = d.workspace(torch.float64)
+    out = torch.empty(d.n_values, dtype=torch.float64, device="cuda")
+    shm.projectors_prepare(d, torch.float64, ws, stream=stream, strict=True)
+    fn = lambda: shm.projectors_run(d, torch.float64, out, ws, stream=stream)  # noqa: E731
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    per, _ = timed_launches(fn, max(5, min(args.steps, 30)), stream)
+    ms = statistics.mean(per)
+    algo_bytes = d.n_values * 8 + d.n_points * 4
+    gbs = algo_bytes / (ms * 1e-3) / 1e9
+    res["projectors_512atoms_fp64_strict"] = {
+        "value": d.n_values / (ms * 1e-3), "unit": "projector values/s", "ms_per_call": ms,
+        "launches_per_call": 1, "error_bits": shm.projectors_check(ws, stream=stream),
+        "arithmetic": "binary64 throughout (SHM_STRICT_FP64)",
+        "roofline": {"bound": "alu", "pipe": "fp64", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
+                     "hbm_frac": gbs / hbm_peak, "unit": "GB/s", "peak_source": peaks_src,
+                     "algorithmic_bytes": algo_bytes}}
+    del out, ws
     # the oracle on the same problem (all host cores): the CPU baseline of this workload
     import oracle
     oracle.build()

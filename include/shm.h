@@ -230,9 +230,14 @@ size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dty
  * 1,024 table values up to the SM count -- for SHM_F32 they convert the
  * radial tables, for SHM_F64 they write each table interval's interpolating
  * cubic --, then the persistent launch).
- *   dtype     : SHM_F64 (FP64 arithmetic, double out; the 4-point Lagrange
- *               interpolation evaluated as the interval's cubic in the
- *               fractional index, the same polynomial up to rounding) or
+ *   dtype     : SHM_F64 (double out; binary64 for the displacement, r^2, 1/r
+ *               and the unit vector, float-float (two FP32 numbers, ~48-bit
+ *               significand) for the log-grid index, the radial cubic and
+ *               the rows of lmax <= 4, hybrid rows above: within 1e-13 of
+ *               F_sl sqrt((2l+1)/4pi); all-binary64 with shm_projectors_ex
+ *               and SHM_STRICT_FP64; the 4-point Lagrange interpolation
+ *               evaluated as the interval's cubic in the fractional index,
+ *               the same polynomial up to rounding) or
  *               SHM_F32 (FP32 arithmetic on FP32 copies of the tables, float
  *               out; grid displacements are formed exactly before rounding to
  *               float, 1/r in FP64 for |d| < 1e-2).
@@ -252,6 +257,15 @@ size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dty
 shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
                           size_t workspace_bytes, void* stream);
 
+/* shm_projectors with flags.  SHM_STRICT_FP64 (SHM_F64; ignored for SHM_F32):
+ * every value in binary64 arithmetic -- the interval cubics kept and
+ * evaluated in binary64 (Horner), the log-grid index from CUDA's binary64 log
+ * of |d|^2, the all-binary64 harmonic rows of shm_eval_ex with the flag, and
+ * one binary64 product f_l x R_l^m per value -- instead of the default FP64
+ * form's float-float log, cubics and short rows.  Other bits: SHM_EINVAL. */
+shm_status shm_projectors_ex(const shm_proj_problem* prob, shm_dtype dtype, unsigned flags, void* out,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
 /*
  * shm_projectors_prepare -- the per-problem set-up of shm_projectors, done
  * once: one launch on `stream` that validates every atom's offsets and
@@ -266,6 +280,11 @@ shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* o
  */
 shm_status shm_projectors_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* workspace,
                                   size_t workspace_bytes, void* stream);
+
+/* shm_projectors_prepare with flags (SHM_STRICT_FP64 as for shm_projectors_ex);
+ * the runs of the workspace then use that arithmetic. */
+shm_status shm_projectors_prepare_ex(const shm_proj_problem* prob, shm_dtype dtype, unsigned flags, void* workspace,
+                                     size_t workspace_bytes, void* stream);
 
 /*
  * shm_projectors_run -- the projector values on a prepared workspace: ONE

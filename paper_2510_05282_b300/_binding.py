@@ -297,6 +297,10 @@ _EXTRA_DECLS.extend([
                                 ctypes.c_int)),
     ("shm_projectors_prepare", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                  ctypes.c_void_p], ctypes.c_int)),
+    ("shm_projectors_prepare_ex", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_uint, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int)),
+    ("shm_projectors_ex", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_uint, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int)),
     ("shm_projectors_run", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                              ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int)),
     ("shm_projectors_autotune", ([ctypes.POINTER(_ProjProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -343,23 +347,24 @@ class DeviceProjectors:
         return torch.empty(max(self.workspace_size(dtype), 256), dtype=torch.uint8, device=self.atom_pos.device)
 
 
-def projectors(dprob: DeviceProjectors, dtype, out=None, workspace=None, stream=None):
-    """Fused projector values (flat CSR, [n_values]) of a DeviceProjectors problem."""
+def projectors(dprob: DeviceProjectors, dtype, out=None, workspace=None, stream=None, strict: bool = False):
+    """Fused projector values (flat CSR, [n_values]) of a DeviceProjectors problem
+    (strict: all-binary64 for float64)."""
     import torch
     tdt = torch.float64 if _dtype_code(dtype) == SHM_F64 else torch.float32
     if out is None:
         out = torch.empty(dprob.n_values, dtype=tdt, device=dprob.atom_pos.device)
     if workspace is None:
         workspace = dprob.workspace(dtype)
-    check(lib().shm_projectors(ctypes.byref(dprob.c), _dtype_code(dtype), out.data_ptr(), workspace.data_ptr(),
-                               workspace.numel(), _stream_ptr(stream)))
+    check(lib().shm_projectors_ex(ctypes.byref(dprob.c), _dtype_code(dtype), _flags(False, strict), out.data_ptr(),
+                                  workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)))
     return out
 
 
-def projectors_prepare(dprob: DeviceProjectors, dtype, workspace, stream=None) -> None:
-    """shm_projectors_prepare: the per-problem set-up launch into `workspace`."""
-    check(lib().shm_projectors_prepare(ctypes.byref(dprob.c), _dtype_code(dtype), workspace.data_ptr(),
-                                       workspace.numel(), _stream_ptr(stream)))
+def projectors_prepare(dprob: DeviceProjectors, dtype, workspace, stream=None, strict: bool = False) -> None:
+    """shm_projectors_prepare_ex: the per-problem set-up launch into `workspace`."""
+    check(lib().shm_projectors_prepare_ex(ctypes.byref(dprob.c), _dtype_code(dtype), _flags(False, strict),
+                                          workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)))
 
 
 def projectors_run(dprob: DeviceProjectors, dtype, out, workspace, stream=None):

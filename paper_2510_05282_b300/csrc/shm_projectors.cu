@@ -64,7 +64,8 @@ struct ProjWs {
   size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
   size_t atomf = 0;        // FP32: AtomF32[n_atoms] (atom coordinates in grid units)
   size_t rad32 = 0;        // FP32: float radial[n_species][lstride][n_rad]
-  size_t coef = 0;         // FP64: float-float {a0, a1, a2, a3}[n_species][lstride][n_rad] (cubic per interval)
+  size_t coef = 0;         // FP64: {a0, a1, a2, a3}[n_species][lstride][n_rad] (cubic per interval), float-float
+                           // (32 bytes a node) or, with SHM_STRICT_FP64, binary64 (32 bytes a node)
   size_t hg = 0;           // FP64: double i * h for i < ng (grid coordinates, rounded as the definition)
   size_t total = 0;
 };
@@ -159,7 +160,8 @@ struct ProjParams {
   int2* etab;
   float* rad32;
   AtomF32* atomf;
-  float4* coef;  // two per node: {a0.hi, a0.lo, a1.hi, a1.lo}, {a2.hi, a2.lo, a3.hi, a3.lo}
+  float4* coef;  // two per node: {a0.hi, a0.lo, a1.hi, a1.lo}, {a2.hi, a2.lo, a3.hi, a3.lo}; strict: one double4
+  int strict;    // FP64 with SHM_STRICT_FP64: binary64 tables, log-grid index and rows
   double* hg;
 };
 
@@ -195,6 +197,10 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
       const double b3 = d3 / 6.0, b2 = 0.5 * (d2 - d3), b1 = d1 - 0.5 * d2 + d3 / 3.0;
       const double x0 = (double)(it - i0);
       const double c0 = F[it - i0], c1 = b1 + x0 * (2.0 * b2 + 3.0 * b3 * x0), c2 = b2 + 3.0 * b3 * x0;
+      if (P.strict) {  // the cubic kept in binary64 (the strict rows evaluate it by binary64 Horner)
+        reinterpret_cast<double4*>(P.coef)[i] = make_double4(c0, c1, c2, b3);
+        continue;
+      }
       const ff f0 = ff_from_double(c0), f1 = ff_from_double(c1), f2 = ff_from_double(c2), f3 = ff_from_double(b3);
       P.coef[2 * i] = make_float4(f0.hi, f0.lo, f1.hi, f1.lo);
       P.coef[2 * i + 1] = make_float4(f2.hi, f2.lo, f3.hi, f3.lo);
@@ -455,11 +461,26 @@ __device__ __forceinline__ float interp4(const Lagrange4& L, const float* F) {
 // FP32 row, float-float for the FP64 row), then write f_l(r) R_l^m into
 // row[0..(LMAX+1)^2).  (dx, dy, dz) is the displacement, or with `unit` its
 // unit vector.
-template <int LMAX, typename T, typename Radial>
+// STRICT (FP64): radial(l) returns binary64 f_l and the row is
+// f_l(r) x R_l^m of the all-binary64 sh_row, one binary64 product per value.
+template <int LMAX, bool STRICT = false, typename T, typename Radial>
 __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool unit, Radial&& radial,
                                          T* __restrict__ row) {
   T xb = dx, yb = dy, zb = dz;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (STRICT) {
+    static_assert(sizeof(T) == 8, "strict rows are FP64");
+    double f[LMAX + 1];
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l) f[l] = radial(l);
+    if (origin) {
+      row[0] = kInvSqrt4Pi * f[0];
+#pragma unroll
+      for (int k = 1; k < NH<LMAX>::value; ++k) row[k] = 0.0;
+      return;
+    }
+    if (!unit) unit_dir(dx, dy, dz, xb, yb, zb);
+    sh_row<LMAX>(xb, yb, zb, [&](int k, double v) { row[k] = f[l_of_k(k)] * v; });
+  } else if constexpr (sizeof(T) == 4) {
     float f[LMAX + 1];
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) f[l] = radial(l);
@@ -497,26 +518,30 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool uni
   }
 }
 
-template <typename T, typename Radial>
+template <bool STRICT = false, typename T, typename Radial>
 __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin, bool unit,
                                                   Radial&& L, T* row) {
   switch (lmax) {
-    case 0: proj_row<0>(dx, dy, dz, origin, unit, L, row); break;
-    case 1: proj_row<1>(dx, dy, dz, origin, unit, L, row); break;
-    case 2: proj_row<2>(dx, dy, dz, origin, unit, L, row); break;
-    case 3: proj_row<3>(dx, dy, dz, origin, unit, L, row); break;
-    case 4: proj_row<4>(dx, dy, dz, origin, unit, L, row); break;
-    case 5: proj_row<5>(dx, dy, dz, origin, unit, L, row); break;
-    case 6: proj_row<6>(dx, dy, dz, origin, unit, L, row); break;
-    case 7: proj_row<7>(dx, dy, dz, origin, unit, L, row); break;
-    case 8: proj_row<8>(dx, dy, dz, origin, unit, L, row); break;
-    default: proj_row<9>(dx, dy, dz, origin, unit, L, row); break;
+    case 0: proj_row<0, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    case 1: proj_row<1, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    case 2: proj_row<2, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    case 3: proj_row<3, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    case 4: proj_row<4, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    case 5: proj_row<5, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    case 6: proj_row<6, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    case 7: proj_row<7, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    case 8: proj_row<8, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    default: proj_row<9, STRICT>(dx, dy, dz, origin, unit, L, row); break;
   }
 }
 
 // FP64 row: the displacement is formed exactly as the definition states
 // (grid point i*h minus the atom, then the minimum image), without FMA
 // contraction, so it is the correctly rounded binary64 value of each step.
+// STRICT (SHM_STRICT_FP64): the log-grid index from CUDA's binary64 log of
+// r^2, the interval cubic by binary64 Horner from binary64 coefficients, and
+// the all-binary64 harmonic row times f_l.
+template <bool STRICT = false>
 __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, double ax, double ay, double az,
                                                int s, int lmax, double inv_box, double inv_rmin,
                                                double inv_dlog, const LogGrid64& G, double* row) {
@@ -553,7 +578,10 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
 #pragma unroll
       for (int c = 0; c < 3; ++c) d[c] *= ri;
       unit = true;
-      t = log_grid_index(r2, G);
+      if constexpr (STRICT)
+        t = fma(log(r2), G.K2, G.K0);  // (ln(r^2) / 2 - ln r_min) / dlog
+      else
+        t = log_grid_index(r2, G);
     } else {
       t = log(sqrt(r2) * inv_rmin) * inv_dlog;
     }
@@ -569,16 +597,25 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
     it = 0;  // below the grid, or t = -inf or NaN (u not finite)
     u = 0.0;
   }
-  // f_l(r): the interval's cubic in u by Horner's rule in float-float (FP32
-  // pipe), two 16-byte loads per l
-  const float4* c = P.coef + 2 * ((int64_t)s * P.lstride * P.n_rad + it);
-  const ff U = ff_from_double(u);
-  proj_row_dispatch<double>(lmax, d[0], d[1], d[2], origin, unit, [&](int l) {
-    const float4 a01 = __ldg(c + 2 * (int64_t)l * P.n_rad), a23 = __ldg(c + 2 * (int64_t)l * P.n_rad + 1);
-    ff p = ff_add(ff_mul_u(ff{a23.z, a23.w}, U), ff{a23.x, a23.y});
-    p = ff_add(ff_mul_u(p, U), ff{a01.z, a01.w});
-    return ff_add(ff_mul_u(p, U), ff{a01.x, a01.y});
-  }, row);
+  if constexpr (STRICT) {
+    // f_l(r): the interval's cubic in u by binary64 Horner, one 32-byte node
+    const double4* c = reinterpret_cast<const double4*>(P.coef) + ((int64_t)s * P.lstride * P.n_rad + it);
+    proj_row_dispatch<true, double>(lmax, d[0], d[1], d[2], origin, unit, [&](int l) {
+      const double4 a = c[(int64_t)l * P.n_rad];
+      return fma(fma(fma(a.w, u, a.z), u, a.y), u, a.x);
+    }, row);
+  } else {
+    // f_l(r): the interval's cubic in u by Horner's rule in float-float (FP32
+    // pipe), two 16-byte loads per l
+    const float4* c = P.coef + 2 * ((int64_t)s * P.lstride * P.n_rad + it);
+    const ff U = ff_from_double(u);
+    proj_row_dispatch<false, double>(lmax, d[0], d[1], d[2], origin, unit, [&](int l) {
+      const float4 a01 = __ldg(c + 2 * (int64_t)l * P.n_rad), a23 = __ldg(c + 2 * (int64_t)l * P.n_rad + 1);
+      ff p = ff_add(ff_mul_u(ff{a23.z, a23.w}, U), ff{a23.x, a23.y});
+      p = ff_add(ff_mul_u(p, U), ff{a01.z, a01.w});
+      return ff_add(ff_mul_u(p, U), ff{a01.x, a01.y});
+    }, row);
+  }
 }
 
 // FP32 row.  The displacement in grid units, (i - U) - frac with U = floor of
@@ -646,7 +683,7 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
   }
   const Lagrange4 L = lagrange_at(it, u, P.n_rad);
   const float* tab = P.rad32 + (int64_t)s * P.lstride * P.n_rad + L.i0;
-  proj_row_dispatch<float>(lmax, d[0], d[1], d[2], origin, true,
+  proj_row_dispatch<false, float>(lmax, d[0], d[1], d[2], origin, true,
                            [&](int l) { return interp4(L, tab + (int64_t)l * P.n_rad); }, row);
 }
 
@@ -727,7 +764,7 @@ constexpr int kSmemAtoms = 4096;
 // workspace that does not hold this problem's tables sets error bits instead
 // of reading or writing out of bounds; tile_limit caps the tile count read
 // from the workspace.
-template <typename T, int TILE, int PPT, int MINB>
+template <typename T, int TILE, int PPT, int MINB, bool STRICT = false>
 __global__ void __launch_bounds__(TILE / PPT, MINB) k_proj(ProjParams P, T* __restrict__ out, int tile_bytes,
                                                           int64_t tile_limit, int bulk) {
   constexpr int NT = TILE / PPT;
@@ -807,7 +844,7 @@ __global__ void __launch_bounds__(TILE / PPT, MINB) k_proj(ProjParams P, T* __re
           atomicOr(P.err, kErrGrid);
           for (int k = 0; k < L2; ++k) row[k] = (T)0;
         } else if constexpr (sizeof(T) == 8) {
-          proj_point_f64(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
+          proj_point_f64<STRICT>(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
                          inv_rmin, inv_dlog, G, reinterpret_cast<double*>(row));
         } else {
           const int4* ap = reinterpret_cast<const int4*>(P.atomf + a);
@@ -880,12 +917,13 @@ struct ProjPrepared {
   int variant;
   shm_dtype dtype;
   int64_t n_atoms, n_points, n_values;
+  bool strict;
 };
 std::unordered_map<const void*, ProjPrepared> g_prepared;
 
-template <typename T, int TILE, int PPT, int MINB>
+template <typename T, int TILE, int PPT, int MINB, bool STRICT = false>
 shm_status launch_proj_v(const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, bool bulk, cudaStream_t s) {
-  auto kern = k_proj<T, TILE, PPT, MINB>;
+  auto kern = k_proj<T, TILE, PPT, MINB, STRICT>;
   const int dev = current_device();
   const size_t tile_bytes = proj_tile_bytes(TILE, max_lmax, sizeof(T));
   const size_t smem = tile_bytes + (P.n_atoms + 1 <= kSmemAtoms ? (size_t)(P.n_atoms + 1) * 4 : 0);
@@ -915,6 +953,10 @@ shm_status launch_proj_v(const ProjParams& P, int max_lmax, T* out, int64_t tile
 template <typename T>
 shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, cudaStream_t s) {
   const bool bulk = kProjVariants[variant].bulk;
+  if constexpr (sizeof(T) == 8) {
+    // SHM_STRICT_FP64: one launch shape (the default variant's)
+    if (P.strict) return launch_proj_v<T, 128, 1, 0, true>(P, max_lmax, out, tile_upper, true, s);
+  }
   switch (variant) {
     case 0:
     case 1: return launch_proj_v<T, 128, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
@@ -1021,7 +1063,8 @@ shm_status check_out(const shm_proj_problem* prob, shm_dtype dtype, void* out) {
 
 // The variant a prepare uses: the tuned (or pinned) choice for the dtype if
 // its shared memory fits this problem, else the default.
-int prepare_variant(shm_dtype dtype, int max_lmax, int64_t n_atoms) {
+int prepare_variant(shm_dtype dtype, int max_lmax, int64_t n_atoms, bool strict = false) {
+  if (strict) return kDefaultProjVariant;
   int v;
   {
     std::lock_guard<std::mutex> lk(g_proj_mu);
@@ -1035,20 +1078,21 @@ int prepare_variant(shm_dtype dtype, int max_lmax, int64_t n_atoms) {
 
 // Set-up launch into `workspace` for `variant`, recorded for later runs.
 shm_status prepare_in(const shm_proj_problem* prob, shm_dtype dtype, void* workspace, size_t ws_bytes, int variant,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool strict = false) {
   ProjParams P;
   int max_lmax = 0;
   int64_t tile_upper = 0;
   shm_status st = proj_params(prob, dtype, workspace, ws_bytes, kProjVariants[variant].tile, &P, &max_lmax,
                               &tile_upper);
   if (st != SHM_OK) return st;
+  P.strict = strict ? 1 : 0;
   if (proj_smem(variant, max_lmax, dtype == SHM_F64 ? 8 : 4, prob->n_atoms) > kProjMaxSmem)
     return fail(SHM_EINVAL, "projector tile does not fit in shared memory for this lmax");
   k_proj_setup<<<setup_grid(P, dtype), 1024, 0, s>>>(P, kProjVariants[variant].tile, dtype == SHM_F32 ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
   std::lock_guard<std::mutex> lk(g_proj_mu);
-  g_prepared[workspace] = ProjPrepared{variant, dtype, prob->n_atoms, prob->n_points, prob->n_values};
+  g_prepared[workspace] = ProjPrepared{variant, dtype, prob->n_atoms, prob->n_points, prob->n_values, strict};
   return SHM_OK;
 }
 
@@ -1072,6 +1116,7 @@ shm_status run_in(const shm_proj_problem* prob, shm_dtype dtype, void* out, void
   shm_status st = proj_params(prob, dtype, workspace, ws_bytes, kProjVariants[rec.variant].tile, &P, &max_lmax,
                               &tile_upper);
   if (st != SHM_OK) return st;
+  P.strict = rec.strict ? 1 : 0;
   if ((st = check_out(prob, dtype, out)) != SHM_OK) return st;
   if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
   return dtype == SHM_F64 ? launch_proj<double>(rec.variant, P, max_lmax, (double*)out, tile_upper, s)
@@ -1083,17 +1128,24 @@ void load_proj_tune_cache();
 }  // namespace
 }  // namespace shm
 
-extern "C" shm_status shm_projectors_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* workspace,
-                                             size_t workspace_bytes, void* stream) {
+extern "C" shm_status shm_projectors_prepare_ex(const shm_proj_problem* prob, shm_dtype dtype, unsigned flags,
+                                                void* workspace, size_t workspace_bytes, void* stream) {
   using namespace shm;
   NvtxRange nvtx_range("shm_projectors_prepare");
   clear_error();
   int ml = 0;
   shm_status st = proj_validate(prob, dtype, &ml);
   if (st != SHM_OK) return st;
+  if (flags & ~SHM_STRICT_FP64) return fail(SHM_EINVAL, "unknown flag bits");
+  const bool strict = dtype == SHM_F64 && (flags & SHM_STRICT_FP64) != 0;
   load_proj_tune_cache();
-  return prepare_in(prob, dtype, workspace, workspace_bytes, prepare_variant(dtype, ml, prob->n_atoms),
-                    (cudaStream_t)stream);
+  return prepare_in(prob, dtype, workspace, workspace_bytes, prepare_variant(dtype, ml, prob->n_atoms, strict),
+                    (cudaStream_t)stream, strict);
+}
+
+extern "C" shm_status shm_projectors_prepare(const shm_proj_problem* prob, shm_dtype dtype, void* workspace,
+                                             size_t workspace_bytes, void* stream) {
+  return shm_projectors_prepare_ex(prob, dtype, 0u, workspace, workspace_bytes, stream);
 }
 
 extern "C" shm_status shm_projectors_run(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
@@ -1107,20 +1159,28 @@ extern "C" shm_status shm_projectors_run(const shm_proj_problem* prob, shm_dtype
   return run_in(prob, dtype, out, workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
-extern "C" shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
-                                     size_t workspace_bytes, void* stream) {
+extern "C" shm_status shm_projectors_ex(const shm_proj_problem* prob, shm_dtype dtype, unsigned flags, void* out,
+                                        void* workspace, size_t workspace_bytes, void* stream) {
   using namespace shm;
   NvtxRange nvtx_range("shm_projectors");
   clear_error();
   int ml = 0;
   shm_status st = proj_validate(prob, dtype, &ml);
   if (st != SHM_OK) return st;
+  if (flags & ~SHM_STRICT_FP64) return fail(SHM_EINVAL, "unknown flag bits");
+  const bool strict = dtype == SHM_F64 && (flags & SHM_STRICT_FP64) != 0;
   if ((st = check_out(prob, dtype, out)) != SHM_OK) return st;
   load_proj_tune_cache();
   cudaStream_t s = (cudaStream_t)stream;
-  st = prepare_in(prob, dtype, workspace, workspace_bytes, prepare_variant(dtype, ml, prob->n_atoms), s);
+  st = prepare_in(prob, dtype, workspace, workspace_bytes, prepare_variant(dtype, ml, prob->n_atoms, strict), s,
+                  strict);
   if (st != SHM_OK) return st;
   return run_in(prob, dtype, out, workspace, workspace_bytes, s);
+}
+
+extern "C" shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+  return shm_projectors_ex(prob, dtype, 0u, out, workspace, workspace_bytes, stream);
 }
 
 namespace shm {

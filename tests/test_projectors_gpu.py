@@ -348,3 +348,58 @@ def test_run_on_a_corrupted_workspace_stays_in_bounds():
     shm.projectors_run(d, torch.float64, out, ws)
     torch.cuda.synchronize()
     assert torch.equal(out, ref) and shm.projectors_check(ws) == 0
+
+
+# ------------------------------------------------- all-binary64 projectors (SHM_STRICT_FP64)
+
+def run_strict(prob):
+    d = shm.DeviceProjectors(prob)
+    ws = d.workspace(torch.float64)
+    out = shm.projectors(d, torch.float64, workspace=ws, strict=True)
+    torch.cuda.synchronize()
+    assert shm.projectors_check(ws) == 0
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("prob_kw", [dict(extra=20), dict(extra=21, n_atoms=10, n_species=10,
+                                                          lmax_choices=tuple(range(10))),
+                                     dict(extra=22, n_rad=5, r_min=0.05, r_max=2.5)])
+def test_strict_fp64_projectors(oracle_mod, prob_kw):
+    """Binary64 tables, log-grid index and rows: within the FP64 tolerance of
+    the oracle, tighter than the default FP64 form."""
+    prob = small_problem(**prob_kw)
+    got = run_strict(prob)
+    worst = check(prob, got, oracle_mod.projectors(prob), PROJ_TOL_F64, "strict FP64 projectors")
+    assert worst <= 2e-14
+
+
+def test_strict_fp64_projectors_full_workload(oracle_mod, capsys):
+    prob = inputs.projector_problem()
+    got = run_strict(prob)
+    worst = check(prob, got, oracle_mod.projectors(prob), PROJ_TOL_F64, "strict full workload")
+    with capsys.disabled():
+        print(f"\nstrict FP64 projectors, 512 atoms: max scaled error {worst:.2e}")
+
+
+def test_strict_prepared_runs_and_graph():
+    prob = small_problem(23)
+    d = shm.DeviceProjectors(prob)
+    ws = d.workspace(torch.float64)
+    ref = shm.projectors(d, torch.float64, workspace=ws, strict=True).clone()
+    shm.projectors_prepare(d, torch.float64, ws, strict=True)
+    out = torch.zeros(d.n_values, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        shm.projectors_run(d, torch.float64, out, ws, stream=s)
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    # the default form differs (float-float), within tolerance
+    dflt = shm.projectors(d, torch.float64, workspace=d.workspace(torch.float64))
+    torch.cuda.synchronize()
+    assert not torch.equal(dflt, ref)
