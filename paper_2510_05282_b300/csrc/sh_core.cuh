@@ -684,10 +684,18 @@ __device__ __forceinline__ void sh_row_hybrid(double xb, double yb, double zb, S
 // working on them with FP32 instructions.
 // Ends: the phase plan (ends_phase(l): shell l closes a phase), by default
 // groups of whole shells of at most PHMAX values.
+// EMU (a mask of kEmuScale, kEmuOut): the binary64 products of the m = 0, 1
+// columns -- their scales S q (kEmuScale) and the m = 1 outputs s x, s y
+// (kEmuOut) -- on the integer pipes by dmul_int, the same bits; returns 1
+// when dmul_int declined one of them (the caller then writes the row again
+// with sh_row_hybrid), 0 otherwise and always for EMU = 0.
 template <int LMAX, bool CX = false, int PHMAX = 37, bool NEG_FF = false, typename Ends = LPhases<LMAX, PHMAX>,
-          typename Store, typename Phase>
-__device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, double zb, Store&& store,
-                                                     Phase&& phase) {
+          int EMU = 0, typename Store, typename Phase>
+__device__ __forceinline__ unsigned sh_row_hybrid_lmajor(double xb, double yb, double zb, Store&& store,
+                                                         Phase&& phase) {
+  unsigned bad = 0u;
+  auto mul = [&](bool emu, double a, double b) { return emu ? dmul_int(a, b, bad) : a * b; };
+  constexpr bool ESC = (EMU & kEmuScale) != 0, EOUT = (EMU & kEmuOut) != 0;
   auto store_neg_d = [&](int k, int kbase, double v) {
     if constexpr (NEG_FF)
       store(k, kbase, ff_from_double(v));
@@ -725,20 +733,20 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
           d2[m] = 1.0;
           d1[m] = 1.0;
         } else if (l == m + 1) {
-          s = Sd<CX>(l, m) * zb;
+          s = mul(ESC, Sd<CX>(l, m), zb);
           d2[m] = 1.0;
           d1[m] = zb;
         } else {
           const double q = fma(zb, d1[m], -SHM_G[l][m] * d2[m]);
-          s = Sd<CX>(l, m) * q;
+          s = mul(ESC, Sd<CX>(l, m), q);
           d2[m] = d1[m];
           d1[m] = q;
         }
         if (m == 0) {
           store(kc, k0, s);
         } else {
-          store(kc + 1, k0, (l == 1) ? Sd<CX>(1, 1) * xb : s * xb);
-          store_neg_d(kc - 1, k0, (l == 1) ? Sd<CX>(1, 1) * yb : s * yb);
+          store(kc + 1, k0, mul(EOUT, (l == 1) ? Sd<CX>(1, 1) : s, xb));
+          store_neg_d(kc - 1, k0, mul(EOUT, (l == 1) ? Sd<CX>(1, 1) : s, yb));
         }
       } else {  // float-float columns
         if (l == m) {
@@ -766,6 +774,7 @@ __device__ __forceinline__ void sh_row_hybrid_lmajor(double xb, double yb, doubl
       k0 = (l + 1) * (l + 1);
     }
   }
+  return bad;
 }
 
 // Short FP64 row (LMAX <= 4) entirely in float-float, every value of shell

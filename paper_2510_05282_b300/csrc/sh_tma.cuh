@@ -115,10 +115,16 @@ inline bool tma_plan_feasible(int lmax) {
 // [p0, p0 + TPB) of the output described by map_a / map_b (boxes of
 // TmaPlan::box_a() / box_b() columns by TPB rows; rows past n are clipped by
 // the TMA unit).  `tile` is 128-byte aligned, TPB x max_width() doubles.
-template <int LMAX, int TPB>
+// EMU != 0 (phased-hybrid-tma-emu-128): the binary64 products of the m = 0, 1
+// columns on the integer pipes (sh_row_hybrid_lmajor<..., EMU>, the same
+// bits); a thread whose point made dmul_int decline one writes its row again
+// with sh_row_hybrid, straight to `out`, after the tile's TMA writes have
+// completed (a per-tile vote; no such row in most tiles).
+template <int LMAX, int TPB, int EMU = 0>
 __device__ __forceinline__ void phased_rows_tma(double xb, double yb, double zb, bool origin, int64_t p0,
                                                 double* __restrict__ tile, const CUtensorMap* map_a,
-                                                const CUtensorMap* map_b) {
+                                                const CUtensorMap* map_b, double* __restrict__ out = nullptr,
+                                                bool valid = true) {
   using Plan = TmaPlan<LMAX>;
   const bool bad = nonfinite3(xb, yb, zb);  // NaN row but l = 0 (the hybrid row code needs a finite direction)
   const int t = (int)threadIdx.x;
@@ -153,15 +159,34 @@ __device__ __forceinline__ void phased_rows_tma(double xb, double yb, double zb,
     }
     __syncthreads();
   };
-  sh_row_hybrid_lmajor<LMAX>(xb, yb, zb, store, flush);
+  const unsigned declined =
+      sh_row_hybrid_lmajor<LMAX, false, 37, false, LPhases<LMAX, 37>, EMU>(xb, yb, zb, store, flush);
+  if constexpr (EMU != 0) {
+    const bool redo = declined != 0u && valid && !origin && !bad;
+    if (__syncthreads_or(redo)) {
+      if (t == 0) {  // the tile's TMA writes are complete and visible before the overwrite
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+      }
+      __syncthreads();
+      if (redo) {
+        double* row = out + (p0 + t) * Plan::L2;
+        sh_row_hybrid<LMAX>(xb, yb, zb, [&](int k, double v) { row[k] = v; });
+      }
+    }
+  }
 }
 
-// Registers capped as k_eval_phased (five 128-thread CTAs per SM).
-template <int LMAX, int TPB, int IN = kInPoints>
+// Registers capped as k_eval_phased (five 128-thread CTAs per SM).  With
+// EMU the integer products spill at l = 9 (96 registers: 300 bytes of spill
+// loads per thread; still 92 bytes at a 128-register cap), so the integer
+// form pays at l = 5 only.
+template <int LMAX, int TPB, int IN = kInPoints, int EMU = 0>
 __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased_tma(const double* __restrict__ in, int64_t n,
                                                                     int64_t ntiles, int normalized,
                                                                     const __grid_constant__ CUtensorMap map_a,
-                                                                    const __grid_constant__ CUtensorMap map_b) {
+                                                                    const __grid_constant__ CUtensorMap map_b,
+                                                                    double* __restrict__ out) {
   static_assert(TmaPlan<LMAX>::feasible(), "no TMA phase plan for this lmax");
   extern __shared__ unsigned char smem_tma[];
   // TMA needs 128-byte aligned shared addresses: round the base up (the
@@ -197,7 +222,7 @@ __global__ void __launch_bounds__(TPB, 640 / TPB) k_eval_phased_tma(const double
         }
       }
     }
-    phased_rows_tma<LMAX, TPB>(xb, yb, zb, origin, p0, tile, &map_a, &map_b);
+    phased_rows_tma<LMAX, TPB, EMU>(xb, yb, zb, origin, p0, tile, &map_a, &map_b, out, valid);
   }
   // the last stores' global writes complete before the CTA retires
   if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -389,7 +414,7 @@ inline shm_status launch_phased_tma2(const double* in, int64_t n, double* out, b
 // *launched = false with SHM_OK when TMA does not apply (no plan for LMAX,
 // output not 16-byte aligned, n >= 2^31, or no driver entry point): the
 // caller then runs k_eval_phased.
-template <int LMAX, int TPB, int IN>
+template <int LMAX, int TPB, int IN, int EMU = 0>
 inline shm_status launch_phased_tma(const double* in, int64_t n, double* out, bool normalized, cudaStream_t stream,
                              bool* launched) {
   *launched = false;
@@ -403,7 +428,7 @@ inline shm_status launch_phased_tma(const double* in, int64_t n, double* out, bo
     static int blocks_per_sm[MAXDEV] = {0};
     const int dev = current_device();
     if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
-    auto kern = k_eval_phased_tma<LMAX, TPB, IN>;
+    auto kern = k_eval_phased_tma<LMAX, TPB, IN, EMU>;
     const size_t smem = Plan::smem_bytes(TPB);
     if (blocks_per_sm[dev] == 0) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -415,7 +440,7 @@ inline shm_status launch_phased_tma(const double* in, int64_t n, double* out, bo
     }
     const int64_t ntiles = (n + TPB - 1) / TPB;
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(dev) * blocks_per_sm[dev]);
-    kern<<<(unsigned)grid, TPB, smem, stream>>>(in, n, ntiles, normalized ? 1 : 0, ma, mb);
+    kern<<<(unsigned)grid, TPB, smem, stream>>>(in, n, ntiles, normalized ? 1 : 0, ma, mb, out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(e, "k_eval_phased_tma launch");
     *launched = true;

@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(TPB) k_eval(const T* __restrict__ pts, int64_t
 // stores).  For FP32 these variants are the staged path.
 // kRowsTmaEmu* (FP64): k_eval_rows_tma with part of the binary64 products on
 // the integer pipes (dmul_int: bitwise the FP64 instruction's results).
+// kPhasedHybridTmaEmu* (FP64): k_eval_phased_tma with the binary64 products
+// of the hybrid rows' m = 0, 1 columns on the integer pipes, the same bits.
 enum {
   kPhased = 2,
   kPhasedHybrid = 4,
@@ -81,12 +83,19 @@ enum {
   kPhasedHybridTma2 = 6,
   kRowsTma = 7,
   kRowsTmaEmuO = 8,  // output products
-  kRowsTmaEmuOS = 9  // + scales
+  kRowsTmaEmuOS = 9,  // + scales
+  kPhasedHybridTmaEmuO = 10,
+  kPhasedHybridTmaEmuOS = 11
 };
 
 constexpr bool rows_tma_path(int p) { return p == kRowsTma || p == kRowsTmaEmuO || p == kRowsTmaEmuOS; }
+constexpr bool phased_tma_path(int p) {
+  return p == kPhasedHybridTma || p == kPhasedHybridTmaEmuO || p == kPhasedHybridTmaEmuOS;
+}
 constexpr int emu_mask(int p) {
-  return p == kRowsTmaEmuO ? kEmuOut : (p == kRowsTmaEmuOS ? (kEmuOut | kEmuScale) : 0);
+  return (p == kRowsTmaEmuO || p == kPhasedHybridTmaEmuO)
+             ? kEmuOut
+             : ((p == kRowsTmaEmuOS || p == kPhasedHybridTmaEmuOS) ? (kEmuOut | kEmuScale) : 0);
 }
 
 // Store paths whose FP64 rows are computed entirely in binary64 arithmetic
@@ -101,7 +110,8 @@ constexpr Variant kVariants[] = {{kStaged, 128}, {kStaged, 64},  {kStaged, 256},
                                  {kDirect, 256}, {kPhased, 64}, {kPhased, 128}, {kHybrid, 64},
                                  {kHybrid, 128}, {kHybrid, 256}, {kPhasedHybrid, 64}, {kPhasedHybrid, 128},
                                  {kPhasedHybridTma, 128}, {kPhasedHybridTma2, 128}, {kRowsTma, 64},
-                                 {kRowsTma, 32}, {kRowsTmaEmuO, 32}, {kRowsTmaEmuOS, 32}};
+                                 {kRowsTma, 32}, {kRowsTmaEmuO, 32}, {kRowsTmaEmuOS, 32},
+                                 {kPhasedHybridTmaEmuO, 128}, {kPhasedHybridTmaEmuOS, 128}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // For FP32 the phased and hybrid variants run the staged-64 kernel (FP32 rows
@@ -114,14 +124,14 @@ inline size_t variant_smem(int v, int lmax, size_t es) {
   if (p == kDirect) return 0;
   if (p == kPhasedHybridTma2) return (size_t)2 * tpb * 20 * 8 + 128;
   if (rows_tma_path(p)) return (size_t)tpb * L2 * 8 + 128;
-  if (p == kPhased || p == kPhasedHybrid || p == kPhasedHybridTma) {
+  if (p == kPhased || p == kPhasedHybrid || phased_tma_path(p)) {
     int w = 0, mx = 0;  // LPhases<LMAX>::max_width()
     for (int l = 0; l <= lmax; ++l) {
       if (w > 0 && w + 2 * l + 1 > 37) w = 0;
       w += 2 * l + 1;
       mx = std::max(mx, w);
     }
-    return p == kPhasedHybridTma ? (size_t)tpb * mx * 8 + 128 : (size_t)tpb * (mx | 1) * 8;
+    return phased_tma_path(p) ? (size_t)tpb * mx * 8 + 128 : (size_t)tpb * (mx | 1) * 8;
   }
   return (size_t)tpb * (size_t)(L2 % 2 ? L2 : L2 + 1) * es;
 }
@@ -137,14 +147,14 @@ constexpr size_t kMaxSmemPerCta = 232448;  // B300 opt-in limit per CTA
 inline int effective_variant(bool fp64, int v, int lmax = 0) {
   const int p = kVariants[v].path;
   if (!fp64) {
-    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid || p == kPhasedHybridTma || p == kPhasedHybridTma2 ||
+    v = (p == kPhased || p == kHybrid || p == kPhasedHybrid || phased_tma_path(p) || p == kPhasedHybridTma2 ||
          rows_tma_path(p))
             ? 1
             : v;
   } else if (rows_tma_path(p) && !rows_tma_feasible(lmax)) {
     v = 1;  // staged-64: the same all-binary64 rows with the copy-out loop
 
-  } else if (p == kPhasedHybridTma && !tma_plan_feasible(lmax)) {
+  } else if (phased_tma_path(p) && !tma_plan_feasible(lmax)) {
     v = lmax > SHM_LMAX_CAP ? 6 : 11;
   } else if (p == kPhasedHybridTma2 && !(lmax == 3 || lmax == 5 || lmax == 7 || lmax == 9)) {
     v = lmax > SHM_LMAX_CAP ? 6 : (tma_plan_feasible(lmax) ? 12 : 11);
@@ -167,7 +177,10 @@ inline int effective_variant(bool fp64, int v, int lmax = 0) {
 // (effective_variant).
 // At l = 5 and 7 the double-buffered TMA form is faster (0.63 / 0.88 ms
 // against 0.64 / 0.93 ms on the 192^3 grid); at l = 9 its six phases cost
-// more in barriers than the waits they save (1.99 against 1.30 ms).
+// more in barriers than the waits they save (1.99 against 1.30 ms).  At
+// l = 5 the binary64 products of the m = 0, 1 columns on the integer pipes
+// are faster still (phased-hybrid-tma-emu-o-128: 0.571 ms against 0.626 for
+// tma2); at l = 7 (0.99 ms) and l = 9 (2.24 ms, register spills) slower.
 // With SHM_STRICT_FP64 the FP64 rows are all-binary64: rows-tma-emu-o-32 by
 // default (the output products on the integer pipes; staged-64 at even
 // lmax, where the row pitch rules TMA out); measured on the 192^3 grid at
@@ -179,7 +192,7 @@ constexpr int kDefaultVariantF32 = 1;
 constexpr int kDefaultVariantStrict = 16;
 inline int default_variant(bool fp64, int lmax = 9, bool strict = false) {
   if (fp64 && strict) return kDefaultVariantStrict;
-  return fp64 ? ((lmax == 5 || lmax == 7) ? 13 : kDefaultVariantF64) : kDefaultVariantF32;
+  return fp64 ? (lmax == 5 ? 18 : lmax == 7 ? 13 : kDefaultVariantF64) : kDefaultVariantF32;
 }
 
 // The choice table a call reads: 0 = FP32, 1 = FP64, 2 = FP64 with
@@ -195,7 +208,7 @@ template <typename T, int LMAX, int TPB, int PATH>
 size_t eval_smem_bytes() {
   if (rows_tma_path(PATH)) return RowsTmaPlan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhasedHybridTma2) return Tma2Plan<LMAX>::smem_bytes(TPB);
-  if (PATH == kPhasedHybridTma) return TmaPlan<LMAX>::smem_bytes(TPB);
+  if (phased_tma_path(PATH)) return TmaPlan<LMAX>::smem_bytes(TPB);
   if (PATH == kPhased || PATH == kPhasedHybrid)
     return (size_t)TPB * (LPhases<LMAX>::max_width() | 1) * sizeof(double);
   return (PATH == kStaged || PATH == kHybrid) ? (size_t)TPB * TileShape<LMAX>::RS * sizeof(T) : 0;
@@ -203,7 +216,7 @@ size_t eval_smem_bytes() {
 
 template <typename T, int LMAX, int TPB, int PATH>
 auto pick_kernel() {
-  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid || PATH == kPhasedHybridTma || PATH == kPhasedHybridTma2) &&
+  if constexpr ((PATH == kPhased || PATH == kPhasedHybrid || phased_tma_path(PATH) || PATH == kPhasedHybridTma2) &&
                 sizeof(T) == 8) {
     return k_eval_phased<LMAX, TPB, PATH != kPhased>;
   } else {
@@ -217,15 +230,16 @@ template <typename T, int LMAX, int TPB, int PATH>
 shm_status eval_launch_v(const T* pts, int64_t n, T* out, bool normalized, bool vec, cudaStream_t stream) {
   constexpr int MAXDEV = 64;
   static int blocks_per_sm[MAXDEV] = {0};
-  if constexpr (PATH == kPhased || PATH == kPhasedHybrid || PATH == kPhasedHybridTma || PATH == kPhasedHybridTma2) {
+  if constexpr (PATH == kPhased || PATH == kPhasedHybrid || phased_tma_path(PATH) || PATH == kPhasedHybridTma2) {
     if constexpr (sizeof(T) == 4) {
       return eval_launch_v<T, LMAX, 64, kStaged>(pts, n, out, normalized, vec, stream);
     }
   }
-  if constexpr (PATH == kPhasedHybridTma && sizeof(T) == 8) {
+  if constexpr (phased_tma_path(PATH) && sizeof(T) == 8) {
     bool launched = false;
     if (vec) {
-      shm_status st = launch_phased_tma<LMAX, TPB, kInPoints>(pts, n, out, normalized, stream, &launched);
+      shm_status st =
+          launch_phased_tma<LMAX, TPB, kInPoints, emu_mask(PATH)>(pts, n, out, normalized, stream, &launched);
       if (st != SHM_OK || launched) return st;
     }
     return eval_launch_v<T, LMAX, TPB, kPhasedHybrid>(pts, n, out, normalized, vec, stream);
@@ -313,6 +327,8 @@ shm_status eval_launch(const T* pts, int64_t n, T* out, bool normalized, bool ve
     case 15: return eval_launch_v<T, LMAX, 32, kRowsTma>(pts, n, out, normalized, vec, s);
     case 16: return eval_launch_v<T, LMAX, 32, kRowsTmaEmuO>(pts, n, out, normalized, vec, s);
     case 17: return eval_launch_v<T, LMAX, 32, kRowsTmaEmuOS>(pts, n, out, normalized, vec, s);
+    case 18: return eval_launch_v<T, LMAX, 128, kPhasedHybridTmaEmuO>(pts, n, out, normalized, vec, s);
+    case 19: return eval_launch_v<T, LMAX, 128, kPhasedHybridTmaEmuOS>(pts, n, out, normalized, vec, s);
   }
   return fail(SHM_EINVAL, "unknown launch variant");
 }
@@ -501,7 +517,8 @@ const char* kVariantNames[kNumVariants] = {"staged-128", "staged-64",  "staged-2
                                            "phased-64",  "phased-128", "hybrid-64",  "hybrid-128", "hybrid-256",
                                            "phased-hybrid-64", "phased-hybrid-128", "phased-hybrid-tma-128",
                                            "phased-hybrid-tma2-128", "rows-tma-64", "rows-tma-32",
-                                           "rows-tma-emu-o-32", "rows-tma-emu-os-32"};
+                                           "rows-tma-emu-o-32", "rows-tma-emu-os-32",
+                                           "phased-hybrid-tma-emu-o-128", "phased-hybrid-tma-emu-os-128"};
 
 std::mutex g_tune_mu;
 bool g_cache_loaded = false;

@@ -182,6 +182,7 @@ def test_unaligned_output_uses_scalar_path(oracle_mod):
 TMA_VARIANT = 12
 TMA2_VARIANT = 13
 COPY_OUT_VARIANT = 11
+TMA_EMU_VARIANTS = {18: "phased-hybrid-tma-emu-o-128", 19: "phased-hybrid-tma-emu-os-128"}
 
 
 def _tma_test_points(n):
@@ -227,7 +228,42 @@ def test_tma_variants_match_copy_out_variant(variant, lmax, n):
         shm.set_eval_variant(lmax, torch.float64, -1)
 
 
-@pytest.mark.parametrize("variant", [TMA_VARIANT, TMA2_VARIANT])
+@pytest.mark.parametrize("variant", sorted(TMA_EMU_VARIANTS))
+@pytest.mark.parametrize("lmax", [1, 2, 3, 5, 7, 9, 11])
+@pytest.mark.parametrize("n", [129, 4099, 200_003])
+def test_tma_integer_pipe_variants_with_declined_products(variant, lmax, n):
+    """phased-hybrid-tma-emu-*-128 take the binary64 products of the hybrid
+    rows' m = 0, 1 columns on the integer pipes; the integer product declines
+    zero operands, so a point with xb, yb or zb exactly 0 has its row written
+    again by the FP64 code after the tile's TMA stores.  Such points are put
+    in many tiles (one tile made only of them, the ragged last tile, next to
+    origin and non-finite rows): the rows are the bits of phased-hybrid-128."""
+    pts = _tma_test_points(n)
+    rng = np.random.default_rng(20510 + n)
+    idx = rng.choice(n, size=max(n // 40, 3), replace=False)
+    for j, i in enumerate(idx):
+        pts[i, j % 3] = 0.0                        # xb, yb or zb exactly 0
+    if n >= 512:
+        pts[256:384, 1] = 0.0                      # a whole tile on the xz-plane
+    pts[n - 2] = [0.0, 3.0, 0.0]                   # on an axis, in the last tile
+    p = torch.from_numpy(pts).cuda()
+    has_tma = lmax % 2 == 1 and lmax <= 9
+    expect = TMA_EMU_VARIANTS[variant] if has_tma else "phased-hybrid-128" if lmax <= 9 else "phased-128"
+    try:
+        shm.set_eval_variant(lmax, torch.float64, variant)
+        assert shm.eval_variant(lmax, torch.float64) == expect, lmax
+        out = torch.full((n, (lmax + 1) ** 2), 7.0, dtype=torch.float64, device="cuda")
+        shm.eval_sh(p, lmax, out=out)
+        shm.set_eval_variant(lmax, torch.float64, COPY_OUT_VARIANT)
+        ref = shm.eval_sh(p, lmax)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.nan_to_num(out, nan=5.0), torch.nan_to_num(ref, nan=5.0)), (lmax, n)
+        assert torch.equal(torch.isnan(out), torch.isnan(ref))
+    finally:
+        shm.set_eval_variant(lmax, torch.float64, -1)
+
+
+@pytest.mark.parametrize("variant", [TMA_VARIANT, TMA2_VARIANT, *sorted(TMA_EMU_VARIANTS)])
 def test_tma_variant_next_to_other_allocations(variant):
     """The TMA stores of the last (ragged) tile stop at row n: the bytes
     after the output, inside the same allocation, are left untouched."""
