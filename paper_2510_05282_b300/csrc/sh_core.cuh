@@ -904,19 +904,21 @@ __device__ __forceinline__ void sh_column_f32(float zb, float qq, float A, float
 // (sh_column_f32), for short rows only.
 template <int LMAX, bool CX = false, bool FF01 = true, typename Store>
 __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& store) {
-  // q = xb^2 + yb^2 + zb^2 as a float-float, then dq = q - 1
-  const ff px = two_prod(xb, xb), py = two_prod(yb, yb), pz = two_prod(zb, zb);
-  const ff s1 = two_sum(px.hi, py.hi);
-  const ff s2 = two_sum(s1.hi, pz.hi);
-  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), px.lo), __fadd_rn(py.lo, pz.lo));
-  const ff qf = fast_two_sum(s2.hi, lo);
-  const float dq = __fadd_rn(__fsub_rn(qf.hi, 1.0f), qf.lo);
-  const float qq = qf.hi;
-
+  float qq;
   if constexpr (FF01) {
+    // q = xb^2 + yb^2 + zb^2 as a float-float, then dq = q - 1
+    const ff px = two_prod(xb, xb), py = two_prod(yb, yb), pz = two_prod(zb, zb);
+    const ff s1 = two_sum(px.hi, py.hi);
+    const ff s2 = two_sum(s1.hi, pz.hi);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), px.lo), __fadd_rn(py.lo, pz.lo));
+    const ff qf = fast_two_sum(s2.hi, lo);
+    const float dq = __fadd_rn(__fsub_rn(qf.hi, 1.0f), qf.lo);
+    qq = qf.hi;
     sh_column_ff<LMAX, 0, CX>(zb, dq, 0.0f, 0.0f, store);
     if constexpr (LMAX >= 1) sh_column_ff<LMAX, 1, CX>(zb, dq, xb, yb, store);
   } else {
+    // the plain recurrences need q only to FP32 accuracy: two FMAs and a product
+    qq = fmaf(xb, xb, fmaf(yb, yb, zb * zb));
     sh_column_f32<LMAX, 0, CX>(zb, qq, 0.0f, 0.0f, store);
     if constexpr (LMAX >= 1) sh_column_f32<LMAX, 1, CX>(zb, qq, xb, yb, store);
   }

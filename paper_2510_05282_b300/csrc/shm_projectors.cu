@@ -8,25 +8,26 @@
 //     (atom_order), validates every atom's offsets and species, builds the
 //     tile table in that order (tiles = TILE consecutive sphere points of one
 //     atom; tile_offsets[j] = number of tiles of the atoms before
-//     atom_order[j], 0 tiles for an atom that failed validation), zeroes the
-//     work counter, the finish count and the error word; with the other CTAs
-//     it converts the radial tables (FP32: float copies and the exponent
-//     table of the log-grid index; FP64: the interval cubics).  Tiles of one
-//     lmax then run together, so the SMs execute one row code path at a time
+//     atom_order[j], 0 tiles for an atom that failed validation) and one
+//     descriptor per tile (first point, first output value, atom, species,
+//     rows), and zeroes the error word; with the other CTAs it converts the
+//     radial tables (FP32: float copies and the exponent table of the
+//     log-grid index; FP64: the interval cubics).  Tiles of one lmax then run
+//     together, so the SMs execute one row code path at a time
 //     (instruction-cache locality); the output layout, by atom, is unchanged.
 //  2. run, every call (shm_projectors_run): k_proj (persistent: SMs x
-//     resident CTAs) -- each CTA takes the next tile from an atomic work
-//     counter, evaluates its rows -- minimum-image displacement, 1/r, log-grid
-//     index, 4-point Lagrange interpolation of the l radial functions, the
-//     real harmonics (sh_core.cuh), and their product -- into a shared-memory
-//     tile with an odd row stride, then copies the tile (one contiguous block
-//     of the output) out with coalesced stores or one bulk copy; the last CTA
-//     to finish resets the counter for the next run.  One launch per call.
+//     resident CTAs, tiles dealt round robin) -- each CTA reads its next
+//     tile's descriptor, evaluates its rows -- minimum-image displacement,
+//     1/r, log-grid index, 4-point Lagrange interpolation of the l radial
+//     functions, the real harmonics (sh_core.cuh), and their product -- into
+//     a shared-memory tile, then copies the tile (one contiguous block of the
+//     output) out with coalesced stores or one bulk copy.  The run writes
+//     nothing but the output and the error word: one launch per call.
 //  The launch variant (tile size, points per thread, register cap, store
 //  path) is the tuner's choice (shm_projectors_autotune) or the default.
-// Uneven sphere sizes (4k..65k points) and per-species lmax balance through
-// the dynamic queue; a tile never spans two atoms, so every row of a tile has
-// the same width.
+// Uneven sphere sizes (4k..65k points) become equal tiles, and the lmax
+// order deals every CTA the same mix of row widths; a tile never spans two
+// atoms, so every row of a tile has the same width.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,15 +57,26 @@ struct __align__(16) AtomF32 {  // 48 bytes: three 16-byte loads
   float fhi[4], flo[4];
 };
 
+// Tile descriptor (32 bytes), written by the set-up launch: the tile's first
+// sphere point and first output value, its atom, species and row count.
+struct __align__(16) ProjTile {
+  long long p0, o0;
+  int atom, species, rows, pad;
+};
+// Smallest tile of any launch variant: bounds the descriptor count of a
+// problem, n_points / kProjMinTile + n_atoms.
+constexpr int kProjMinTile = 128;
+
 // Workspace layout (byte offsets; every block 256-byte aligned).
 struct ProjWs {
-  size_t counter = 0;      // unsigned long long work counter, uint32 error word at +8, uint32 finish count at +12
+  size_t words = 0;        // uint32 error word at +8
   size_t tiles = 256;      // int64 tile_offsets[n_atoms + 1]
   size_t order = 0;        // int32 atom_order[n_atoms]
+  size_t desc = 0;         // ProjTile[n_points / kProjMinTile + n_atoms + 1]
   size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
   size_t atomf = 0;        // FP32: AtomF32[n_atoms] (atom coordinates in grid units)
-  size_t rad32 = 0;        // FP32: float radial[n_species][lstride][n_rad]
-  size_t coef = 0;         // FP64: {a0, a1, a2, a3}[n_species][lstride][n_rad] (cubic per interval), float-float
+  size_t rad32 = 0;        // FP32: float4 {a0, a1, a2, a3}[n_species][n_rad][lstride] (cubic per interval)
+  size_t coef = 0;         // FP64: {a0, a1, a2, a3}[n_species][n_rad][lstride] (cubic per interval), float-float
                            // (32 bytes a node) or, with SHM_STRICT_FP64, binary64 (32 bytes a node)
   size_t hg = 0;           // FP64: double i * h for i < ng (grid coordinates, rounded as the definition)
   size_t total = 0;
@@ -121,13 +133,15 @@ ProjWs proj_layout(const shm_proj_problem& p, shm_dtype dt) {
   size_t end = w.tiles + round256((size_t)(p.n_atoms + 1) * 8);
   w.order = end;
   end += round256((size_t)std::max<int64_t>(p.n_atoms, 1) * 4);
+  w.desc = end;
+  end += round256((size_t)(p.n_points / kProjMinTile + p.n_atoms + 1) * sizeof(ProjTile));
   if (dt == SHM_F32) {
     w.etab = end;
     end += round256((size_t)kExpN * 8);
     w.atomf = end;
     end += round256((size_t)p.n_atoms * sizeof(AtomF32));
     w.rad32 = end;
-    end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 4);
+    end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 16);
   } else {
     w.coef = end;
     end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 32);
@@ -152,82 +166,92 @@ struct ProjParams {
   unsigned ng_magic;  // division by ng without division instructions (see div_ng)
   int ng_shift;
   // workspace views
-  unsigned long long* counter;
   unsigned* err;
-  unsigned* done;  // CTAs of the current launch that have finished
   int64_t* tile_offsets;
+  ProjTile* tiles;
   int32_t* atom_order;
   int2* etab;
-  float* rad32;
+  float4* rad32;
   AtomF32* atomf;
   float4* coef;  // two per node: {a0.hi, a0.lo, a1.hi, a1.lo}, {a2.hi, a2.lo, a3.hi, a3.lo}; strict: one double4
   int strict;    // FP64 with SHM_STRICT_FP64: binary64 tables, log-grid index and rows
   double* hg;
+  // derived on the host: 1/box, 1/r_min, 1/dlog, the log-grid constants
+  // K0 = -ln(r_min)/dlog, K1 = ln2/(2 dlog), K2 = 1/(2 dlog), and FP32 h, 1/dlog
+  double inv_box, inv_rmin, inv_dlog, lg_k0, lg_k1, lg_k2;
+  float h32, inv_dlog32;
 };
 
 enum : unsigned { kErrOffsets = 1u, kErrSpecies = 2u, kErrGrid = 4u, kErrOut = 8u };
 
 // ---------------------------------------------------------------------------
-// Set-up: validation, tile table (block-wide scan), counters, FP32 tables.
+// Set-up: validation, tile table (block-wide scan), tile descriptors, error
+// word, FP32 tables.
 
 __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int fp32) {
   __shared__ int64_t warp_sums[32];
   __shared__ int64_t carry;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  {  // FP32 radial tables, or the FP64 interval cubics, spread over every CTA of the grid
+  {  // the interval cubics of the radial tables, spread over every CTA of the grid
     const int64_t nt = (int64_t)P.n_species * P.lstride * P.n_rad;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
-      if (fp32) {
-        P.rad32[i] = (float)P.radial[i];
-        continue;
-      }
       // 4-point Lagrange interpolation on the interval [it, it + 1] of the
       // table (stencil i0..i0+3, i0 = clamp(it - 1, 0, n_rad - 4)) as the
       // cubic a0 + a1 u + a2 u^2 + a3 u^3 in u = t - it: the stencil
       // polynomial b0 + b1 x + b2 x^2 + b3 x^3 in x = t - i0 from its forward
       // differences, shifted to x0 = it - i0, computed in binary64 and stored
-      // as float-float (the FP64 row takes f_l in float-float).  (The FP32 path keeps the
-      // weights form: its 4-byte table stays in L1, the 16-byte cubics of a
-      // species do not, and it is bound by issue and loads, not arithmetic.)
-      const int64_t row = i / P.n_rad;
+      // as float-float (the FP64 row takes f_l in float-float), binary64
+      // (strict rows) or FP32 (FP32 rows: one 16-byte load and three FMAs
+      // per l, where the Lagrange weights of the stencil took four loads, four
+      // FMAs and the weights' own arithmetic).
+      const int64_t row = i / P.n_rad;  // s * lstride + l
       const int it = (int)(i - row * P.n_rad);
       const int i0 = min(max(it - 1, 0), P.n_rad - 4);
+      // stored node-major: the cubics of all l of one interval are adjacent
+      // (one or two cache lines per point), at ((s n_rad + it) lstride + l)
+      const int64_t sp = row / P.lstride, l = row - sp * P.lstride;
+      const int64_t o = (sp * P.n_rad + it) * P.lstride + l;
       const double* F = P.radial + row * P.n_rad + i0;
       const double d1 = F[1] - F[0], d2 = F[2] - 2.0 * F[1] + F[0], d3 = F[3] - 3.0 * F[2] + 3.0 * F[1] - F[0];
       const double b3 = d3 / 6.0, b2 = 0.5 * (d2 - d3), b1 = d1 - 0.5 * d2 + d3 / 3.0;
       const double x0 = (double)(it - i0);
       const double c0 = F[it - i0], c1 = b1 + x0 * (2.0 * b2 + 3.0 * b3 * x0), c2 = b2 + 3.0 * b3 * x0;
+      if (fp32) {
+        P.rad32[o] = make_float4((float)c0, (float)c1, (float)c2, (float)b3);
+        continue;
+      }
       if (P.strict) {  // the cubic kept in binary64 (the strict rows evaluate it by binary64 Horner)
-        reinterpret_cast<double4*>(P.coef)[i] = make_double4(c0, c1, c2, b3);
+        reinterpret_cast<double4*>(P.coef)[o] = make_double4(c0, c1, c2, b3);
         continue;
       }
       const ff f0 = ff_from_double(c0), f1 = ff_from_double(c1), f2 = ff_from_double(c2), f3 = ff_from_double(b3);
-      P.coef[2 * i] = make_float4(f0.hi, f0.lo, f1.hi, f1.lo);
-      P.coef[2 * i + 1] = make_float4(f2.hi, f2.lo, f3.hi, f3.lo);
+      P.coef[2 * o] = make_float4(f0.hi, f0.lo, f1.hi, f1.lo);
+      P.coef[2 * o + 1] = make_float4(f2.hi, f2.lo, f3.hi, f3.lo);
     }
   }
   if (blockIdx.x != 0) return;  // the rest is one CTA's work
   if (tid == 0) {
-    *P.counter = 0ull;
     *P.err = 0u;
-    *P.done = 0u;
     carry = 0;
     P.tile_offsets[0] = 0;
   }
-  // atom_order: a counting sort of the atoms by the lmax of their species
-  // (invalid species count as lmax 0), largest lmax first
-  __shared__ int key_count[SHM_LMAX_CAP + 1], key_next[SHM_LMAX_CAP + 1];
+  // atom_order: a counting sort of the atoms by the lmax of their species,
+  // largest lmax first, then by species (invalid species count as lmax 0
+  // and come last): tiles of one species run together, so the SMs' L1
+  // holds one species' radial cubics at a time
+  constexpr int kKeys = (SHM_LMAX_CAP + 1) * SHM_PROJ_MAX_SPECIES;
+  __shared__ int key_count[kKeys], key_next[kKeys];
   auto key_of = [&](int64_t a) {
     const int s = P.atom_species[a];
-    return (s >= 0 && s < P.n_species) ? (int)P.lmax[s] : 0;
+    return (s >= 0 && s < P.n_species) ? (SHM_LMAX_CAP - (int)P.lmax[s]) * SHM_PROJ_MAX_SPECIES + s : kKeys - 1;
   };
-  if (tid <= SHM_LMAX_CAP) key_count[tid] = 0;
+  for (int k = tid; k < kKeys; k += blockDim.x) key_count[k] = 0;
   __syncthreads();
   for (int64_t a = tid; a < P.n_atoms; a += blockDim.x) atomicAdd(&key_count[key_of(a)], 1);
   __syncthreads();
   if (tid == 0) {
     int start = 0;
-    for (int k = SHM_LMAX_CAP; k >= 0; --k) {
+    for (int k = 0; k < kKeys; ++k) {
       key_next[k] = start;
       start += key_count[k];
     }
@@ -289,6 +313,27 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
     __syncthreads();
   }
   if (err) atomicOr(P.err, err);
+  // one descriptor per tile, each atom's tiles written by one warp (the
+  // offsets of the scan above are visible to the whole CTA after its barriers)
+  for (int64_t j = wid; j < P.n_atoms; j += blockDim.x >> 5) {
+    const int64_t t0 = P.tile_offsets[j], nt = P.tile_offsets[j + 1] - t0;
+    if (nt <= 0) continue;
+    const int a = P.atom_order[j];
+    const int s = P.atom_species[a];
+    const int64_t pa0 = P.point_offsets[a], pa1 = P.point_offsets[a + 1], oa0 = P.out_offsets[a];
+    const int64_t L2 = (int64_t)(P.lmax[s] + 1) * (P.lmax[s] + 1);
+    for (int64_t c = lane; c < nt; c += 32) {
+      const int64_t p0 = pa0 + c * tpb;
+      ProjTile D;
+      D.p0 = p0;
+      D.o0 = oa0 + (p0 - pa0) * L2;
+      D.atom = a;
+      D.species = s;
+      D.rows = (int)min((int64_t)tpb, pa1 - p0);
+      D.pad = 0;
+      P.tiles[t0 + c] = D;
+    }
+  }
   if (!fp32)
     for (int i = tid; i < P.ng; i += blockDim.x) P.hg[i] = __dmul_rn((double)i, P.h);
   if (fp32) {
@@ -434,29 +479,6 @@ __device__ __forceinline__ double log_grid_index(double r2, const LogGrid64& G) 
 // ---------------------------------------------------------------------------
 // Per-row pieces.
 
-// Stencil and weights of 4-point Lagrange interpolation at t = it + u
-// (already clamped to [0, n_rad - 1], 0 <= u < 1), FP32 path.
-struct Lagrange4 {
-  int i0;
-  float w[4];
-};
-__device__ __forceinline__ Lagrange4 lagrange_at(int it, float u, int n_rad) {
-  Lagrange4 L;
-  int i0 = it - 1;
-  i0 = i0 < 0 ? 0 : (i0 > n_rad - 4 ? n_rad - 4 : i0);
-  const float x = small_int_to_float(it - i0) + u;  // t - i0, in [0, 3]
-  const float x1 = x - 1.0f, x2 = x - 2.0f, x3 = x - 3.0f;
-  L.i0 = i0;
-  L.w[0] = -(x1 * x2 * x3) * (1.0f / 6.0f);
-  L.w[1] = (x * x2 * x3) * 0.5f;
-  L.w[2] = -(x * x1 * x3) * 0.5f;
-  L.w[3] = (x * x1 * x2) * (1.0f / 6.0f);
-  return L;
-}
-__device__ __forceinline__ float interp4(const Lagrange4& L, const float* F) {
-  return fmaf(L.w[3], F[3], fmaf(L.w[2], F[2], fmaf(L.w[1], F[1], L.w[0] * F[0])));
-}
-
 // One row (lmax = LMAX): f_l(r) = radial(l) for l = 0..LMAX (float for the
 // FP32 row, float-float for the FP64 row), then write f_l(r) R_l^m into
 // row[0..(LMAX+1)^2).  (dx, dy, dz) is the displacement, or with `unit` its
@@ -541,10 +563,14 @@ __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bo
 // STRICT (SHM_STRICT_FP64): the log-grid index from CUDA's binary64 log of
 // r^2, the interval cubic by binary64 Horner from binary64 coefficients, and
 // the all-binary64 harmonic row times f_l.
-template <bool STRICT = false>
+// before_row() runs once, after the point's preamble and before its first
+// write to `row` (the warp-granular kernel waits there for its staging
+// buffer).
+template <bool STRICT = false, typename BeforeRow>
 __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, double ax, double ay, double az,
-                                               int s, int lmax, double inv_box, double inv_rmin,
-                                               double inv_dlog, const LogGrid64& G, double* row) {
+                                               int s, int lmax, double* row, BeforeRow&& before_row) {
+  const double inv_box = P.inv_box, inv_rmin = P.inv_rmin, inv_dlog = P.inv_dlog;
+  const LogGrid64 G = {P.lg_k0, P.lg_k1, P.lg_k2};
   const int ng = P.ng;
   const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
   const int gi = (int)div_ng((unsigned)q1, P.ng_magic, P.ng_shift);
@@ -597,24 +623,27 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
     it = 0;  // below the grid, or t = -inf or NaN (u not finite)
     u = 0.0;
   }
+  before_row();
   if constexpr (STRICT) {
     // f_l(r): the interval's cubic in u by binary64 Horner, one 32-byte node
-    const double4* c = reinterpret_cast<const double4*>(P.coef) + ((int64_t)s * P.lstride * P.n_rad + it);
-    proj_row_dispatch<true, double>(lmax, d[0], d[1], d[2], origin, unit, [&](int l) {
-      const double4 a = c[(int64_t)l * P.n_rad];
+    const double4* c = reinterpret_cast<const double4*>(P.coef) + ((int64_t)s * P.n_rad + it) * P.lstride;
+    auto radial = [&](int l) {
+      const double4 a = c[l];
       return fma(fma(fma(a.w, u, a.z), u, a.y), u, a.x);
-    }, row);
+    };
+    proj_row_dispatch<true, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
   } else {
     // f_l(r): the interval's cubic in u by Horner's rule in float-float (FP32
     // pipe), two 16-byte loads per l
-    const float4* c = P.coef + 2 * ((int64_t)s * P.lstride * P.n_rad + it);
+    const float4* c = P.coef + 2 * ((int64_t)s * P.n_rad + it) * P.lstride;
     const ff U = ff_from_double(u);
-    proj_row_dispatch<false, double>(lmax, d[0], d[1], d[2], origin, unit, [&](int l) {
-      const float4 a01 = __ldg(c + 2 * (int64_t)l * P.n_rad), a23 = __ldg(c + 2 * (int64_t)l * P.n_rad + 1);
+    auto radial = [&](int l) {
+      const float4 a01 = __ldg(c + 2 * l), a23 = __ldg(c + 2 * l + 1);
       ff p = ff_add(ff_mul_u(ff{a23.z, a23.w}, U), ff{a23.x, a23.y});
       p = ff_add(ff_mul_u(p, U), ff{a01.z, a01.w});
       return ff_add(ff_mul_u(p, U), ff{a01.x, a01.y});
-    }, row);
+    };
+    proj_row_dispatch<false, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
   }
 }
 
@@ -623,9 +652,13 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
 // integer part is exact; frac is split into hi + lo on the host side of the
 // tile), then rounded once; the log-grid index uses the exponent table so
 // that only ln(mantissa) is taken in FP32 and t keeps ~1e-5 absolute accuracy
-// at t ~ 2000.
+// at t ~ 2000.  before_row() as for proj_point_f64.  LFIX >= 0: the row of
+// lmax LFIX (lmax is then ignored), written with compile-time indices (row
+// may be a register array).
+template <int LFIX = -1, typename BeforeRow>
 __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const AtomF32& A, int s, int lmax,
-                                               float h, float inv_dlog, float* row) {
+                                               float* row, BeforeRow&& before_row) {
+  const float h = P.h32, inv_dlog = P.inv_dlog32;
   const int ng = P.ng;
   const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
   const int gi = (int)div_ng((unsigned)q1, P.ng_magic, P.ng_shift);
@@ -681,10 +714,99 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
     }
     it = (int)itl;
   }
-  const Lagrange4 L = lagrange_at(it, u, P.n_rad);
-  const float* tab = P.rad32 + (int64_t)s * P.lstride * P.n_rad + L.i0;
-  proj_row_dispatch<false, float>(lmax, d[0], d[1], d[2], origin, true,
-                           [&](int l) { return interp4(L, tab + (int64_t)l * P.n_rad); }, row);
+  // f_l(r): the interval's cubic in u, one 16-byte node per l
+  const float4* tab = P.rad32 + ((int64_t)s * P.n_rad + it) * P.lstride;
+  before_row();
+  auto radial = [&](int l) {
+    const float4 c = __ldg(tab + l);
+    return fmaf(fmaf(fmaf(c.w, u, c.z), u, c.y), u, c.x);
+  };
+  if constexpr (LFIX >= 0)
+    proj_row<LFIX, false, float>(d[0], d[1], d[2], origin, true, radial, row);
+  else
+    proj_row_dispatch<false, float>(lmax, d[0], d[1], d[2], origin, true, radial, row);
+}
+
+// Rows of 16 floats (lmax 3) staged contiguously with 16-byte stores.  The
+// round's rows go to buf + p + 16 r (buf 16-byte aligned, p = the 16-byte
+// phase of the output in floats), where a bulk copy sends them out; with
+// p > 0 a row straddles 16-byte chunks, so the chunk that starts row r also
+// holds the last p values of row r - 1, which come from the lane before by
+// shuffles.  Lane 0 of a warp writes its first values one by one, and the
+// last lane of a warp and the last row of the round write their last p
+// values one by one (nobody after them in the warp holds them).  Every lane
+// of the warp calls this (the shuffles); `active`: this lane has a row.
+// Four 16-byte stores per row instead of sixteen 4-byte stores into a
+// padded tile and the copy-out loop's loads, index arithmetic and stores.
+__device__ __forceinline__ void stage_rows16(float* __restrict__ buf, int p, int r, bool active, bool last,
+                                             const float (&v)[16]) {
+  const int lane = (int)(threadIdx.x & 31u);
+  float4* c4 = reinterpret_cast<float4*>(buf + 16 * r);  // the chunk that starts row r
+  switch (p) {
+    case 0:
+      if (active) {
+        c4[0] = make_float4(v[0], v[1], v[2], v[3]);
+        c4[1] = make_float4(v[4], v[5], v[6], v[7]);
+        c4[2] = make_float4(v[8], v[9], v[10], v[11]);
+        c4[3] = make_float4(v[12], v[13], v[14], v[15]);
+      }
+      break;
+    case 1: {
+      const float x15 = __shfl_up_sync(0xffffffffu, v[15], 1);
+      if (active) {
+        if (lane == 0) {
+          buf[16 * r + 1] = v[0];
+          buf[16 * r + 2] = v[1];
+          buf[16 * r + 3] = v[2];
+        } else {
+          c4[0] = make_float4(x15, v[0], v[1], v[2]);
+        }
+        c4[1] = make_float4(v[3], v[4], v[5], v[6]);
+        c4[2] = make_float4(v[7], v[8], v[9], v[10]);
+        c4[3] = make_float4(v[11], v[12], v[13], v[14]);
+        if (last || lane == 31) buf[16 * r + 16] = v[15];
+      }
+      break;
+    }
+    case 2: {
+      const float x14 = __shfl_up_sync(0xffffffffu, v[14], 1), x15 = __shfl_up_sync(0xffffffffu, v[15], 1);
+      if (active) {
+        if (lane == 0) {
+          buf[16 * r + 2] = v[0];
+          buf[16 * r + 3] = v[1];
+        } else {
+          c4[0] = make_float4(x14, x15, v[0], v[1]);
+        }
+        c4[1] = make_float4(v[2], v[3], v[4], v[5]);
+        c4[2] = make_float4(v[6], v[7], v[8], v[9]);
+        c4[3] = make_float4(v[10], v[11], v[12], v[13]);
+        if (last || lane == 31) {
+          buf[16 * r + 16] = v[14];
+          buf[16 * r + 17] = v[15];
+        }
+      }
+      break;
+    }
+    default: {
+      const float x13 = __shfl_up_sync(0xffffffffu, v[13], 1), x14 = __shfl_up_sync(0xffffffffu, v[14], 1),
+                  x15 = __shfl_up_sync(0xffffffffu, v[15], 1);
+      if (active) {
+        if (lane == 0)
+          buf[16 * r + 3] = v[0];
+        else
+          c4[0] = make_float4(x13, x14, x15, v[0]);
+        c4[1] = make_float4(v[1], v[2], v[3], v[4]);
+        c4[2] = make_float4(v[5], v[6], v[7], v[8]);
+        c4[3] = make_float4(v[9], v[10], v[11], v[12]);
+        if (last || lane == 31) {
+          buf[16 * r + 16] = v[13];
+          buf[16 * r + 17] = v[14];
+          buf[16 * r + 18] = v[15];
+        }
+      }
+      break;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -696,20 +818,24 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
 // scalar head and tail by plain stores.  stage must have dst's address
 // modulo 16, and the writers must have fenced their shared-memory stores for
 // the async proxy before the barrier that precedes this call.
+// tid: the calling thread's index among the copying threads (thread 0
+// issues the copy); wait_read: thread 0 waits until the copy has read the
+// staging buffer (else the caller waits before it next writes the buffer).
 template <typename T>
-__device__ __forceinline__ void bulk_rows_out(const T* stage, int nv, T* __restrict__ dst) {
+__device__ __forceinline__ void bulk_rows_out(const T* stage, int nv, T* __restrict__ dst, int tid = threadIdx.x,
+                                              bool wait_read = true) {
   const int head = min(nv, (int)(((16u - ((unsigned)(uintptr_t)dst & 15u)) & 15u) / sizeof(T)));
   const int nbody = (int)((((size_t)(nv - head) * sizeof(T)) & ~(size_t)15) / sizeof(T));
   const int tail = nv - head - nbody;
-  if (threadIdx.x == 0 && nbody > 0) {
+  if (tid == 0 && nbody > 0) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst + head),
                  "r"((unsigned)__cvta_generic_to_shared(stage + head)), "r"((unsigned)(nbody * sizeof(T)))
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    if (wait_read) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
   }
-  if ((int)threadIdx.x < head) __stcs(dst + threadIdx.x, stage[threadIdx.x]);
-  if ((int)threadIdx.x < tail) __stcs(dst + head + nbody + threadIdx.x, stage[head + nbody + threadIdx.x]);
+  if (tid < head) __stcs(dst + tid, stage[tid]);
+  if (tid < tail) __stcs(dst + head + nbody + tid, stage[head + nbody + tid]);
 }
 
 // Copies rows [0, rows) of a staged tile (row stride RS) to dst[rows * L2],
@@ -721,7 +847,8 @@ __device__ __forceinline__ void bulk_rows_out(const T* stage, int nv, T* __restr
 // conversions to the narrow FP64-class pipe.
 template <typename T>
 __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int rows, int L2, int RS,
-                                              T* __restrict__ dst) {
+                                              T* __restrict__ dst, int tid = threadIdx.x,
+                                              int nthreads = blockDim.x) {
   constexpr int E = Vec16<T>::n;
   using V = typename Vec16<T>::type;
   const int nv = rows * L2;
@@ -733,180 +860,237 @@ __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int ro
     return r * RS + (j - r * L2);
   };
   const int head = min(nv, (int)(((16u - ((unsigned)(uintptr_t)dst & 15u)) & 15u) / sizeof(T)));
-  for (int j = threadIdx.x; j < head; j += blockDim.x) __stcs(dst + j, tile[src(j)]);
+  for (int j = tid; j < head; j += nthreads) __stcs(dst + j, tile[src(j)]);
   const int nq = (nv - head) / E;
   V* d = reinterpret_cast<V*>(dst + head);
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+  for (int q = tid; q < nq; q += nthreads) {
     const int j = head + q * E;
     T v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = tile[src(j + i)];
     st_stream(d + q, v);
   }
-  for (int j = head + nq * E + threadIdx.x; j < nv; j += blockDim.x) __stcs(dst + j, tile[src(j)]);
+  for (int j = head + nq * E + tid; j < nv; j += nthreads) __stcs(dst + j, tile[src(j)]);
 }
 
-// Atoms whose tile table a CTA keeps in shared memory (int32 entries); larger
-// problems search the table in global memory.
-constexpr int kSmemAtoms = 4096;
-
-// The persistent kernel.  TILE sphere points of one atom per tile, PPT
-// points per thread (TILE / PPT threads per CTA), MINB resident CTAs per SM
-// asked of the register allocator (0: no cap).  bulk: tiles of odd row width
-// leave by one bulk copy, else by the copy-out loop.
+// The persistent kernel.  NT threads per CTA; tiles of TILE = NT x ROUNDS
+// sphere points of one atom, evaluated in ROUNDS rounds of NT rows (one per
+// thread), each staged in shared memory and sent out before the next (the
+// staging buffer holds NT rows); MINB resident CTAs per SM asked of the
+// register allocator (0: no cap).  bulk: rows of odd width leave by one bulk
+// copy per round, else by the copy-out loop.  The per-tile work (descriptor,
+// checks, prefetches) is shared by the ROUNDS rounds.
 //
-// Each CTA draws tiles from the work counter until the counter passes the
-// tile count; the last CTA to finish resets the counter (and the finish
-// count) to zero, so every launch starts from a clean counter with no other
-// work on the stream: one launch per call, replayable from a CUDA graph.
-// Every index the kernel follows is checked against the problem (the atom
-// of a tile, its species, offsets and output block, every grid index), so a
-// workspace that does not hold this problem's tables sets error bits instead
-// of reading or writing out of bounds; tile_limit caps the tile count read
-// from the workspace.
-template <typename T, int TILE, int PPT, int MINB, bool STRICT = false>
-__global__ void __launch_bounds__(TILE / PPT, MINB) k_proj(ProjParams P, T* __restrict__ out, int tile_bytes,
-                                                          int64_t tile_limit, int bulk) {
-  constexpr int NT = TILE / PPT;
+// Static schedule: of G CTAs, CTA b takes tiles b, b + G, b + 2G, ...  The
+// tiles are ordered by the lmax of their atom, largest first, then by
+// species, so every CTA gets the same mix of row widths, and no counter,
+// atomic or search sits between two tiles.  Everything a tile reads from
+// global memory besides its radial tables arrives in shared memory ahead of
+// it by cp.async: thread 0 fetches descriptors two tiles ahead (a ring of
+// three), and all threads fetch the next tile's grid indices and thread 0
+// its atom data one tile ahead (two buffers), so neither the index stream
+// from DRAM nor the descriptor chain stalls the tile's arithmetic; two
+// barriers per tile remain (before and after the tile's stores).  Every
+// descriptor is checked against the problem (atom, species, row count, point
+// and value ranges) before it is used, and every grid index per point, so a
+// workspace that does not hold this problem's tables sets error bits
+// instead of reading or writing out of bounds; tile_limit caps the tile
+// count read from the workspace.  Nothing in the workspace changes during a
+// run: every launch is the same, and a CUDA graph replays it.
+template <typename T, int NT, int ROUNDS, int MINB, bool STRICT = false>
+__global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__ out, int tile_bytes,
+                                                  int64_t tile_limit, int bulk) {
+  constexpr int TILE = NT * ROUNDS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
-  int* tt = reinterpret_cast<int*>(smem_raw + tile_bytes);
-  __shared__ long long s_next;
-  __shared__ int s_atom;
-  const double inv_box = 1.0 / P.box, inv_rmin = 1.0 / P.r_min, inv_dlog = 1.0 / P.dlog;
-  const LogGrid64 G = {-log(P.r_min) * inv_dlog, 0.69314718055994530942 * 0.5 * inv_dlog, 0.5 * inv_dlog};
-  // exact tile count, from the table the set-up kernel built
+  (void)tile_bytes;
+  __shared__ __align__(16) ProjTile s_desc[3];
+  // grid indices of a tile: index p0 + r at s_idx[.][r + sh], sh the 16-byte
+  // phase of &point_index[p0] in 4-byte units, so that the 16-byte aligned
+  // part of the index stream arrives by 16-byte copies that bypass L1 (which
+  // keeps the radial cubics)
+  __shared__ __align__(16) int s_idx[2][TILE + 8];
+  __shared__ __align__(16) AtomF32 s_atom[2];  // FP32: the atom in grid units; FP64: its position (3 doubles)
   const int64_t total_tiles = min(max(P.tile_offsets[P.n_atoms], (int64_t)0), tile_limit);
-  const bool cached = P.n_atoms + 1 <= kSmemAtoms;
-  if (cached)
-    for (int i = threadIdx.x; i <= P.n_atoms; i += NT) tt[i] = (int)P.tile_offsets[i];
-  __syncthreads();
-  // owning atom of tile t: atom_order[j] for the last j with tile_offsets[j]
-  // <= t (one thread searches, for the next tile while the others work on
-  // the current one)
-  auto owner = [&](int64_t t) {
-    int64_t lo = 0, hi = P.n_atoms - 1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if ((cached ? (int64_t)tt[mid] : P.tile_offsets[mid]) <= t) lo = mid;
-      else hi = mid - 1;
-    }
-    return (int)lo;
+  const int64_t G = gridDim.x;
+  auto cp16 = [](void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
   };
-  if (threadIdx.x == 0) {
-    s_next = (long long)atomicAdd(P.counter, 1ull);
-    s_atom = s_next < total_tiles ? owner(s_next) : 0;
-  }
-  __syncthreads();
-  for (;;) {
-    const int64_t t = s_next;
-    const int64_t j = s_atom;
-    if (t >= total_tiles) break;
-    __syncthreads();  // every thread has read s_next and s_atom
-    if (threadIdx.x == 0) {  // next tile and its atom, fetched early
-      s_next = (long long)atomicAdd(P.counter, 1ull);
-      s_atom = s_next < total_tiles ? owner(s_next) : 0;
+  auto cp8 = [](void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+  };
+  auto cp4 = [](void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+  };
+  auto commit = [] { asm volatile("cp.async.commit_group;" ::: "memory"); };
+  auto wait_all = [] { asm volatile("cp.async.wait_group 0;" ::: "memory"); };
+  // thread 0: the descriptor of tile t into ring slot ds
+  auto fetch_desc = [&](int64_t t, int ds) {
+    if (t < total_tiles) {
+      cp16(&s_desc[ds], P.tiles + t);
+      cp16(reinterpret_cast<char*>(&s_desc[ds]) + 16, reinterpret_cast<const char*>(P.tiles + t) + 16);
     }
-    // the tile's atom and its blocks, checked against the problem
-    const int64_t a = P.atom_order[j];
-    bool ok = a >= 0 && a < P.n_atoms;
-    const int64_t pa0 = ok ? P.point_offsets[a] : 0, pa1 = ok ? P.point_offsets[a + 1] : 0;
-    const int s = ok ? P.atom_species[a] : 0;
-    ok = ok && s >= 0 && s < P.n_species && pa0 >= 0 && pa1 >= pa0 && pa1 <= P.n_points;
-    const int lmax = ok ? P.lmax[s] : 0;
-    const int L2 = (lmax + 1) * (lmax + 1);
-    const int64_t c = t - (cached ? (int64_t)tt[j] : P.tile_offsets[j]);
-    const int64_t p0 = pa0 + c * TILE;
-    const int64_t oa0 = ok ? P.out_offsets[a] : 0, oa1 = ok ? P.out_offsets[a + 1] : 0;
-    ok = ok && c >= 0 && p0 < pa1 && oa0 >= 0 && oa1 <= P.n_values && oa1 - oa0 == (pa1 - pa0) * L2;
-    if (!ok) {  // the same decision in every thread: skip the tile
-      if (threadIdx.x == 0) atomicOr(P.err, kErrOut);
-      __syncthreads();  // s_next and s_atom hold the next tile
-      continue;
-    }
-    const int rows = (int)min((int64_t)TILE, pa1 - p0);
-    const int RS = L2 | 1;
-    const int64_t o0 = oa0 + c * TILE * (int64_t)L2;
-    // odd row widths: the tile is staged contiguously (RS = L2), shifted so
-    // that it has the 16-byte phase of its place in the output, and leaves by
-    // one bulk copy
-    const bool flat = bulk && (L2 & 1) != 0;
-    T* const dst = out + o0;
-    T* const stage = tile + (flat ? (int)(((uintptr_t)dst & 15u) / sizeof(T)) : 0);
-#pragma unroll
-    for (int u = 0; u < PPT; ++u) {
-      const int r = (int)threadIdx.x + u * NT;
-      if (r < rows) {
-        const int64_t pt = p0 + r;
-        const int g = P.point_index[pt];
-        T* row = stage + r * RS;
-        if (g < 0 || g >= P.ng * P.ng * P.ng) {
-          atomicOr(P.err, kErrGrid);
-          for (int k = 0; k < L2; ++k) row[k] = (T)0;
-        } else if constexpr (sizeof(T) == 8) {
-          proj_point_f64<STRICT>(P, g, P.atom_pos[3 * a], P.atom_pos[3 * a + 1], P.atom_pos[3 * a + 2], s, lmax, inv_box,
-                         inv_rmin, inv_dlog, G, reinterpret_cast<double*>(row));
-        } else {
-          const int4* ap = reinterpret_cast<const int4*>(P.atomf + a);
-          const int4 u4 = __ldg(ap), fh4 = __ldg(ap + 1), fl4 = __ldg(ap + 2);
-          const AtomF32 A = {{u4.x, u4.y, u4.z, 0},
-                             {__int_as_float(fh4.x), __int_as_float(fh4.y), __int_as_float(fh4.z), 0.0f},
-                             {__int_as_float(fl4.x), __int_as_float(fl4.y), __int_as_float(fl4.z), 0.0f}};
-          proj_point_f32(P, g, A, s, lmax, (float)P.h, (float)inv_dlog, reinterpret_cast<float*>(row));
-        }
+  };
+  // all threads: the grid indices (and, thread 0, the atom data) of tile t,
+  // whose descriptor is in ring slot ds, into buffer slot k; nothing for a
+  // descriptor whose ranges do not fit the problem (the tile is skipped)
+  auto fetch_tile = [&](int64_t t, int k, int ds) {
+    if (t >= total_tiles) return;
+    const ProjTile D = s_desc[ds];
+    if (!(D.rows >= 1 && D.rows <= TILE && D.p0 >= 0 && D.p0 <= P.n_points - D.rows && D.atom >= 0 &&
+          D.atom < P.n_atoms))
+      return;
+    const int* src = P.point_index + D.p0;
+    const int sh = (int)(((uintptr_t)src >> 2) & 3u);
+    const int head = min(D.rows, (4 - sh) & 3);           // indices before the first 16-byte boundary
+    const int nq = (D.rows - head) >> 2;                   // 16-byte groups
+    const int tail0 = head + 4 * nq;
+    for (int q = threadIdx.x; q < nq; q += NT) cp16(&s_idx[k][sh + head + 4 * q], src + head + 4 * q);
+    if ((int)threadIdx.x < head) cp4(&s_idx[k][sh + threadIdx.x], src + threadIdx.x);
+    if ((int)threadIdx.x < D.rows - tail0) cp4(&s_idx[k][sh + tail0 + threadIdx.x], src + tail0 + threadIdx.x);
+    if (threadIdx.x == 0) {
+      if constexpr (sizeof(T) == 4) {
+        const char* src = reinterpret_cast<const char*>(P.atomf + D.atom);
+        char* dst = reinterpret_cast<char*>(&s_atom[k]);
+        cp16(dst, src);
+        cp16(dst + 16, src + 16);
+        cp16(dst + 32, src + 32);
+      } else {
+        double* dst = reinterpret_cast<double*>(&s_atom[k]);
+        for (int c = 0; c < 3; ++c) cp8(dst + c, P.atom_pos + 3 * (int64_t)D.atom + c);
       }
     }
-    if (flat) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the rows, visible to the bulk copy
-      __syncthreads();
-      bulk_rows_out<T>(stage, rows * L2, dst);
-    } else {
-      __syncthreads();
-      copy_rows_out<T>(tile, rows, L2, RS, dst);
-    }
-    __syncthreads();  // the tile buffer is free and s_next holds the next tile
-  }
+  };
   if (threadIdx.x == 0) {
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    // every CTA draws from the counter until it passes the tile count, so
-    // once all have finished nothing reads it again in this launch: the last
-    // to finish clears it for the next launch
-    __threadfence();
-    if (atomicAdd(P.done, 1u) == gridDim.x - 1) {
-      *P.counter = 0ull;
-      *P.done = 0u;
-      __threadfence();
-    }
+    fetch_desc(blockIdx.x, 0);
+    fetch_desc(blockIdx.x + G, 1);
+    commit();
+    wait_all();
   }
+  __syncthreads();
+  fetch_tile(blockIdx.x, 0, 0);
+  commit();
+  wait_all();
+  __syncthreads();
+  int k = 0, ds = 0;
+  for (int64_t t = blockIdx.x; t < total_tiles; t += G) {
+    const int ds1 = ds == 2 ? 0 : ds + 1, ds2 = ds1 == 2 ? 0 : ds1 + 1;
+    if (threadIdx.x == 0) fetch_desc(t + 2 * G, ds2);
+    fetch_tile(t + G, k ^ 1, ds1);
+    commit();
+    const ProjTile D = s_desc[ds];
+    // the tile's atom, species and blocks, checked against the problem
+    const int64_t a = D.atom;
+    const int s = D.species;
+    bool ok = a >= 0 && a < P.n_atoms && s >= 0 && s < P.n_species;
+    const int lmax = ok ? P.lmax[s] : 0;
+    const int L2 = (lmax + 1) * (lmax + 1);
+    const int rows = D.rows;
+    const int64_t p0 = D.p0, o0 = D.o0;
+    ok = ok && rows >= 1 && rows <= TILE && p0 >= 0 && p0 <= P.n_points - rows && o0 >= 0 &&
+         o0 <= P.n_values - (int64_t)rows * L2;
+    const int RS = L2 | 1;
+    // odd row widths: each round's rows are staged contiguously (RS = L2),
+    // shifted so that they have the 16-byte phase of their place in the
+    // output (the same for every round: NT L2 values are a multiple of 16
+    // bytes), and leave by one bulk copy
+    // FP32 rows of 16 values (lmax 3) are staged contiguously too, by
+    // stage_rows16, and leave by the same bulk copy (for FP64 the sixteen
+    // values held in registers cost more occupancy than the copy-out loop:
+    // 96 registers instead of 56, 1.08 against 1.02 ms on the 512-atom
+    // problem)
+    const bool rows16 = sizeof(T) == 4 && ok && bulk && L2 == 16;
+    const bool flat = ok && bulk && ((L2 & 1) != 0 || rows16);
+    T* dst = out + o0;
+    const int phase = (int)(((uintptr_t)dst & 15u) / sizeof(T));
+    T* const stage = tile + (flat ? phase : 0);
+    if (!ok && threadIdx.x == 0) atomicOr(P.err, kErrOut);  // the same decision in every thread: the tile is skipped
+    const int nrounds = ok ? (rows + NT - 1) / NT : 0;
+#pragma unroll 1
+    for (int rd = 0; rd < nrounds; ++rd) {
+      const int r0 = rd * NT, rr = min(NT, rows - r0);
+      if constexpr (sizeof(T) == 4) {
+        if (rows16) {
+          const bool active = (int)threadIdx.x < rr;
+          float v[16];
+          if (active) {
+            const int g = s_idx[k][(int)(((uintptr_t)(P.point_index + p0) >> 2) & 3u) + r0 + threadIdx.x];
+            if (g < 0 || g >= P.ng * P.ng * P.ng) {
+              atomicOr(P.err, kErrGrid);
+#pragma unroll
+              for (int kk = 0; kk < 16; ++kk) v[kk] = 0.0f;
+            } else {
+              proj_point_f32<3>(P, g, s_atom[k], s, 3, v, [] {});
+            }
+          }
+          stage_rows16(tile, phase, (int)threadIdx.x, active, (int)threadIdx.x == rr - 1, v);
+        }
+      }
+      if (!rows16 && (int)threadIdx.x < rr) {
+        const int g = s_idx[k][(int)(((uintptr_t)(P.point_index + p0) >> 2) & 3u) + r0 + threadIdx.x];
+        T* row = stage + threadIdx.x * (flat ? L2 : RS);
+        if (g < 0 || g >= P.ng * P.ng * P.ng) {
+          atomicOr(P.err, kErrGrid);
+          for (int kk = 0; kk < L2; ++kk) row[kk] = (T)0;
+        } else if constexpr (sizeof(T) == 8) {
+          const double* ap = reinterpret_cast<const double*>(&s_atom[k]);
+          proj_point_f64<STRICT>(P, g, ap[0], ap[1], ap[2], s, lmax, reinterpret_cast<double*>(row), [] {});
+        } else {
+          proj_point_f32(P, g, s_atom[k], s, lmax, reinterpret_cast<float*>(row), [] {});
+        }
+      }
+      if (flat) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the rows, visible to the bulk copy
+      __syncthreads();  // every thread has written its row
+      if (flat)
+        bulk_rows_out<T>(stage, rr * L2, dst);  // thread 0 waits until the copy has read the buffer
+      else
+        copy_rows_out<T>(tile, rr, L2, RS, dst);
+      dst += (int64_t)rr * L2;
+      if (rd + 1 < nrounds) __syncthreads();  // the buffer is free for the next round
+    }
+    wait_all();       // this thread's copies for the next tiles have landed
+    __syncthreads();  // the tile buffer is free; the next tile's descriptor, indices and atom are visible
+    k ^= 1;
+    ds = ds1;
+  }
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // Launch variants of the persistent kernel (index = variant id): tile size,
-// points per thread, resident-CTA request for the register allocator, and
-// the store path of odd-width tiles.
+// threads per CTA (rows per round), resident-CTA request for the register
+// allocator, and the store path of odd-width rows.  (Tiles of 64 points,
+// two points per thread in one round, and a form with one 32-point work
+// unit per warp and no CTA barriers were measured slower on the 512-atom
+// problem and are not kept.)
 struct ProjVariant {
-  int tile, ppt, minb;
+  int tile, nt, minb;
   bool bulk;
   const char* name;
 };
 constexpr ProjVariant kProjVariants[] = {
-    {128, 1, 0, true, "tile128"},          {128, 1, 0, false, "tile128-copyout"},
-    {128, 1, 8, true, "tile128-regcap64"}, {128, 2, 0, true, "tile128-2ppt"},
-    {64, 1, 0, true, "tile64"},            {256, 1, 0, true, "tile256"},
+    {128, 128, 0, true, "tile128"},           {128, 128, 0, false, "tile128-copyout"},
+    {128, 128, 8, true, "tile128-regcap64"},  {256, 128, 0, true, "tile256-2rounds"},
+    {512, 128, 0, true, "tile512-4rounds"},   {256, 256, 0, true, "tile256"},
+    {512, 128, 8, true, "tile512-4rounds-regcap64"}, {512, 128, 10, true, "tile512-4rounds-regcap48"},
 };
+static_assert(kProjMinTile == 128, "every variant's tile is at least kProjMinTile points");
 constexpr int kNumProjVariants = sizeof(kProjVariants) / sizeof(kProjVariants[0]);
-constexpr int kDefaultProjVariant = 0;
+constexpr int kDefaultProjVariant = 4;  // tile512-4rounds: the fastest for FP32 and FP64 on the 512-atom problem
+constexpr int kStrictProjVariant = 0;  // SHM_STRICT_FP64 runs one launch shape: tile128
 constexpr size_t kProjMaxSmem = 232448;  // B300 opt-in shared memory per CTA
 
 // Shared memory of a launch: the staging tile (with room for the 16-byte
-// shift of a bulk-copied tile) and, for up to kSmemAtoms atoms, the tile
-// table.
+// shift of a bulk-copied tile).
 inline size_t proj_tile_bytes(int tile, int max_lmax, size_t es) {
   const int RS = ((max_lmax + 1) * (max_lmax + 1)) | 1;
   return ((size_t)tile * RS * es + 15) / 16 * 16 + 16;
 }
 inline size_t proj_smem(int variant, int max_lmax, size_t es, int64_t n_atoms) {
-  return proj_tile_bytes(kProjVariants[variant].tile, max_lmax, es) +
-         (n_atoms + 1 <= kSmemAtoms ? (size_t)(n_atoms + 1) * 4 : 0);
+  (void)n_atoms;
+  return proj_tile_bytes(kProjVariants[variant].nt, max_lmax, es);
 }
 
 std::mutex g_proj_mu;
@@ -921,12 +1105,12 @@ struct ProjPrepared {
 };
 std::unordered_map<const void*, ProjPrepared> g_prepared;
 
-template <typename T, int TILE, int PPT, int MINB, bool STRICT = false>
+template <typename T, int NT, int ROUNDS, int MINB, bool STRICT = false>
 shm_status launch_proj_v(const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, bool bulk, cudaStream_t s) {
-  auto kern = k_proj<T, TILE, PPT, MINB, STRICT>;
+  auto kern = k_proj<T, NT, ROUNDS, MINB, STRICT>;
   const int dev = current_device();
-  const size_t tile_bytes = proj_tile_bytes(TILE, max_lmax, sizeof(T));
-  const size_t smem = tile_bytes + (P.n_atoms + 1 <= kSmemAtoms ? (size_t)(P.n_atoms + 1) * 4 : 0);
+  const size_t tile_bytes = proj_tile_bytes(NT, max_lmax, sizeof(T));
+  const size_t smem = tile_bytes;
   {
     // the shared-memory opt-in, once per device (kept at the largest size any
     // problem needs)
@@ -941,10 +1125,10 @@ shm_status launch_proj_v(const ProjParams& P, int max_lmax, T* out, int64_t tile
     }
   }
   int b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TILE / PPT, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NT, smem);
   if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_proj)");
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tile_upper, (int64_t)sm_count(dev) * std::max(b, 1)));
-  kern<<<(unsigned)grid, TILE / PPT, smem, s>>>(P, out, (int)tile_bytes, tile_upper, bulk ? 1 : 0);
+  kern<<<(unsigned)grid, NT, smem, s>>>(P, out, (int)tile_bytes, tile_upper, bulk ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_proj launch");
   return SHM_OK;
@@ -954,7 +1138,7 @@ template <typename T>
 shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, cudaStream_t s) {
   const bool bulk = kProjVariants[variant].bulk;
   if constexpr (sizeof(T) == 8) {
-    // SHM_STRICT_FP64: one launch shape (the default variant's)
+    // SHM_STRICT_FP64: one launch shape (kStrictProjVariant's)
     if (P.strict) return launch_proj_v<T, 128, 1, 0, true>(P, max_lmax, out, tile_upper, true, s);
   }
   switch (variant) {
@@ -962,8 +1146,10 @@ shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, i
     case 1: return launch_proj_v<T, 128, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
     case 2: return launch_proj_v<T, 128, 1, 8>(P, max_lmax, out, tile_upper, bulk, s);
     case 3: return launch_proj_v<T, 128, 2, 0>(P, max_lmax, out, tile_upper, bulk, s);
-    case 4: return launch_proj_v<T, 64, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 4: return launch_proj_v<T, 128, 4, 0>(P, max_lmax, out, tile_upper, bulk, s);
     case 5: return launch_proj_v<T, 256, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 6: return launch_proj_v<T, 128, 4, 8>(P, max_lmax, out, tile_upper, bulk, s);
+    case 7: return launch_proj_v<T, 128, 4, 10>(P, max_lmax, out, tile_upper, bulk, s);
   }
   return fail(SHM_EINVAL, "unknown projector launch variant");
 }
@@ -983,6 +1169,11 @@ shm_status proj_params(const shm_proj_problem* prob, shm_dtype dtype, void* work
   shm_status st;
   const size_t es = dtype == SHM_F64 ? 8 : 4;
   if ((st = check_device_range(workspace, w.total, "workspace")) != SHM_OK) return st;
+  // the run copies indices and atom positions by cp.async, which needs
+  // naturally aligned sources
+  if (!aligned(p.point_index, 4) || !aligned(p.atom_pos, 8) || !aligned(p.atom_species, 4) ||
+      !aligned(p.point_offsets, 8) || !aligned(p.out_offsets, 8) || !aligned(p.radial, 8))
+    return fail(SHM_EINVAL, "problem arrays must be aligned to their element size");
   if (p.n_atoms > 0) {
     if ((st = check_device_range(p.atom_pos, (size_t)p.n_atoms * 24, "atom_pos")) != SHM_OK) return st;
     if ((st = check_device_range(p.atom_species, (size_t)p.n_atoms * 4, "atom_species")) != SHM_OK) return st;
@@ -1012,6 +1203,14 @@ shm_status proj_params(const shm_proj_problem* prob, shm_dtype dtype, void* work
   P->box = p.box;
   P->h = p.h;
   for (int s = 0; s < p.n_species; ++s) P->lmax[s] = (signed char)p.species_lmax[s];
+  P->inv_box = 1.0 / p.box;
+  P->inv_rmin = 1.0 / p.r_min;
+  P->inv_dlog = 1.0 / p.dlog;
+  P->lg_k0 = -std::log(p.r_min) * P->inv_dlog;
+  P->lg_k1 = 0.69314718055994530942 * 0.5 * P->inv_dlog;
+  P->lg_k2 = 0.5 * P->inv_dlog;
+  P->h32 = (float)p.h;
+  P->inv_dlog32 = (float)P->inv_dlog;
   {  // Granlund-Montgomery constants for division by ng (unsigned, dividends < 2^31)
     int l = 0;
     while ((1u << l) < (unsigned)p.ng) ++l;
@@ -1020,14 +1219,13 @@ shm_status proj_params(const shm_proj_problem* prob, shm_dtype dtype, void* work
     P->ng_shift = l;
   }
   char* ws = (char*)workspace;
-  P->counter = (unsigned long long*)(ws + w.counter);
-  P->err = (unsigned*)(ws + w.counter + 8);
-  P->done = (unsigned*)(ws + w.counter + 12);
+  P->err = (unsigned*)(ws + w.words + 8);
   P->tile_offsets = (int64_t*)(ws + w.tiles);
+  P->tiles = (ProjTile*)(ws + w.desc);
   P->atom_order = (int32_t*)(ws + w.order);
   P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
   P->atomf = dtype == SHM_F32 ? (AtomF32*)(ws + w.atomf) : nullptr;
-  P->rad32 = dtype == SHM_F32 ? (float*)(ws + w.rad32) : nullptr;
+  P->rad32 = dtype == SHM_F32 ? (float4*)(ws + w.rad32) : nullptr;
   P->coef = dtype == SHM_F64 ? (float4*)(ws + w.coef) : nullptr;
   P->hg = dtype == SHM_F64 ? (double*)(ws + w.hg) : nullptr;
   *max_lmax = ml;
@@ -1064,7 +1262,7 @@ shm_status check_out(const shm_proj_problem* prob, shm_dtype dtype, void* out) {
 // The variant a prepare uses: the tuned (or pinned) choice for the dtype if
 // its shared memory fits this problem, else the default.
 int prepare_variant(shm_dtype dtype, int max_lmax, int64_t n_atoms, bool strict = false) {
-  if (strict) return kDefaultProjVariant;
+  if (strict) return kStrictProjVariant;
   int v;
   {
     std::lock_guard<std::mutex> lk(g_proj_mu);
@@ -1358,8 +1556,8 @@ extern "C" shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_d
   if (st != SHM_OK) return st;
   if ((st = check_out(prob, dtype, out)) != SHM_OK) return st;
   load_proj_tune_cache();
-  // the set-up launch clears the work counter, the finish count and the
-  // error word before the persistent launch reads them
+  // the set-up launch writes the tile descriptors and clears the error word
+  // before the persistent launch reads them
   cudaStream_t s = (cudaStream_t)stream;
   st = prepare_in(prob, dtype, scratch, SHM_PROJ_NOALLOC_SCRATCH_BYTES, prepare_variant(dtype, ml, prob->n_atoms),
                   s);

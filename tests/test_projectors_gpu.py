@@ -321,9 +321,10 @@ def test_run_needs_a_prepared_workspace():
 
 
 def test_run_on_a_corrupted_workspace_stays_in_bounds():
-    """Garbage in the tile table and the atom order of a prepared workspace:
-    the run checks every index it follows against the problem, flags the
-    tiles that do not fit it and writes only inside the output; a new
+    """Garbage in the tile table, the atom order and the tile descriptors of
+    a prepared workspace, and a tile count above the problem's: the run
+    checks every descriptor and index it follows against the problem, flags
+    the tiles that do not fit it and writes only inside the output; a new
     prepare restores the correct values."""
     prob = small_problem(16)
     d = shm.DeviceProjectors(prob)
@@ -334,10 +335,16 @@ def test_run_on_a_corrupted_workspace_stays_in_bounds():
     n_atoms = prob.n_atoms
     g = torch.Generator().manual_seed(5)
     tiles = ws[256:256 + 8 * (n_atoms + 1)].view(torch.int64)
+    n_tiles = int(tiles[-1].item())
+    assert n_tiles > 0
     tiles.copy_(torch.randint(-50, 400, (n_atoms + 1,), generator=g))
+    tiles[-1] = n_tiles + 50
     order_off = 256 + ((8 * (n_atoms + 1) + 255) // 256) * 256
     order = ws[order_off:order_off + 4 * n_atoms].view(torch.int32)
     order.copy_(torch.randint(-3, n_atoms + 3, (n_atoms,), generator=g, dtype=torch.int32))
+    desc_off = order_off + ((4 * n_atoms + 255) // 256) * 256
+    desc = ws[desc_off:desc_off + 32 * n_tiles].view(torch.int32)
+    desc.copy_(torch.randint(-(1 << 31), (1 << 31) - 1, (8 * n_tiles,), generator=g, dtype=torch.int32))
     guard = torch.full((d.n_values + 64,), -7.0, dtype=torch.float64, device="cuda")
     shm.projectors_run(d, torch.float64, guard[:d.n_values], ws)
     torch.cuda.synchronize()
