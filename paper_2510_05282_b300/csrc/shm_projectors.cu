@@ -2,19 +2,21 @@
 // atom spheres of a periodic real-space grid (the use the paper's Sec. I
 // motivates: projectors of pseudopotential / PAW methods on a 3-D grid).
 //
-// Launch structure (both on the caller's stream):
+// Launch structure (all on the caller's stream):
 //  1. prepare, once per problem (shm_projectors_prepare): k_proj_setup (CTA
-//     0) orders the atoms by the lmax of their species, largest first
-//     (atom_order), validates every atom's offsets and species, builds the
-//     tile table in that order (tiles = TILE consecutive sphere points of one
-//     atom; tile_offsets[j] = number of tiles of the atoms before
-//     atom_order[j], 0 tiles for an atom that failed validation) and one
-//     descriptor per tile (first point, first output value, atom, species,
-//     rows), and zeroes the error word; with the other CTAs it converts the
-//     radial tables (FP32: float copies and the exponent table of the
-//     log-grid index; FP64: the interval cubics).  Tiles of one lmax then run
-//     together, so the SMs execute one row code path at a time
-//     (instruction-cache locality); the output layout, by atom, is unchanged.
+//     0) orders the atoms by the lmax of their species, largest first, then
+//     by species (atom_order), validates every atom's offsets and species,
+//     builds the tile table in that order (tiles = TILE consecutive sphere
+//     points of one atom; tile_offsets[j] = number of tiles of the atoms
+//     before atom_order[j], 0 tiles for an atom that failed validation) and
+//     one descriptor per tile (first point, first output value, atom,
+//     species, rows), and zeroes the error word; with the other CTAs it
+//     writes the radial tables' interval cubics (FP32, float-float or
+//     binary64) and, FP32, the exponent table of the log-grid index;
+//     k_proj_disp writes the displacement tables (per atom, axis and grid
+//     coordinate).  Tiles of one lmax then run together, so the SMs execute
+//     one row code path at a time (instruction-cache locality); the output
+//     layout, by atom, is unchanged.
 //  2. run, every call (shm_projectors_run): k_proj (persistent: SMs x
 //     resident CTAs, tiles dealt round robin) -- each CTA reads its next
 //     tile's descriptor, evaluates its rows -- minimum-image displacement,
@@ -50,13 +52,6 @@ constexpr int kExpLo = -160;  // FP32 log-grid exponent table covers frexpf expo
 constexpr int kExpHi = 140;
 constexpr int kExpN = kExpHi - kExpLo + 1;
 
-// An atom coordinate in grid units, q = pos / h = U + frac + (whole boxes),
-// U in [0, ng), frac in [0, 1) held as the float-float fhi + flo (FP32 path).
-struct __align__(16) AtomF32 {  // 48 bytes: three 16-byte loads
-  int U[4];
-  float fhi[4], flo[4];
-};
-
 // Tile descriptor (32 bytes), written by the set-up launch: the tile's first
 // sphere point and first output value, its atom, species and row count.
 struct __align__(16) ProjTile {
@@ -74,11 +69,10 @@ struct ProjWs {
   size_t order = 0;        // int32 atom_order[n_atoms]
   size_t desc = 0;         // ProjTile[n_points / kProjMinTile + n_atoms + 1]
   size_t etab = 0;         // FP32: int2 {I_e, bits(c_e)}[kExpN]
-  size_t atomf = 0;        // FP32: AtomF32[n_atoms] (atom coordinates in grid units)
+  size_t disp = 0;         // float (FP32) or double (FP64) disp[n_atoms][3][ng]: displacement tables
   size_t rad32 = 0;        // FP32: float4 {a0, a1, a2, a3}[n_species][n_rad][lstride] (cubic per interval)
   size_t coef = 0;         // FP64: {a0, a1, a2, a3}[n_species][n_rad][lstride] (cubic per interval), float-float
                            // (32 bytes a node) or, with SHM_STRICT_FP64, binary64 (32 bytes a node)
-  size_t hg = 0;           // FP64: double i * h for i < ng (grid coordinates, rounded as the definition)
   size_t total = 0;
 };
 
@@ -138,16 +132,14 @@ ProjWs proj_layout(const shm_proj_problem& p, shm_dtype dt) {
   if (dt == SHM_F32) {
     w.etab = end;
     end += round256((size_t)kExpN * 8);
-    w.atomf = end;
-    end += round256((size_t)p.n_atoms * sizeof(AtomF32));
     w.rad32 = end;
     end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 16);
   } else {
     w.coef = end;
     end += round256((size_t)p.n_species * p.radial_lstride * p.n_rad * 32);
-    w.hg = end;
-    end += round256((size_t)p.ng * 8);
   }
+  w.disp = end;
+  end += round256((size_t)p.n_atoms * 3 * p.ng * (dt == SHM_F64 ? 8 : 4));
   w.total = end;
   return w;
 }
@@ -172,10 +164,10 @@ struct ProjParams {
   int32_t* atom_order;
   int2* etab;
   float4* rad32;
-  AtomF32* atomf;
+  float* disp32;   // FP32: displacement tables [n_atoms][3][ng]
   float4* coef;  // two per node: {a0.hi, a0.lo, a1.hi, a1.lo}, {a2.hi, a2.lo, a3.hi, a3.lo}; strict: one double4
   int strict;    // FP64 with SHM_STRICT_FP64: binary64 tables, log-grid index and rows
-  double* hg;
+  double* disp64;  // FP64: displacement tables [n_atoms][3][ng]
   // derived on the host: 1/box, 1/r_min, 1/dlog, the log-grid constants
   // K0 = -ln(r_min)/dlog, K1 = ln2/(2 dlog), K2 = 1/(2 dlog), and FP32 h, 1/dlog
   double inv_box, inv_rmin, inv_dlog, lg_k0, lg_k1, lg_k2;
@@ -334,8 +326,6 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
       P.tiles[t0 + c] = D;
     }
   }
-  if (!fp32)
-    for (int i = tid; i < P.ng; i += blockDim.x) P.hg[i] = __dmul_rn((double)i, P.h);
   if (fp32) {
     // exponent table: r = m 2^e (m in [0.5, 1)), t = (e ln2 - ln r_min)/dlog + ln(m)/dlog
     //                 = I_e + c_e + ln(m)/dlog with I_e integer, c_e in [0, 1)
@@ -345,23 +335,6 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
       const double I = floor(C);
       const double I_cl = fmin(fmax(I, -2147483000.0), 2147483000.0);
       P.etab[i] = make_int2((int)I_cl, __float_as_int((float)(C - I)));
-    }
-    for (int64_t a = tid; a < P.n_atoms; a += blockDim.x) {
-      AtomF32 A = {};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double q = P.atom_pos[3 * a + c] / P.h;  // atom coordinate in grid units
-        const double U = floor(q);
-        const double fr = q - U;
-        // U modulo ng (whole boxes do not change the minimum image), so that
-        // the point's i - U lies in (-ng, ng) and one wrap reaches the image
-        double Um = U - (double)P.ng * floor(U / (double)P.ng);
-        Um = Um < 0.0 ? Um + (double)P.ng : (Um >= (double)P.ng ? Um - (double)P.ng : Um);
-        A.U[c] = (int)Um;
-        A.fhi[c] = (float)fr;
-        A.flo[c] = (float)(fr - (double)A.fhi[c]);
-      }
-      P.atomf[a] = A;
     }
   }
 }
@@ -454,6 +427,72 @@ __device__ __forceinline__ ff ff_log_mantissa(double f) {
   P = ff_add(ff_mul_u(P, z), ff{1.0f, 0.0f});
   const ff L = ff_mul(S, P);
   return {2.0f * L.hi, 2.0f * L.lo};
+}
+
+// ---------------------------------------------------------------------------
+// Displacement tables.  The minimum-image displacement of a grid point from
+// an atom is separable: its component along axis c depends only on the
+// point's grid coordinate i_c.  The set-up writes it for every atom, axis and
+// i < ng (k_proj_disp), so a point reads three values instead of forming
+// them: the same bits the formulas below give, with no per-point arithmetic.
+
+// FP64: grid coordinate i h (the binary64 product) minus the atom coordinate,
+// then the minimum image, d - box rint(d / box): the shift is decided on the
+// bit pattern of |d| (0 up to box/2, +-box up to 1.5 box; ties at exactly
+// box/2 go to 0 like rint's), the rounded product only beyond 1.5 box.  Each
+// step is the correctly rounded binary64 operation the definition states.
+__device__ __forceinline__ double disp_axis_f64(int i, double ac, const ProjParams& P) {
+  double d = __dsub_rn(__dmul_rn((double)i, P.h), ac);
+  const long long half_box = __double_as_longlong(0.5 * P.box), three_half_box = __double_as_longlong(1.5 * P.box);
+  const long long b = __double_as_longlong(d);
+  const long long mag = b & 0x7fffffffffffffffll;
+  if (mag > half_box) {
+    if (mag <= three_half_box)
+      d = __dsub_rn(d, __longlong_as_double(__double_as_longlong(P.box) | (b & (long long)0x8000000000000000ull)));
+    else
+      d = __dsub_rn(d, __dmul_rn(P.box, rint(d * P.inv_box)));
+  }
+  return d;
+}
+
+// FP32: the atom coordinate in grid units, q = pos / h = U + frac + (whole
+// boxes), U in [0, ng), frac in [0, 1) as the float-float fhi + flo; the
+// displacement in grid units, (i - U) - frac, minimum image in [-ng/2,
+// ng/2), formed exactly as a float-float (the integer part is exact), then
+// rounded once, times h.
+__device__ __forceinline__ float disp_axis_f32(int i, double pos, const ProjParams& P) {
+  const int ng = P.ng;
+  const double q = pos / P.h;
+  const double Uf = floor(q);
+  const double fr = q - Uf;
+  // U modulo ng (whole boxes do not change the minimum image), so that
+  // i - U lies in (-ng, ng) and one wrap reaches the image
+  double Um = Uf - (double)ng * floor(Uf / (double)ng);
+  Um = Um < 0.0 ? Um + (double)ng : (Um >= (double)ng ? Um - (double)ng : Um);
+  const int U = (int)Um;
+  const float fhi = (float)fr, flo = (float)(fr - (double)fhi);
+  const float half_box = 0.5f * small_int_to_float(ng);
+  int n = i - U;
+  const float dn = small_int_to_float(n) - fhi;
+  n = dn >= half_box ? n - ng : (dn < -half_box ? n + ng : n);
+  const ff sdiff = two_sum(small_int_to_float(n), -fhi);
+  const float lo = __fsub_rn(sdiff.lo, flo);
+  const float v = __fadd_rn(sdiff.hi, lo);  // grid units, rounded once
+  return v * P.h32;
+}
+
+// disp[a][c][i] for every atom, axis and grid coordinate (grid-stride).
+__global__ void __launch_bounds__(256) k_proj_disp(ProjParams P, int fp32) {
+  const int64_t ng = P.ng, n = P.n_atoms * 3 * ng;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ac = e / ng;  // a * 3 + c
+    const int i = (int)(e - ac * ng);
+    const double pos = P.atom_pos[ac];  // atom_pos[3 a + c]
+    if (fp32)
+      P.disp32[e] = disp_axis_f32(i, pos, P);
+    else
+      P.disp64[e] = disp_axis_f64(i, pos, P);
+  }
 }
 
 // Continuous log-grid index t = ln(r / r_min) / dlog from r^2 (a positive
@@ -557,41 +596,22 @@ __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bo
   }
 }
 
-// FP64 row: the displacement is formed exactly as the definition states
-// (grid point i*h minus the atom, then the minimum image), without FMA
-// contraction, so it is the correctly rounded binary64 value of each step.
-// STRICT (SHM_STRICT_FP64): the log-grid index from CUDA's binary64 log of
-// r^2, the interval cubic by binary64 Horner from binary64 coefficients, and
-// the all-binary64 harmonic row times f_l.
-// before_row() runs once, after the point's preamble and before its first
-// write to `row` (the warp-granular kernel waits there for its staging
-// buffer).
-template <bool STRICT = false, typename BeforeRow>
-__device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, double ax, double ay, double az,
-                                               int s, int lmax, double* row, BeforeRow&& before_row) {
-  const double inv_box = P.inv_box, inv_rmin = P.inv_rmin, inv_dlog = P.inv_dlog;
+// FP64 row of grid point g for the atom whose displacement tables start at
+// tb (the correctly rounded binary64 value of each step of the definition,
+// disp_axis_f64).  STRICT (SHM_STRICT_FP64): the log-grid index from CUDA's
+// binary64 log of r^2, the interval cubic by binary64 Horner from binary64
+// coefficients, and the all-binary64 harmonic row times f_l.
+template <bool STRICT = false>
+__device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const double* __restrict__ tb,
+                                               int s, int lmax, double* row) {
+  const double inv_rmin = P.inv_rmin, inv_dlog = P.inv_dlog;
   const LogGrid64 G = {P.lg_k0, P.lg_k1, P.lg_k2};
   const int ng = P.ng;
   const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
   const int gi = (int)div_ng((unsigned)q1, P.ng_magic, P.ng_shift);
   const int gj = q1 - gi * ng, gk = g - q1 * ng;
-  // i * h from the set-up table (the same binary64 product), minus the atom
-  double d[3] = {__dsub_rn(__ldg(P.hg + gi), ax), __dsub_rn(__ldg(P.hg + gj), ay), __dsub_rn(__ldg(P.hg + gk), az)};
-  // minimum image, d - box rint(d / box): the shift is decided on the bit
-  // pattern of |d| (0 up to box/2, +-box up to 1.5 box; ties at exactly box/2
-  // go to 0 like rint's), the rounded product only beyond 1.5 box
-  const long long half_box = __double_as_longlong(0.5 * P.box), three_half_box = __double_as_longlong(1.5 * P.box);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const long long b = __double_as_longlong(d[c]);
-    const long long mag = b & 0x7fffffffffffffffll;
-    if (mag > half_box) {
-      if (mag <= three_half_box)
-        d[c] = __dsub_rn(d[c], __longlong_as_double(__double_as_longlong(P.box) | (b & (long long)0x8000000000000000ull)));
-      else
-        d[c] = __dsub_rn(d[c], __dmul_rn(P.box, rint(d[c] * inv_box)));
-    }
-  }
+  // the minimum-image displacement from the atom's tables (disp_axis_f64)
+  double d[3] = {__ldg(tb + gi), __ldg(tb + ng + gj), __ldg(tb + 2 * ng + gk)};
   const bool origin = is_origin(d[0], d[1], d[2]);
   double t = 0.0;
   bool unit = false;
@@ -623,7 +643,6 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
     it = 0;  // below the grid, or t = -inf or NaN (u not finite)
     u = 0.0;
   }
-  before_row();
   if constexpr (STRICT) {
     // f_l(r): the interval's cubic in u by binary64 Horner, one 32-byte node
     const double4* c = reinterpret_cast<const double4*>(P.coef) + ((int64_t)s * P.n_rad + it) * P.lstride;
@@ -647,34 +666,20 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, doubl
   }
 }
 
-// FP32 row.  The displacement in grid units, (i - U) - frac with U = floor of
-// the atom coordinate in grid units, is formed exactly as a float-float (the
-// integer part is exact; frac is split into hi + lo on the host side of the
-// tile), then rounded once; the log-grid index uses the exponent table so
-// that only ln(mantissa) is taken in FP32 and t keeps ~1e-5 absolute accuracy
-// at t ~ 2000.  before_row() as for proj_point_f64.  LFIX >= 0: the row of
-// lmax LFIX (lmax is then ignored), written with compile-time indices (row
-// may be a register array).
-template <int LFIX = -1, typename BeforeRow>
-__device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const AtomF32& A, int s, int lmax,
-                                               float* row, BeforeRow&& before_row) {
-  const float h = P.h32, inv_dlog = P.inv_dlog32;
+// FP32 row of grid point g for the atom whose displacement tables start at
+// tb (disp_axis_f32); the log-grid index uses the exponent table so that
+// only ln(mantissa) is taken in FP32 and t keeps ~1e-5 absolute accuracy at
+// t ~ 2000.  LFIX >= 0: the row of lmax LFIX (lmax is then ignored), written
+// with compile-time indices (row may be a register array).
+template <int LFIX = -1>
+__device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const float* __restrict__ tb, int s,
+                                               int lmax, float* row) {
+  const float inv_dlog = P.inv_dlog32;
   const int ng = P.ng;
   const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
   const int gi = (int)div_ng((unsigned)q1, P.ng_magic, P.ng_shift);
-  const int gg[3] = {gi, q1 - gi * ng, g - q1 * ng};
-  const float half_box = 0.5f * small_int_to_float(ng);
-  float d[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    int n = gg[c] - A.U[c];  // whole grid units; displacement n - frac, minimum image in [-ng/2, ng/2)
-    const float dn = small_int_to_float(n) - A.fhi[c];
-    n = dn >= half_box ? n - ng : (dn < -half_box ? n + ng : n);
-    const ff sdiff = two_sum(small_int_to_float(n), -A.fhi[c]);
-    const float lo = __fsub_rn(sdiff.lo, A.flo[c]);
-    const float v = __fadd_rn(sdiff.hi, lo);  // grid units, rounded once
-    d[c] = v * h;
-  }
+  // the minimum-image displacement from the atom's tables (disp_axis_f32)
+  float d[3] = {__ldg(tb + gi), __ldg(tb + ng + (q1 - gi * ng)), __ldg(tb + 2 * ng + (g - q1 * ng))};
   const bool origin = is_origin(d[0], d[1], d[2]);
   int it = 0;
   float u = 0.0f;
@@ -716,7 +721,6 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
   }
   // f_l(r): the interval's cubic in u, one 16-byte node per l
   const float4* tab = P.rad32 + ((int64_t)s * P.n_rad + it) * P.lstride;
-  before_row();
   auto radial = [&](int l) {
     const float4 c = __ldg(tab + l);
     return fmaf(fmaf(fmaf(c.w, u, c.z), u, c.y), u, c.x);
@@ -885,12 +889,12 @@ __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int ro
 // tiles are ordered by the lmax of their atom, largest first, then by
 // species, so every CTA gets the same mix of row widths, and no counter,
 // atomic or search sits between two tiles.  Everything a tile reads from
-// global memory besides its radial tables arrives in shared memory ahead of
-// it by cp.async: thread 0 fetches descriptors two tiles ahead (a ring of
-// three), and all threads fetch the next tile's grid indices and thread 0
-// its atom data one tile ahead (two buffers), so neither the index stream
-// from DRAM nor the descriptor chain stalls the tile's arithmetic; two
-// barriers per tile remain (before and after the tile's stores).  Every
+// global memory besides its radial and displacement tables arrives in
+// shared memory ahead of it by cp.async: thread 0 fetches descriptors two
+// tiles ahead (a ring of three), and all threads fetch the next tile's grid
+// indices one tile ahead (two buffers), so neither the index stream from
+// DRAM nor the descriptor chain stalls the tile's arithmetic; two barriers
+// per round remain (before and after its stores).  Every
 // descriptor is checked against the problem (atom, species, row count, point
 // and value ranges) before it is used, and every grid index per point, so a
 // workspace that does not hold this problem's tables sets error bits
@@ -910,15 +914,10 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
   // part of the index stream arrives by 16-byte copies that bypass L1 (which
   // keeps the radial cubics)
   __shared__ __align__(16) int s_idx[2][TILE + 8];
-  __shared__ __align__(16) AtomF32 s_atom[2];  // FP32: the atom in grid units; FP64: its position (3 doubles)
   const int64_t total_tiles = min(max(P.tile_offsets[P.n_atoms], (int64_t)0), tile_limit);
   const int64_t G = gridDim.x;
   auto cp16 = [](void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-  };
-  auto cp8 = [](void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
   };
   auto cp4 = [](void* dst, const void* src) {
@@ -934,9 +933,9 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
       cp16(reinterpret_cast<char*>(&s_desc[ds]) + 16, reinterpret_cast<const char*>(P.tiles + t) + 16);
     }
   };
-  // all threads: the grid indices (and, thread 0, the atom data) of tile t,
-  // whose descriptor is in ring slot ds, into buffer slot k; nothing for a
-  // descriptor whose ranges do not fit the problem (the tile is skipped)
+  // all threads: the grid indices of tile t, whose descriptor is in ring
+  // slot ds, into buffer slot k; nothing for a descriptor whose ranges do not
+  // fit the problem (the tile is skipped)
   auto fetch_tile = [&](int64_t t, int k, int ds) {
     if (t >= total_tiles) return;
     const ProjTile D = s_desc[ds];
@@ -951,18 +950,6 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
     for (int q = threadIdx.x; q < nq; q += NT) cp16(&s_idx[k][sh + head + 4 * q], src + head + 4 * q);
     if ((int)threadIdx.x < head) cp4(&s_idx[k][sh + threadIdx.x], src + threadIdx.x);
     if ((int)threadIdx.x < D.rows - tail0) cp4(&s_idx[k][sh + tail0 + threadIdx.x], src + tail0 + threadIdx.x);
-    if (threadIdx.x == 0) {
-      if constexpr (sizeof(T) == 4) {
-        const char* src = reinterpret_cast<const char*>(P.atomf + D.atom);
-        char* dst = reinterpret_cast<char*>(&s_atom[k]);
-        cp16(dst, src);
-        cp16(dst + 16, src + 16);
-        cp16(dst + 32, src + 32);
-      } else {
-        double* dst = reinterpret_cast<double*>(&s_atom[k]);
-        for (int c = 0; c < 3; ++c) cp8(dst + c, P.atom_pos + 3 * (int64_t)D.atom + c);
-      }
-    }
   };
   if (threadIdx.x == 0) {
     fetch_desc(blockIdx.x, 0);
@@ -1023,7 +1010,7 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
 #pragma unroll
               for (int kk = 0; kk < 16; ++kk) v[kk] = 0.0f;
             } else {
-              proj_point_f32<3>(P, g, s_atom[k], s, 3, v, [] {});
+              proj_point_f32<3>(P, g, P.disp32 + a * 3 * P.ng, s, 3, v);
             }
           }
           stage_rows16(tile, phase, (int)threadIdx.x, active, (int)threadIdx.x == rr - 1, v);
@@ -1036,10 +1023,9 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
           atomicOr(P.err, kErrGrid);
           for (int kk = 0; kk < L2; ++kk) row[kk] = (T)0;
         } else if constexpr (sizeof(T) == 8) {
-          const double* ap = reinterpret_cast<const double*>(&s_atom[k]);
-          proj_point_f64<STRICT>(P, g, ap[0], ap[1], ap[2], s, lmax, reinterpret_cast<double*>(row), [] {});
+          proj_point_f64<STRICT>(P, g, P.disp64 + a * 3 * P.ng, s, lmax, reinterpret_cast<double*>(row));
         } else {
-          proj_point_f32(P, g, s_atom[k], s, lmax, reinterpret_cast<float*>(row), [] {});
+          proj_point_f32(P, g, P.disp32 + a * 3 * P.ng, s, lmax, reinterpret_cast<float*>(row));
         }
       }
       if (flat) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the rows, visible to the bulk copy
@@ -1224,10 +1210,10 @@ shm_status proj_params(const shm_proj_problem* prob, shm_dtype dtype, void* work
   P->tiles = (ProjTile*)(ws + w.desc);
   P->atom_order = (int32_t*)(ws + w.order);
   P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
-  P->atomf = dtype == SHM_F32 ? (AtomF32*)(ws + w.atomf) : nullptr;
+  P->disp32 = dtype == SHM_F32 ? (float*)(ws + w.disp) : nullptr;
   P->rad32 = dtype == SHM_F32 ? (float4*)(ws + w.rad32) : nullptr;
   P->coef = dtype == SHM_F64 ? (float4*)(ws + w.coef) : nullptr;
-  P->hg = dtype == SHM_F64 ? (double*)(ws + w.hg) : nullptr;
+  P->disp64 = dtype == SHM_F64 ? (double*)(ws + w.disp) : nullptr;
   *max_lmax = ml;
   // an upper bound of the tile count: every point of every atom in its own partial tile
   *tile_upper = p.n_points / tile + p.n_atoms;
@@ -1289,6 +1275,14 @@ shm_status prepare_in(const shm_proj_problem* prob, shm_dtype dtype, void* works
   k_proj_setup<<<setup_grid(P, dtype), 1024, 0, s>>>(P, kProjVariants[variant].tile, dtype == SHM_F32 ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, "k_proj_setup launch");
+  if (P.n_atoms > 0) {
+    const int dev = current_device();
+    const int64_t nd = P.n_atoms * 3 * (int64_t)P.ng;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nd + 255) / 256, (int64_t)(dev >= 0 ? sm_count(dev) : 1) * 8));
+    k_proj_disp<<<(unsigned)grid, 256, 0, s>>>(P, dtype == SHM_F32 ? 1 : 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "k_proj_disp launch");
+  }
   std::lock_guard<std::mutex> lk(g_proj_mu);
   g_prepared[workspace] = ProjPrepared{variant, dtype, prob->n_atoms, prob->n_points, prob->n_values, strict};
   return SHM_OK;
