@@ -579,20 +579,30 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool uni
   }
 }
 
-template <bool STRICT = false, typename T, typename Radial>
+// Row of a runtime lmax.  LCAP: the largest lmax the instantiation holds
+// code for (4 or 9; the launch picks 4 when no species goes above it, so
+// that the register allocation and the code follow the short rows alone).
+template <int LCAP, bool STRICT = false, typename T, typename Radial>
 __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin, bool unit,
                                                   Radial&& L, T* row) {
+  static_assert(LCAP == 4 || LCAP == 9, "LCAP is 4 or 9");
   switch (lmax) {
     case 0: proj_row<0, STRICT>(dx, dy, dz, origin, unit, L, row); break;
     case 1: proj_row<1, STRICT>(dx, dy, dz, origin, unit, L, row); break;
     case 2: proj_row<2, STRICT>(dx, dy, dz, origin, unit, L, row); break;
     case 3: proj_row<3, STRICT>(dx, dy, dz, origin, unit, L, row); break;
     case 4: proj_row<4, STRICT>(dx, dy, dz, origin, unit, L, row); break;
-    case 5: proj_row<5, STRICT>(dx, dy, dz, origin, unit, L, row); break;
-    case 6: proj_row<6, STRICT>(dx, dy, dz, origin, unit, L, row); break;
-    case 7: proj_row<7, STRICT>(dx, dy, dz, origin, unit, L, row); break;
-    case 8: proj_row<8, STRICT>(dx, dy, dz, origin, unit, L, row); break;
-    default: proj_row<9, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+    default:
+      if constexpr (LCAP == 9) {
+        switch (lmax) {
+          case 5: proj_row<5, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+          case 6: proj_row<6, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+          case 7: proj_row<7, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+          case 8: proj_row<8, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+          default: proj_row<9, STRICT>(dx, dy, dz, origin, unit, L, row); break;
+        }
+      }
+      break;
   }
 }
 
@@ -601,7 +611,7 @@ __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bo
 // disp_axis_f64).  STRICT (SHM_STRICT_FP64): the log-grid index from CUDA's
 // binary64 log of r^2, the interval cubic by binary64 Horner from binary64
 // coefficients, and the all-binary64 harmonic row times f_l.
-template <bool STRICT = false>
+template <int LCAP, bool STRICT = false>
 __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const double* __restrict__ tb,
                                                int s, int lmax, double* row) {
   const double inv_rmin = P.inv_rmin, inv_dlog = P.inv_dlog;
@@ -650,7 +660,7 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const
       const double4 a = c[l];
       return fma(fma(fma(a.w, u, a.z), u, a.y), u, a.x);
     };
-    proj_row_dispatch<true, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
+    proj_row_dispatch<LCAP, true, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
   } else {
     // f_l(r): the interval's cubic in u by Horner's rule in float-float (FP32
     // pipe), two 16-byte loads per l
@@ -662,7 +672,7 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const
       p = ff_add(ff_mul_u(p, U), ff{a01.z, a01.w});
       return ff_add(ff_mul_u(p, U), ff{a01.x, a01.y});
     };
-    proj_row_dispatch<false, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
+    proj_row_dispatch<LCAP, false, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
   }
 }
 
@@ -671,7 +681,7 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const
 // only ln(mantissa) is taken in FP32 and t keeps ~1e-5 absolute accuracy at
 // t ~ 2000.  LFIX >= 0: the row of lmax LFIX (lmax is then ignored), written
 // with compile-time indices (row may be a register array).
-template <int LFIX = -1>
+template <int LCAP, int LFIX = -1>
 __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const float* __restrict__ tb, int s,
                                                int lmax, float* row) {
   const float inv_dlog = P.inv_dlog32;
@@ -728,7 +738,7 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
   if constexpr (LFIX >= 0)
     proj_row<LFIX, false, float>(d[0], d[1], d[2], origin, true, radial, row);
   else
-    proj_row_dispatch<false, float>(lmax, d[0], d[1], d[2], origin, true, radial, row);
+    proj_row_dispatch<LCAP, false, float>(lmax, d[0], d[1], d[2], origin, true, radial, row);
 }
 
 // Rows of 16 floats (lmax 3) staged contiguously with 16-byte stores.  The
@@ -901,12 +911,16 @@ __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int ro
 // instead of reading or writing out of bounds; tile_limit caps the tile
 // count read from the workspace.  Nothing in the workspace changes during a
 // run: every launch is the same, and a CUDA graph replays it.
-template <typename T, int NT, int ROUNDS, int MINB, bool STRICT = false>
+// LCAP: rows up to lmax 4 or 9 (proj_row_dispatch).  (Two staging buffers
+// used in turn by consecutive rounds, which drop the barrier after each
+// round's stores, cost more in occupancy than they save: 0.258 against
+// 0.246 ms for FP32 on the 512-atom problem.)
+template <typename T, int NT, int ROUNDS, int MINB, bool STRICT = false, int LCAP = 9>
 __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__ out, int tile_bytes,
                                                   int64_t tile_limit, int bulk) {
   constexpr int TILE = NT * ROUNDS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tile = reinterpret_cast<T*>(smem_raw);
+  T* const tile = reinterpret_cast<T*>(smem_raw);
   (void)tile_bytes;
   __shared__ __align__(16) ProjTile s_desc[3];
   // grid indices of a tile: index p0 + r at s_idx[.][r + sh], sh the 16-byte
@@ -993,12 +1007,12 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
     const bool flat = ok && bulk && ((L2 & 1) != 0 || rows16);
     T* dst = out + o0;
     const int phase = (int)(((uintptr_t)dst & 15u) / sizeof(T));
-    T* const stage = tile + (flat ? phase : 0);
     if (!ok && threadIdx.x == 0) atomicOr(P.err, kErrOut);  // the same decision in every thread: the tile is skipped
     const int nrounds = ok ? (rows + NT - 1) / NT : 0;
 #pragma unroll 1
     for (int rd = 0; rd < nrounds; ++rd) {
       const int r0 = rd * NT, rr = min(NT, rows - r0);
+      T* const stage = tile + (flat ? phase : 0);
       if constexpr (sizeof(T) == 4) {
         if (rows16) {
           const bool active = (int)threadIdx.x < rr;
@@ -1010,7 +1024,7 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
 #pragma unroll
               for (int kk = 0; kk < 16; ++kk) v[kk] = 0.0f;
             } else {
-              proj_point_f32<3>(P, g, P.disp32 + a * 3 * P.ng, s, 3, v);
+              proj_point_f32<LCAP, 3>(P, g, P.disp32 + a * 3 * P.ng, s, 3, v);
             }
           }
           stage_rows16(tile, phase, (int)threadIdx.x, active, (int)threadIdx.x == rr - 1, v);
@@ -1023,9 +1037,9 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
           atomicOr(P.err, kErrGrid);
           for (int kk = 0; kk < L2; ++kk) row[kk] = (T)0;
         } else if constexpr (sizeof(T) == 8) {
-          proj_point_f64<STRICT>(P, g, P.disp64 + a * 3 * P.ng, s, lmax, reinterpret_cast<double*>(row));
+          proj_point_f64<LCAP, STRICT>(P, g, P.disp64 + a * 3 * P.ng, s, lmax, reinterpret_cast<double*>(row));
         } else {
-          proj_point_f32(P, g, P.disp32 + a * 3 * P.ng, s, lmax, reinterpret_cast<float*>(row));
+          proj_point_f32<LCAP>(P, g, P.disp32 + a * 3 * P.ng, s, lmax, reinterpret_cast<float*>(row));
         }
       }
       if (flat) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the rows, visible to the bulk copy
@@ -1061,11 +1075,15 @@ constexpr ProjVariant kProjVariants[] = {
     {128, 128, 8, true, "tile128-regcap64"},  {256, 128, 0, true, "tile256-2rounds"},
     {512, 128, 0, true, "tile512-4rounds"},   {256, 256, 0, true, "tile256"},
     {512, 128, 8, true, "tile512-4rounds-regcap64"}, {512, 128, 10, true, "tile512-4rounds-regcap48"},
+    {512, 64, 20, true, "tile512-8rounds-64t-regcap48"}, {512, 256, 5, true, "tile512-2rounds-256t-regcap48"},
 };
 static_assert(kProjMinTile == 128, "every variant's tile is at least kProjMinTile points");
 constexpr int kNumProjVariants = sizeof(kProjVariants) / sizeof(kProjVariants[0]);
-constexpr int kDefaultProjVariant = 4;  // tile512-4rounds: the fastest for FP32 and FP64 on the 512-atom problem
-constexpr int kStrictProjVariant = 0;  // SHM_STRICT_FP64 runs one launch shape: tile128
+// Defaults before (or without) tuning, the fastest on the 512-atom problem:
+// tile512-4rounds-regcap48 for FP32 (0.229 ms against 0.246 uncapped),
+// tile512-4rounds for FP64 (0.895 ms).
+inline int default_proj_variant(shm_dtype dt) { return dt == SHM_F32 ? 7 : 4; }
+constexpr int kStrictProjVariant = 4;  // SHM_STRICT_FP64 runs one launch shape: tile512-4rounds
 constexpr size_t kProjMaxSmem = 232448;  // B300 opt-in shared memory per CTA
 
 // Shared memory of a launch: the staging tile (with room for the 16-byte
@@ -1093,21 +1111,22 @@ std::unordered_map<const void*, ProjPrepared> g_prepared;
 
 template <typename T, int NT, int ROUNDS, int MINB, bool STRICT = false>
 shm_status launch_proj_v(const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, bool bulk, cudaStream_t s) {
-  auto kern = k_proj<T, NT, ROUNDS, MINB, STRICT>;
+  auto kern = max_lmax <= 4 ? k_proj<T, NT, ROUNDS, MINB, STRICT, 4> : k_proj<T, NT, ROUNDS, MINB, STRICT, 9>;
   const int dev = current_device();
   const size_t tile_bytes = proj_tile_bytes(NT, max_lmax, sizeof(T));
   const size_t smem = tile_bytes;
   {
-    // the shared-memory opt-in, once per device (kept at the largest size any
-    // problem needs)
+    // the shared-memory opt-in, once per kernel and device (kept at the
+    // largest size any problem needs)
     constexpr int MAXDEV = 64;
-    static size_t optin[MAXDEV] = {};
+    static size_t optin[2][MAXDEV] = {};
     std::lock_guard<std::mutex> lk(g_proj_mu);
     if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
-    if (optin[dev] < smem) {
+    size_t& done = optin[max_lmax <= 4 ? 0 : 1][dev];
+    if (done < smem) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_proj)");
-      optin[dev] = smem;
+      done = smem;
     }
   }
   int b = 0;
@@ -1125,7 +1144,7 @@ shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, i
   const bool bulk = kProjVariants[variant].bulk;
   if constexpr (sizeof(T) == 8) {
     // SHM_STRICT_FP64: one launch shape (kStrictProjVariant's)
-    if (P.strict) return launch_proj_v<T, 128, 1, 0, true>(P, max_lmax, out, tile_upper, true, s);
+    if (P.strict) return launch_proj_v<T, 128, 4, 0, true>(P, max_lmax, out, tile_upper, true, s);
   }
   switch (variant) {
     case 0:
@@ -1136,6 +1155,8 @@ shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, i
     case 5: return launch_proj_v<T, 256, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
     case 6: return launch_proj_v<T, 128, 4, 8>(P, max_lmax, out, tile_upper, bulk, s);
     case 7: return launch_proj_v<T, 128, 4, 10>(P, max_lmax, out, tile_upper, bulk, s);
+    case 8: return launch_proj_v<T, 64, 8, 20>(P, max_lmax, out, tile_upper, bulk, s);
+    case 9: return launch_proj_v<T, 256, 2, 5>(P, max_lmax, out, tile_upper, bulk, s);
   }
   return fail(SHM_EINVAL, "unknown projector launch variant");
 }
@@ -1254,9 +1275,9 @@ int prepare_variant(shm_dtype dtype, int max_lmax, int64_t n_atoms, bool strict 
     std::lock_guard<std::mutex> lk(g_proj_mu);
     v = g_proj_choice[dtype == SHM_F64 ? 1 : 0];
   }
-  if (v < 0) v = kDefaultProjVariant;
+  if (v < 0) v = default_proj_variant(dtype);
   const size_t es = dtype == SHM_F64 ? 8 : 4;
-  if (proj_smem(v, max_lmax, es, n_atoms) > kProjMaxSmem) v = kDefaultProjVariant;
+  if (proj_smem(v, max_lmax, es, n_atoms) > kProjMaxSmem) v = default_proj_variant(dtype);
   return v;
 }
 
@@ -1476,7 +1497,7 @@ extern "C" const char* shm_projectors_variant(shm_dtype dtype) {
   load_proj_tune_cache();
   std::lock_guard<std::mutex> lk(g_proj_mu);
   const int v = g_proj_choice[dtype == SHM_F64 ? 1 : 0];
-  return kProjVariants[v < 0 ? kDefaultProjVariant : v].name;
+  return kProjVariants[v < 0 ? default_proj_variant(dtype) : v].name;
 }
 
 extern "C" shm_status shm_projectors_set_variant(shm_dtype dtype, int variant) {
