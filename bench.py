@@ -636,9 +636,9 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
             "atoms": prob.n_atoms, "points": d.n_points, "values": d.n_values, "error_bits": err_bits,
             "launches_per_call": 1, "prepare_ms_once": prepare_ms, "launch_variant": shm.projectors_variant(dt),
             "autotune_best_ms": tuned_ms, "cuda_graph_replay": graph,
-            "arithmetic": ("FP64 out: binary64 displacement, r^2, 1/r and unit vector; float-float (2 x FP32) "
-                           "log-grid index, radial cubic and harmonic rows; within 1e-13 of the oracle"
-                           if es == 8 else "FP32 (FP64 1/r for |d| < 1e-2)"),
+            "arithmetic": ("FP64 out: binary64 displacement (per-atom tables), r^2, 1/r and unit vector; "
+                           "float-float (2 x FP32) log-grid index, radial cubic and harmonic rows; within 1e-13 "
+                           "of the oracle" if es == 8 else "FP32 (FP64 1/r for |d| < 1e-2)"),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": gbs / hbm_peak, "peak_source": peaks_src, "algorithmic_bytes": algo_bytes,
                          "def": "values x element size + 4 B grid index per point, / mean launch time"}}

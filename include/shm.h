@@ -226,10 +226,8 @@ size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dty
 
 /*
  * shm_projectors -- the fused projector values: shm_projectors_prepare then
- * shm_projectors_run on `stream` (two launches: the set-up, one CTA per
- * 1,024 table values up to the SM count -- for SHM_F32 they convert the
- * radial tables, for SHM_F64 they write each table interval's interpolating
- * cubic --, then the persistent launch).
+ * shm_projectors_run on `stream` (the set-up's two launches, then the
+ * persistent launch).
  *   dtype     : SHM_F64 (double out; binary64 for the displacement, r^2, 1/r
  *               and the unit vector, float-float (two FP32 numbers, ~48-bit
  *               significand) for the log-grid index, the radial cubic and
@@ -238,14 +236,17 @@ size_t shm_projectors_workspace_size(const shm_proj_problem* prob, shm_dtype dty
  *               and SHM_STRICT_FP64; the 4-point Lagrange interpolation
  *               evaluated as the interval's cubic in the fractional index,
  *               the same polynomial up to rounding) or
- *               SHM_F32 (FP32 arithmetic on FP32 copies of the tables, float
- *               out; grid displacements are formed exactly before rounding to
- *               float, 1/r in FP64 for |d| < 1e-2).
+ *               SHM_F32 (FP32 arithmetic on FP32 interval cubics of the
+ *               tables, float out; grid displacements are formed exactly
+ *               before rounding to float, 1/r in FP64 for |d| < 1e-2).
  *   out       : device [n_values] of dtype, caller-owned.
  *   workspace : device scratch of >= shm_projectors_workspace_size() bytes,
- *               caller-owned; it holds the work-queue counter, the per-atom
- *               tile table, an error word and the FP32 tables (SHM_F32) or
- *               the interval cubics (SHM_F64, 32 bytes per table node).  One
+ *               caller-owned; it holds the per-atom tile table and atom
+ *               order, one 32-byte descriptor per tile (n_points / 128 +
+ *               n_atoms + 1 of them), an error word, the interval cubics of
+ *               the radial tables (16 bytes per table node for SHM_F32, 32
+ *               for SHM_F64) and the displacement tables (per atom, axis and
+ *               grid coordinate: 3 ng values of dtype per atom).  One
  *               workspace must not be shared by calls that overlap on the GPU.
  * The kernel checks every index it reads through (species, grid index, table
  * stencil, output range) against the problem's sizes; an inconsistent problem
@@ -268,11 +269,12 @@ shm_status shm_projectors_ex(const shm_proj_problem* prob, shm_dtype dtype, unsi
 
 /*
  * shm_projectors_prepare -- the per-problem set-up of shm_projectors, done
- * once: one launch on `stream` that validates every atom's offsets and
- * species, orders the atoms by species lmax, builds the tile table (tiles of
- * the current launch variant's size) and writes the FP32 tables or the FP64
- * interval cubics into `workspace`; it clears the work counter and the error
- * word.  The workspace is then "prepared" for this problem and dtype, and
+ * once: two launches on `stream` that validate every atom's offsets and
+ * species, order the atoms by species lmax (then species), build the tile
+ * table and the tile descriptors (tiles of the current launch variant's
+ * size), write the interval cubics of the radial tables and the
+ * displacement tables into `workspace`, and clear the error word.  The
+ * workspace is then "prepared" for this problem and dtype, and
  * shm_projectors_run computes the values with one launch per call.  Prepare
  * again after changing any array of the problem or the variant choice.
  *   prob, dtype, workspace, workspace_bytes, stream : as shm_projectors.
@@ -288,11 +290,12 @@ shm_status shm_projectors_prepare_ex(const shm_proj_problem* prob, shm_dtype dty
 
 /*
  * shm_projectors_run -- the projector values on a prepared workspace: ONE
- * persistent launch on `stream` (SMs x resident CTAs drawing tiles from the
- * workspace's work counter; the last CTA to finish resets the counter for
- * the next run).  It allocates nothing and enqueues only that kernel, so it
+ * persistent launch on `stream` (SMs x resident CTAs taking the tiles round
+ * robin; it writes only the output and the error word, so every run is the
+ * same launch).  It allocates nothing and enqueues only that kernel, so it
  * can be captured into a CUDA graph and replayed.  Runs of one workspace on
- * different streams must not overlap on the GPU (they share the counter).
+ * different streams may overlap on the GPU only with different outputs
+ * (they share the error word).
  * Every index the kernel follows is checked on the device against the
  * problem; tiles that do not match it set error bit 8 and are skipped.
  * Errors: as shm_projectors; SHM_EINVAL when the workspace has not been
@@ -443,17 +446,15 @@ void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3]);
  * own pool (a further cudaMalloc fails or fragments that pool), or a time-step
  * loop with a fixed memory budget that may not grow or synchronise the device
  * through cudaMalloc/cudaFree.  They pass only the problem and the output;
- * the scratch (work counter, error word, per-atom tile table and, for
- * SHM_F32, the FP32 copies of the radial tables, for SHM_F64 the cubic of
- * each table interval, 32 bytes per node) lives in a static device
- * array of SHM_PROJ_NOALLOC_SCRATCH_BYTES bytes inside this library, which
- * every GPU that loads the library holds until the process exits.
+ * the scratch (the workspace of shm_projectors: tile table, descriptors,
+ * error word, interval cubics and displacement tables) lives in a static
+ * device array of SHM_PROJ_NOALLOC_SCRATCH_BYTES bytes inside this library,
+ * which every GPU that loads the library holds until the process exits.
  *   prob, dtype, out, stream : as shm_projectors.
  * The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress, with the device current) and caches it; make that
  * first call before any stream capture.  No call allocates or frees memory.
- * The counter and the error word are cleared at the start of every call, on
- * `stream`.  All calls share the one array: calls that overlap on the GPU
+ * The error word is cleared at the start of every call, on `stream`.  All calls share the one array: calls that overlap on the GPU
  * (on different streams or threads) race and must not be issued; calls on
  * one stream are ordered and safe.  The error word of this variant cannot be
  * read back (use shm_projectors with a workspace for that report); rows the
@@ -463,7 +464,7 @@ void shm_serve_generated_point(uint64_t seed, int64_t i, double xyz[3]);
  * SHM_PROJ_NOALLOC_SCRATCH_BYTES (shm_projectors_workspace_size tells how
  * much); SHM_ECUDA if the symbol lookup fails.
  */
-#define SHM_PROJ_NOALLOC_SCRATCH_BYTES (1u << 23)
+#define SHM_PROJ_NOALLOC_SCRATCH_BYTES (1u << 25)
 shm_status shm_projectors_noalloc(const shm_proj_problem* prob, shm_dtype dtype, void* out, void* stream);
 
 /*

@@ -310,7 +310,7 @@ _EXTRA_DECLS.extend([
     ("shm_projectors_set_variant", ([ctypes.c_int, ctypes.c_int], ctypes.c_int)),
 ])
 
-PROJ_NOALLOC_SCRATCH_BYTES = 1 << 23
+PROJ_NOALLOC_SCRATCH_BYTES = 1 << 25
 
 
 class DeviceProjectors:

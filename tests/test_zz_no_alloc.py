@@ -66,7 +66,7 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
                                     lmax_choices=(2, 3, 4), n_rad=200, r_min=1e-3, r_max=3.0, extra=10)
     d = shm.DeviceProjectors(prob)
     big = _binding._ProjProblem.from_buffer_copy(d.c)
-    big.n_rad = 200_000          # FP32 tables of 3 x 5 x 200000 floats: 12 MB > 8 MiB
+    big.n_rad = 200_000          # FP32 interval cubics of 3 x 5 x 200000 nodes, 16 bytes each: 48 MB > 32 MiB
     out = torch.zeros(d.n_values, dtype=torch.float32, device="cuda")
     L = shm.lib()
     assert L.shm_projectors_noalloc(ctypes.byref(big), shm.SHM_F32, out.data_ptr(), None) == 1
