@@ -263,6 +263,77 @@ def test_every_projector_variant_is_bitwise_the_same(dtype):
     assert len(names) == shm.projectors_variant_count()
 
 
+def _reshape(prob, species_lmax, atom_species, counts, radial=None):
+    """The problem with its species, and each atom's sphere list cut to its
+    first counts[a] points (every listed point stays inside its sphere), with
+    the offsets rebuilt."""
+    import dataclasses
+    poff = np.asarray(prob.point_offsets)
+    lists = [np.asarray(prob.point_index)[poff[a]:poff[a] + c] for a, c in enumerate(counts)]
+    n = np.array([len(x) for x in lists], dtype=np.int64)
+    lm = np.asarray(species_lmax)[np.asarray(atom_species)].astype(np.int64)
+    return dataclasses.replace(
+        prob, species_lmax=np.asarray(species_lmax, dtype=np.int32),
+        atom_species=np.asarray(atom_species, dtype=np.int32),
+        radial=prob.radial if radial is None else radial,
+        point_offsets=np.concatenate([[0], np.cumsum(n)]).astype(np.int64),
+        point_index=np.concatenate(lists).astype(np.int32),
+        out_offsets=np.concatenate([[0], np.cumsum(n * (lm + 1) ** 2)]).astype(np.int64))
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, PROJ_TOL_F64), (torch.float32, PROJ_TOL_F32)])
+def test_lmax3_rows_at_every_output_phase(oracle_mod, dtype, tol):
+    """Rows of 16 values (lmax 3) go out by 16-byte staging and one bulk copy
+    (FP32), the straddled 16-byte chunks completed from the lane before: atoms
+    of lmax 0 (one value per point) in front of each lmax-3 atom shift its
+    block to every 16-byte phase of the output, with ragged last tiles; the
+    values match the oracle and, bit for bit, the copy-out variant."""
+    base = small_problem(21, n_atoms=8, lmax_choices=(0, 3), n_species=2)
+    n = np.diff(np.asarray(base.point_offsets))
+    counts, total = [], 0
+    for a in range(8):
+        if a % 2 == 0:  # lmax 0, sized so that the next block starts at phase (a // 2) of 4 values
+            c = int(n[a]) - ((total + int(n[a]) - a // 2) % 4)
+            assert c > 0
+        else:
+            c = int(n[a]) - (int(n[a]) % 128 == 0)  # a ragged last tile
+        counts.append(c)
+        total += c * (1 if a % 2 == 0 else 16)
+    prob = _reshape(base, [0, 3], [a % 2 for a in range(8)], counts)
+    ooff = np.asarray(prob.out_offsets)
+    assert sorted(int(ooff[a]) % 4 for a in (1, 3, 5, 7)) == [0, 1, 2, 3]
+    d = shm.DeviceProjectors(prob)
+    got = run(prob, dtype)
+    check(prob, got, oracle_mod.projectors(prob), tol, f"lmax-3 phases {dtype}")
+    try:
+        shm.set_projectors_variant(dtype, 1)        # tile128-copyout
+        ws = d.workspace(dtype)
+        ref = shm.projectors(d, dtype, workspace=ws)
+        torch.cuda.synchronize()
+        assert shm.projectors_check(ws) == 0
+    finally:
+        shm.set_projectors_variant(dtype, -1)
+    assert np.array_equal(got, ref.cpu().numpy())
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_rows_up_to_lmax4_and_up_to_lmax9_agree(dtype):
+    """A problem whose species all have lmax <= 4 runs the row code built up
+    to lmax 4; the same atoms with one more (unused) species of lmax 9 run
+    the code built up to lmax 9: the same bits."""
+    prob = small_problem(4, n_atoms=8)
+    S, Ls, nr = prob.radial.shape
+    radial9 = np.zeros((S + 1, 10, nr))
+    radial9[:S, :Ls] = prob.radial
+    radial9[S] = prob.radial[0, 0]
+    n = np.diff(np.asarray(prob.point_offsets))
+    wide = _reshape(prob, list(prob.species_lmax) + [9], prob.atom_species, n, radial=radial9)
+    assert int(np.max(prob.species_lmax)) <= 4
+    a = run(prob, dtype)
+    b = run(wide, dtype)
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_run_captured_in_a_cuda_graph(dtype):
     """shm_projectors_run is one launch that allocates nothing: captured into
