@@ -222,7 +222,7 @@ def _prob_all_lmax():
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, PROJ_TOL_F64), (torch.float32, PROJ_TOL_F32)])
 def test_prepare_once_run_many(oracle_mod, dtype, tol):
     """One set-up launch, then several single-launch runs: each run gives the
-    same bits (the last CTA of a run resets the work counter for the next)."""
+    same bits (a run writes nothing in the workspace but the error word)."""
     prob = _prob_all_lmax()
     d = shm.DeviceProjectors(prob)
     ws = d.workspace(dtype)
