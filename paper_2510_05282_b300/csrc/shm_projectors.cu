@@ -161,6 +161,7 @@ struct ProjParams {
   unsigned* err;
   int64_t* tile_offsets;
   ProjTile* tiles;
+  int64_t tiles_cap;  // descriptors the workspace holds (n_points / kProjMinTile + n_atoms + 1)
   int32_t* atom_order;
   int2* etab;
   float4* rad32;
@@ -306,9 +307,15 @@ __global__ void __launch_bounds__(1024) k_proj_setup(ProjParams P, int tpb, int 
   }
   if (err) atomicOr(P.err, err);
   // one descriptor per tile, each atom's tiles written by one warp (the
-  // offsets of the scan above are visible to the whole CTA after its barriers)
+  // offsets of the scan above are visible to the whole CTA after its
+  // barriers).  Atoms whose point ranges overlap can claim more tiles than
+  // the problem has points for: nothing is written past the workspace's
+  // descriptors (the run reads no further than that either), and the
+  // offsets error bit is set.
+  if (tid == 0 && P.tile_offsets[P.n_atoms] > P.tiles_cap) atomicOr(P.err, kErrOffsets);
   for (int64_t j = wid; j < P.n_atoms; j += blockDim.x >> 5) {
-    const int64_t t0 = P.tile_offsets[j], nt = P.tile_offsets[j + 1] - t0;
+    const int64_t t0 = P.tile_offsets[j];
+    const int64_t nt = min(P.tile_offsets[j + 1], P.tiles_cap) - t0;
     if (nt <= 0) continue;
     const int a = P.atom_order[j];
     const int s = P.atom_species[a];
@@ -1272,6 +1279,7 @@ shm_status proj_params(const shm_proj_problem* prob, shm_dtype dtype, void* work
   P->err = (unsigned*)(ws + w.words + 8);
   P->tile_offsets = (int64_t*)(ws + w.tiles);
   P->tiles = (ProjTile*)(ws + w.desc);
+  P->tiles_cap = p.n_points / kProjMinTile + p.n_atoms + 1;
   P->atom_order = (int32_t*)(ws + w.order);
   P->etab = dtype == SHM_F32 ? (int2*)(ws + w.etab) : nullptr;
   P->disp32 = dtype == SHM_F32 ? (float*)(ws + w.disp) : nullptr;

@@ -428,6 +428,38 @@ def test_run_on_a_corrupted_workspace_stays_in_bounds():
     assert torch.equal(out, ref) and shm.projectors_check(ws) == 0
 
 
+def test_overlapping_atom_ranges_stay_in_bounds():
+    """Point offsets whose valid atoms overlap (each even atom claims every
+    point; the odd atoms between them have reversed offsets and are
+    rejected) claim more tiles than the workspace has descriptors for: the
+    set-up writes none past them and flags the offsets, and the run writes
+    only inside the output."""
+    import dataclasses
+    base = small_problem(7)
+    n, A = base.n_points, base.n_atoms
+    assert A == 6
+    poff = np.array([0, n, 0, n, 0, n, 0], dtype=np.int64)
+    lm = np.asarray(base.species_lmax)[np.asarray(base.atom_species)].astype(np.int64)
+    ooff = [0]
+    for a in range(A):
+        ooff.append(ooff[-1] + (n * (lm[a] + 1) ** 2 if a % 2 == 0 else 0))
+    prob = dataclasses.replace(base, point_offsets=poff, out_offsets=np.array(ooff, dtype=np.int64))
+    d = shm.DeviceProjectors(prob)
+    assert d.n_values == ooff[-1]
+    assert 3 * -(-n // 128) > n // 128 + A + 1     # 128-point tiles: more than the descriptors
+    for dtype in (torch.float64, torch.float32):
+        try:
+            shm.set_projectors_variant(dtype, 0)    # tile128
+            ws = d.workspace(dtype)
+            guard = torch.full((d.n_values + 64,), -7.0, dtype=dtype, device="cuda")
+            shm.projectors(d, dtype, out=guard[:d.n_values], workspace=ws)
+            torch.cuda.synchronize()
+        finally:
+            shm.set_projectors_variant(dtype, -1)
+        assert torch.all(guard[d.n_values:] == -7.0)
+        assert shm.projectors_check(ws) & 1
+
+
 # ------------------------------------------------- all-binary64 projectors (SHM_STRICT_FP64)
 
 def run_strict(prob):
