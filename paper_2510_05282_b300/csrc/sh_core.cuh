@@ -951,8 +951,10 @@ __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& sto
 }
 
 // Full point: Cartesian (or already normalised) input -> row of harmonics.
-// HYBRID selects sh_row_hybrid for binary64 rows.
-template <int LMAX, bool HYBRID = false, bool CX = false, typename T, typename Store>
+// HYBRID selects sh_row_hybrid for binary64 rows.  EMU (all-binary64 rows,
+// CX = false): sh_row_emu<LMAX, EMU>, the same bits, with sh_row for a point
+// where dmul_int declines a product.
+template <int LMAX, bool HYBRID = false, bool CX = false, int EMU = 0, typename T, typename Store>
 __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&& store) {
   if (is_origin(x, y, z)) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
     store(0, (T)kInvSqrt4Pi);
@@ -968,10 +970,13 @@ __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&&
     for (int k = 1; k < NH<LMAX>::value; ++k) store(k, (T)__longlong_as_double(0x7ff8000000000000ll));
     return;
   }
-  if constexpr (HYBRID && sizeof(T) == 8)
+  if constexpr (HYBRID && sizeof(T) == 8) {
     sh_row_hybrid<LMAX, CX>(xb, yb, zb, store);
-  else
+  } else if constexpr (EMU != 0 && !CX && sizeof(T) == 8) {
+    if (sh_row_emu<LMAX, EMU>(xb, yb, zb, store)) sh_row<LMAX>(xb, yb, zb, store);
+  } else {
     sh_row<LMAX, CX>(xb, yb, zb, store);
+  }
 }
 
 }  // namespace shm

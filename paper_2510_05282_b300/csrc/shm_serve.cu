@@ -196,8 +196,9 @@ __device__ __forceinline__ void serve_tile64(const ServeChunk& c, long long p, i
 }
 
 // All-binary64 rows (SHM_REQ_STRICT_FP64): shm_eval's staged-64 tile (the
-// m-major rows of sh_row staged whole, coalesced copy-out), bitwise the rows
-// of shm_eval_ex with SHM_STRICT_FP64.
+// m-major rows staged whole, coalesced copy-out) with the output products
+// on the integer pipes, bitwise the rows of shm_eval_ex with
+// SHM_STRICT_FP64.
 template <int LMAX>
 __device__ __forceinline__ void serve_tile64s(const ServeChunk& c, long long p, int rows, double* tile) {
   constexpr int L2 = TileShape<LMAX>::L2;
@@ -214,7 +215,9 @@ __device__ __forceinline__ void serve_tile64s(const ServeChunk& c, long long p, 
       gen_point_dev(c.seed, pi, x, y, z);
     }
     double* row = tile + threadIdx.x * RS;
-    sh_point<LMAX>(x, y, z, false, [&](int k, double v) { row[k] = v; });
+    // the output products on the integer pipes (dmul_int), as the default
+    // all-binary64 variant of shm_eval: the same bits
+    sh_point<LMAX, false, false, kEmuOut>(x, y, z, false, [&](int k, double v) { row[k] = v; });
   }
   __syncthreads();
   double* dst = reinterpret_cast<double*>(c.out) + p * L2;
