@@ -362,7 +362,9 @@ shm_status ang_launch(const T* ang, int64_t n, T* out, bool vec, cudaStream_t s,
   if constexpr (sizeof(T) == 8) {
     if (vec) {
       bool launched = false;
-      shm_status st = strict ? launch_rows_tma<LMAX, 64, kInAngles>(ang, n, out, false, s, &launched)
+      // strict: the default all-binary64 form of shm_eval (rows-tma-emu-o-32:
+      // the output products on the integer pipes, the same bits)
+      shm_status st = strict ? launch_rows_tma<LMAX, 32, kInAngles, kEmuOut>(ang, n, out, false, s, &launched)
                              : launch_phased_tma<LMAX, kAngTPB64, kInAngles>(ang, n, out, false, s, &launched);
       if (st != SHM_OK || launched) return st;
     }
