@@ -212,20 +212,20 @@ __device__ __forceinline__ double dmul_int(double a, double b, unsigned& bad) {
 // x + iy, for instance on an axis, takes that path).
 enum : int { kEmuOut = 1, kEmuScale = 2, kEmuRec = 4, kEmuM0 = 8 };
 
-template <int LMAX, int EMU, typename Store>
+template <int LMAX, int EMU, bool CX = false, typename Store>
 __device__ __forceinline__ unsigned sh_row_emu(double xb, double yb, double zb, Store&& store) {
   unsigned bad = 0u;
   auto mul = [&](bool emu, double a, double b) { return emu ? dmul_int(a, b, bad) : a * b; };
   constexpr bool OUT = (EMU & kEmuOut) != 0, SCL = (EMU & kEmuScale) != 0, REC = (EMU & kEmuRec) != 0,
                  M0 = (EMU & kEmuM0) != 0;
-  store(0, Sd<false>(0, 0));
+  store(0, Sd<CX>(0, 0));
   if constexpr (LMAX >= 1) {
-    store(2, mul(M0, Sd<false>(1, 0), zb));
+    store(2, mul(M0, Sd<CX>(1, 0), zb));
     double q2 = 1.0, q1 = zb;
 #pragma unroll
     for (int l = 2; l <= LMAX; ++l) {
       const double q = fma(zb, q1, -mul(M0, SHM_G[l][0], q2));
-      store(l * l + l, mul(M0, Sd<false>(l, 0), q));
+      store(l * l + l, mul(M0, Sd<CX>(l, 0), q));
       q2 = q1;
       q1 = q;
     }
@@ -239,10 +239,10 @@ __device__ __forceinline__ unsigned sh_row_emu(double xb, double yb, double zb, 
       A = An;
       B = Bn;
     }
-    store(m * m + 2 * m, mul(OUT, Sd<false>(m, m), A));
-    store(m * m, mul(OUT, Sd<false>(m, m), B));
+    store(m * m + 2 * m, mul(OUT, Sd<CX>(m, m), A));
+    store(m * m, mul(OUT, Sd<CX>(m, m), B));
     if (m + 1 <= LMAX) {
-      const double s = mul(SCL, Sd<false>(m + 1, m), zb);
+      const double s = mul(SCL, Sd<CX>(m + 1, m), zb);
       const int k0 = (m + 1) * (m + 1) + (m + 1);
       store(k0 + m, mul(OUT, s, A));
       store(k0 - m, mul(OUT, s, B));
@@ -251,7 +251,7 @@ __device__ __forceinline__ unsigned sh_row_emu(double xb, double yb, double zb, 
 #pragma unroll
     for (int l = m + 2; l <= LMAX; ++l) {
       const double q = fma(zb, q1, -mul(REC, SHM_G[l][m], q2));
-      const double s = mul(SCL, Sd<false>(l, m), q);
+      const double s = mul(SCL, Sd<CX>(l, m), q);
       store(l * l + l + m, mul(OUT, s, A));
       store(l * l + l - m, mul(OUT, s, B));
       q2 = q1;
@@ -951,9 +951,9 @@ __device__ __forceinline__ void sh_row(float xb, float yb, float zb, Store&& sto
 }
 
 // Full point: Cartesian (or already normalised) input -> row of harmonics.
-// HYBRID selects sh_row_hybrid for binary64 rows.  EMU (all-binary64 rows,
-// CX = false): sh_row_emu<LMAX, EMU>, the same bits, with sh_row for a point
-// where dmul_int declines a product.
+// HYBRID selects sh_row_hybrid for binary64 rows.  EMU (all-binary64 rows):
+// sh_row_emu<LMAX, EMU, CX>, the same bits, with sh_row for a point where
+// dmul_int declines a product.
 template <int LMAX, bool HYBRID = false, bool CX = false, int EMU = 0, typename T, typename Store>
 __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&& store) {
   if (is_origin(x, y, z)) {  // Sec. II: Y = 0 at r = 0 except the constant l = 0
@@ -972,8 +972,8 @@ __device__ __forceinline__ void sh_point(T x, T y, T z, bool normalized, Store&&
   }
   if constexpr (HYBRID && sizeof(T) == 8) {
     sh_row_hybrid<LMAX, CX>(xb, yb, zb, store);
-  } else if constexpr (EMU != 0 && !CX && sizeof(T) == 8) {
-    if (sh_row_emu<LMAX, EMU>(xb, yb, zb, store)) sh_row<LMAX>(xb, yb, zb, store);
+  } else if constexpr (EMU != 0 && sizeof(T) == 8) {
+    if (sh_row_emu<LMAX, EMU, CX>(xb, yb, zb, store)) sh_row<LMAX, CX>(xb, yb, zb, store);
   } else {
     sh_row<LMAX, CX>(xb, yb, zb, store);
   }

@@ -269,8 +269,9 @@ __global__ void __launch_bounds__(kSpTPBs) k_eval_spinor64s(const double* __rest
     if ((int)threadIdx.x < rows) {
       const int64_t p = p0 + threadIdx.x;
       double* row = tile + threadIdx.x * RS;
-      sh_point<LMAX>(pts[3 * p], pts[3 * p + 1], pts[3 * p + 2], normalized != 0,
-                     [&](int k, double v) { row[k] = v; });
+      // the output products on the integer pipes (dmul_int): the same bits
+      sh_point<LMAX, false, false, kEmuOut>(pts[3 * p], pts[3 * p + 1], pts[3 * p + 2], normalized != 0,
+                                            [&](int k, double v) { row[k] = v; });
     }
     __syncthreads();
     const int nv = rows * NC;
