@@ -156,14 +156,24 @@ def cpu_oracle_rate(points: np.ndarray, lmax: int, budget_s: float, nthreads: in
     return oracle_timing(points, lmax, budget_s / 4, 3, 1, nthreads)
 
 
+def reference_step_budget(args) -> float:
+    """Seconds of oracle work per step of the reference arm for this
+    invocation's --steps / --warmup / --cpu-seconds: about two minutes for the
+    whole run, at most --cpu-seconds (and 20 s) per step."""
+    return min(args.cpu_seconds, 20.0, max(0.05, 120.0 / max(1, args.steps + args.warmup)))
+
+
 def reference_arm_baseline(args):
     """The GPU line's cpu_baseline: the reference arm of this file (the oracle
-    on the host cores) run as a fresh process, so that both lines time the
-    oracle with the same program in the same kind of process; three timed
-    steps after three warm-up steps of about args.cpu_seconds / 6 each."""
-    step_s = max(0.5, args.cpu_seconds / 6)
+    on the host cores) run as a fresh process with the per-step budget the
+    reference arm gets for the same --steps / --warmup, so that both lines
+    time the same prefix of the grid with the same program in the same kind
+    of process (the oracle's rate depends on the prefix size: its threads'
+    start-up is a larger share of a short call); three timed steps after
+    three warm-up steps."""
+    step_s = reference_step_budget(args)
     cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "3", "--warmup", "3",
-           "--cpu-seconds", str(step_s)]
+           "--step-budget", str(step_s)]
     try:
         r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=dict(os.environ, WORLD_SIZE="1",
                                                                                       RANK="0"))
@@ -171,7 +181,8 @@ def reference_arm_baseline(args):
         ref = json.loads(lines[-1])
         cb = dict(ref["cpu_baseline"])
         cb["protocol"] = (cb.get("protocol", "") + "; measured by `bench.py --impl reference --steps 3 --warmup 3 "
-                          f"--cpu-seconds {step_s}` as a separate process")
+                          f"--step-budget {step_s:.3g}` as a separate process (the reference arm's per-step budget "
+                          "for this invocation's --steps / --warmup)")
         return cb
     except Exception as e:  # reported, never silently dropped
         return {"value": None, "unit": UNIT, "kind": "oracle", "error": repr(e)}
@@ -186,7 +197,7 @@ def run_reference(args, rank, world):
     # about two minutes for the whole run whatever --steps and --warmup are,
     # and at most --cpu-seconds per step; the same protocol as the GPU arm's
     # cpu_baseline (oracle_timing), with one call per step
-    budget = min(args.cpu_seconds, 20.0, max(0.05, 120.0 / max(1, args.steps + args.warmup)))
+    budget = args.step_budget if args.step_budget is not None else reference_step_budget(args)
     value, sample_pts, cores = oracle_timing(pts, LMAX, budget, args.steps, args.warmup)
     ms = pts.shape[0] * nh / value * 1e3
     line = {
@@ -788,6 +799,8 @@ def main():
     ap.add_argument("--grid", type=int, default=N_SIDE, help="grid side (192 = the benchmark workload; "
                     "smaller sides only for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--step-budget", type=float, default=None,
+                    help="reference arm: seconds of oracle work per step (default: from --steps/--warmup)")
     ap.add_argument("--serve-seconds", type=float, default=30.0,
                     help="length of each Poisson request stream of the serving extra")
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")],
