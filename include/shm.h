@@ -305,9 +305,10 @@ shm_status shm_projectors_run(const shm_proj_problem* prob, shm_dtype dtype, voi
                               size_t workspace_bytes, void* stream);
 
 /*
- * shm_projectors_autotune -- times every projector launch variant (tile size
- * 64/128/256 sphere points, one or two points per thread, a 64-register cap,
- * bulk copy or copy-out of odd-width tiles) on this problem: for each, a
+ * shm_projectors_autotune -- times every projector launch variant (tiles of
+ * 128/256/512 sphere points in rounds of 64/128/256 rows, register caps of
+ * 48 or 64, bulk copy or copy-out of the staged rows) on this problem: for
+ * each, a
  * prepare and four runs into `out` (the first a warm-up), keeping the fastest
  * for later prepares of this dtype in this process (and in the file
  * SHM_TUNE_CACHE names, if set).  Leaves `workspace` prepared for the chosen
@@ -326,9 +327,11 @@ const char* shm_projectors_variant(shm_dtype dtype);
 shm_status shm_projectors_set_variant(shm_dtype dtype, int variant);
 
 /* Error bits a projector launch found (0 = none); waits for `stream`.
- * 1: point_offsets not non-decreasing or beyond n_points; 2: species index out
- * of range; 4: grid index out of range; 8: output block beyond n_values or
- * inconsistent with out_offsets (or a tile that does not match the problem).
+ * 1: point_offsets not non-decreasing or beyond n_points (or valid atoms'
+ * point ranges overlapping beyond the workspace's tile descriptors); 2:
+ * species index out of range; 4: grid index out of range; 8: output block
+ * beyond n_values or inconsistent with out_offsets (or a tile that does not
+ * match the problem).
  * The bits accumulate from the last prepare on. */
 shm_status shm_projectors_check(const void* workspace, void* stream, uint32_t* error_bits);
 
