@@ -1111,20 +1111,19 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
 
 // Launch variants of the persistent kernel (index = variant id): tile size,
 // threads per CTA (rows per round), resident-CTA request for the register
-// allocator, and the store path of odd-width rows.  (Tiles of 64 points,
-// two points per thread in one round, and a form with one 32-point work
-// unit per warp and no CTA barriers were measured slower on the 512-atom
-// problem and are not kept.)
+// allocator, and the store path of odd-width rows.  (Tiles of 64 points, one
+// round of 256 rows, two points per thread in one round, and a form with
+// one 32-point work unit per warp and no CTA barriers were measured slower
+// on the 512-atom problem and are not kept.)
 struct ProjVariant {
   int tile, nt, minb;
   bool bulk;
   const char* name;
 };
 constexpr ProjVariant kProjVariants[] = {
-    {128, 128, 0, true, "tile128"},           {128, 128, 0, false, "tile128-copyout"},
-    {128, 128, 8, true, "tile128-regcap64"},  {256, 128, 0, true, "tile256-2rounds"},
-    {512, 128, 0, true, "tile512-4rounds"},   {256, 256, 0, true, "tile256"},
-    {512, 128, 8, true, "tile512-4rounds-regcap64"}, {512, 128, 10, true, "tile512-4rounds-regcap48"},
+    {512, 128, 0, true, "tile512-4rounds"},           {512, 128, 0, false, "tile512-4rounds-copyout"},
+    {512, 128, 8, true, "tile512-4rounds-regcap64"},  {512, 128, 10, true, "tile512-4rounds-regcap48"},
+    {256, 128, 0, true, "tile256-2rounds"},           {128, 128, 0, true, "tile128"},
     {512, 64, 20, true, "tile512-8rounds-64t-regcap48"}, {512, 256, 5, true, "tile512-2rounds-256t-regcap48"},
 };
 static_assert(kProjMinTile == 128, "every variant's tile is at least kProjMinTile points");
@@ -1132,8 +1131,8 @@ constexpr int kNumProjVariants = sizeof(kProjVariants) / sizeof(kProjVariants[0]
 // Defaults before (or without) tuning, the fastest on the 512-atom problem:
 // tile512-4rounds-regcap48 for FP32 (0.229 ms against 0.246 uncapped),
 // tile512-4rounds for FP64 (0.895 ms).
-inline int default_proj_variant(shm_dtype dt) { return dt == SHM_F32 ? 7 : 4; }
-constexpr int kStrictProjVariant = 4;  // SHM_STRICT_FP64 runs one launch shape: tile512-4rounds
+inline int default_proj_variant(shm_dtype dt) { return dt == SHM_F32 ? 3 : 0; }
+constexpr int kStrictProjVariant = 0;  // SHM_STRICT_FP64 runs one launch shape: tile512-4rounds
 constexpr size_t kProjMaxSmem = 232448;  // B300 opt-in shared memory per CTA
 
 // Shared memory of a launch: the staging tile (with room for the 16-byte
@@ -1198,15 +1197,13 @@ shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, i
   }
   switch (variant) {
     case 0:
-    case 1: return launch_proj_v<T, 128, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
-    case 2: return launch_proj_v<T, 128, 1, 8>(P, max_lmax, out, tile_upper, bulk, s);
-    case 3: return launch_proj_v<T, 128, 2, 0>(P, max_lmax, out, tile_upper, bulk, s);
-    case 4: return launch_proj_v<T, 128, 4, 0>(P, max_lmax, out, tile_upper, bulk, s);
-    case 5: return launch_proj_v<T, 256, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
-    case 6: return launch_proj_v<T, 128, 4, 8>(P, max_lmax, out, tile_upper, bulk, s);
-    case 7: return launch_proj_v<T, 128, 4, 10>(P, max_lmax, out, tile_upper, bulk, s);
-    case 8: return launch_proj_v<T, 64, 8, 20>(P, max_lmax, out, tile_upper, bulk, s);
-    case 9: return launch_proj_v<T, 256, 2, 5>(P, max_lmax, out, tile_upper, bulk, s);
+    case 1: return launch_proj_v<T, 128, 4, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 2: return launch_proj_v<T, 128, 4, 8>(P, max_lmax, out, tile_upper, bulk, s);
+    case 3: return launch_proj_v<T, 128, 4, 10>(P, max_lmax, out, tile_upper, bulk, s);
+    case 4: return launch_proj_v<T, 128, 2, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 5: return launch_proj_v<T, 128, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 6: return launch_proj_v<T, 64, 8, 20>(P, max_lmax, out, tile_upper, bulk, s);
+    case 7: return launch_proj_v<T, 256, 2, 5>(P, max_lmax, out, tile_upper, bulk, s);
   }
   return fail(SHM_EINVAL, "unknown projector launch variant");
 }

@@ -306,7 +306,7 @@ def test_lmax3_rows_at_every_output_phase(oracle_mod, dtype, tol):
     got = run(prob, dtype)
     check(prob, got, oracle_mod.projectors(prob), tol, f"lmax-3 phases {dtype}")
     try:
-        shm.set_projectors_variant(dtype, 1)        # tile128-copyout
+        shm.set_projectors_variant(dtype, 1)        # tile512-4rounds-copyout
         ws = d.workspace(dtype)
         ref = shm.projectors(d, dtype, workspace=ws)
         torch.cuda.synchronize()
@@ -449,7 +449,7 @@ def test_overlapping_atom_ranges_stay_in_bounds():
     assert 3 * -(-n // 128) > n // 128 + A + 1     # 128-point tiles: more than the descriptors
     for dtype in (torch.float64, torch.float32):
         try:
-            shm.set_projectors_variant(dtype, 0)    # tile128
+            shm.set_projectors_variant(dtype, 5)    # tile128
             ws = d.workspace(dtype)
             guard = torch.full((d.n_values + 64,), -7.0, dtype=dtype, device="cuda")
             shm.projectors(d, dtype, out=guard[:d.n_values], workspace=ws)
