@@ -1164,23 +1164,35 @@ shm_status launch_proj_v(const ProjParams& P, int max_lmax, T* out, int64_t tile
   const int dev = current_device();
   const size_t tile_bytes = proj_tile_bytes(NT, max_lmax, sizeof(T));
   const size_t smem = tile_bytes;
+  int b = 0;
   {
     // the shared-memory opt-in, once per kernel and device (kept at the
-    // largest size any problem needs)
+    // largest size any problem needs), and the resident-CTA count, once per
+    // kernel, device and staging size (the occupancy query is not repeated
+    // on every run)
     constexpr int MAXDEV = 64;
     static size_t optin[2][MAXDEV] = {};
+    static std::unordered_map<unsigned long long, int> resident;
     std::lock_guard<std::mutex> lk(g_proj_mu);
     if (dev < 0 || dev >= MAXDEV) return fail(SHM_EUNSUPPORTED, "device index out of range");
-    size_t& done = optin[max_lmax <= 4 ? 0 : 1][dev];
+    const int lc = max_lmax <= 4 ? 0 : 1;
+    size_t& done = optin[lc][dev];
     if (done < smem) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(k_proj)");
       done = smem;
     }
+    const unsigned long long key = ((unsigned long long)smem << 8) | ((unsigned long long)dev << 1) | (unsigned)lc;
+    auto it = resident.find(key);
+    if (it != resident.end()) {
+      b = it->second;
+    } else {
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NT, smem);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_proj)");
+      resident.emplace(key, b);
+    }
   }
-  int b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NT, smem);
-  if (e != cudaSuccess) return fail_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_proj)");
+  cudaError_t e;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tile_upper, (int64_t)sm_count(dev) * std::max(b, 1)));
   kern<<<(unsigned)grid, NT, smem, s>>>(P, out, (int)tile_bytes, tile_upper, bulk ? 1 : 0);
   e = cudaGetLastError();
