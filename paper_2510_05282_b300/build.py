@@ -50,14 +50,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(objdir, exist_ok=True)
     objs = []
     procs = []
+    headers = [d for d in _deps() if not d.endswith((".cu", ".cpp"))]
+    newest_header = max((os.path.getmtime(h) for h in headers), default=0.0)
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        objs.append(obj)
+        # an object is reused when it is newer than its source and every header
+        if (not force and os.path.exists(obj)
+                and os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header)):
+            continue
         cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
                "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         if os.environ.get("SHM_PTXAS_VERBOSE"):
             cmd.insert(1, "-Xptxas=-v")
         procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True), src))
-        objs.append(obj)
     failed = []
     for p, src in procs:
         out, _ = p.communicate()
@@ -65,6 +71,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(out)
         if p.returncode != 0:
             failed.append(src)
+            obj = os.path.join(objdir, os.path.basename(src) + ".o")
+            if os.path.exists(obj):
+                os.remove(obj)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
     tmp = LIB + f".tmp{os.getpid()}"
