@@ -948,13 +948,15 @@ __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int ro
 // Static schedule: of G CTAs, CTA b takes tiles b, b + G, b + 2G, ...  The
 // tiles are ordered by the lmax of their atom, largest first, then by
 // species, so every CTA gets the same mix of row widths, and no counter,
-// atomic or search sits between two tiles.  Everything a tile reads from
-// global memory besides its radial and displacement tables arrives in
-// shared memory ahead of it by cp.async: thread 0 fetches descriptors two
-// tiles ahead (a ring of three), and all threads fetch the next tile's grid
-// indices one tile ahead (two buffers), so neither the index stream from
-// DRAM nor the descriptor chain stalls the tile's arithmetic; two barriers
-// per round remain (before and after its stores).  Every
+// atomic or search sits between two tiles.  Thread 0 fetches descriptors
+// two tiles ahead into shared memory by cp.async (a ring of three), and each
+// thread reads the grid index of its next row (in this tile or the next) one
+// round ahead into a register, so neither the index stream from DRAM nor
+// the descriptor chain stalls the tile's arithmetic, and no shared memory
+// holds indices (an index buffer of two tiles, filled by cp.async a tile
+// ahead, cost 4 KB per CTA: seven CTAs per SM in FP64 instead of eight, and
+// 0.893 against 0.875 ms FP64, 0.232 against 0.217 ms FP32 on the 512-atom
+// problem); two barriers per round remain (before and after its stores).  Every
 // descriptor is checked against the problem (atom, species, row count, point
 // and value ranges) before it is used, and every grid index per point, so a
 // workspace that does not hold this problem's tables sets error bits
@@ -973,19 +975,10 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
   T* const tile = reinterpret_cast<T*>(smem_raw);
   (void)tile_bytes;
   __shared__ __align__(16) ProjTile s_desc[3];
-  // grid indices of a tile: index p0 + r at s_idx[.][r + sh], sh the 16-byte
-  // phase of &point_index[p0] in 4-byte units, so that the 16-byte aligned
-  // part of the index stream arrives by 16-byte copies that bypass L1 (which
-  // keeps the radial cubics)
-  __shared__ __align__(16) int s_idx[2][TILE + 8];
   const int64_t total_tiles = min(max(P.tile_offsets[P.n_atoms], (int64_t)0), tile_limit);
   const int64_t G = gridDim.x;
   auto cp16 = [](void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-  };
-  auto cp4 = [](void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
   };
   auto commit = [] { asm volatile("cp.async.commit_group;" ::: "memory"); };
@@ -997,23 +990,17 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
       cp16(reinterpret_cast<char*>(&s_desc[ds]) + 16, reinterpret_cast<const char*>(P.tiles + t) + 16);
     }
   };
-  // all threads: the grid indices of tile t, whose descriptor is in ring
-  // slot ds, into buffer slot k; nothing for a descriptor whose ranges do not
-  // fit the problem (the tile is skipped)
-  auto fetch_tile = [&](int64_t t, int k, int ds) {
-    if (t >= total_tiles) return;
+  // the grid index of row r of tile t, whose descriptor is in ring slot ds
+  // (-1 past the tile's rows, past the last tile, or for a descriptor whose
+  // ranges do not fit the problem: the tile is skipped), read with the
+  // streaming hint so that L1 keeps the radial cubics
+  auto fetch_index = [&](int64_t t, int ds, int r) -> int {
+    if (t >= total_tiles) return -1;
     const ProjTile D = s_desc[ds];
     if (!(D.rows >= 1 && D.rows <= TILE && D.p0 >= 0 && D.p0 <= P.n_points - D.rows && D.atom >= 0 &&
-          D.atom < P.n_atoms))
-      return;
-    const int* src = P.point_index + D.p0;
-    const int sh = (int)(((uintptr_t)src >> 2) & 3u);
-    const int head = min(D.rows, (4 - sh) & 3);           // indices before the first 16-byte boundary
-    const int nq = (D.rows - head) >> 2;                   // 16-byte groups
-    const int tail0 = head + 4 * nq;
-    for (int q = threadIdx.x; q < nq; q += NT) cp16(&s_idx[k][sh + head + 4 * q], src + head + 4 * q);
-    if ((int)threadIdx.x < head) cp4(&s_idx[k][sh + threadIdx.x], src + threadIdx.x);
-    if ((int)threadIdx.x < D.rows - tail0) cp4(&s_idx[k][sh + tail0 + threadIdx.x], src + tail0 + threadIdx.x);
+          D.atom < P.n_atoms) || r >= D.rows)
+      return -1;
+    return __ldcs(P.point_index + D.p0 + r);
   };
   if (threadIdx.x == 0) {
     fetch_desc(blockIdx.x, 0);
@@ -1022,16 +1009,16 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
     wait_all();
   }
   __syncthreads();
-  fetch_tile(blockIdx.x, 0, 0);
-  commit();
-  wait_all();
-  __syncthreads();
-  int k = 0, ds = 0;
+  // each thread's grid index for its row of the next round, read one round
+  // ahead (a register, not a shared-memory buffer of the tile's indices)
+  int g_next = fetch_index(blockIdx.x, 0, (int)threadIdx.x);
+  int ds = 0;
   for (int64_t t = blockIdx.x; t < total_tiles; t += G) {
     const int ds1 = ds == 2 ? 0 : ds + 1, ds2 = ds1 == 2 ? 0 : ds1 + 1;
-    if (threadIdx.x == 0) fetch_desc(t + 2 * G, ds2);
-    fetch_tile(t + G, k ^ 1, ds1);
-    commit();
+    if (threadIdx.x == 0) {
+      fetch_desc(t + 2 * G, ds2);
+      commit();
+    }
     const ProjTile D = s_desc[ds];
     // the tile's atom, species and blocks, checked against the problem
     const int64_t a = D.atom;
@@ -1059,16 +1046,22 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
     const int phase = (int)(((uintptr_t)dst & 15u) / sizeof(T));
     if (!ok && threadIdx.x == 0) atomicOr(P.err, kErrOut);  // the same decision in every thread: the tile is skipped
     const int nrounds = ok ? (rows + NT - 1) / NT : 0;
+    if (nrounds == 0) g_next = fetch_index(t + G, ds1, (int)threadIdx.x);
 #pragma unroll 1
     for (int rd = 0; rd < nrounds; ++rd) {
       const int r0 = rd * NT, rr = min(NT, rows - r0);
+      const int g = g_next;  // this thread's row r0 + threadIdx.x (if < rr)
+      {
+        const int rn = r0 + NT + (int)threadIdx.x;  // its row of the next round
+        g_next = rd + 1 < nrounds ? (rn < rows ? __ldcs(P.point_index + p0 + rn) : -1)
+                                  : fetch_index(t + G, ds1, (int)threadIdx.x);
+      }
       T* const stage = tile + (flat ? phase : 0);
       if constexpr (sizeof(T) == 4) {
         if (rows16) {
           const bool active = (int)threadIdx.x < rr;
           float v[16];
           if (active) {
-            const int g = s_idx[k][(int)(((uintptr_t)(P.point_index + p0) >> 2) & 3u) + r0 + threadIdx.x];
             if (g < 0 || g >= P.ng * P.ng * P.ng) {
               atomicOr(P.err, kErrGrid);
 #pragma unroll
@@ -1081,7 +1074,6 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
         }
       }
       if (!rows16 && (int)threadIdx.x < rr) {
-        const int g = s_idx[k][(int)(((uintptr_t)(P.point_index + p0) >> 2) & 3u) + r0 + threadIdx.x];
         T* row = stage + threadIdx.x * (flat ? L2 : RS);
         if (g < 0 || g >= P.ng * P.ng * P.ng) {
           atomicOr(P.err, kErrGrid);
@@ -1101,9 +1093,8 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
       dst += (int64_t)rr * L2;
       if (rd + 1 < nrounds) __syncthreads();  // the buffer is free for the next round
     }
-    wait_all();       // this thread's copies for the next tiles have landed
-    __syncthreads();  // the tile buffer is free; the next tile's descriptor, indices and atom are visible
-    k ^= 1;
+    if (threadIdx.x == 0) wait_all();  // the descriptor copies have landed
+    __syncthreads();  // the tile buffer is free; the next tiles' descriptors are visible
     ds = ds1;
   }
   if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -1125,13 +1116,15 @@ constexpr ProjVariant kProjVariants[] = {
     {512, 128, 8, true, "tile512-4rounds-regcap64"},  {512, 128, 10, true, "tile512-4rounds-regcap48"},
     {256, 128, 0, true, "tile256-2rounds"},           {128, 128, 0, true, "tile128"},
     {512, 64, 20, true, "tile512-8rounds-64t-regcap48"}, {512, 256, 5, true, "tile512-2rounds-256t-regcap48"},
+    {512, 64, 0, true, "tile512-8rounds-64t"},        {256, 64, 0, true, "tile256-4rounds-64t"},
 };
 static_assert(kProjMinTile == 128, "every variant's tile is at least kProjMinTile points");
 constexpr int kNumProjVariants = sizeof(kProjVariants) / sizeof(kProjVariants[0]);
 // Defaults before (or without) tuning, the fastest on the 512-atom problem:
-// tile512-4rounds-regcap48 for FP32 (0.229 ms against 0.246 uncapped),
-// tile512-4rounds for FP64 (0.895 ms).
-inline int default_proj_variant(shm_dtype dt) { return dt == SHM_F32 ? 3 : 0; }
+// tile512-8rounds-64t for FP32 (0.216 ms; 0.217 with 128-thread rounds, 0.249
+// with the register cap of 48, which spills), tile512-4rounds for FP64
+// (0.875 ms).
+inline int default_proj_variant(shm_dtype dt) { return dt == SHM_F32 ? 8 : 0; }
 constexpr int kStrictProjVariant = 0;  // SHM_STRICT_FP64 runs one launch shape: tile512-4rounds
 constexpr size_t kProjMaxSmem = 232448;  // B300 opt-in shared memory per CTA
 
@@ -1216,6 +1209,8 @@ shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, i
     case 5: return launch_proj_v<T, 128, 1, 0>(P, max_lmax, out, tile_upper, bulk, s);
     case 6: return launch_proj_v<T, 64, 8, 20>(P, max_lmax, out, tile_upper, bulk, s);
     case 7: return launch_proj_v<T, 256, 2, 5>(P, max_lmax, out, tile_upper, bulk, s);
+    case 8: return launch_proj_v<T, 64, 8, 0>(P, max_lmax, out, tile_upper, bulk, s);
+    case 9: return launch_proj_v<T, 64, 4, 0>(P, max_lmax, out, tile_upper, bulk, s);
   }
   return fail(SHM_EINVAL, "unknown projector launch variant");
 }
