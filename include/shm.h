@@ -267,6 +267,25 @@ shm_status shm_projectors(const shm_proj_problem* prob, shm_dtype dtype, void* o
 shm_status shm_projectors_ex(const shm_proj_problem* prob, shm_dtype dtype, unsigned flags, void* out,
                              void* workspace, size_t workspace_bytes, void* stream);
 
+/* Row form of the SHM_STRICT_FP64 projectors, for later prepares in this
+ * process (a prepared workspace keeps the form it was prepared with):
+ *   1 -- every binary64 product on the FP64 pipe;
+ *   2 -- the products that leave the harmonic row (S_lm A_m, S_lm B_m,
+ *        s A_m, s B_m of Sec. II Eq. 6) and f_l x R_l^m computed on the
+ *        integer pipes: the IEEE-754 round-to-nearest-even product from
+ *        32-bit integer multiply-adds, the same bits as the FP64 multiply; a
+ *        row with a zero, subnormal or out-of-range product (an axis point,
+ *        f_l = 0) is computed again with the FP64 instructions;
+ *   3 -- (default) as 2, with every other product of the row as well (the
+ *        scales S_lm Qh, the recurrence products G_lm Qh and the m = 0
+ *        column).
+ * All forms give the same bits; on a B300 the FP64 pipe binds form 1, and
+ * forms 2 and 3 move 30-40 of its ~107 instructions per point to the
+ * otherwise idle integer pipes.  shm_projectors_strict_form returns the
+ * current form.  Errors: SHM_EINVAL for any other form. */
+shm_status shm_projectors_set_strict_form(int form);
+int shm_projectors_strict_form(void);
+
 /*
  * shm_projectors_prepare -- the per-problem set-up of shm_projectors, done
  * once: two launches on `stream` that validate every atom's offsets and

@@ -10,5 +10,6 @@ from ._binding import (LMAX_CAP, SHM_F32, SHM_F64, ShmError, autotune, check, ev
                        num_harmonics, set_eval_variant, DeviceProjectors, projectors, projectors_check,
                        projectors_noalloc, Server, serve_generated_point, probe_fp64_rate, probe_dmul,
                        SHM_STRICT_FP64, projectors_prepare, projectors_run, projectors_autotune,
-                       projectors_variant, projectors_variant_count, set_projectors_variant)
+                       projectors_variant, projectors_variant_count, set_projectors_variant,
+                       set_projectors_strict_form, projectors_strict_form)
 from . import inputs  # noqa: F401

@@ -308,6 +308,8 @@ _EXTRA_DECLS.extend([
     ("shm_projectors_variant_count", ([], ctypes.c_int)),
     ("shm_projectors_variant", ([ctypes.c_int], ctypes.c_char_p)),
     ("shm_projectors_set_variant", ([ctypes.c_int, ctypes.c_int], ctypes.c_int)),
+    ("shm_projectors_set_strict_form", ([ctypes.c_int], ctypes.c_int)),
+    ("shm_projectors_strict_form", ([], ctypes.c_int)),
 ])
 
 PROJ_NOALLOC_SCRATCH_BYTES = 1 << 25
@@ -393,6 +395,17 @@ def projectors_variant_count() -> int:
 
 def set_projectors_variant(dtype, variant: int) -> None:
     check(lib().shm_projectors_set_variant(_dtype_code(dtype), int(variant)))
+
+
+def set_projectors_strict_form(form: int) -> None:
+    """Row form of later SHM_STRICT_FP64 projector prepares: 1 every product
+    on the FP64 pipe, 2 the output products, 3 (default) every product of the
+    row on the integer pipes (the same bits)."""
+    check(lib().shm_projectors_set_strict_form(int(form)))
+
+
+def projectors_strict_form() -> int:
+    return int(lib().shm_projectors_strict_form())
 
 
 def projectors_check(workspace, stream=None) -> int:

@@ -167,7 +167,8 @@ struct ProjParams {
   float4* rad32;
   float* disp32;   // FP32: displacement tables [n_atoms][3][ng]
   float4* coef;  // two per node: {a0.hi, a0.lo, a1.hi, a1.lo}, {a2.hi, a2.lo, a3.hi, a3.lo}; strict: one double4
-  int strict;    // FP64 with SHM_STRICT_FP64: binary64 tables, log-grid index and rows
+  int strict;    // FP64 with SHM_STRICT_FP64: binary64 tables, log-grid index and rows (1: products on
+                 // the FP64 pipe; 2: the row's output products, 3: all its products on the integer pipes)
   double* disp64;  // FP64: displacement tables [n_atoms][3][ng]
   // derived on the host: 1/box, 1/r_min, 1/dlog, the log-grid constants
   // K0 = -ln(r_min)/dlog, K1 = ln2/(2 dlog), K2 = 1/(2 dlog), and FP32 h, 1/dlog
@@ -569,8 +570,12 @@ __device__ __forceinline__ void proj_row_f32_short(float xb, float yb, float zb,
 // row[0..(LMAX+1)^2).  (dx, dy, dz) is the displacement, or with `unit` its
 // unit vector.
 // STRICT (FP64): radial(l) returns binary64 f_l and the row is
-// f_l(r) x R_l^m of the all-binary64 sh_row, one binary64 product per value.
-template <int LMAX, bool STRICT = false, typename T, typename Radial>
+// f_l(r) x R_l^m of the all-binary64 sh_row, one binary64 product per value;
+// STRICT 1 runs every product on the FP64 pipe, STRICT 2 the products that
+// leave the row (S A, S B, s A, s B and f_l R) on the integer pipes
+// (dmul_int, the same bits), STRICT 3 every product of the row (also the
+// scales, the G q products of the recurrences and the m = 0 column).
+template <int LMAX, int STRICT = 0, typename T, typename Radial>
 __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool unit, Radial&& radial,
                                          T* __restrict__ row) {
   T xb = dx, yb = dy, zb = dz;
@@ -586,7 +591,20 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool uni
       return;
     }
     if (!unit) unit_dir(dx, dy, dz, xb, yb, zb);
-    sh_row<LMAX>(xb, yb, zb, [&](int k, double v) { row[k] = f[l_of_k(k)] * v; });
+    if constexpr (STRICT >= 2) {
+      // the same binary64 operations with the products that leave the row
+      // (S A, S B, s A, s B, then f_l R; STRICT 3: every product) by dmul_int
+      // on the integer pipes: the same bits; a row where dmul_int declines a
+      // product (a zero or subnormal factor, e.g. f_l = 0 or a point on an
+      // axis) is written again with the FP64 instructions
+      unsigned bad_f = 0u;
+      const unsigned bad =
+          sh_row_emu<LMAX, STRICT == 3 ? (kEmuOut | kEmuScale | kEmuRec | kEmuM0) : kEmuOut>(
+              xb, yb, zb, [&](int k, double v) { row[k] = dmul_int(f[l_of_k(k)], v, bad_f); });
+      if (bad | bad_f) sh_row<LMAX>(xb, yb, zb, [&](int k, double v) { row[k] = f[l_of_k(k)] * v; });
+    } else {
+      sh_row<LMAX>(xb, yb, zb, [&](int k, double v) { row[k] = f[l_of_k(k)] * v; });
+    }
   } else if constexpr (sizeof(T) == 4) {
     float f[LMAX + 1];
 #pragma unroll
@@ -630,7 +648,7 @@ __device__ __forceinline__ void proj_row(T dx, T dy, T dz, bool origin, bool uni
 // Row of a runtime lmax.  LCAP: the largest lmax the instantiation holds
 // code for (4 or 9; the launch picks 4 when no species goes above it, so
 // that the register allocation and the code follow the short rows alone).
-template <int LCAP, bool STRICT = false, typename T, typename Radial>
+template <int LCAP, int STRICT = 0, typename T, typename Radial>
 __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bool origin, bool unit,
                                                   Radial&& L, T* row) {
   static_assert(LCAP == 4 || LCAP == 9, "LCAP is 4 or 9");
@@ -659,7 +677,7 @@ __device__ __forceinline__ void proj_row_dispatch(int lmax, T dx, T dy, T dz, bo
 // disp_axis_f64).  STRICT (SHM_STRICT_FP64): the log-grid index from CUDA's
 // binary64 log of r^2, the interval cubic by binary64 Horner from binary64
 // coefficients, and the all-binary64 harmonic row times f_l.
-template <int LCAP, bool STRICT = false>
+template <int LCAP, int STRICT = 0>
 __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const double* __restrict__ tb,
                                                int s, int lmax, double* row) {
   const double inv_rmin = P.inv_rmin, inv_dlog = P.inv_dlog;
@@ -708,7 +726,7 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const
       const double4 a = c[l];
       return fma(fma(fma(a.w, u, a.z), u, a.y), u, a.x);
     };
-    proj_row_dispatch<LCAP, true, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
+    proj_row_dispatch<LCAP, STRICT, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
   } else {
     // f_l(r): the interval's cubic in u by Horner's rule in float-float (FP32
     // pipe), two 16-byte loads per l
@@ -720,7 +738,7 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const
       p = ff_add(ff_mul_u(p, U), ff{a01.z, a01.w});
       return ff_add(ff_mul_u(p, U), ff{a01.x, a01.y});
     };
-    proj_row_dispatch<LCAP, false, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
+    proj_row_dispatch<LCAP, 0, double>(lmax, d[0], d[1], d[2], origin, unit, radial, row);
   }
 }
 
@@ -788,7 +806,7 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
   if constexpr (LFIX >= 0)
     proj_row<LFIX, false, float>(d[0], d[1], d[2], origin, true, radial, row);
   else
-    proj_row_dispatch<LCAP, false, float>(lmax, d[0], d[1], d[2], origin, true, radial, row);
+    proj_row_dispatch<LCAP, 0, float>(lmax, d[0], d[1], d[2], origin, true, radial, row);
 }
 
 // Rows of 16 floats (lmax 3) staged contiguously with 16-byte stores.  The
@@ -967,7 +985,7 @@ __device__ __forceinline__ void copy_rows_out(const T* __restrict__ tile, int ro
 // used in turn by consecutive rounds, which drop the barrier after each
 // round's stores, cost more in occupancy than they save: 0.258 against
 // 0.246 ms for FP32 on the 512-atom problem.)
-template <typename T, int NT, int ROUNDS, int MINB, bool STRICT = false, int LCAP = 9>
+template <typename T, int NT, int ROUNDS, int MINB, int STRICT = 0, int LCAP = 9>
 __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__ out, int tile_bytes,
                                                   int64_t tile_limit, int bulk) {
   constexpr int TILE = NT * ROUNDS;
@@ -1147,11 +1165,17 @@ struct ProjPrepared {
   int variant;
   shm_dtype dtype;
   int64_t n_atoms, n_points, n_values;
-  bool strict;
+  int strict;  // ProjParams::strict of the prepare
 };
 std::unordered_map<const void*, ProjPrepared> g_prepared;
+// Row form of later SHM_STRICT_FP64 prepares: 1 every binary64 product on
+// the FP64 pipe, 2 the row's output products on the integer pipes, 3 (the
+// default) every product of the row on the integer pipes; the same bits.
+// On the 512-atom problem: 2.81, 2.08 and 1.97 ms.  (The unit vector's three
+// products on the integer pipes as well: 2.00 ms.)
+int g_strict_form = 3;
 
-template <typename T, int NT, int ROUNDS, int MINB, bool STRICT = false>
+template <typename T, int NT, int ROUNDS, int MINB, int STRICT = 0>
 shm_status launch_proj_v(const ProjParams& P, int max_lmax, T* out, int64_t tile_upper, bool bulk, cudaStream_t s) {
   auto kern = max_lmax <= 4 ? k_proj<T, NT, ROUNDS, MINB, STRICT, 4> : k_proj<T, NT, ROUNDS, MINB, STRICT, 9>;
   const int dev = current_device();
@@ -1198,7 +1222,9 @@ shm_status launch_proj(int variant, const ProjParams& P, int max_lmax, T* out, i
   const bool bulk = kProjVariants[variant].bulk;
   if constexpr (sizeof(T) == 8) {
     // SHM_STRICT_FP64: one launch shape (kStrictProjVariant's)
-    if (P.strict) return launch_proj_v<T, 128, 4, 0, true>(P, max_lmax, out, tile_upper, true, s);
+    if (P.strict == 3) return launch_proj_v<T, 128, 4, 0, 3>(P, max_lmax, out, tile_upper, true, s);
+    if (P.strict == 2) return launch_proj_v<T, 128, 4, 0, 2>(P, max_lmax, out, tile_upper, true, s);
+    if (P.strict) return launch_proj_v<T, 128, 4, 0, 1>(P, max_lmax, out, tile_upper, true, s);
   }
   switch (variant) {
     case 0:
@@ -1345,7 +1371,10 @@ shm_status prepare_in(const shm_proj_problem* prob, shm_dtype dtype, void* works
   shm_status st = proj_params(prob, dtype, workspace, ws_bytes, kProjVariants[variant].tile, &P, &max_lmax,
                               &tile_upper);
   if (st != SHM_OK) return st;
-  P.strict = strict ? 1 : 0;
+  {
+    std::lock_guard<std::mutex> lk(g_proj_mu);
+    P.strict = strict ? g_strict_form : 0;
+  }
   if (proj_smem(variant, max_lmax, dtype == SHM_F64 ? 8 : 4, prob->n_atoms) > kProjMaxSmem)
     return fail(SHM_EINVAL, "projector tile does not fit in shared memory for this lmax");
   k_proj_setup<<<setup_grid(P, dtype), 1024, 0, s>>>(P, kProjVariants[variant].tile, dtype == SHM_F32 ? 1 : 0);
@@ -1360,7 +1389,7 @@ shm_status prepare_in(const shm_proj_problem* prob, shm_dtype dtype, void* works
     if (e != cudaSuccess) return fail_cuda(e, "k_proj_disp launch");
   }
   std::lock_guard<std::mutex> lk(g_proj_mu);
-  g_prepared[workspace] = ProjPrepared{variant, dtype, prob->n_atoms, prob->n_points, prob->n_values, strict};
+  g_prepared[workspace] = ProjPrepared{variant, dtype, prob->n_atoms, prob->n_points, prob->n_values, P.strict};
   return SHM_OK;
 }
 
@@ -1384,7 +1413,7 @@ shm_status run_in(const shm_proj_problem* prob, shm_dtype dtype, void* out, void
   shm_status st = proj_params(prob, dtype, workspace, ws_bytes, kProjVariants[rec.variant].tile, &P, &max_lmax,
                               &tile_upper);
   if (st != SHM_OK) return st;
-  P.strict = rec.strict ? 1 : 0;
+  P.strict = rec.strict;
   if ((st = check_out(prob, dtype, out)) != SHM_OK) return st;
   if (prob->n_atoms == 0 || prob->n_points == 0) return SHM_OK;
   return dtype == SHM_F64 ? launch_proj<double>(rec.variant, P, max_lmax, (double*)out, tile_upper, s)
@@ -1564,6 +1593,23 @@ extern "C" shm_status shm_projectors_set_variant(shm_dtype dtype, int variant) {
   std::lock_guard<std::mutex> lk(g_proj_mu);
   g_proj_choice[dtype == SHM_F64 ? 1 : 0] = variant;
   return SHM_OK;
+}
+
+extern "C" shm_status shm_projectors_set_strict_form(int form) {
+  using namespace shm;
+  clear_error();
+  if (form < 1 || form > 3)
+    return fail(SHM_EINVAL, "form must be 1 (every product on the FP64 pipe), 2 (the output products on the "
+                            "integer pipes) or 3 (every product of the row on the integer pipes)");
+  std::lock_guard<std::mutex> lk(g_proj_mu);
+  g_strict_form = form;
+  return SHM_OK;
+}
+
+extern "C" int shm_projectors_strict_form(void) {
+  using namespace shm;
+  std::lock_guard<std::mutex> lk(g_proj_mu);
+  return g_strict_form;
 }
 
 extern "C" shm_status shm_projectors_check(const void* workspace, void* stream, uint32_t* error_bits) {

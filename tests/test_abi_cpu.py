@@ -161,3 +161,12 @@ def test_strict_flag_host_side(L):
     assert L.shm_eval_set_variant_ex(9, 1, 4, 0) == 1                   # unknown bit
     assert L.shm_eval_ex(8, 1, 3, 1, 0x4, 64, None) == 1
     assert L.shm_eval_angles_ex(8, 1, 3, 1, 0x1, 64, None) == 1         # angles take no normalised flag
+
+
+def test_strict_projector_form_is_validated_on_the_host(L):
+    assert L.shm_projectors_strict_form() == 3
+    for bad in (0, 4, -1):
+        assert L.shm_projectors_set_strict_form(bad) == 1
+        assert b"form" in L.shm_last_error()
+    for form in (1, 2, 3):
+        assert L.shm_projectors_set_strict_form(form) == 0 and L.shm_projectors_strict_form() == form

@@ -513,3 +513,45 @@ def test_strict_prepared_runs_and_graph():
     dflt = shm.projectors(d, torch.float64, workspace=d.workspace(torch.float64))
     torch.cuda.synchronize()
     assert not torch.equal(dflt, ref)
+
+
+def _strict_run_form(prob, form):
+    d = shm.DeviceProjectors(prob)
+    ws = d.workspace(torch.float64)
+    try:
+        shm.set_projectors_strict_form(form)
+        out = shm.projectors(d, torch.float64, workspace=ws, strict=True)
+        torch.cuda.synchronize()
+    finally:
+        shm.set_projectors_strict_form(3)
+    assert shm.projectors_check(ws) == 0
+    return out
+
+
+def _strict_form_problems():
+    on_grid = small_problem(24)
+    on_grid.atom_pos[0] = np.array([8, 9, 10], dtype=np.float64) * on_grid.h  # origin and axis points
+    zero_f = small_problem(25)
+    zero_f.radial[1, 2] = 0.0                                                  # f_l = 0 for one (species, l)
+    return {"on_grid": on_grid, "zero_f": zero_f,
+            "all_lmax": small_problem(26, n_atoms=10, n_species=10, lmax_choices=tuple(range(10))),
+            "full": inputs.projector_problem()}
+
+
+@pytest.mark.parametrize("which", ["on_grid", "zero_f", "all_lmax", "full"])
+def test_strict_forms_are_bitwise_the_same(oracle_mod, which):
+    """SHM_STRICT_FP64 rows with every product on the FP64 pipe (form 1),
+    with the output products (form 2) or every product of the row (form 3,
+    the default) on the integer pipes by dmul_int: the same bits, including
+    rows that dmul_int declines (a zero f_l, points on the atom's axes, the
+    atom's own grid point) and fall back to the FP64 instructions."""
+    assert shm.projectors_strict_form() == 3
+    prob = _strict_form_problems()[which]
+    f1 = _strict_run_form(prob, 1)
+    for form in (2, 3):
+        f = _strict_run_form(prob, form)
+        assert torch.equal(f1, f), f"form {form}"
+        if which != "full":
+            check(prob, f.cpu().numpy(), oracle_mod.projectors(prob), PROJ_TOL_F64, f"strict form {form} {which}")
+    with pytest.raises(shm.ShmError):
+        shm.set_projectors_strict_form(4)
