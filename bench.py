@@ -52,6 +52,12 @@ HBM_FALLBACK_GBS = 6400.0
 # FP64 pipe instructions per point of the all-binary64 rows at lmax 9
 # (sh_row: DMUL + DFMA, counted by ncu sass__inst_executed_per_opcode).
 STRICT_DP_PER_POINT_L9 = 242
+# All-binary64 projectors on the 512-atom problem (lmax 2-4, 13,163,477
+# points), FP64-pipe instructions per point counted by ncu
+# (smsp__inst_executed_pipe_fp64.sum x 32 / points): 107.1 with every product
+# on the FP64 pipe (strict form 1), 68.8 with the row products on the integer
+# pipes (form 3, the default; the same bits).
+STRICT_PROJ_DP_PER_POINT = {1: 107.1, 3: 68.8}
 # binary64 products per point that the rows-tma-emu variants compute on the
 # integer pipes instead (dmul_int, bitwise the DMUL results): the 90 output
 # products s A, s B at lmax 9, and with the scales s = S q another 36.
@@ -565,7 +571,7 @@ def run_extras(args, shm, torch, inputs, stream, peaks, peaks_src, fp64):
                      "peak_source": peaks_src, "note": "420 MB out: partly absorbed by the 126 MB L2"}}
     for fn in EXTRA_WORKLOADS:
         try:
-            res.update(fn(args, shm, torch, inputs, stream, peaks, peaks_src))
+            res.update(fn(args, shm, torch, inputs, stream, dict(peaks, fp64_probe=fp64), peaks_src))
         except Exception as e:  # reported, never silently dropped
             res[getattr(fn, "__name__", "extra")] = {"error": repr(e)}
     res["fp64_peak_probe"] = fp64
@@ -666,13 +672,28 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
     ms = statistics.mean(per)
     algo_bytes = d.n_values * 8 + d.n_points * 4
     gbs = algo_bytes / (ms * 1e-3) / 1e9
+    form = shm.projectors_strict_form()
+    roof = {"bound": "alu", "pipe": "fp64", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
+            "hbm_frac": gbs / hbm_peak, "hbm_unit": "GB/s", "hbm_peak_source": peaks_src,
+            "algorithmic_bytes": algo_bytes}
+    fp64 = peaks.get("fp64_probe")
+    if fp64 and form in STRICT_PROJ_DP_PER_POINT:
+        dp = STRICT_PROJ_DP_PER_POINT[form]
+        ach = 2.0 * dp * d.n_points / (ms * 1e-3) / 1e12
+        eq = 2.0 * STRICT_PROJ_DP_PER_POINT[1] * d.n_points / (ms * 1e-3) / 1e12
+        roof.update({"achieved": ach, "peak": fp64["tflops"], "unit": "TFLOP/s", "frac": ach / fp64["tflops"],
+                     "achieved_def": f"{dp} FP64 pipe instructions per point (ncu, this problem) x 2 x points / "
+                                     "mean launch time", "peak_source": fp64["source"],
+                     "binary64_equivalent_tflops": eq, "binary64_equivalent_frac_of_fp64_peak": eq / fp64["tflops"],
+                     "binary64_equivalent_def": f"{STRICT_PROJ_DP_PER_POINT[1]} FP64 instructions per point of the "
+                                                "form with every product on the FP64 pipe, at this time"})
     res["projectors_512atoms_fp64_strict"] = {
         "value": d.n_values / (ms * 1e-3), "unit": "projector values/s", "ms_per_call": ms,
         "launches_per_call": 1, "error_bits": shm.projectors_check(ws, stream=stream),
-        "arithmetic": "binary64 throughout (SHM_STRICT_FP64)",
-        "roofline": {"bound": "alu", "pipe": "fp64", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
-                     "hbm_frac": gbs / hbm_peak, "unit": "GB/s", "peak_source": peaks_src,
-                     "algorithmic_bytes": algo_bytes}}
+        "arithmetic": "binary64 throughout (SHM_STRICT_FP64)", "strict_form": form,
+        "strict_form_def": "1: every product on the FP64 pipe; 2: the row's output products, 3: all its products "
+                           "on the integer pipes (dmul_int, the same bits)",
+        "roofline": roof}
     del out, ws
     # the oracle on the same problem (all host cores): the CPU baseline of this workload
     import oracle
