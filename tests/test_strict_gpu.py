@@ -283,3 +283,58 @@ def test_emulated_product_variants_on_awkward_points(oracle_mod, lmax):
             assert _same(out, ref), name
     finally:
         shm.set_eval_variant(lmax, torch.float64, -1, strict=True)
+
+
+def _spinor_terms(lmax):
+    """(ka, kb, cre, cim, im_zero) of every output component q = 2 spinor + c
+    of Eq. 7, with the coefficients formed by the same binary64 operations
+    (a correctly rounded quotient and square root, exact sign changes, one
+    product by 1/sqrt2)."""
+    rs2 = 0.70710678118654752440
+    terms = []
+    for l in range(lmax + 1):
+        for s, tj in ((-1, 2 * l - 1), (1, 2 * l + 1)):
+            if tj < 0:
+                continue
+            for t in range(tj + 1):
+                tmj = 2 * t - tj
+                for c in (0, 1):
+                    m = (tmj - 1) // 2 if c == 0 else (tmj + 1) // 2
+                    num = 2 * l + s * tmj + 1 if c == 0 else 2 * l - s * tmj + 1
+                    a = math.sqrt(float(num) / float(2 * (2 * l + 1)))
+                    if c == 0 and s < 0:
+                        a = -a
+                    mu = abs(m)
+                    if mu > l:
+                        a, mu = 0.0, 0
+                    if mu == 0:
+                        cre, cim = a, 0.0
+                    elif m > 0:
+                        cre = cim = (-a if m & 1 else a) * rs2
+                    else:
+                        cre = a * rs2
+                        cim = -cre
+                    terms.append((l * l + l + mu, l * l + l - mu, cre, cim, mu == 0))
+    return terms
+
+
+@pytest.mark.parametrize("lmax", [1, 4, 9])
+def test_strict_spinor_is_coefficient_times_strict_row_bitwise(lmax):
+    """Every strict spinor component is one binary64 product coefficient x
+    real harmonic of the strict row (Eq. 7 with Y from R): the GPU values
+    equal numpy's IEEE products of the same operands bit for bit, whichever
+    pipe computes the product; points on the axes and poles (zero harmonics)
+    included."""
+    pts = np.concatenate([inputs.random_sphere_points(3001, stream="tests", with_axes=False), inputs.edge_points()])
+    pts = pts[np.all(np.isfinite(pts), axis=1) & (np.linalg.norm(pts, axis=1) > 0)]
+    p = torch.from_numpy(pts).cuda()
+    got = shm.eval_spinor(p, lmax, strict=True).cpu().numpy()       # [n, 2 L2, 2] complex
+    R = shm.eval_sh(p, lmax, strict=True).cpu().numpy()
+    terms = _spinor_terms(lmax)
+    assert len(terms) == 4 * (lmax + 1) ** 2
+    flat = got.reshape(got.shape[0], -1)                            # component q = 2 spinor + c
+    for q, (ka, kb, cre, cim, imz) in enumerate(terms):
+        re = cre * R[:, ka]
+        im = np.zeros_like(re) if imz else cim * R[:, kb]
+        assert np.array_equal(flat[:, q].real.view(np.int64), re.view(np.int64)), (lmax, q)
+        assert np.array_equal(flat[:, q].imag.view(np.int64), im.view(np.int64)), (lmax, q)
