@@ -585,10 +585,10 @@ def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     nh = (LMAX + 1) ** 2
     g = inputs.dft_grid_points(N_SIDE)
-    for dt, name, es in ((torch.float64, "fp64", 8), (torch.float32, "fp32", 4)):
+    for dt, name, es, strict in _xdtypes(torch):
         p = torch.from_numpy(g).to(device="cuda", dtype=dt)
         out = torch.empty((p.shape[0], nh, 2), dtype=dt, device="cuda")
-        fn = lambda: shm.eval_complex(p, LMAX, out=out, stream=stream)  # noqa: E731
+        fn = lambda: shm.eval_complex(p, LMAX, out=out, stream=stream, strict=strict)  # noqa: E731
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -597,25 +597,48 @@ def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
         gbs = p.shape[0] * (3 + 2 * nh) * es / (ms * 1e-3) / 1e9
         res[f"complex_dft_grid_192cubed_{name}_lmax9"] = {
             "value": p.shape[0] * nh / (ms * 1e-3), "unit": "complex Y_lm/s", "kernel_ms": ms,
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                         "peak_source": peaks_src}}
+            **xdtype_label(name),
+            "roofline": {"bound": "alu" if strict else "hbm", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
+                         "unit": "GB/s", "hbm_frac": gbs / hbm_peak, "peak_source": peaks_src}}
         del out, p
     # the angular interface on the same directions
     r = np.linalg.norm(g, axis=1)
     ang = np.stack([np.arccos(np.clip(g[:, 2] / r, -1, 1)), np.arctan2(g[:, 1], g[:, 0])], axis=1)
-    for dt, name in ((torch.float64, "fp64"), (torch.float32, "fp32")):
+    for dt, name, es, strict in _xdtypes(torch):
         a = torch.from_numpy(ang).to(device="cuda", dtype=dt)
         out = torch.empty((a.shape[0], nh), dtype=dt, device="cuda")
-        fn = lambda: shm.eval_angles(a, LMAX, out=out, stream=stream)  # noqa: E731
+        fn = lambda: shm.eval_angles(a, LMAX, out=out, stream=stream, strict=strict)  # noqa: E731
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
         per, _ = timed_launches(fn, max(5, min(args.steps, 30)), stream)
         ms = statistics.mean(per)
         res[f"angular_input_192cubed_directions_{name}_lmax9"] = {"value": a.shape[0] * nh / (ms * 1e-3),
-                                                                  "unit": UNIT, "kernel_ms": ms}
+                                                                  "unit": UNIT, "kernel_ms": ms,
+                                                                  **xdtype_label(name)}
         del out, a
     return res
+
+
+# The extras' FP64 forms: "fp64" is binary64 throughout (SHM_STRICT_FP64);
+# "f64out_ffarith" is the default FP64-out form with float-float m >= 2
+# columns, labelled as such, never as FP64 arithmetic.
+XDTYPES = ((None, "fp64", 8, True), (None, "f64out_ffarith", 8, False), (None, "fp32", 4, False))
+
+
+def _xdtypes(torch):
+    return tuple((torch.float32 if name == "fp32" else torch.float64, name, es, strict)
+                 for _, name, es, strict in XDTYPES)
+
+
+def xdtype_label(name):
+    if name == "fp64":
+        return {"dtype": "f64", "arithmetic": "binary64 throughout (SHM_STRICT_FP64)"}
+    if name == "f64out_ffarith":
+        return {"dtype": "f64-out/ff-arith",
+                "arithmetic": "FP64 out; binary64 1/r and m = 0, 1 columns, float-float (2 x FP32) m >= 2 columns; "
+                              "within 1e-13 of the l-shell norm of the FP64 oracle"}
+    return {"dtype": "f32", "arithmetic": "FP32 (FP64 1/r for r < 1e-2)"}
 
 
 def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
@@ -648,8 +671,10 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
         err_bits = shm.projectors_check(ws, stream=stream)
         algo_bytes = d.n_values * es + d.n_points * 4
         gbs = algo_bytes / (ms * 1e-3) / 1e9
-        res[f"projectors_512atoms_{name}"] = {
+        key = "projectors_512atoms_f64out_ffarith" if es == 8 else f"projectors_512atoms_{name}"
+        res[key] = {
             "value": d.n_values / (ms * 1e-3), "unit": "projector values/s", "ms_per_call": ms,
+            "dtype": "f64-out/ff-arith" if es == 8 else "f32",
             "atoms": prob.n_atoms, "points": d.n_points, "values": d.n_values, "error_bits": err_bits,
             "launches_per_call": 1, "prepare_ms_once": prepare_ms, "launch_variant": shm.projectors_variant(dt),
             "autotune_best_ms": tuned_ms, "cuda_graph_replay": graph,
@@ -687,8 +712,8 @@ def extra_projectors(args, shm, torch, inputs, stream, peaks, peaks_src):
                      "binary64_equivalent_tflops": eq, "binary64_equivalent_frac_of_fp64_peak": eq / fp64["tflops"],
                      "binary64_equivalent_def": f"{STRICT_PROJ_DP_PER_POINT[1]} FP64 instructions per point of the "
                                                 "form with every product on the FP64 pipe, at this time"})
-    res["projectors_512atoms_fp64_strict"] = {
-        "value": d.n_values / (ms * 1e-3), "unit": "projector values/s", "ms_per_call": ms,
+    res["projectors_512atoms_fp64"] = {
+        "value": d.n_values / (ms * 1e-3), "unit": "projector values/s", "ms_per_call": ms, "dtype": "f64",
         "launches_per_call": 1, "error_bits": shm.projectors_check(ws, stream=stream),
         "arithmetic": "binary64 throughout (SHM_STRICT_FP64)", "strict_form": form,
         "strict_form_def": "1: every product on the FP64 pipe; 2: the row's output products, 3: all its products "
@@ -788,10 +813,10 @@ def extra_spinor(args, shm, torch, inputs, stream, peaks, peaks_src):
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     nh = (LMAX + 1) ** 2
     g = inputs.dft_grid_points(N_SIDE)
-    for dt, name, es in ((torch.float64, "fp64", 8), (torch.float32, "fp32", 4)):
+    for dt, name, es, strict in _xdtypes(torch):
         p = torch.from_numpy(g).to(device="cuda", dtype=dt)
         out = torch.empty((p.shape[0], 2 * nh, 2, 2), dtype=dt, device="cuda")
-        fn = lambda: shm.eval_spinor(p, LMAX, out=out, stream=stream)  # noqa: E731
+        fn = lambda: shm.eval_spinor(p, LMAX, out=out, stream=stream, strict=strict)  # noqa: E731
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -800,8 +825,9 @@ def extra_spinor(args, shm, torch, inputs, stream, peaks, peaks_src):
         gbs = p.shape[0] * (3 + 8 * nh) * es / (ms * 1e-3) / 1e9
         res[f"spinor_dft_grid_192cubed_{name}_lmax9"] = {
             "value": p.shape[0] * 2 * nh / (ms * 1e-3), "unit": "spinor harmonics/s", "kernel_ms": ms,
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                         "peak_source": peaks_src}}
+            **xdtype_label(name),
+            "roofline": {"bound": "alu" if strict else "hbm", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
+                         "unit": "GB/s", "hbm_frac": gbs / hbm_peak, "peak_source": peaks_src}}
         del out, p
         torch.cuda.empty_cache()
     return res
