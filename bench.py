@@ -58,6 +58,11 @@ STRICT_DP_PER_POINT_L9 = 242
 # on the FP64 pipe (strict form 1), 68.8 with the row products on the integer
 # pipes (form 3, the default; the same bits).
 STRICT_PROJ_DP_PER_POINT = {1: 107.1, 3: 68.8}
+# FP64-pipe instructions per point of the all-binary64 complex, angle-input
+# and spinor kernels at lmax 9 (ncu smsp__inst_executed_pipe_fp64.sum x 32 /
+# points on the 96^3 grid; the output products of the complex and angle rows
+# on the integer pipes).
+STRICT_X_DP_PER_POINT = {"complex": 153.0, "angular": 192.0, "spinor": 960.5}
 # binary64 products per point that the rows-tma-emu variants compute on the
 # integer pipes instead (dmul_int, bitwise the DMUL results): the 90 output
 # products s A, s B at lmax 9, and with the scales s = S q another 36.
@@ -598,8 +603,9 @@ def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
         res[f"complex_dft_grid_192cubed_{name}_lmax9"] = {
             "value": p.shape[0] * nh / (ms * 1e-3), "unit": "complex Y_lm/s", "kernel_ms": ms,
             **xdtype_label(name),
-            "roofline": {"bound": "alu" if strict else "hbm", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
-                         "unit": "GB/s", "hbm_frac": gbs / hbm_peak, "peak_source": peaks_src}}
+            "roofline": (({"bound": "alu", **fp64_roofline("complex", p.shape[0], ms, peaks)}) if strict else
+                         {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                          "peak_source": peaks_src}) | {"hbm_frac": gbs / hbm_peak}}
         del out, p
     # the angular interface on the same directions
     r = np.linalg.norm(g, axis=1)
@@ -613,9 +619,9 @@ def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
         torch.cuda.synchronize()
         per, _ = timed_launches(fn, max(5, min(args.steps, 30)), stream)
         ms = statistics.mean(per)
-        res[f"angular_input_192cubed_directions_{name}_lmax9"] = {"value": a.shape[0] * nh / (ms * 1e-3),
-                                                                  "unit": UNIT, "kernel_ms": ms,
-                                                                  **xdtype_label(name)}
+        res[f"angular_input_192cubed_directions_{name}_lmax9"] = {
+            "value": a.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, **xdtype_label(name),
+            **({"roofline": {"bound": "alu", **fp64_roofline("angular", a.shape[0], ms, peaks)}} if strict else {})}
         del out, a
     return res
 
@@ -629,6 +635,19 @@ XDTYPES = ((None, "fp64", 8, True), (None, "f64out_ffarith", 8, False), (None, "
 def _xdtypes(torch):
     return tuple((torch.float32 if name == "fp32" else torch.float64, name, es, strict)
                  for _, name, es, strict in XDTYPES)
+
+
+def fp64_roofline(kind, n_points, ms, peaks):
+    """FP64-pipe fraction of an all-binary64 extra (measured DFMA rate of
+    this run), from its FP64 instructions per point."""
+    fp64 = peaks.get("fp64_probe")
+    if not fp64:
+        return {}
+    dp = STRICT_X_DP_PER_POINT[kind]
+    ach = 2.0 * dp * n_points / (ms * 1e-3) / 1e12
+    return {"pipe": "fp64", "achieved": ach, "peak": fp64["tflops"], "unit": "TFLOP/s", "frac": ach / fp64["tflops"],
+            "achieved_def": f"{dp} FP64 pipe instructions per point (ncu, lmax 9) x 2 x points / mean launch time",
+            "fp64_peak_source": fp64["source"]}
 
 
 def xdtype_label(name):
@@ -826,8 +845,9 @@ def extra_spinor(args, shm, torch, inputs, stream, peaks, peaks_src):
         res[f"spinor_dft_grid_192cubed_{name}_lmax9"] = {
             "value": p.shape[0] * 2 * nh / (ms * 1e-3), "unit": "spinor harmonics/s", "kernel_ms": ms,
             **xdtype_label(name),
-            "roofline": {"bound": "alu" if strict else "hbm", "hbm_achieved": gbs, "hbm_peak": hbm_peak,
-                         "unit": "GB/s", "hbm_frac": gbs / hbm_peak, "peak_source": peaks_src}}
+            "roofline": (({"bound": "alu", **fp64_roofline("spinor", p.shape[0], ms, peaks)}) if strict else
+                         {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                          "peak_source": peaks_src}) | {"hbm_frac": gbs / hbm_peak}}
         del out, p
         torch.cuda.empty_cache()
     return res
