@@ -750,8 +750,8 @@ __device__ __forceinline__ void proj_point_f64(const ProjParams& P, int g, const
 // to 1.0e-6; not used.)  LFIX >= 0: the row of lmax LFIX (lmax is then ignored), written
 // with compile-time indices (row may be a register array).
 template <int LCAP, int LFIX = -1>
-__device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const float* __restrict__ tb, int s,
-                                               int lmax, float* row) {
+__device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const float* __restrict__ tb,
+                                               const float4* __restrict__ rs, int lmax, float* row) {
   const float inv_dlog = P.inv_dlog32;
   const int ng = P.ng;
   const int q1 = (int)div_ng((unsigned)g, P.ng_magic, P.ng_shift);
@@ -787,18 +787,19 @@ __device__ __forceinline__ void proj_point_f32(const ProjParams& P, int g, const
     const float v = __int_as_float(E.y) + lm * inv_dlog;  // |v| < 64
     const int fl = floor_small(v);
     u = v - small_int_to_float(fl);
-    long long itl = (long long)E.x + fl;
-    if (itl < 0) {
-      itl = 0;
+    it = E.x + fl;  // |E.x| <= 2147483000 (clamped by the set-up), |fl| < 64: no int32 overflow
+    if (it < 0) {
+      it = 0;
       u = 0.0f;
-    } else if (itl >= P.n_rad - 1) {
-      itl = P.n_rad - 1;
+    } else if (it >= P.n_rad - 1) {
+      it = P.n_rad - 1;
       u = 0.0f;
     }
-    it = (int)itl;
   }
-  // f_l(r): the interval's cubic in u, one 16-byte node per l
-  const float4* tab = P.rad32 + ((int64_t)s * P.n_rad + it) * P.lstride;
+  // f_l(r): the interval's cubic in u, one 16-byte node per l (rs: the
+  // species' table of n_rad x lstride nodes; 0 <= it < 2^26 and lstride <= 64,
+  // so the unsigned product fits 32 bits)
+  const float4* tab = rs + (unsigned)it * (unsigned)P.lstride;
   auto radial = [&](int l) {
     const float4 c = __ldg(tab + l);
     return fmaf(fmaf(fmaf(c.w, u, c.z), u, c.y), u, c.x);
@@ -1049,6 +1050,9 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
     ok = ok && rows >= 1 && rows <= TILE && p0 >= 0 && p0 <= P.n_points - rows && o0 >= 0 &&
          o0 <= P.n_values - (int64_t)rows * L2;
     const int RS = L2 | 1;
+    // FP32: the species' interval cubics, once per tile
+    const float4* const rad_s = (sizeof(T) == 4 && ok) ? P.rad32 + (int64_t)s * P.n_rad * P.lstride : nullptr;
+    (void)rad_s;
     // odd row widths: each round's rows are staged contiguously (RS = L2),
     // shifted so that they have the 16-byte phase of their place in the
     // output (the same for every round: NT L2 values are a multiple of 16
@@ -1085,7 +1089,7 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
 #pragma unroll
               for (int kk = 0; kk < 16; ++kk) v[kk] = 0.0f;
             } else {
-              proj_point_f32<LCAP, 3>(P, g, P.disp32 + a * 3 * P.ng, s, 3, v);
+              proj_point_f32<LCAP, 3>(P, g, P.disp32 + a * 3 * P.ng, rad_s, 3, v);
             }
           }
           stage_rows16(tile, phase, (int)threadIdx.x, active, (int)threadIdx.x == rr - 1, v);
@@ -1099,7 +1103,7 @@ __global__ void __launch_bounds__(NT, MINB) k_proj(ProjParams P, T* __restrict__
         } else if constexpr (sizeof(T) == 8) {
           proj_point_f64<LCAP, STRICT>(P, g, P.disp64 + a * 3 * P.ng, s, lmax, reinterpret_cast<double*>(row));
         } else {
-          proj_point_f32<LCAP>(P, g, P.disp32 + a * 3 * P.ng, s, lmax, reinterpret_cast<float*>(row));
+          proj_point_f32<LCAP>(P, g, P.disp32 + a * 3 * P.ng, rad_s, lmax, reinterpret_cast<float*>(row));
         }
       }
       if (flat) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the rows, visible to the bulk copy
