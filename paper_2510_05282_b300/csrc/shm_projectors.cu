@@ -1260,8 +1260,8 @@ shm_status proj_params(const shm_proj_problem* prob, shm_dtype dtype, void* work
   shm_status st;
   const size_t es = dtype == SHM_F64 ? 8 : 4;
   if ((st = check_device_range(workspace, w.total, "workspace")) != SHM_OK) return st;
-  // the run copies indices and atom positions by cp.async, which needs
-  // naturally aligned sources
+  // the set-up and the run read every array with loads of its element
+  // size, which need naturally aligned sources
   if (!aligned(p.point_index, 4) || !aligned(p.atom_pos, 8) || !aligned(p.atom_species, 4) ||
       !aligned(p.point_offsets, 8) || !aligned(p.out_offsets, 8) || !aligned(p.radial, 8))
     return fail(SHM_EINVAL, "problem arrays must be aligned to their element size");
