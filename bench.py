@@ -619,9 +619,12 @@ def extra_complex(args, shm, torch, inputs, stream, peaks, peaks_src):
         torch.cuda.synchronize()
         per, _ = timed_launches(fn, max(5, min(args.steps, 30)), stream)
         ms = statistics.mean(per)
+        gbs = a.shape[0] * (2 + nh) * es / (ms * 1e-3) / 1e9  # (theta, phi) in, the row out
         res[f"angular_input_192cubed_directions_{name}_lmax9"] = {
             "value": a.shape[0] * nh / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms, **xdtype_label(name),
-            **({"roofline": {"bound": "alu", **fp64_roofline("angular", a.shape[0], ms, peaks)}} if strict else {})}
+            "roofline": (({"bound": "alu", **fp64_roofline("angular", a.shape[0], ms, peaks)}) if strict else
+                         {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                          "peak_source": peaks_src}) | {"hbm_frac": gbs / hbm_peak}}
         del out, a
     return res
 
