@@ -1142,11 +1142,11 @@ constexpr ProjVariant kProjVariants[] = {
 };
 static_assert(kProjMinTile == 128, "every variant's tile is at least kProjMinTile points");
 constexpr int kNumProjVariants = sizeof(kProjVariants) / sizeof(kProjVariants[0]);
-// Defaults before (or without) tuning, the fastest on the 512-atom problem:
-// tile512-8rounds-64t for FP32 (0.216 ms; 0.217 with 128-thread rounds, 0.249
-// with the register cap of 48, which spills), tile512-4rounds for FP64
-// (0.875 ms).
-inline int default_proj_variant(shm_dtype dt) { return dt == SHM_F32 ? 8 : 0; }
+// Default before (or without) tuning, the fastest on the 512-atom problem
+// for both dtypes: tile512-8rounds-64t (FP32 0.215 ms, 0.216 with 128-thread
+// rounds; FP64 0.873 ms, 0.876 with 128-thread rounds).  The all-binary64
+// projectors run tile512-4rounds (kStrictProjVariant).
+inline int default_proj_variant(shm_dtype) { return 8; }
 constexpr int kStrictProjVariant = 0;  // SHM_STRICT_FP64 runs one launch shape: tile512-4rounds
 constexpr size_t kProjMaxSmem = 232448;  // B300 opt-in shared memory per CTA
 
